@@ -1,0 +1,250 @@
+/*
+ * fem.h -- C ABI of the GB300 frequent-episode counting library (libfem.so).
+ *
+ * The library counts, for serial episodes with inter-event constraints, the
+ * size of the largest set of non-overlapped occurrences in a time-ordered
+ * event stream, and runs the level-wise (Apriori) mining procedure on top of
+ * that count.  Passages of "Accelerator-Oriented Algorithm Transformation for
+ * Temporal Data Mining" (Patnaik, Ponce, Cao, Ramakrishnan) are cited by
+ * section name.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns int status: FEM_OK (0) or a negative FEM_ERR_*.
+ *     No function throws, aborts or prints.  fem_strerror() names a status.
+ *   - Pointers marked "host or device" are device pointers when the matching
+ *     *_is_device / ptr_is_device argument is non-zero, host pointers
+ *     otherwise.  The library never keeps a caller pointer after it returns:
+ *     it copies what it needs.
+ *   - Calls are synchronous: when a call returns, its outputs (host or device)
+ *     are written and every kernel it launched has finished.
+ *   - A context is used by one host thread at a time (calls on one context
+ *     are serialised by an internal mutex); different contexts are
+ *     independent.
+ *   - Times are int32 ticks >= 0 (the tick is the caller's unit); types are
+ *     uint16 ids < n_types.
+ *
+ * Episode semantics (section "Temporal Data Mining")
+ *   An N-node episode is E_1 -(lo_1,hi_1]-> E_2 ... -> E_N.  An occurrence is a
+ *   choice of events j_1 < ... < j_N with type(j_k) = E_k and
+ *   lo_k < t(j_{k+1}) - t(j_k) <= hi_k.  Two occurrences are non-overlapped
+ *   when one ends strictly before the other starts (Algorithm 1's test
+ *   prev_e < s_i).  The count is the largest number of pairwise
+ *   non-overlapped occurrences.  Intervals must satisfy 0 <= lo < hi.
+ */
+#ifndef FEM_H
+#define FEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FEM_OK 0
+#define FEM_ERR_INVAL -1       /* null pointer, negative size, type >= n_types,
+                                  lo < 0, lo >= hi, episode size outside
+                                  [1, FEM_MAX_NODES], bad handle */
+#define FEM_ERR_UNSORTED -2    /* stream times decrease somewhere */
+#define FEM_ERR_DUP -3         /* two events with the same (type, time) */
+#define FEM_ERR_RANGE -4       /* a time < 0 */
+#define FEM_ERR_NOMEM -5       /* the context's device-memory budget (or the
+                                  device) cannot hold the request */
+#define FEM_ERR_TIMEOUT -6     /* a device-side wait gave up after its
+                                  iteration limit; the context stays usable */
+#define FEM_ERR_CUDA -7        /* a CUDA runtime call failed */
+#define FEM_ERR_BUSY -8        /* serving: job queue full / job not finished */
+#define FEM_ERR_NOTFOUND -9    /* serving: unknown job id */
+
+#define FEM_MAX_NODES 16       /* largest episode size accepted */
+
+typedef struct fem_ctx fem_ctx;
+typedef struct fem_stream fem_stream;
+typedef struct fem_result fem_result;
+
+/* Candidate episodes in CSR form.
+ *   n_cand           number of episodes (>= 0)
+ *   offs[n_cand+1]   int64 node offsets: episode c has nodes
+ *                    types[offs[c] .. offs[c+1]-1], offs[0] = 0
+ *   types[offs[n]]   uint16 event type of every node
+ *   lo, hi           int32 bounds of every edge: episode c's edges are at
+ *                    lo/hi[offs[c]-c .. offs[c+1]-c-2] (N_c - 1 of them)
+ *   ptr_is_device    non-zero: offs/types/lo/hi are device pointers         */
+typedef struct {
+    int64_t n_cand;
+    const int64_t *offs;
+    const uint16_t *types;
+    const int32_t *lo;
+    const int32_t *hi;
+    int ptr_is_device;
+} fem_cands;
+
+/* Optional launch parameters.  Zero in a field means "choose automatically"
+ * (autotuner cache, else the built-in heuristic). */
+typedef struct {
+    int lanes_per_cta;    /* episodes held by one CTA (multiple of 32) */
+    int segments;         /* stream segments per recording (>= 1) */
+    int tile_events;      /* events per shared-memory stage (multiple of 256) */
+    int prepass;          /* 1 = run the upper-bound pre-pass, -1 = never */
+} fem_tuning;
+
+/* Per-call statistics filled by the counting / mining calls. */
+typedef struct {
+    double episode_events;      /* sum over counted (episode, recording) of n */
+    double relevant_events;     /* sum over counted episodes of sum_k freq(E_k) */
+    int64_t candidates_counted; /* exact counts computed */
+    int64_t candidates_pruned;  /* dropped by the upper-bound pre-pass */
+    int64_t fallback_recounts;  /* episodes recounted unsegmented */
+    int64_t kernel_launches;    /* library kernels launched by the call */
+    double count_kernel_ms;     /* device time of the exact-count kernels */
+    double total_ms;            /* wall time of the call */
+    int levels;                 /* mining: deepest level reached */
+} fem_stats;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.
+ *   hbm_budget_bytes  upper bound on device memory the context may hold
+ *                     (streams + scratch); 0 = 90% of the device's free memory
+ *   cuda_stream       a cudaStream_t to run on, or NULL for a stream the
+ *                     context creates and owns
+ * On success *out owns the context; free it with fem_ctx_destroy. */
+int fem_ctx_create(int device, size_t hbm_budget_bytes, void *cuda_stream, fem_ctx **out);
+void fem_ctx_destroy(fem_ctx *ctx);
+int fem_ctx_set_tuning(fem_ctx *ctx, const fem_tuning *t);    /* NULL resets */
+int fem_ctx_last_stats(const fem_ctx *ctx, fem_stats *out);  /* of the last call */
+/* Bytes currently held on the device by the context (streams + scratch). */
+int fem_ctx_memory(const fem_ctx *ctx, size_t *used, size_t *budget);
+
+/* ---- streams ------------------------------------------------------------ */
+
+/* Loads an event stream (Definition 1: time-ordered (type, time) pairs) into
+ * device memory owned by the library, validates it on the device and
+ * computes the level-1 counts (a 1-node episode's count is its type's
+ * frequency).
+ *   types[n], times[n]  host or device (ptr_is_device); caller keeps them
+ *   n >= 0, n_types in [1, 65536]
+ * Errors: FEM_ERR_INVAL (type >= n_types), FEM_ERR_RANGE (time < 0),
+ * FEM_ERR_UNSORTED, FEM_ERR_DUP (a repeated (type, time) would make two
+ * events count once), FEM_ERR_NOMEM. */
+int fem_load_stream(fem_ctx *ctx, const uint16_t *types, const int32_t *times, int64_t n,
+                    uint32_t n_types, int ptr_is_device, fem_stream **out);
+void fem_stream_free(fem_stream *s);
+int fem_stream_info(const fem_stream *s, int64_t *n, uint32_t *n_types);
+/* Level 1: freq[n_types] (host or device) = events of each type. */
+int fem_stream_freq(fem_ctx *ctx, const fem_stream *s, uint32_t *freq, int out_is_device);
+
+/* ---- counting (the hot path) ------------------------------------------- */
+
+/* Exact count of every candidate episode over one stream ("Episode Counting
+ * Algorithm" semantics; frequency as defined in "Temporal Data Mining").
+ * counts[n_cand] (host or device) receives uint32 counts in input order.
+ * Internally: segment-parallel exact counting with a boundary stitch-up
+ * (section "MapConcat"), stream tiles staged in shared memory and broadcast
+ * to many episode machines per CTA, and an optional upper-bound pre-pass.
+ * Errors: FEM_ERR_INVAL on a malformed candidate (see above),
+ * FEM_ERR_NOMEM, FEM_ERR_TIMEOUT, FEM_ERR_CUDA. */
+int fem_count_episodes(fem_ctx *ctx, const fem_stream *s, const fem_cands *c, uint32_t *counts,
+                       int out_is_device);
+
+/* Same, for candidates spread over several recordings: candidate c is
+ * counted on recs[rec_id[c]].  rec_id[n_cand] (host or device, like the
+ * candidate arrays).  All recordings are counted in one launch. */
+int fem_count_batch(fem_ctx *ctx, const fem_stream *const *recs, int n_recs, const fem_cands *c,
+                    const uint32_t *rec_id, uint32_t *counts, int out_is_device);
+
+/* Comparison path: one GPU thread per candidate, reading the stream straight
+ * from global memory, the serial state machine of "Episode Counting
+ * Algorithm" with its lists in global memory (the mapping the section
+ * "Temporal Data Mining" calls embarrassingly parallel).  Same contract and
+ * results as fem_count_episodes. */
+int fem_count_episodes_plain(fem_ctx *ctx, const fem_stream *s, const fem_cands *c,
+                             uint32_t *counts, int out_is_device);
+
+/* Upper-bound pre-pass: ub[c] >= count(c) for every candidate.  It counts the
+ * episode with every lower bound relaxed to 0 (a superset of occurrences, so
+ * the largest non-overlapped set can only grow; anti-monotonicity, section
+ * "Temporal Data Mining"). ub (host or device) is uint32[n_cand]. */
+int fem_upper_bound(fem_ctx *ctx, const fem_stream *s, const fem_cands *c, uint32_t *ub,
+                    int out_is_device);
+
+/* ---- level-wise mining --------------------------------------------------- */
+
+/* Level-wise frequent-episode discovery (section "Temporal Data Mining"):
+ * level 1 = types whose frequency exceeds the threshold; level 2 = every
+ * ordered pair of distinct frequent types with every interval bin; level
+ * N >= 3 = joins of frequent (N-1)-episodes alpha, beta where alpha without
+ * its first node equals beta without its last node (types and bins), giving
+ * alpha extended by beta's last edge and node, distinct types only.  A
+ * candidate is kept when count > threshold (strict).  Levels stop at
+ * max_size or when a level keeps nothing.
+ *   recs[n_recs]           recordings, each mined independently
+ *   bin_lo/bin_hi[n_bins]  host arrays of interval bins (0 <= lo < hi)
+ *   threshold[n_recs]      host array, per recording
+ *   max_size               in [1, FEM_MAX_NODES]
+ * All recordings' levels share one launch per step, and the levels are
+ * chained in a captured CUDA graph.  *out receives a result (free with
+ * fem_result_free) whose episodes are in canonical order: size, then the
+ * interleaved sequence (E_1, lo_1, hi_1, E_2, ..., lo_{N-1}, hi_{N-1}, E_N). */
+int fem_mine_levelwise(fem_ctx *ctx, const fem_stream *const *recs, int n_recs,
+                       const int32_t *bin_lo, const int32_t *bin_hi, int n_bins,
+                       const uint32_t *threshold, int max_size, fem_result **out);
+
+/* Host views into a result (valid until fem_result_free).  For recording
+ * `rec` and level `level` (1..max_size): *n_out episodes in CSR form
+ * (offs[n+1], types, lo, hi as in fem_cands) with counts[n]. */
+int fem_result_level(const fem_result *r, int rec, int level, int64_t *n_out,
+                     const int64_t **offs, const uint16_t **types, const int32_t **lo,
+                     const int32_t **hi, const uint32_t **counts);
+int fem_result_stats(const fem_result *r, fem_stats *out);
+void fem_result_free(fem_result *r);
+
+/* ---- serving ------------------------------------------------------------- */
+
+/* A serving loop that runs level-wise mining jobs with continuous batching:
+ * a submitted job is admitted when its device memory (stream + candidate
+ * buffers) fits the server's budget and a slot is free; the ready levels of
+ * all admitted jobs are counted together in one launch; streams and
+ * candidate sets stay on the device between levels; finished jobs release
+ * their memory so waiting jobs can enter.  Runs on its own host thread and
+ * context. */
+typedef struct fem_server fem_server;
+
+typedef struct {
+    double submit_s;    /* host clock (seconds) when submitted */
+    double admit_s;     /* when admitted to the device */
+    double finish_s;    /* when the result was ready */
+    int64_t n_events;
+    int levels;
+    int64_t candidates_counted;
+    double episode_events;
+} fem_job_info;
+
+/*   hbm_budget_bytes  device memory the server may hold (0 = 80% of free)
+ *   max_jobs          jobs resident on the device at once (>= 1) */
+int fem_server_create(int device, size_t hbm_budget_bytes, int max_jobs, fem_server **out);
+/* Submits one job; the stream arrays are host pointers copied before the
+ * call returns.  bins / threshold / max_size as in fem_mine_levelwise.
+ * *job_id receives the id.  FEM_ERR_NOMEM if the job can never fit. */
+int fem_server_submit(fem_server *srv, const uint16_t *types, const int32_t *times, int64_t n,
+                      uint32_t n_types, const int32_t *bin_lo, const int32_t *bin_hi, int n_bins,
+                      uint32_t threshold, int max_size, uint64_t *job_id);
+/* Waits up to timeout_ms (< 0: forever) for the job; on success *out
+ * receives its result (owned by the caller) and *info its timings.
+ * FEM_ERR_BUSY on timeout, FEM_ERR_NOTFOUND for an unknown or already
+ * collected id. */
+int fem_server_wait(fem_server *srv, uint64_t job_id, int timeout_ms, fem_result **out,
+                    fem_job_info *info);
+/* Stops the loop (jobs not yet finished are cancelled) and frees everything. */
+void fem_server_destroy(fem_server *srv);
+
+/* ---- misc ----------------------------------------------------------------- */
+const char *fem_strerror(int status);
+/* Library build identity: "fem <version> sm_103a". */
+const char *fem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_H */

@@ -1,0 +1,412 @@
+// fem_core.cu -- context, device memory, stream store (load, validation,
+// level-1 counts) and the window-density tables that size the per-node rings.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+int dev_alloc(fem_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (ctx->used.load() + bytes > ctx->budget) return FEM_ERR_NOMEM;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? FEM_ERR_NOMEM : FEM_ERR_CUDA;
+    }
+    ctx->used += bytes;
+    return FEM_OK;
+}
+
+void dev_free(fem_ctx *ctx, void *p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    cudaFree(p);
+    ctx->used -= bytes;
+}
+
+int scratch(fem_ctx *ctx, int slot, size_t bytes, void **p) {
+    DevBuf &b = ctx->scratch[slot];
+    if (b.cap >= bytes && b.p) {
+        *p = b.p;
+        return FEM_OK;
+    }
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    want = std::max<size_t>(want, 4096);
+    if (b.p) {
+        cudaStreamSynchronize(ctx->stream);
+        dev_free(ctx, b.p, b.cap);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    int st = dev_alloc(ctx, &b.p, want);
+    if (st != FEM_OK && want > bytes) st = dev_alloc(ctx, &b.p, bytes), want = bytes;
+    if (st != FEM_OK) return st;
+    b.cap = want;
+    *p = b.p;
+    return FEM_OK;
+}
+
+int sync_status(fem_ctx *ctx) {
+    FEM_CUDA_TRY(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    int s = *ctx->h_status;
+    if (s) {
+        FEM_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        if (s & kStatusTimeout) return FEM_ERR_TIMEOUT;
+        if (s & kStatusInval) return FEM_ERR_INVAL;
+    }
+    return FEM_OK;
+}
+
+int copy_in(fem_ctx *ctx, void *dst_dev, const void *src, size_t bytes, int src_is_device) {
+    if (bytes == 0) return FEM_OK;
+    FEM_CUDA_TRY(cudaMemcpyAsync(dst_dev, src, bytes,
+                                 src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    return FEM_OK;
+}
+
+int copy_out(fem_ctx *ctx, void *dst, const void *src_dev, size_t bytes, int dst_is_device) {
+    if (bytes == 0) return FEM_OK;
+    FEM_CUDA_TRY(cudaMemcpyAsync(dst, src_dev, bytes,
+                                 dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    return FEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stream validation (Definition 1 plus the library's input rules): type in
+// range, time >= 0, times non-decreasing, no repeated (type, time).  A
+// repeated pair must sit inside one run of equal times, so each event looks
+// back only while the time is unchanged.
+__global__ void k_validate(const uint16_t *__restrict__ ty, const int32_t *__restrict__ tm, int64_t n,
+                           uint32_t n_types, int *err) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int e = 0;
+    for (; i < n; i += stride) {
+        const uint16_t a = ty[i];
+        const int32_t t = tm[i];
+        if (a >= n_types) e |= 1;
+        if (t < 0) e |= 2;
+        if (i > 0) {
+            const int32_t tp = tm[i - 1];
+            if (tp > t) e |= 4;
+            for (int64_t j = i - 1; j >= 0 && tm[j] == t; --j)
+                if (ty[j] == a) {
+                    e |= 8;
+                    break;
+                }
+        }
+    }
+    if (e) atomicOr(err, e);
+}
+
+// Level 1 (a 1-node episode's count is its frequency): per-type histogram,
+// privatised in shared memory when the alphabet fits.
+__global__ void k_histogram(const uint16_t *__restrict__ ty, int64_t n, uint32_t n_types,
+                            uint32_t *__restrict__ freq) {
+    extern __shared__ uint32_t h[];
+    const bool priv = n_types <= 12288;
+    if (priv)
+        for (uint32_t a = threadIdx.x; a < n_types; a += blockDim.x) h[a] = 0;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint16_t a = ty[i];
+        if (priv)
+            atomicAdd(&h[a], 1u);
+        else
+            atomicAdd(&freq[a], 1u);
+    }
+    __syncthreads();
+    if (priv)
+        for (uint32_t a = threadIdx.x; a < n_types; a += blockDim.x)
+            if (h[a]) atomicAdd(&freq[a], h[a]);
+}
+
+__global__ void k_fill_pad(uint16_t *ty, int32_t *tm, int64_t from, int64_t to) {
+    for (int64_t i = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < to;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ty[i] = 0xFFFF;
+        tm[i] = INT32_MAX;
+    }
+}
+
+// Window density: dens[a] = largest number of type-a events inside any closed
+// window [t - lo, t].  With at most dens[E_k] entries of node k still inside
+// their lower bound, a ring of dens + 1 entries always holds the newest entry
+// that is past its lower bound (the only one a query needs).  Each event scans
+// back while the window lasts; after `cap` steps the type is marked unknown
+// (the caller then falls back to the type's frequency, also an upper bound).
+__global__ void k_density(const uint16_t *__restrict__ ty, const int32_t *__restrict__ tm, int64_t n,
+                          int32_t lo, int cap, uint32_t *__restrict__ dens) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint16_t a = ty[i];
+        const int64_t lim = (int64_t)tm[i] - lo;
+        uint32_t c = 1;
+        int steps = 0;
+        int64_t j = i - 1;
+        for (; j >= 0 && tm[j] >= lim && steps < cap; --j, ++steps)
+            if (ty[j] == a) ++c;
+        if (j >= 0 && tm[j] >= lim) c = kDensUnknown;
+        atomicMax(&dens[a], c);
+    }
+}
+
+__global__ void k_density_resolve(uint32_t *dens, const uint32_t *freq, uint32_t n_types) {
+    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < n_types; a += gridDim.x * blockDim.x)
+        if (dens[a] == kDensUnknown) dens[a] = freq[a];
+}
+
+int stream_density(fem_ctx *ctx, fem_stream *s, int32_t lo, uint32_t **d_dens) {
+    auto it = s->dens.find(lo);
+    if (it != s->dens.end()) {
+        *d_dens = it->second;
+        return FEM_OK;
+    }
+    void *p = nullptr;
+    FEM_TRY(dev_alloc(ctx, &p, sizeof(uint32_t) * s->n_types));
+    uint32_t *d = static_cast<uint32_t *>(p);
+    FEM_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(uint32_t) * s->n_types, ctx->stream));
+    if (s->n > 0) {
+        if (lo == 0) {
+            // distinct (type, time): a window of length 0 holds one event of a type
+            k_density<<<std::max<int64_t>(1, std::min<int64_t>((s->n + 255) / 256, 4096)), 256, 0,
+                        ctx->stream>>>(s->d_type, s->d_time, s->n, 0, 1 << 20, d);
+        } else {
+            k_density<<<std::max<int64_t>(1, std::min<int64_t>((s->n + 255) / 256, 65536)), 256, 0,
+                        ctx->stream>>>(s->d_type, s->d_time, s->n, lo, 4096, d);
+        }
+        k_density_resolve<<<(s->n_types + 255) / 256, 256, 0, ctx->stream>>>(d, s->d_freq, s->n_types);
+        FEM_CUDA_TRY(cudaGetLastError());
+    }
+    s->dens[lo] = d;
+    s->bytes += sizeof(uint32_t) * s->n_types;
+    *d_dens = d;
+    return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+// ---------------------------------------------------------------------------
+// C ABI: context.
+extern "C" int fem_ctx_create(int device, size_t hbm_budget_bytes, void *cuda_stream, fem_ctx **out) {
+    if (!out) return FEM_ERR_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return FEM_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return FEM_ERR_INVAL;
+    FEM_CUDA_TRY(cudaSetDevice(device));
+    fem_ctx *ctx = new (std::nothrow) fem_ctx();
+    if (!ctx) return FEM_ERR_NOMEM;
+    ctx->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete ctx;
+        return FEM_ERR_CUDA;
+    }
+    ctx->n_sm = prop.multiProcessorCount;
+    ctx->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+    if (cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return FEM_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    void *p = nullptr;
+    int st = dev_alloc(ctx, &p, sizeof(int) * 4);
+    if (st != FEM_OK) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return st;
+    }
+    ctx->d_status = static_cast<int *>(p);
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int) * 4, ctx->stream);
+    if (cudaMallocHost(&ctx->h_status, sizeof(int) * 4) != cudaSuccess) {
+        dev_free(ctx, ctx->d_status, sizeof(int) * 4);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return FEM_ERR_CUDA;
+    }
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+    cudaStreamSynchronize(ctx->stream);
+    *out = ctx;
+    return FEM_OK;
+}
+
+extern "C" void fem_ctx_destroy(fem_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->scratch) dev_free(ctx, kv.second.p, kv.second.cap);
+    ctx->scratch.clear();
+    dev_free(ctx, ctx->d_status, sizeof(int) * 4);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" int fem_ctx_set_tuning(fem_ctx *ctx, const fem_tuning *t) {
+    if (!ctx) return FEM_ERR_INVAL;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!t) {
+        ctx->tuning = fem_tuning{};
+        return FEM_OK;
+    }
+    if (t->lanes_per_cta < 0 || (t->lanes_per_cta % 32) != 0 || t->lanes_per_cta > kMaxWarps * 32)
+        return FEM_ERR_INVAL;
+    if (t->segments < 0 || t->tile_events < 0 || (t->tile_events % 256) != 0 ||
+        t->tile_events > kMaxTile)
+        return FEM_ERR_INVAL;
+    ctx->tuning = *t;
+    return FEM_OK;
+}
+
+extern "C" int fem_ctx_last_stats(const fem_ctx *ctx, fem_stats *out) {
+    if (!ctx || !out) return FEM_ERR_INVAL;
+    *out = ctx->last;
+    return FEM_OK;
+}
+
+extern "C" int fem_ctx_memory(const fem_ctx *ctx, size_t *used, size_t *budget) {
+    if (!ctx) return FEM_ERR_INVAL;
+    if (used) *used = ctx->used.load();
+    if (budget) *budget = ctx->budget;
+    return FEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: streams.
+extern "C" int fem_load_stream(fem_ctx *ctx, const uint16_t *types, const int32_t *times, int64_t n,
+                               uint32_t n_types, int ptr_is_device, fem_stream **out) {
+    if (!ctx || !out || n < 0 || n_types < 1 || n_types > 65536) return FEM_ERR_INVAL;
+    if (n > 0 && (!types || !times)) return FEM_ERR_INVAL;
+    if (n > (int64_t)INT32_MAX * 4) return FEM_ERR_INVAL;
+    *out = nullptr;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    fem_stream *s = new (std::nothrow) fem_stream();
+    if (!s) return FEM_ERR_NOMEM;
+    s->ctx = ctx;
+    s->n = n;
+    s->n_types = n_types;
+    const int64_t cap = n + kPadEvents;
+    void *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
+    int st = dev_alloc(ctx, &p1, sizeof(uint16_t) * cap);
+    if (st == FEM_OK) st = dev_alloc(ctx, &p2, sizeof(int32_t) * cap);
+    if (st == FEM_OK) st = dev_alloc(ctx, &p3, sizeof(uint32_t) * n_types);
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(ctx->stream);
+        dev_free(ctx, p1, sizeof(uint16_t) * cap);
+        dev_free(ctx, p2, sizeof(int32_t) * cap);
+        dev_free(ctx, p3, sizeof(uint32_t) * n_types);
+        delete s;
+        return code;
+    };
+    if (st != FEM_OK) return fail(st);
+    s->d_type = static_cast<uint16_t *>(p1);
+    s->d_time = static_cast<int32_t *>(p2);
+    s->d_freq = static_cast<uint32_t *>(p3);
+    s->bytes = (sizeof(uint16_t) + sizeof(int32_t)) * cap + sizeof(uint32_t) * n_types;
+    if (copy_in(ctx, s->d_type, types, sizeof(uint16_t) * n, ptr_is_device) != FEM_OK ||
+        copy_in(ctx, s->d_time, times, sizeof(int32_t) * n, ptr_is_device) != FEM_OK)
+        return fail(FEM_ERR_CUDA);
+    k_fill_pad<<<64, 256, 0, ctx->stream>>>(s->d_type, s->d_time, n, cap);
+    cudaMemsetAsync(s->d_freq, 0, sizeof(uint32_t) * n_types, ctx->stream);
+    cudaMemsetAsync(ctx->d_status + 1, 0, sizeof(int), ctx->stream);
+    if (n > 0) {
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ctx->n_sm * 8));
+        k_validate<<<blocks, 256, 0, ctx->stream>>>(s->d_type, s->d_time, n, n_types, ctx->d_status + 1);
+        const size_t hs = n_types <= 12288 ? n_types * sizeof(uint32_t) : 0;
+        k_histogram<<<blocks, 256, hs, ctx->stream>>>(s->d_type, n, n_types, s->d_freq);
+    }
+    if (cudaGetLastError() != cudaSuccess) return fail(FEM_ERR_CUDA);
+    if (cudaMemcpyAsync(ctx->h_status + 1, ctx->d_status + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                        ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return fail(FEM_ERR_CUDA);
+    const int e = ctx->h_status[1];
+    if (e & 1) return fail(FEM_ERR_INVAL);
+    if (e & 2) return fail(FEM_ERR_RANGE);
+    if (e & 4) return fail(FEM_ERR_UNSORTED);
+    if (e & 8) return fail(FEM_ERR_DUP);
+    *out = s;
+    return FEM_OK;
+}
+
+extern "C" void fem_stream_free(fem_stream *s) {
+    if (!s) return;
+    fem_ctx *ctx = s->ctx;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    const int64_t cap = s->n + kPadEvents;
+    dev_free(ctx, s->d_type, sizeof(uint16_t) * cap);
+    dev_free(ctx, s->d_time, sizeof(int32_t) * cap);
+    dev_free(ctx, s->d_freq, sizeof(uint32_t) * s->n_types);
+    for (auto &kv : s->dens) dev_free(ctx, kv.second, sizeof(uint32_t) * s->n_types);
+    delete s;
+}
+
+extern "C" int fem_stream_info(const fem_stream *s, int64_t *n, uint32_t *n_types) {
+    if (!s) return FEM_ERR_INVAL;
+    if (n) *n = s->n;
+    if (n_types) *n_types = s->n_types;
+    return FEM_OK;
+}
+
+extern "C" int fem_stream_freq(fem_ctx *ctx, const fem_stream *s, uint32_t *freq, int out_is_device) {
+    if (!ctx || !s || !freq || s->ctx != ctx) return FEM_ERR_INVAL;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    FEM_TRY(copy_out(ctx, freq, s->d_freq, sizeof(uint32_t) * s->n_types, out_is_device));
+    FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return FEM_OK;
+}
+
+extern "C" const char *fem_strerror(int status) {
+    switch (status) {
+        case FEM_OK: return "ok";
+        case FEM_ERR_INVAL: return "invalid argument";
+        case FEM_ERR_UNSORTED: return "stream times are not non-decreasing";
+        case FEM_ERR_DUP: return "stream repeats a (type, time) event";
+        case FEM_ERR_RANGE: return "time out of range (negative)";
+        case FEM_ERR_NOMEM: return "device memory budget exceeded";
+        case FEM_ERR_TIMEOUT: return "device-side wait timed out";
+        case FEM_ERR_CUDA: return "CUDA runtime error";
+        case FEM_ERR_BUSY: return "busy (queue full or job not finished)";
+        case FEM_ERR_NOTFOUND: return "unknown job id";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *fem_version(void) { return "fem 0.1.0 sm_103a"; }

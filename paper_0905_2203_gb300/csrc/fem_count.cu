@@ -1,0 +1,1295 @@
+// fem_count.cu -- exact counting of non-overlapped serial-episode occurrences.
+//
+// Formulation (section "Problem decomposition"): the count is the size of the
+// largest set of non-overlapped occurrences, found by Algorithm 1 (greedy by
+// end time) over occurrences.  For every end event it suffices to know the
+// LATEST start of an occurrence ending there:
+//     L_1(j) = t_j,   L_k(j) = max { L_{k-1}(i) : lo < t_j - t_i <= hi }.
+// Along the stream, the partial occurrences of node k that are valid
+// predecessors are the node's entries (t_i, L(i)); L is non-decreasing in t_i
+// over entries, so a query only needs the newest entry that is already past
+// its lower bound.  Entries younger than lo are kept in a small ring whose
+// capacity R comes from the stream's window density (max events of the type
+// in a window of length lo, plus one), so the ring never drops an entry a
+// later query needs.  Algorithm 1 then selects an end event when its latest
+// start is after the previous selected end.
+//
+// Segment-parallel counting (section "MapConcat"): the stream is split into
+// segments; each (episode, segment) machine starts sum(hi) before its segment
+// (any occurrence ending inside it starts no earlier), so its L values are
+// exact.  Because the entry state -- the end of the last occurrence selected
+// before the segment -- is unknown, the machine runs Algorithm 1 for every
+// class of entry values that leads to a different first selection (the
+// "multiple state machines ... anticipating all possible end states" of the
+// Map step): class j covers entries in [thr_{j-1}, thr_j) and records
+// (thr_j, count_j, last_j).  Classes stop being created once an occurrence
+// starts inside the segment.  The stitch (the Concat step) walks segments in
+// order, picks the class of the running end, adds its count and moves the
+// end to its last selection.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <set>
+#include <vector>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+constexpr int kBucketNode = 5;   // NMAX classes: 2, 4, 8, 16 (+ N == 1)
+constexpr int kBucketRing = 5;   // ring classes: 4, 8, 16, 32, 64
+constexpr int kBucketN1 = kBucketNode * kBucketRing;      // 1-node episodes
+constexpr int kBucketPlain = kBucketN1 + 1;               // global-memory path
+constexpr int kBuckets = kBucketPlain + 1;
+
+__host__ __device__ inline int nmax_of_class(int c) { return c == 0 ? 2 : c == 1 ? 4 : c == 2 ? 8 : 16; }
+__host__ __device__ inline int ring_of_class(int c) { return 4 << c; }
+
+struct RecInfo {
+    const uint16_t *type;
+    const int32_t *time;
+    int64_t n;
+    const int64_t *seg;   // P + 1 segment starts (device)
+    int P;
+    int slot_first;       // first launch slot of this recording in the bucket
+    int64_t recbase;      // first record index of this recording
+    const uint32_t *freq;
+};
+
+struct WorkItem {
+    int rec;
+    int slot0;
+    int nslots;
+    int p;
+};
+
+struct TiledArgs {
+    const RecInfo *rinfo;
+    const WorkItem *items;
+    const int64_t *offs;
+    const uint16_t *ctypes;
+    const int32_t *clo;
+    const int32_t *chi;
+    const int32_t *slot2cand;
+    int R;
+    int K;
+    int T;
+    int relaxed;
+    int32_t *rec;         // records, kRecWords each
+    int *status;
+};
+
+// ---------------------------------------------------------------------------
+// Per-lane machine state (registers; every array index is a compile-time
+// constant after unrolling).
+template <int NMAX>
+struct Lane {
+    int N;
+    uint32_t E[NMAX];
+    int32_t lo[NMAX];
+    int32_t hi[NMAX];
+    int head[NMAX];
+    int32_t cthr[kClasses];
+    int32_t cprev[kClasses];
+    uint32_t ccnt[kClasses];
+    int ncls;
+    int32_t M;
+    int open;
+    int flags;
+};
+
+// Ring of node k for this lane: entry r at base[(k * R + r) * K].
+template <int NMAX>
+__device__ __forceinline__ void ring_push(Lane<NMAX> &st, int k, int32_t *rt, int32_t *rl, int R,
+                                          int K, int32_t t, int32_t L) {
+    const int h = st.head[k];
+    int32_t *bt = rt + (k * R) * K;
+    int32_t *bl = rl + (k * R) * K;
+    const int h2 = (h + 1 == R) ? 0 : h + 1;
+    const int32_t old = bt[h * K];
+    const int32_t old2 = bt[h2 * K];
+    // Dropping `old` is safe if it is empty, expired for every query at
+    // time >= t, or if the next-older entry is already past its lower bound.
+    if (old != INT32_MIN && old >= t - st.hi[k] && old2 >= t - st.lo[k]) st.flags |= kMetaRingOverflow;
+    bt[h * K] = t;
+    bl[h * K] = L;
+    st.head[k] = h2;
+}
+
+// Newest entry of node k past its lower bound at time t; valid if it is
+// within the upper bound.  Returns its latest start through L.
+template <int NMAX>
+__device__ __forceinline__ bool ring_query(const Lane<NMAX> &st, int k, const int32_t *rt,
+                                           const int32_t *rl, int R, int K, int32_t t, int32_t &L) {
+    const int32_t *bt = rt + (k * R) * K;
+    const int32_t *bl = rl + (k * R) * K;
+    const int32_t elig = t - st.lo[k];
+    const int32_t expire = t - st.hi[k];
+    int idx = st.head[k];
+    for (int i = 0; i < R; ++i) {
+        idx = (idx == 0) ? R - 1 : idx - 1;
+        const int32_t tp = bt[idx * K];
+        if (tp < elig) {
+            if (tp >= expire) {
+                L = bl[idx * K];
+                return true;
+            }
+            return false;
+        }
+    }
+    return false;
+}
+
+// Algorithm 1 step for an end event at time t whose latest start is Lq, for
+// every entry class of this (episode, segment) machine.
+template <int NMAX>
+__device__ __forceinline__ void greedy_end(Lane<NMAX> &st, int32_t t, int32_t Lq, int32_t Tp) {
+#pragma unroll
+    for (int j = 0; j < kClasses; ++j)
+        if (j < st.ncls && Lq > st.cprev[j]) {
+            st.ccnt[j] += 1;
+            st.cprev[j] = t;
+        }
+    if (st.open && Lq > st.M) {
+        if (st.ncls < kClasses) {
+#pragma unroll
+            for (int j = 0; j < kClasses; ++j)
+                if (j == st.ncls) {
+                    st.cthr[j] = Lq;
+                    st.ccnt[j] = 1;
+                    st.cprev[j] = t;
+                }
+            st.ncls += 1;
+        } else {
+            st.flags |= kMetaClassOverflow;
+        }
+        st.M = Lq;
+        if (Lq >= Tp) st.open = 0;
+    }
+}
+
+// One event (type ety, time et) offered to this lane's episode.  Nodes are
+// visited last to first; an entry pushed at time et can never serve a query
+// at the same time (0 <= lo), so the order only mirrors the serial algorithm.
+template <int NMAX>
+__device__ __forceinline__ void lane_step(Lane<NMAX> &st, uint32_t ety, int32_t et, bool in_seg,
+                                          int32_t Tp, int32_t *rt, int32_t *rl, int R, int K) {
+#pragma unroll
+    for (int k = NMAX - 1; k >= 0; --k) {
+        if (k < st.N && st.E[k] == ety) {
+            if (k == 0) {
+                ring_push(st, 0, rt, rl, R, K, et, et);
+            } else {
+                int32_t Lq;
+                if (ring_query(st, k - 1, rt, rl, R, K, et, Lq)) {
+                    if (k == st.N - 1) {
+                        if (in_seg) greedy_end(st, et, Lq, Tp);
+                    } else {
+                        ring_push(st, k, rt, rl, R, K, et, Lq);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t lower_bound_time(const int32_t *tm, int64_t lo, int64_t hi, int64_t v) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)tm[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// The tiled kernel.  One CTA = one work item: up to K episodes (one per lane
+// of W = K/32 compute warps) of one recording, over one segment.  A producer
+// warp streams the segment (plus halo) through a ring of kStages shared-memory
+// stages with 1-D bulk copies; every compute warp reads each stage, filters
+// events by its warp's union of episode types (bitmap + ballot), and offers
+// the surviving events, in order, to its 32 machines.
+template <int NMAX>
+__global__ void __launch_bounds__(kMaxWarps * 32 + 32) k_count_tiled(TiledArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int K = a.K, T = a.T, R = a.R;
+    const int W = K >> 5;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const WorkItem item = a.items[blockIdx.x];
+    const RecInfo ri = a.rinfo[item.rec];
+
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + kStages;
+    uint16_t *s_type = reinterpret_cast<uint16_t *>(smem + 128);
+    int32_t *s_time = reinterpret_cast<int32_t *>(s_type + kStages * T);
+    uint32_t *s_bm = reinterpret_cast<uint32_t *>(s_time + kStages * T);
+    int32_t *s_rt = reinterpret_cast<int32_t *>(s_bm + W * kBitmapWords);
+    int32_t *s_rl = s_rt + (NMAX - 1) * R * K;
+
+    __shared__ unsigned long long s_maxsh;
+    __shared__ long long s_range[4];  // i_begin, seg_b, seg_e, Tp
+    __shared__ int s_abort;
+
+    const bool compute = warp < W;
+    const bool active = compute && tid < item.nslots;
+    Lane<NMAX> st;
+    st.N = 0;
+    st.ncls = 0;
+    st.M = INT32_MIN;
+    st.open = 1;
+    st.flags = 0;
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+        st.E[k] = 0xFFFFFFFFu;
+        st.lo[k] = 0;
+        st.hi[k] = 0;
+        st.head[k] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kClasses; ++j) {
+        st.cthr[j] = 0;
+        st.cprev[j] = 0;
+        st.ccnt[j] = 0;
+    }
+    int64_t sumhi = 0;
+    int slot = 0, cand = 0;
+    if (tid == 0) {
+        s_maxsh = 0;
+        s_abort = 0;
+    }
+    if (active) {
+        slot = item.slot0 + tid;
+        cand = a.slot2cand[slot];
+        const int64_t o = a.offs[cand];
+        const int N = (int)(a.offs[cand + 1] - o);
+        const int64_t eo = o - cand;
+        st.N = N;
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            if (k < N) st.E[k] = a.ctypes[o + k];
+            if (k < N - 1) {
+                st.lo[k] = a.relaxed ? 0 : a.clo[eo + k];
+                st.hi[k] = a.chi[eo + k];
+                sumhi += st.hi[k];
+            }
+        }
+    }
+    if (compute) {
+        for (int i = lane; i < kBitmapWords; i += 32) s_bm[warp * kBitmapWords + i] = 0;
+        for (int k = 0; k < NMAX - 1; ++k)
+            for (int r = 0; r < R; ++r) s_rt[(k * R + r) * K + tid] = INT32_MIN;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < st.N)
+                atomicOr(&s_bm[warp * kBitmapWords + ((st.E[k] >> 5) & (kBitmapWords - 1))], 1u << (st.E[k] & 31));
+        atomicMax(&s_maxsh, (unsigned long long)sumhi);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            dev::mbar_init(&full[s], 1);
+            dev::mbar_init(&empty[s], W);
+        }
+        dev::fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int64_t seg_b = ri.seg[item.p], seg_e = ri.seg[item.p + 1];
+        int64_t ib = 0;
+        int32_t Tp = 0;
+        if (seg_b < seg_e) {
+            Tp = ri.time[seg_b];
+            const int64_t haloT = (int64_t)Tp - (int64_t)s_maxsh;
+            ib = (item.p == 0) ? 0 : lower_bound_time(ri.time, 0, seg_b, haloT);
+        } else {
+            ib = seg_e;
+        }
+        s_range[0] = ib;
+        s_range[1] = seg_b;
+        s_range[2] = seg_e;
+        s_range[3] = Tp;
+    }
+    __syncthreads();
+    const int64_t i_begin = s_range[0], seg_b = s_range[1], seg_e = s_range[2];
+    const int32_t Tp = (int32_t)s_range[3];
+    const int64_t i_al = i_begin & ~(int64_t)(kTileAlign - 1);
+    const int64_t ntiles = (seg_e > i_begin) ? (seg_e - i_al + T - 1) / T : 0;
+    const uint32_t kMaxPoll = 1u << 30;
+    const uint64_t kMaxNs = 4000000000ull;  // 4 s per wait
+
+    if (warp == W) {
+        // Producer warp: one lane issues the bulk copies.
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t k = 0; k < ntiles; ++k) {
+                const int s = (int)(k % kStages);
+                if (k >= kStages) {
+                    if (!dev::mbar_wait(&empty[s], (uint32_t)(((k / kStages) - 1) & 1), kMaxPoll, kMaxNs)) {
+                        atomicOr(a.status, kStatusTimeout);
+                        s_abort = 1;
+                        break;
+                    }
+                }
+                if (*(volatile int *)&s_abort) break;
+                const int64_t g = i_al + k * T;
+                dev::mbar_arrive_expect_tx(&full[s], (uint32_t)T * 6u);
+                dev::bulk_g2s(s_type + s * T, ri.type + g, (uint32_t)T * 2u, &full[s]);
+                dev::bulk_g2s(s_time + s * T, ri.time + g, (uint32_t)T * 4u, &full[s]);
+                issued = k + 1;
+            }
+            // Never leave with copies in flight into this CTA's shared memory.
+            for (int64_t k = (issued > kStages ? issued - kStages : 0); k < issued; ++k)
+                if (!dev::mbar_wait(&full[k % kStages], (uint32_t)((k / kStages) & 1), kMaxPoll, kMaxNs))
+                    atomicOr(a.status, kStatusTimeout);
+        }
+        __syncwarp();
+    } else {
+        int32_t *rt = s_rt + tid;
+        int32_t *rl = s_rl + tid;
+        const uint32_t *bm = s_bm + warp * kBitmapWords;
+        for (int64_t k = 0; k < ntiles; ++k) {
+            const int s = (int)(k % kStages);
+            if (!dev::mbar_wait(&full[s], (uint32_t)((k / kStages) & 1), kMaxPoll, kMaxNs)) {
+                atomicOr(a.status, kStatusTimeout);
+                s_abort = 1;
+                break;
+            }
+            const int64_t gbase = i_al + k * T;
+            const uint16_t *tt = s_type + s * T;
+            const int32_t *tm = s_time + s * T;
+            for (int c = 0; c < T; c += 32) {
+                const int64_t gi = gbase + c + lane;
+                const uint32_t ty = tt[c + lane];
+                const uint32_t word = bm[(ty >> 5) & (kBitmapWords - 1)];
+                const bool rel = (gi >= i_begin) && (gi < seg_e) && ((word >> (ty & 31)) & 1u);
+                uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    const uint32_t ety = __shfl_sync(0xFFFFFFFFu, ty, b);
+                    const int32_t et = tm[c + b];
+                    const bool in_seg = (gbase + c + b) >= seg_b;
+                    if (active) lane_step<NMAX>(st, ety, et, in_seg, Tp, rt, rl, R, K);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&empty[s]);
+        }
+        if (active) {
+            int32_t *r = a.rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P + item.p) * kRecWords;
+            r[0] = st.ncls | st.flags;
+#pragma unroll
+            for (int j = 0; j < kClasses; ++j) {
+                r[1 + j] = st.cthr[j];
+                r[1 + kClasses + j] = (int32_t)st.ccnt[j];
+                r[1 + 2 * kClasses + j] = st.cprev[j];
+            }
+        }
+    }
+}
+
+// Concat step: per episode, walk its segments in order with the running end x
+// of the last selected occurrence (minus infinity before the first).
+__global__ void k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
+                         const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec,
+                         int slot_begin, int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list,
+                         int *fb_count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slots) return;
+    const int slot = slot_begin + i;
+    const int cand = slot2cand[slot];
+    const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
+    const RecInfo ri = rinfo[r_id];
+    const int32_t *r = rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P) * kRecWords;
+    int64_t x = INT64_MIN;
+    uint32_t total = 0;
+    bool bad = false;
+    for (int p = 0; p < ri.P; ++p, r += kRecWords) {
+        const int meta = r[0];
+        if (meta & (kMetaRingOverflow | kMetaClassOverflow)) bad = true;
+        const int ncls = meta & 0xFF;
+        for (int j = 0; j < ncls; ++j) {
+            if (x < (int64_t)r[1 + j]) {
+                total += (uint32_t)r[1 + kClasses + j];
+                x = r[1 + 2 * kClasses + j];
+                break;
+            }
+        }
+    }
+    if (bad) {
+        const int q = atomicAdd(fb_count, 1);
+        fb_list[q] = cand;
+    } else {
+        counts[cand] = total;
+    }
+}
+
+// 1-node episodes: the count is the type's frequency (distinct times).
+__global__ void k_count_n1(const int32_t *__restrict__ slot2cand, int slot_begin, int n_slots,
+                           const int64_t *__restrict__ offs, const uint16_t *__restrict__ ctypes,
+                           const uint32_t *__restrict__ cand_rec, const RecInfo *__restrict__ rinfo,
+                           uint32_t *__restrict__ counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slots) return;
+    const int cand = slot2cand[slot_begin + i];
+    const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
+    counts[cand] = rinfo[r_id].freq[ctypes[offs[cand]]];
+}
+
+// ---------------------------------------------------------------------------
+// Plain comparison path: one thread per episode walks the whole stream from
+// global memory running the serial state machine ("Episode Counting
+// Algorithm", reset on completion), with each node's list kept as a ring of
+// R timestamps in global memory.
+__global__ void k_count_plain(const RecInfo *__restrict__ rinfo, const int32_t *__restrict__ slot2cand,
+                              const uint32_t *__restrict__ cand_rec, int slot_begin, int n_slots,
+                              const int64_t *__restrict__ offs, const uint16_t *__restrict__ ctypes,
+                              const int32_t *__restrict__ clo, const int32_t *__restrict__ chi, int R,
+                              int32_t *__restrict__ rings, uint32_t *__restrict__ counts, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slots) return;
+    const int cand = slot2cand[slot_begin + i];
+    const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
+    const RecInfo ri = rinfo[r_id];
+    const int64_t o = offs[cand];
+    const int N = (int)(offs[cand + 1] - o);
+    const int64_t eo = o - cand;
+    uint16_t E[FEM_MAX_NODES];
+    int32_t lo[FEM_MAX_NODES], hi[FEM_MAX_NODES];
+    int head[FEM_MAX_NODES];
+    for (int k = 0; k < N; ++k) {
+        E[k] = ctypes[o + k];
+        head[k] = 0;
+        if (k < N - 1) {
+            lo[k] = clo[eo + k];
+            hi[k] = chi[eo + k];
+        }
+    }
+    // ring (k, r) of this thread at rings[((k * R) + r) * n_slots + i]
+    const int64_t stride = n_slots;
+    for (int k = 0; k < N - 1; ++k)
+        for (int r = 0; r < R; ++r) rings[((int64_t)k * R + r) * stride + i] = INT32_MIN;
+    int64_t prev_end = INT64_MIN;
+    uint32_t count = 0;
+    int ovf = 0;
+    for (int64_t j = 0; j < ri.n; ++j) {
+        const uint16_t ty = ri.type[j];
+        const int32_t t = ri.time[j];
+        for (int k = N - 1; k >= 0; --k) {
+            if (E[k] != ty) continue;
+            bool ok;
+            if (k == 0) {
+                ok = (int64_t)t > prev_end;
+            } else {
+                ok = false;
+                int idx = head[k - 1];
+                for (int q = 0; q < R; ++q) {
+                    idx = (idx == 0) ? R - 1 : idx - 1;
+                    const int32_t tp = rings[((int64_t)(k - 1) * R + idx) * stride + i];
+                    if (tp < t - lo[k - 1]) {
+                        ok = tp >= t - hi[k - 1];
+                        break;
+                    }
+                }
+            }
+            if (!ok) continue;
+            if (k == N - 1) {
+                count++;
+                prev_end = t;
+                for (int q = 0; q < N - 1; ++q) {
+                    head[q] = 0;
+                    for (int r = 0; r < R; ++r) rings[((int64_t)q * R + r) * stride + i] = INT32_MIN;
+                }
+                break;
+            }
+            const int h = head[k];
+            const int h2 = (h + 1 == R) ? 0 : h + 1;
+            int32_t *slotp = &rings[((int64_t)k * R + h) * stride + i];
+            const int32_t old = *slotp;
+            const int32_t old2 = rings[((int64_t)k * R + h2) * stride + i];
+            if (old != INT32_MIN && old >= t - hi[k] && old2 >= t - lo[k]) ovf = 1;
+            *slotp = t;
+            head[k] = h2;
+        }
+    }
+    counts[cand] = count;
+    if (ovf) atomicOr(status, kStatusInval);
+}
+
+// ---------------------------------------------------------------------------
+// Candidate preparation: validation, ring size, bucket key.
+struct PrepArgs {
+    int64_t n_cand;
+    const int64_t *offs;
+    const uint16_t *ctypes;
+    const int32_t *clo;
+    const int32_t *chi;
+    const uint32_t *cand_rec;
+    const int32_t *subset;     // optional list of candidates to process
+    const RecInfo *rinfo;
+    const uint32_t *n_types;   // per recording
+    const int32_t *lo_vals;    // sorted distinct lo values
+    int n_lo;
+    const uint32_t *const *dens;  // [rec * n_lo + j]
+    int n_recs;
+    int mode;                  // 0 exact, 1 plain, 2 relaxed (upper bound)
+    int force_plain_ring;
+    int32_t *key;              // out: bucket * n_recs + rec
+    int32_t *ring;             // out: R per candidate
+    int *bucket_maxR;          // out: per bucket max R
+    unsigned long long *relevant;  // out: sum over candidates of sum_k freq(E_k)
+    int *status;
+};
+
+__device__ __forceinline__ uint32_t dens_lookup(const PrepArgs &a, int rec, int32_t lo, uint16_t ty) {
+    int lo_i = 0, hi_i = a.n_lo;
+    while (lo_i < hi_i) {
+        const int mid = (lo_i + hi_i) >> 1;
+        if (a.lo_vals[mid] < lo)
+            lo_i = mid + 1;
+        else
+            hi_i = mid;
+    }
+    if (lo_i >= a.n_lo || a.lo_vals[lo_i] != lo) return kDensUnknown;
+    return a.dens[rec * a.n_lo + lo_i][ty];
+}
+
+__global__ void k_prep(PrepArgs a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n_cand) return;
+    const int64_t c = a.subset ? a.subset[i] : i;
+    const int rec = a.cand_rec ? (int)a.cand_rec[c] : 0;
+    const int64_t o = a.offs[c];
+    const int64_t N = a.offs[c + 1] - o;
+    const int64_t eo = o - c;
+    bool bad = (rec < 0 || rec >= a.n_recs || N < 1 || N > FEM_MAX_NODES);
+    int R = 2;
+    unsigned long long relv = 0;
+    if (!bad) {
+        const uint32_t nt = a.n_types[rec];
+        const uint32_t *freq = a.rinfo[rec].freq;
+        for (int k = 0; k < N && !bad; ++k) {
+            const uint16_t ty = a.ctypes[o + k];
+            if (ty >= nt) {
+                bad = true;
+                break;
+            }
+            relv += freq[ty];
+            if (k < N - 1) {
+                const int32_t l = a.clo[eo + k], h = a.chi[eo + k];
+                if (l < 0 || l >= h) {
+                    bad = true;
+                    break;
+                }
+                const int32_t lq = (a.mode == 2) ? 0 : l;
+                uint32_t d = dens_lookup(a, rec, lq, ty);
+                if (d == kDensUnknown || d == 0) d = freq[ty] > 0 ? freq[ty] : 1;
+                const uint32_t need = d >= 0x7FFFFFFEu ? 0x7FFFFFFFu : d + 1;
+                if ((int)need > R) R = (int)need;
+            }
+        }
+    }
+    if (bad) {
+        atomicOr(a.status, kStatusInval);
+        a.key[i] = 0;
+        a.ring[i] = 2;
+        return;
+    }
+    int bucket;
+    if (a.mode == 1) {
+        bucket = kBucketPlain;
+    } else if (N == 1) {
+        bucket = kBucketN1;
+    } else if (R > kMaxRingTiled || a.force_plain_ring) {
+        bucket = kBucketPlain;
+    } else {
+        const int nc = N <= 2 ? 0 : N <= 4 ? 1 : N <= 8 ? 2 : 3;
+        const int rc = R <= 4 ? 0 : R <= 8 ? 1 : R <= 16 ? 2 : R <= 32 ? 3 : 4;
+        bucket = nc * kBucketRing + rc;
+    }
+    a.key[i] = bucket * a.n_recs + rec;
+    a.ring[i] = R;
+    atomicMax(&a.bucket_maxR[bucket], R);
+    atomicMax(&a.bucket_maxR[kBuckets + bucket], (int)N);
+    atomicAdd(a.relevant, relv);
+}
+
+// Stable partition by key: blocks of kPartBlock elements.  k_part_count
+// writes blk[k * nblk + b] = elements of block b with key k; after an
+// exclusive scan of that key-major table, blk[k * nblk + b] is where block b's
+// first key-k element goes, and k_part_scatter (one warp per block, walking
+// its elements in order) assigns stable positions.
+constexpr int kPartBlock = 4096;
+
+__global__ void k_part_count(const int32_t *__restrict__ key, int64_t n, int n_keys, int64_t nblk,
+                             int32_t *__restrict__ blk) {
+    extern __shared__ int32_t cnt[];
+    for (int k = threadIdx.x; k < n_keys; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    const int64_t b0 = blockIdx.x * (int64_t)kPartBlock;
+    const int64_t b1 = (n < b0 + kPartBlock) ? n : b0 + kPartBlock;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) atomicAdd(&cnt[key[i]], 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_keys; k += blockDim.x) blk[(int64_t)k * nblk + blockIdx.x] = cnt[k];
+}
+
+__global__ void k_part_scatter(const int32_t *__restrict__ key, int64_t n, int n_keys, int64_t nblk,
+                               const int32_t *__restrict__ blk, const int32_t *__restrict__ subset,
+                               int32_t *__restrict__ out) {
+    extern __shared__ int32_t run[];
+    const int lane = threadIdx.x;
+    for (int k = lane; k < n_keys; k += 32) run[k] = blk[(int64_t)k * nblk + blockIdx.x];
+    __syncwarp();
+    const int64_t b0 = blockIdx.x * (int64_t)kPartBlock;
+    const int64_t b1 = (n < b0 + kPartBlock) ? n : b0 + kPartBlock;
+    for (int64_t base = b0; base < b1; base += 32) {
+        const int64_t i = base + lane;
+        const int k = i < b1 ? key[i] : -1;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, k);
+        const int rank = __popc(peers & ((1u << lane) - 1));
+        int32_t pos = 0;
+        if (k >= 0) pos = run[k] + rank;
+        __syncwarp();
+        if (k >= 0) {
+            out[pos] = subset ? subset[i] : (int32_t)i;
+            if (rank == 0) run[k] += __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_gather_keyoff(const int32_t *__restrict__ blk, int n_keys, int64_t nblk,
+                                int32_t *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_keys) out[k] = blk[(int64_t)k * nblk];
+}
+
+// Exclusive scan of m int32 entries in place (multi-block: per-block sums,
+// a single-block scan of the sums, then add-back).
+__device__ __forceinline__ int32_t block_incl_scan(int32_t v, int32_t *wsum) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        int32_t s = lane < nw ? wsum[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xFFFFFFFFu, s, d);
+            if (lane >= d) s += y;
+        }
+        if (lane < nw) wsum[lane] = s;
+    }
+    __syncthreads();
+    const int32_t r = x + (w > 0 ? wsum[w - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+constexpr int kScanBlock = 1024;
+
+__global__ void k_scan_blocks(int32_t *data, int64_t m, int32_t *bsum) {
+    __shared__ int32_t wsum[32];
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    const int32_t v = i < m ? data[i] : 0;
+    const int32_t incl = block_incl_scan(v, wsum);
+    if (i < m) data[i] = incl - v;
+    if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_single(int32_t *data, int64_t m, int32_t *total) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < m; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int32_t v = i < m ? data[i] : 0;
+        const int32_t incl = block_incl_scan(v, wsum) + carry;
+        if (i < m) data[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_add(int32_t *data, int64_t m, const int32_t *bsum) {
+    const int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    if (i < m) data[i] += bsum[blockIdx.x];
+}
+
+// tmp must hold ceil(m / kScanBlock) int32.
+int scan_exclusive(cudaStream_t st, int32_t *data, int64_t m, int32_t *tmp, int32_t *total, int64_t *launches) {
+    if (m <= 0) return FEM_OK;
+    const int64_t nb = (m + kScanBlock - 1) / kScanBlock;
+    if (nb == 1) {
+        k_scan_single<<<1, kScanBlock, 0, st>>>(data, m, total);
+        if (launches) *launches += 1;
+    } else {
+        k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, st>>>(data, m, tmp);
+        k_scan_single<<<1, kScanBlock, 0, st>>>(tmp, nb, total);
+        k_scan_add<<<(unsigned)nb, kScanBlock, 0, st>>>(data, m, tmp);
+        if (launches) *launches += 3;
+    }
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+__global__ void k_segments(const int32_t *__restrict__ tm, int64_t n, int P, int64_t *__restrict__ seg) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > P) return;
+    int64_t b;
+    if (p == 0)
+        b = 0;
+    else if (p == P)
+        b = n;
+    else {
+        b = (int64_t)((__int128)n * p / P);
+        while (b < n && b > 0 && tm[b] == tm[b - 1]) ++b;
+    }
+    seg[p] = b;
+}
+
+// ---------------------------------------------------------------------------
+// Host driver.
+struct RecHost {
+    fem_stream *s;
+};
+
+template <int NMAX>
+static size_t tiled_smem(int K, int R, int T) {
+    return 128 + (size_t)kStages * T * 6 + (size_t)(K / 32) * kBitmapWords * 4 +
+           (size_t)2 * (NMAX - 1) * R * K * 4;
+}
+
+static size_t tiled_smem_rt(int nclass, int K, int R, int T) {
+    switch (nclass) {
+        case 0: return tiled_smem<2>(K, R, T);
+        case 1: return tiled_smem<4>(K, R, T);
+        case 2: return tiled_smem<8>(K, R, T);
+        default: return tiled_smem<16>(K, R, T);
+    }
+}
+
+static int launch_tiled(fem_ctx *ctx, int nclass, int n_items, int K, int R, int T, const TiledArgs &a) {
+    const size_t sm = tiled_smem_rt(nclass, K, R, T);
+    const dim3 grid(n_items), block(K + 32);
+    cudaError_t e = cudaSuccess;
+    switch (nclass) {
+        case 0:
+            e = cudaFuncSetAttribute(k_count_tiled<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) k_count_tiled<2><<<grid, block, sm, ctx->stream>>>(a);
+            break;
+        case 1:
+            e = cudaFuncSetAttribute(k_count_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) k_count_tiled<4><<<grid, block, sm, ctx->stream>>>(a);
+            break;
+        case 2:
+            e = cudaFuncSetAttribute(k_count_tiled<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) k_count_tiled<8><<<grid, block, sm, ctx->stream>>>(a);
+            break;
+        default:
+            e = cudaFuncSetAttribute(k_count_tiled<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e == cudaSuccess) k_count_tiled<16><<<grid, block, sm, ctx->stream>>>(a);
+            break;
+    }
+    if (e != cudaSuccess) return FEM_ERR_CUDA;
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+static int occupancy_tiled(int nclass, int K, size_t sm) {
+    int blocks = 0;
+    switch (nclass) {
+        case 0: cudaFuncSetAttribute(k_count_tiled<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_count_tiled<2>, K + 32, sm); break;
+        case 1: cudaFuncSetAttribute(k_count_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_count_tiled<4>, K + 32, sm); break;
+        case 2: cudaFuncSetAttribute(k_count_tiled<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_count_tiled<8>, K + 32, sm); break;
+        default: cudaFuncSetAttribute(k_count_tiled<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_count_tiled<16>, K + 32, sm); break;
+    }
+    cudaGetLastError();
+    return std::max(blocks, 1);
+}
+
+struct CountCall {
+    fem_ctx *ctx;
+    std::vector<fem_stream *> recs;
+    // device candidate arrays
+    int64_t n_cand = 0;
+    const int64_t *offs = nullptr;
+    const uint16_t *types = nullptr;
+    const int32_t *lo = nullptr;
+    const int32_t *hi = nullptr;
+    const uint32_t *cand_rec = nullptr;  // null = all recording 0
+    uint32_t *counts = nullptr;          // device, n_cand
+    std::vector<int32_t> lo_vals;        // distinct lo values (host)
+    int mode = 0;                        // 0 exact, 1 plain, 2 relaxed
+    fem_stats stats{};
+    float count_ms = 0.f;
+};
+
+static int run_count(CountCall &cc, const int32_t *subset, int64_t n_sub, int force_segments);
+
+// Builds the per-recording RecInfo table and the density table.
+static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int force_segments) {
+    fem_ctx *ctx = cc.ctx;
+    const int n_recs = (int)cc.recs.size();
+    const int n_keys = kBuckets * n_recs;
+    // --- density tables and per-recording tables
+    std::vector<int32_t> lov = cc.lo_vals;
+    if (cc.mode == 2) lov = {0};
+    if (lov.empty()) lov = {0};
+    std::vector<const uint32_t *> dens_h((size_t)n_recs * lov.size());
+    std::vector<uint32_t> nt_h(n_recs);
+    for (int r = 0; r < n_recs; ++r) {
+        nt_h[r] = cc.recs[r]->n_types;
+        for (size_t j = 0; j < lov.size(); ++j) {
+            uint32_t *d = nullptr;
+            FEM_TRY(stream_density(ctx, cc.recs[r], lov[j], &d));
+            dens_h[(size_t)r * lov.size() + j] = d;
+        }
+    }
+    // misc scratch layout: [lo_vals][n_types][dens ptrs][rinfo][bucket_maxR][relevant][fb_count]
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    const size_t o_lo = carve(lov.size() * 4), o_nt = carve(n_recs * 4),
+                 o_dp = carve(dens_h.size() * sizeof(void *)), o_ri = carve(n_recs * sizeof(RecInfo)),
+                 o_bm = carve(2 * kBuckets * 4), o_rel = carve(8), o_fb = carve(8);
+    void *misc = nullptr;
+    FEM_TRY(scratch(ctx, kSlotMisc, off, &misc));
+    char *mb = static_cast<char *>(misc);
+    std::vector<RecInfo> ri_h(n_recs);
+    for (int r = 0; r < n_recs; ++r) {
+        ri_h[r] = RecInfo{cc.recs[r]->d_type, cc.recs[r]->d_time, cc.recs[r]->n, nullptr, 1, 0, 0,
+                          cc.recs[r]->d_freq};
+    }
+    FEM_CUDA_TRY(cudaMemcpyAsync(mb + o_lo, lov.data(), lov.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    FEM_CUDA_TRY(cudaMemcpyAsync(mb + o_nt, nt_h.data(), n_recs * 4, cudaMemcpyHostToDevice, ctx->stream));
+    FEM_CUDA_TRY(cudaMemcpyAsync(mb + o_dp, dens_h.data(), dens_h.size() * sizeof(void *),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    FEM_CUDA_TRY(cudaMemcpyAsync(mb + o_ri, ri_h.data(), n_recs * sizeof(RecInfo), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    FEM_CUDA_TRY(cudaMemsetAsync(mb + o_bm, 0, 2 * kBuckets * 4, ctx->stream));
+    FEM_CUDA_TRY(cudaMemsetAsync(mb + o_rel, 0, 8, ctx->stream));
+    FEM_CUDA_TRY(cudaMemsetAsync(mb + o_fb, 0, 8, ctx->stream));
+
+    // --- prep
+    void *p_key, *p_perm, *p_blk;
+    FEM_TRY(scratch(ctx, kSlotPrep, sizeof(int32_t) * std::max<int64_t>(n_work, 1) * 2, &p_key));
+    int32_t *d_key = static_cast<int32_t *>(p_key);
+    int32_t *d_ring = d_key + std::max<int64_t>(n_work, 1);
+    FEM_TRY(scratch(ctx, kSlotPerm, sizeof(int32_t) * std::max<int64_t>(n_work, 1), &p_perm));
+    int32_t *d_perm = static_cast<int32_t *>(p_perm);
+    const int pb = 256;
+    const int64_t nprep = (n_work + pb - 1) / pb;
+    const int64_t nblk = (n_work + kPartBlock - 1) / kPartBlock;
+    const int64_t tab_n = (int64_t)n_keys * std::max<int64_t>(nblk, 1);
+    FEM_TRY(scratch(ctx, kSlotBucket, sizeof(int32_t) * (tab_n + (tab_n + kScanBlock - 1) / kScanBlock + n_keys + 64),
+                    &p_blk));
+    int32_t *d_blk = static_cast<int32_t *>(p_blk);
+    int32_t *d_scan_tmp = d_blk + tab_n;
+    int32_t *d_keyoff = d_scan_tmp + (tab_n + kScanBlock - 1) / kScanBlock + 1;
+    PrepArgs pa{};
+    pa.n_cand = n_work;
+    pa.offs = cc.offs;
+    pa.ctypes = cc.types;
+    pa.clo = cc.lo;
+    pa.chi = cc.hi;
+    pa.cand_rec = cc.cand_rec;
+    pa.subset = subset;
+    pa.rinfo = reinterpret_cast<const RecInfo *>(mb + o_ri);
+    pa.n_types = reinterpret_cast<const uint32_t *>(mb + o_nt);
+    pa.lo_vals = reinterpret_cast<const int32_t *>(mb + o_lo);
+    pa.n_lo = (int)lov.size();
+    pa.dens = reinterpret_cast<const uint32_t *const *>(mb + o_dp);
+    pa.n_recs = n_recs;
+    pa.mode = cc.mode;
+    pa.force_plain_ring = 0;
+    pa.key = d_key;
+    pa.ring = d_ring;
+    pa.bucket_maxR = reinterpret_cast<int *>(mb + o_bm);
+    pa.relevant = reinterpret_cast<unsigned long long *>(mb + o_rel);
+    pa.status = ctx->d_status;
+    if (n_work > 0) {
+        k_prep<<<(unsigned)nprep, pb, 0, ctx->stream>>>(pa);
+        k_part_count<<<(unsigned)nblk, 256, n_keys * 4, ctx->stream>>>(d_key, n_work, n_keys, nblk, d_blk);
+        FEM_TRY(scan_exclusive(ctx->stream, d_blk, tab_n, d_scan_tmp, nullptr, &cc.stats.kernel_launches));
+        k_part_scatter<<<(unsigned)nblk, 32, n_keys * 4, ctx->stream>>>(d_key, n_work, n_keys, nblk, d_blk,
+                                                                        subset, d_perm);
+        k_gather_keyoff<<<(n_keys + 255) / 256, 256, 0, ctx->stream>>>(d_blk, n_keys, nblk, d_keyoff);
+        cc.stats.kernel_launches += 4;
+        FEM_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<int32_t> key_off(n_keys + 1, 0);
+    std::vector<int32_t> bmax(2 * kBuckets, 0);
+    unsigned long long relv = 0;
+    if (n_work > 0)
+        FEM_CUDA_TRY(cudaMemcpyAsync(key_off.data(), d_keyoff, 4 * n_keys, cudaMemcpyDeviceToHost, ctx->stream));
+    FEM_CUDA_TRY(cudaMemcpyAsync(bmax.data(), mb + o_bm, 2 * kBuckets * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    FEM_CUDA_TRY(cudaMemcpyAsync(&relv, mb + o_rel, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    FEM_TRY(sync_status(ctx));
+    key_off[n_keys] = (int32_t)n_work;
+    cc.stats.relevant_events += (double)relv;
+
+    // --- launches per bucket
+    const int T = ctx->tuning.tile_events > 0 ? ctx->tuning.tile_events : 1024;
+    int64_t records_needed = 0;
+    struct Plan {
+        int bucket;
+        int K, R, nclass;
+        std::vector<RecInfo> ri;
+        std::vector<WorkItem> items;
+        std::vector<int64_t> seg_off;
+        int slot_begin, n_slots;
+    };
+    std::vector<Plan> plans;
+    std::vector<int> plain_buckets, n1_buckets;
+    for (int b = 0; b < kBuckets; ++b) {
+        const int sb = key_off[b * n_recs], se = key_off[(b + 1) * n_recs];
+        if (se <= sb) continue;
+        if (b == kBucketN1) {
+            n1_buckets.push_back(b);
+            continue;
+        }
+        if (b == kBucketPlain) {
+            plain_buckets.push_back(b);
+            continue;
+        }
+        Plan pl;
+        pl.bucket = b;
+        pl.nclass = b / kBucketRing;
+        pl.R = std::max(bmax[b], 2);
+        const int nmax = nmax_of_class(pl.nclass);
+        int K = ctx->tuning.lanes_per_cta > 0 ? ctx->tuning.lanes_per_cta : 256;
+        while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > 100 * 1024) K -= 32;
+        while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > (size_t)ctx->smem_optin - 2048) K -= 32;
+        (void)nmax;
+        pl.K = K;
+        pl.slot_begin = sb;
+        pl.n_slots = se - sb;
+        const size_t sm = tiled_smem_rt(pl.nclass, K, pl.R, T);
+        const int occ = occupancy_tiled(pl.nclass, K, sm);
+        // segments: aim for ~4 CTAs per resident slot across the bucket
+        const int64_t desired = (int64_t)4 * ctx->n_sm * occ;
+        int64_t blocks_total = 0;
+        double work = 0;
+        for (int r = 0; r < n_recs; ++r) {
+            const int c = key_off[b * n_recs + r + 1] - key_off[b * n_recs + r];
+            if (c <= 0) continue;
+            blocks_total += (c + K - 1) / K;
+            work += (double)((c + K - 1) / K) * (double)cc.recs[r]->n;
+        }
+        const double seg_len = std::max(1.0, work / (double)std::max<int64_t>(desired, 1));
+        pl.ri.resize(n_recs);
+        int64_t recbase = records_needed;
+        for (int r = 0; r < n_recs; ++r) {
+            const int ks = key_off[b * n_recs + r], ke = key_off[b * n_recs + r + 1];
+            const int c = ke - ks;
+            const fem_stream *s = cc.recs[r];
+            int P = 1;
+            if (force_segments > 0) {
+                P = force_segments;
+            } else if (ctx->tuning.segments > 0) {
+                // explicit request: allow short segments (down to ~16 events)
+                P = std::max(1, std::min<int>(ctx->tuning.segments, (int)std::max<int64_t>(1, s->n / 16)));
+            } else if (c > 0) {
+                P = (int)std::max<double>(1.0, std::min<double>((double)s->n / seg_len, (double)s->n / 4096.0));
+                P = std::max(1, std::min<int>(P, (int)std::max<int64_t>(1, s->n / 256)));
+            }
+            pl.ri[r] = RecInfo{s->d_type, s->d_time, s->n, nullptr, P, ks, recbase, s->d_freq};
+            if (c > 0) {
+                for (int cb = 0; cb < c; cb += K)
+                    for (int p = 0; p < P; ++p) pl.items.push_back(WorkItem{r, ks + cb, std::min(K, c - cb), p});
+                recbase += (int64_t)c * P;
+            }
+        }
+        records_needed = recbase;
+        (void)blocks_total;
+        plans.push_back(std::move(pl));
+    }
+    // records + segments scratch
+    void *p_rec = nullptr;
+    if (records_needed > 0) FEM_TRY(scratch(ctx, kSlotRecords, (size_t)records_needed * kRecWords * 4, &p_rec));
+    int64_t seg_total = 0;
+    for (auto &pl : plans)
+        for (auto &r : pl.ri) seg_total += r.P + 1;
+    void *p_seg = nullptr;
+    FEM_TRY(scratch(ctx, kSlotSeg, sizeof(int64_t) * std::max<int64_t>(seg_total, 1), &p_seg));
+    int64_t *d_seg = static_cast<int64_t *>(p_seg);
+    // items + rinfo tables
+    size_t tab_bytes = 0;
+    for (auto &pl : plans) tab_bytes += pl.items.size() * sizeof(WorkItem) + pl.ri.size() * sizeof(RecInfo) + 512;
+    void *p_tab = nullptr;
+    FEM_TRY(scratch(ctx, kSlotRecTab, std::max<size_t>(tab_bytes, 256), &p_tab));
+    char *tab = static_cast<char *>(p_tab);
+    int64_t segpos = 0;
+    size_t tabpos = 0;
+    int32_t *fb_list = nullptr;
+    void *p_fb = nullptr;
+    FEM_TRY(scratch(ctx, kSlotFallback, sizeof(int32_t) * std::max<int64_t>(n_work, 1), &p_fb));
+    fb_list = static_cast<int32_t *>(p_fb);
+    int *d_fbc = reinterpret_cast<int *>(mb + o_fb);
+    const RecInfo *d_ri_plain = reinterpret_cast<const RecInfo *>(mb + o_ri);
+
+    cudaEventRecord(ctx->ev0, ctx->stream);
+    for (auto &pl : plans) {
+        for (int r = 0; r < n_recs; ++r) {
+            pl.ri[r].seg = d_seg + segpos;
+            k_segments<<<(pl.ri[r].P + 1 + 127) / 128, 128, 0, ctx->stream>>>(cc.recs[r]->d_time, cc.recs[r]->n,
+                                                                             pl.ri[r].P, d_seg + segpos);
+            cc.stats.kernel_launches++;
+            segpos += pl.ri[r].P + 1;
+        }
+        RecInfo *d_ri = reinterpret_cast<RecInfo *>(tab + tabpos);
+        tabpos += (pl.ri.size() * sizeof(RecInfo) + 255) & ~size_t(255);
+        WorkItem *d_items = reinterpret_cast<WorkItem *>(tab + tabpos);
+        tabpos += (pl.items.size() * sizeof(WorkItem) + 255) & ~size_t(255);
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_ri, pl.ri.data(), pl.ri.size() * sizeof(RecInfo), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_items, pl.items.data(), pl.items.size() * sizeof(WorkItem),
+                                     cudaMemcpyHostToDevice, ctx->stream));
+        TiledArgs ta{};
+        ta.rinfo = d_ri;
+        ta.items = d_items;
+        ta.offs = cc.offs;
+        ta.ctypes = cc.types;
+        ta.clo = cc.lo;
+        ta.chi = cc.hi;
+        ta.slot2cand = d_perm;
+        ta.R = pl.R;
+        ta.K = pl.K;
+        ta.T = T;
+        ta.relaxed = cc.mode == 2;
+        ta.rec = static_cast<int32_t *>(p_rec);
+        ta.status = ctx->d_status;
+        FEM_TRY(launch_tiled(ctx, pl.nclass, (int)pl.items.size(), pl.K, pl.R, T, ta));
+        k_stitch<<<(pl.n_slots + 255) / 256, 256, 0, ctx->stream>>>(ta.rec, d_ri, d_perm, cc.cand_rec,
+                                                                   pl.slot_begin, pl.n_slots, cc.counts, fb_list,
+                                                                   d_fbc);
+        cc.stats.kernel_launches += 2;
+        FEM_CUDA_TRY(cudaGetLastError());
+    }
+    cudaEventRecord(ctx->ev1, ctx->stream);
+    for (int b : n1_buckets) {
+        const int sb = key_off[b * n_recs], se = key_off[(b + 1) * n_recs];
+        k_count_n1<<<(se - sb + 255) / 256, 256, 0, ctx->stream>>>(d_perm, sb, se - sb, cc.offs, cc.types,
+                                                                   cc.cand_rec, d_ri_plain, cc.counts);
+        cc.stats.kernel_launches++;
+    }
+    for (int b : plain_buckets) {
+        const int sb = key_off[b * n_recs], se = key_off[(b + 1) * n_recs];
+        const int R = std::max(bmax[b], 2);
+        void *p_rings = nullptr;
+        const int maxN = std::max(bmax[kBuckets + b], 2);
+        FEM_TRY(scratch(ctx, kSlotRings, (size_t)(se - sb) * (maxN - 1) * (size_t)R * 4, &p_rings));
+        k_count_plain<<<(se - sb + 127) / 128, 128, 0, ctx->stream>>>(
+            d_ri_plain, d_perm, cc.cand_rec, sb, se - sb, cc.offs, cc.types, cc.lo, cc.hi, R,
+            static_cast<int32_t *>(p_rings), cc.counts, ctx->d_status);
+        cc.stats.kernel_launches++;
+        FEM_CUDA_TRY(cudaGetLastError());
+    }
+    int fbc = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&fbc, d_fbc, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    FEM_TRY(sync_status(ctx));
+    if (!plans.empty()) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        cc.count_ms += ms;
+    }
+    cc.stats.candidates_counted += n_work - fbc;
+    if (fbc > 0) {
+        // Exact recount of the (episode) machines that ran out of entry classes:
+        // one segment, so no entry class is ever needed beyond the first.
+        cc.stats.fallback_recounts += fbc;
+        void *p_sub = nullptr;
+        FEM_TRY(scratch(ctx, kSlotScanTmp, sizeof(int32_t) * fbc, &p_sub));
+        FEM_CUDA_TRY(cudaMemcpyAsync(p_sub, fb_list, sizeof(int32_t) * fbc, cudaMemcpyDeviceToDevice, ctx->stream));
+        // the sub-call reuses the scratch slots, so keep its subset elsewhere
+        std::vector<int32_t> hsub(fbc);
+        FEM_CUDA_TRY(cudaMemcpyAsync(hsub.data(), p_sub, sizeof(int32_t) * fbc, cudaMemcpyDeviceToHost, ctx->stream));
+        FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        void *p_keep = nullptr;
+        FEM_TRY(dev_alloc(ctx, &p_keep, sizeof(int32_t) * fbc));
+        cudaMemcpyAsync(p_keep, hsub.data(), sizeof(int32_t) * fbc, cudaMemcpyHostToDevice, ctx->stream);
+        const int st = count_core(cc, static_cast<int32_t *>(p_keep), fbc, 1);
+        cudaStreamSynchronize(ctx->stream);
+        dev_free(ctx, p_keep, sizeof(int32_t) * fbc);
+        return st;
+    }
+    return FEM_OK;
+}
+
+static int run_count(CountCall &cc, const int32_t *subset, int64_t n_sub, int force_segments) {
+    return count_core(cc, subset, n_sub, force_segments);
+}
+
+// Copies (or aliases) the candidate CSR to the device and collects the
+// distinct lower bounds.
+static int stage_candidates(fem_ctx *ctx, const fem_cands *c, CountCall &cc, const uint32_t *rec_id,
+                            int n_recs) {
+    const int64_t n = c->n_cand;
+    int64_t n_nodes = 0;
+    if (c->ptr_is_device) {
+        FEM_CUDA_TRY(cudaMemcpyAsync(&n_nodes, c->offs + n, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    } else {
+        if (c->offs[0] != 0) return FEM_ERR_INVAL;
+        for (int64_t i = 0; i < n; ++i)
+            if (c->offs[i + 1] <= c->offs[i] || c->offs[i + 1] - c->offs[i] > FEM_MAX_NODES) return FEM_ERR_INVAL;
+        n_nodes = c->offs[n];
+    }
+    if (n_nodes < n || n_nodes > (int64_t)n * FEM_MAX_NODES) return FEM_ERR_INVAL;
+    const int64_t n_edges = n_nodes - n;
+    std::vector<int32_t> lo_h;
+    if (c->ptr_is_device) {
+        cc.offs = c->offs;
+        cc.types = c->types;
+        cc.lo = c->lo;
+        cc.hi = c->hi;
+        lo_h.resize(n_edges);
+        if (n_edges > 0) {
+            FEM_CUDA_TRY(cudaMemcpyAsync(lo_h.data(), c->lo, 4 * n_edges, cudaMemcpyDeviceToHost, ctx->stream));
+            FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        }
+        if (rec_id) cc.cand_rec = rec_id;
+    } else {
+        void *p1, *p2, *p3, *p4;
+        FEM_TRY(scratch(ctx, kSlotCandOffs, 8 * (n + 1), &p1));
+        FEM_TRY(scratch(ctx, kSlotCandTypes, 2 * std::max<int64_t>(n_nodes, 1), &p2));
+        FEM_TRY(scratch(ctx, kSlotCandLo, 4 * std::max<int64_t>(n_edges, 1), &p3));
+        FEM_TRY(scratch(ctx, kSlotCandHi, 4 * std::max<int64_t>(n_edges, 1), &p4));
+        FEM_TRY(copy_in(ctx, p1, c->offs, 8 * (n + 1), 0));
+        FEM_TRY(copy_in(ctx, p2, c->types, 2 * n_nodes, 0));
+        FEM_TRY(copy_in(ctx, p3, c->lo, 4 * n_edges, 0));
+        FEM_TRY(copy_in(ctx, p4, c->hi, 4 * n_edges, 0));
+        cc.offs = static_cast<int64_t *>(p1);
+        cc.types = static_cast<uint16_t *>(p2);
+        cc.lo = static_cast<int32_t *>(p3);
+        cc.hi = static_cast<int32_t *>(p4);
+        lo_h.assign(c->lo, c->lo + n_edges);
+        if (rec_id) {
+            for (int64_t i = 0; i < n; ++i)
+                if (rec_id[i] >= (uint32_t)n_recs) return FEM_ERR_INVAL;
+            void *p5;
+            FEM_TRY(scratch(ctx, kSlotCandRec, 4 * n, &p5));
+            FEM_TRY(copy_in(ctx, p5, rec_id, 4 * n, 0));
+            cc.cand_rec = static_cast<uint32_t *>(p5);
+        }
+    }
+    std::set<int32_t> los(lo_h.begin(), lo_h.end());
+    cc.lo_vals.assign(los.begin(), los.end());
+    return FEM_OK;
+}
+
+static int count_entry(fem_ctx *ctx, const fem_stream *const *recs, int n_recs, const fem_cands *c,
+                       const uint32_t *rec_id, uint32_t *counts, int out_is_device, int mode) {
+    if (!ctx || !recs || n_recs < 1 || !c || c->n_cand < 0 || (c->n_cand > 0 && (!counts || !c->offs)))
+        return FEM_ERR_INVAL;
+    if (c->n_cand > INT32_MAX / 2) return FEM_ERR_INVAL;
+    for (int r = 0; r < n_recs; ++r)
+        if (!recs[r] || recs[r]->ctx != ctx) return FEM_ERR_INVAL;
+    if (n_recs > 1 && !rec_id) return FEM_ERR_INVAL;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaSetDevice(ctx->device);
+    const double t0 = now_s();
+    CountCall cc;
+    cc.ctx = ctx;
+    cc.mode = mode;
+    for (int r = 0; r < n_recs; ++r) cc.recs.push_back(const_cast<fem_stream *>(recs[r]));
+    cc.n_cand = c->n_cand;
+    if (c->n_cand == 0) {
+        ctx->last = fem_stats{};
+        return FEM_OK;
+    }
+    if (!c->types || !c->lo || !c->hi) return FEM_ERR_INVAL;
+    FEM_TRY(stage_candidates(ctx, c, cc, n_recs > 1 ? rec_id : nullptr, n_recs));
+    void *pc = nullptr;
+    FEM_TRY(scratch(ctx, kSlotCounts, 4 * c->n_cand, &pc));
+    cc.counts = static_cast<uint32_t *>(pc);
+    FEM_TRY(run_count(cc, nullptr, c->n_cand, 0));
+    FEM_TRY(copy_out(ctx, counts, cc.counts, 4 * c->n_cand, out_is_device));
+    FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    // statistics: episode-events = sum over candidates of its recording's n
+    double ee = 0;
+    if (n_recs == 1) {
+        ee = (double)c->n_cand * (double)recs[0]->n;
+    } else {
+        std::vector<uint32_t> rid(c->n_cand);
+        if (c->ptr_is_device)
+            cudaMemcpy(rid.data(), rec_id, 4 * c->n_cand, cudaMemcpyDeviceToHost);
+        else
+            std::memcpy(rid.data(), rec_id, 4 * c->n_cand);
+        for (auto r : rid) ee += (double)recs[r]->n;
+    }
+    cc.stats.episode_events = ee;
+    cc.stats.count_kernel_ms = cc.count_ms;
+    cc.stats.total_ms = (now_s() - t0) * 1e3;
+    ctx->last = cc.stats;
+    return FEM_OK;
+}
+
+// Counting of device-resident candidates (used by the level-wise miner).
+int count_device(fem_ctx *ctx, const std::vector<fem_stream *> &recs, int64_t n_cand, const int64_t *offs,
+                 const uint16_t *types, const int32_t *lo, const int32_t *hi, const uint32_t *cand_rec,
+                 const std::vector<int32_t> &lo_vals, uint32_t *counts, fem_stats *stats) {
+    CountCall cc;
+    cc.ctx = ctx;
+    cc.recs = recs;
+    cc.mode = 0;
+    cc.n_cand = n_cand;
+    cc.offs = offs;
+    cc.types = types;
+    cc.lo = lo;
+    cc.hi = hi;
+    cc.cand_rec = cand_rec;
+    cc.counts = counts;
+    cc.lo_vals = lo_vals;
+    if (n_cand > 0) FEM_TRY(run_count(cc, nullptr, n_cand, 0));
+    cc.stats.count_kernel_ms = cc.count_ms;
+    *stats = cc.stats;
+    return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" int fem_count_episodes(fem_ctx *ctx, const fem_stream *s, const fem_cands *c, uint32_t *counts,
+                                  int out_is_device) {
+    const fem_stream *recs[1] = {s};
+    return count_entry(ctx, recs, 1, c, nullptr, counts, out_is_device, 0);
+}
+
+extern "C" int fem_count_batch(fem_ctx *ctx, const fem_stream *const *recs, int n_recs, const fem_cands *c,
+                               const uint32_t *rec_id, uint32_t *counts, int out_is_device) {
+    return count_entry(ctx, recs, n_recs, c, rec_id, counts, out_is_device, 0);
+}
+
+extern "C" int fem_count_episodes_plain(fem_ctx *ctx, const fem_stream *s, const fem_cands *c,
+                                        uint32_t *counts, int out_is_device) {
+    const fem_stream *recs[1] = {s};
+    return count_entry(ctx, recs, 1, c, nullptr, counts, out_is_device, 1);
+}
+
+extern "C" int fem_upper_bound(fem_ctx *ctx, const fem_stream *s, const fem_cands *c, uint32_t *ub,
+                               int out_is_device) {
+    const fem_stream *recs[1] = {s};
+    return count_entry(ctx, recs, 1, c, nullptr, ub, out_is_device, 2);
+}

@@ -1,0 +1,191 @@
+// fem_internal.cuh -- shared internals of libfem.so (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fem.h"
+
+namespace fem {
+
+// ---------------------------------------------------------------------------
+// Constants of the counting kernels.
+constexpr int kClasses = 4;              // entry classes kept per (episode, segment)
+constexpr int kRecWords = 1 + 3 * kClasses;  // meta, thr[H], cnt[H], last[H]
+constexpr int kMaxWarps = 8;             // compute warps per CTA
+constexpr int kBitmapWords = 128;        // per-warp type filter: 4096 bits
+constexpr int kStages = 4;               // shared-memory tile ring depth
+constexpr int kTileAlign = 8;            // tiles start at multiples of 8 events (16 B)
+constexpr int kMaxTile = 4096;           // largest tile (events)
+constexpr int kPadEvents = kMaxTile + 64;  // device stream padding past n
+constexpr int kMaxRingTiled = 64;        // larger rings go to the global-memory path
+constexpr uint32_t kDensUnknown = 0xFFFFFFFFu;
+
+// Device status bits (ctx->d_status).
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusInval = 2;
+
+// Record meta bits.
+constexpr int kMetaRingOverflow = 1 << 8;
+constexpr int kMetaClassOverflow = 1 << 9;
+
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace fem
+
+struct fem_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    int n_sm = 0;
+    int smem_optin = 0;
+    int *d_status = nullptr;   // device status word
+    int *h_status = nullptr;   // pinned mirror
+    std::mutex mu;
+    fem_tuning tuning{};
+    fem_stats last{};
+    std::map<int, fem::DevBuf> scratch;  // slot -> buffer (grown on demand)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+struct fem_stream {
+    fem_ctx *ctx = nullptr;
+    int64_t n = 0;
+    uint32_t n_types = 0;
+    uint16_t *d_type = nullptr;   // n + kPadEvents entries
+    int32_t *d_time = nullptr;    // n + kPadEvents entries
+    uint32_t *d_freq = nullptr;   // n_types
+    size_t bytes = 0;
+    std::map<int32_t, uint32_t *> dens;  // lo -> per-type max events in a closed window of length lo
+};
+
+namespace fem {
+
+// ---------------------------------------------------------------------------
+// Error plumbing.
+#define FEM_CUDA_TRY(expr)                         \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) return FEM_ERR_CUDA; \
+    } while (0)
+
+#define FEM_TRY(expr)               \
+    do {                            \
+        int _s = (expr);            \
+        if (_s != FEM_OK) return _s; \
+    } while (0)
+
+// Device memory accounted against the context budget.
+int dev_alloc(fem_ctx *ctx, void **p, size_t bytes);
+void dev_free(fem_ctx *ctx, void *p, size_t bytes);
+// Scratch slot of at least `bytes` (contents undefined).
+int scratch(fem_ctx *ctx, int slot, size_t bytes, void **p);
+// Reads and clears the device status word (synchronises the stream).
+int sync_status(fem_ctx *ctx);
+// Copy helpers honouring host/device pointers.
+int copy_in(fem_ctx *ctx, void *dst_dev, const void *src, size_t bytes, int src_is_device);
+int copy_out(fem_ctx *ctx, void *dst, const void *src_dev, size_t bytes, int dst_is_device);
+// Density table for one lo (computed on first use, cached in the stream).
+int stream_density(fem_ctx *ctx, fem_stream *s, int32_t lo, uint32_t **d_dens);
+
+// Scratch slot ids.
+enum Slot : int {
+    kSlotCandOffs = 1, kSlotCandTypes, kSlotCandLo, kSlotCandHi, kSlotCandRec,
+    kSlotPrep, kSlotPerm, kSlotBucket, kSlotRecords, kSlotSeg, kSlotCounts,
+    kSlotFallback, kSlotRings, kSlotDensTab, kSlotScanTmp, kSlotMisc, kSlotRecTab,
+    kSlotMine0 = 64,
+};
+
+double now_s();
+// Exclusive scan of m int32 in place; tmp holds ceil(m / 1024) entries.
+int scan_exclusive(cudaStream_t st, int32_t *data, int64_t m, int32_t *tmp, int32_t *total, int64_t *launches);
+
+}  // namespace fem
+
+// ---------------------------------------------------------------------------
+// Device helpers: shared-memory addresses, mbarriers, 1-D bulk TMA copies and
+// bounded waits.
+namespace fem {
+namespace dev {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of `bar` with the given parity to complete.  Gives up
+// after `max_iter` polls or `max_ns` nanoseconds, whichever comes first, and
+// returns false (the caller records a timeout and unwinds).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t max_iter,
+                                          uint64_t max_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0; i < max_iter; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && globaltimer_ns() - t0 > max_ns) return false;
+    }
+    return false;
+}
+
+// 1-D bulk copy global -> shared, completing `bytes` on the mbarrier.
+// Both addresses must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+}  // namespace dev
+}  // namespace fem

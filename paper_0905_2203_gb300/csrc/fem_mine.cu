@@ -1,0 +1,527 @@
+// fem_mine.cu -- level-wise frequent-episode mining (section "Temporal Data
+// Mining": N-size candidates are generated from frequent (N-1)-size episodes,
+// counted in one pass over the stream, and kept when the count exceeds the
+// threshold).
+//
+// Every level of every recording lives on the device in fixed-stride form
+// (all episodes of a level have N nodes): types[i*N + k], lo/hi[i*(N-1) + k],
+// rec[i].  Recordings are concatenated, each recording's episodes contiguous
+// and in canonical order -- the interleaved sequence
+// (E_1, lo_1, hi_1, E_2, ..., lo_{N-1}, hi_{N-1}, E_N).
+//
+// Candidate generation (readings of a point the paper leaves open):
+//   level 2: every ordered pair (a, b) of distinct frequent types with every
+//            bin.  They are counted in (a, b, bin) order so that the episodes
+//            a warp holds share their types (a narrow type filter), and
+//            compacted back in canonical (a, bin, b) order.
+//   level N: alpha, beta frequent (N-1)-episodes of one recording with
+//            alpha[2..] = beta[..N-2] (types and bins) give alpha + beta's last
+//            edge and node, provided that node's type is not already in alpha.
+//            Walking alpha in canonical order and beta in canonical order
+//            emits candidates in canonical order.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "fem_internal.cuh"
+
+struct fem_result {
+    struct Level {
+        std::vector<int64_t> offs{0};
+        std::vector<uint16_t> types;
+        std::vector<int32_t> lo, hi;
+        std::vector<uint32_t> counts;
+    };
+    int n_recs = 0;
+    int max_size = 0;
+    std::vector<std::vector<Level>> lv;  // [rec][level]
+    fem_stats stats{};
+};
+
+namespace fem {
+
+// Level 1: frequent types of every recording, ascending.
+__global__ void k_level1_flags(const uint32_t *const *freq, const uint32_t *n_types_pre, int n_recs,
+                               const uint32_t *thr, int32_t *flags, int64_t total) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int r = 0;
+    while (r + 1 < n_recs && (int64_t)n_types_pre[r + 1] <= g) ++r;
+    const int64_t a = g - n_types_pre[r];
+    flags[g] = freq[r][a] > thr[r] ? 1 : 0;
+}
+
+__global__ void k_level1_write(const int32_t *flags_scanned, const uint32_t *const *freq,
+                               const uint32_t *n_types_pre, int n_recs, const uint32_t *thr, int64_t total,
+                               uint16_t *ftypes, uint32_t *fcounts, uint32_t *frec) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int r = 0;
+    while (r + 1 < n_recs && (int64_t)n_types_pre[r + 1] <= g) ++r;
+    const int64_t a = g - n_types_pre[r];
+    const uint32_t f = freq[r][a];
+    if (f > thr[r]) {
+        const int32_t pos = flags_scanned[g];
+        ftypes[pos] = (uint16_t)a;
+        fcounts[pos] = f;
+        frec[pos] = (uint32_t)r;
+    }
+}
+
+// Level 2 candidates of recording r: local index i = ((ia*(F-1)) + jb)*nb + bin
+// (count order); b = jb < ia ? jb : jb + 1.
+__global__ void k_gen_level2(const uint16_t *ftypes, const int64_t *f_off, const int64_t *c_off, int n_recs,
+                             const int32_t *bin_lo, const int32_t *bin_hi, int nb, int64_t total,
+                             uint16_t *ctypes, int32_t *clo, int32_t *chi, uint32_t *crec, int64_t *coffs) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int lo_r = 0, hi_r = n_recs;  // last r with c_off[r] <= g
+    while (hi_r - lo_r > 1) {
+        const int mid = (lo_r + hi_r) >> 1;
+        if (c_off[mid] <= g) lo_r = mid; else hi_r = mid;
+    }
+    const int r = lo_r;
+    const int64_t i = g - c_off[r];
+    const int64_t F = f_off[r + 1] - f_off[r];
+    const int64_t bin = i % nb;
+    const int64_t q = i / nb;
+    const int64_t ia = q / (F - 1), jb = q % (F - 1);
+    const int64_t ib = jb < ia ? jb : jb + 1;
+    ctypes[2 * g] = ftypes[f_off[r] + ia];
+    ctypes[2 * g + 1] = ftypes[f_off[r] + ib];
+    clo[g] = bin_lo[bin];
+    chi[g] = bin_hi[bin];
+    crec[g] = (uint32_t)r;
+    coffs[g] = 2 * g;
+    if (g == total - 1) coffs[total] = 2 * total;
+}
+
+// Canonical index -> count index for level 2 of recording r.
+__device__ __forceinline__ int64_t canon_to_count2(int64_t i, int64_t F, int nb) {
+    // canonical i = ((ia * nb) + bin) * (F-1) + jb
+    const int64_t jb = i % (F - 1);
+    const int64_t q = i / (F - 1);
+    const int64_t bin = q % nb, ia = q / nb;
+    return ((ia * (F - 1)) + jb) * nb + bin;
+}
+
+// Level N >= 3 join, CountScanWrite style: count partners per alpha, scan,
+// then write.
+__device__ __forceinline__ bool joins(const uint16_t *ft, const int32_t *fl, const int32_t *fh, int M,
+                                      int64_t a, int64_t b) {
+    // M = N-1 nodes per frequent episode, M-1 edges
+    for (int k = 1; k < M; ++k)
+        if (ft[a * M + k] != ft[b * M + k - 1]) return false;
+    for (int k = 1; k < M - 1; ++k)
+        if (fl[a * (M - 1) + k] != fl[b * (M - 1) + k - 1] || fh[a * (M - 1) + k] != fh[b * (M - 1) + k - 1])
+            return false;
+    const uint16_t last = ft[b * M + M - 1];
+    for (int k = 0; k < M; ++k)
+        if (ft[a * M + k] == last) return false;
+    return true;
+}
+
+__global__ void k_join_count(const uint16_t *ft, const int32_t *fl, const int32_t *fh, const uint32_t *frec,
+                             const int64_t *f_off, int M, int64_t F, int32_t *cnt) {
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= F) return;
+    const uint32_t r = frec[a];
+    int32_t c = 0;
+    for (int64_t b = f_off[r]; b < f_off[r + 1]; ++b)
+        if (joins(ft, fl, fh, M, a, b)) ++c;
+    cnt[a] = c;
+}
+
+__global__ void k_join_write(const uint16_t *ft, const int32_t *fl, const int32_t *fh, const uint32_t *frec,
+                             const int64_t *f_off, int M, int64_t F, const int32_t *pos, uint16_t *ct,
+                             int32_t *cl, int32_t *ch, uint32_t *crec, int64_t *coffs, int64_t total) {
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= F) return;
+    const uint32_t r = frec[a];
+    int64_t o = pos[a];
+    const int N = M + 1;
+    for (int64_t b = f_off[r]; b < f_off[r + 1]; ++b) {
+        if (!joins(ft, fl, fh, M, a, b)) continue;
+        for (int k = 0; k < M; ++k) ct[o * N + k] = ft[a * M + k];
+        ct[o * N + M] = ft[b * M + M - 1];
+        for (int k = 0; k < M - 1; ++k) {
+            cl[o * (N - 1) + k] = fl[a * (M - 1) + k];
+            ch[o * (N - 1) + k] = fh[a * (M - 1) + k];
+        }
+        cl[o * (N - 1) + M - 1] = fl[b * (M - 1) + M - 2];
+        ch[o * (N - 1) + M - 1] = fh[b * (M - 1) + M - 2];
+        crec[o] = r;
+        coffs[o] = o * N;
+        ++o;
+    }
+    if (a == F - 1) coffs[total] = total * N;
+}
+
+// Threshold: flags in canonical order (count > threshold, strict).
+__global__ void k_thr_flags(const uint32_t *counts, const uint32_t *crec, const int64_t *c_off, int n_recs,
+                            const int64_t *f_prev_off, int level, int nb, const uint32_t *thr, int64_t total,
+                            int32_t *flags) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    int64_t ci = i;
+    if (level == 2) {
+        int lo_r = 0, hi_r = n_recs;
+        while (hi_r - lo_r > 1) {
+            const int mid = (lo_r + hi_r) >> 1;
+            if (c_off[mid] <= i) lo_r = mid; else hi_r = mid;
+        }
+        const int64_t F = f_prev_off[lo_r + 1] - f_prev_off[lo_r];
+        ci = c_off[lo_r] + canon_to_count2(i - c_off[lo_r], F, nb);
+    }
+    flags[i] = counts[ci] > thr[crec[ci]] ? 1 : 0;
+}
+
+__global__ void k_thr_write(const int32_t *pos, const uint32_t *counts, const uint16_t *ct, const int32_t *cl,
+                            const int32_t *ch, const uint32_t *crec, const int64_t *c_off, int n_recs,
+                            const int64_t *f_prev_off, int level, int nb, const uint32_t *thr, int N, int64_t total,
+                            uint16_t *ft, int32_t *fl, int32_t *fh, uint32_t *frec, uint32_t *fcnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    int64_t ci = i;
+    if (level == 2) {
+        int lo_r = 0, hi_r = n_recs;
+        while (hi_r - lo_r > 1) {
+            const int mid = (lo_r + hi_r) >> 1;
+            if (c_off[mid] <= i) lo_r = mid; else hi_r = mid;
+        }
+        const int64_t F = f_prev_off[lo_r + 1] - f_prev_off[lo_r];
+        ci = c_off[lo_r] + canon_to_count2(i - c_off[lo_r], F, nb);
+    }
+    const uint32_t r = crec[ci];
+    if (!(counts[ci] > thr[r])) return;
+    const int64_t o = pos[i];
+    for (int k = 0; k < N; ++k) ft[o * N + k] = ct[ci * N + k];
+    for (int k = 0; k < N - 1; ++k) {
+        fl[o * (N - 1) + k] = cl[ci * (N - 1) + k];
+        fh[o * (N - 1) + k] = ch[ci * (N - 1) + k];
+    }
+    frec[o] = r;
+    fcnt[o] = counts[ci];
+}
+
+// Per-recording offsets of a rec-sorted array.
+__global__ void k_rec_offsets(const uint32_t *rec, int64_t n, int n_recs, int64_t *off) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > n_recs) return;
+    int64_t lo = 0, hi = n;  // first index with rec >= r
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int)rec[mid] < r) lo = mid + 1; else hi = mid;
+    }
+    off[r] = lo;
+}
+
+// Counting entry shared with fem_count.cu (mode 0, device candidate arrays).
+int count_device(fem_ctx *ctx, const std::vector<fem_stream *> &recs, int64_t n_cand, const int64_t *offs,
+                 const uint16_t *types, const int32_t *lo, const int32_t *hi, const uint32_t *cand_rec,
+                 const std::vector<int32_t> &lo_vals, uint32_t *counts, fem_stats *stats);
+
+namespace {
+
+struct DevLevel {
+    int N = 0;
+    int64_t n = 0;
+    uint16_t *types = nullptr;
+    int32_t *lo = nullptr, *hi = nullptr;
+    uint32_t *rec = nullptr, *counts = nullptr;
+    int64_t *off = nullptr;  // per-recording offsets (n_recs + 1)
+    std::vector<int64_t> h_off;
+};
+
+struct Pool {
+    fem_ctx *ctx;
+    std::vector<std::pair<void *, size_t>> held;
+    ~Pool() {
+        cudaStreamSynchronize(ctx->stream);
+        for (auto &h : held) dev_free(ctx, h.first, h.second);
+    }
+    template <typename T>
+    int get(T **p, size_t n) {
+        void *q = nullptr;
+        const size_t b = std::max<size_t>(n, 1) * sizeof(T);
+        FEM_TRY(dev_alloc(ctx, &q, b));
+        held.push_back({q, b});
+        *p = static_cast<T *>(q);
+        return FEM_OK;
+    }
+};
+
+int copy_level_to_host(fem_ctx *ctx, const DevLevel &L, fem_result *res, int level) {
+    const int N = L.N;
+    std::vector<uint16_t> t(L.n * N);
+    std::vector<int32_t> lo(L.n * (N - 1)), hi(L.n * (N - 1));
+    std::vector<uint32_t> c(L.n);
+    if (L.n > 0) {
+        FEM_CUDA_TRY(cudaMemcpyAsync(t.data(), L.types, 2 * t.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        if (N > 1) {
+            FEM_CUDA_TRY(cudaMemcpyAsync(lo.data(), L.lo, 4 * lo.size(), cudaMemcpyDeviceToHost, ctx->stream));
+            FEM_CUDA_TRY(cudaMemcpyAsync(hi.data(), L.hi, 4 * hi.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        FEM_CUDA_TRY(cudaMemcpyAsync(c.data(), L.counts, 4 * c.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    for (int r = 0; r < res->n_recs; ++r) {
+        fem_result::Level &out = res->lv[r][level];
+        const int64_t b = L.h_off[r], e = L.h_off[r + 1];
+        out.offs.assign(1, 0);
+        for (int64_t i = b; i < e; ++i) {
+            out.types.insert(out.types.end(), t.begin() + i * N, t.begin() + (i + 1) * N);
+            if (N > 1) {
+                out.lo.insert(out.lo.end(), lo.begin() + i * (N - 1), lo.begin() + (i + 1) * (N - 1));
+                out.hi.insert(out.hi.end(), hi.begin() + i * (N - 1), hi.begin() + (i + 1) * (N - 1));
+            }
+            out.counts.push_back(c[i]);
+            out.offs.push_back((int64_t)out.types.size());
+        }
+    }
+    return FEM_OK;
+}
+
+int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
+              const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, int max_size, fem_result *res) {
+    const int n_recs = (int)recs.size();
+    const int nb = (int)blo.size();
+    Pool pool{ctx};
+    cudaStream_t st = ctx->stream;
+    fem_stats &S = res->stats;
+    const int B = 256;
+    // constants on device
+    uint32_t *d_thr;
+    int32_t *d_blo, *d_bhi;
+    FEM_TRY(pool.get(&d_thr, n_recs));
+    FEM_TRY(pool.get(&d_blo, nb));
+    FEM_TRY(pool.get(&d_bhi, nb));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_thr, thr.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_blo, blo.data(), 4 * nb, cudaMemcpyHostToDevice, st));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_bhi, bhi.data(), 4 * nb, cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> lo_vals(blo.begin(), blo.end());
+    std::sort(lo_vals.begin(), lo_vals.end());
+    lo_vals.erase(std::unique(lo_vals.begin(), lo_vals.end()), lo_vals.end());
+
+    // ---- level 1
+    std::vector<uint32_t> nt_pre(n_recs + 1, 0);
+    std::vector<const uint32_t *> freq_p(n_recs);
+    for (int r = 0; r < n_recs; ++r) {
+        nt_pre[r + 1] = nt_pre[r] + recs[r]->n_types;
+        freq_p[r] = recs[r]->d_freq;
+    }
+    const int64_t tot1 = nt_pre[n_recs];
+    uint32_t *d_ntpre;
+    const uint32_t **d_freqp;
+    int32_t *d_flags, *d_scan;
+    FEM_TRY(pool.get(&d_ntpre, n_recs + 1));
+    FEM_TRY(pool.get(&d_freqp, n_recs));
+    FEM_TRY(pool.get(&d_flags, tot1 + 1));
+    FEM_TRY(pool.get(&d_scan, tot1 / 1024 + 2));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_ntpre, nt_pre.data(), 4 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_freqp, freq_p.data(), sizeof(void *) * n_recs, cudaMemcpyHostToDevice, st));
+    k_level1_flags<<<(unsigned)((tot1 + B - 1) / B), B, 0, st>>>(d_freqp, d_ntpre, n_recs, d_thr, d_flags, tot1);
+    int32_t *d_total;
+    FEM_TRY(pool.get(&d_total, 2));
+    FEM_TRY(scan_exclusive(st, d_flags, tot1, d_scan, d_total, &S.kernel_launches));
+    int32_t F1 = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&F1, d_total, 4, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    DevLevel prev;
+    prev.N = 1;
+    prev.n = F1;
+    FEM_TRY(pool.get(&prev.types, F1));
+    FEM_TRY(pool.get(&prev.counts, F1));
+    FEM_TRY(pool.get(&prev.rec, F1));
+    FEM_TRY(pool.get(&prev.off, n_recs + 1));
+    k_level1_write<<<(unsigned)((tot1 + B - 1) / B), B, 0, st>>>(d_flags, d_freqp, d_ntpre, n_recs, d_thr, tot1,
+                                                                prev.types, prev.counts, prev.rec);
+    k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(prev.rec, prev.n, n_recs, prev.off);
+    S.kernel_launches += 3;
+    prev.h_off.resize(n_recs + 1);
+    FEM_CUDA_TRY(cudaMemcpyAsync(prev.h_off.data(), prev.off, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    FEM_TRY(copy_level_to_host(ctx, prev, res, 1));
+    S.levels = 1;
+
+    for (int N = 2; N <= max_size; ++N) {
+        // ---- candidate generation
+        std::vector<int64_t> c_off(n_recs + 1, 0);
+        if (N == 2) {
+            for (int r = 0; r < n_recs; ++r) {
+                const int64_t F = prev.h_off[r + 1] - prev.h_off[r];
+                c_off[r + 1] = c_off[r] + (F >= 2 ? F * (F - 1) * nb : 0);
+            }
+        }
+        int64_t C = 0;
+        DevLevel cand;
+        cand.N = N;
+        int64_t *d_coffs = nullptr;
+        int64_t *d_coff_rec = nullptr;
+        FEM_TRY(pool.get(&d_coff_rec, n_recs + 1));
+        if (N == 2) {
+            C = c_off[n_recs];
+            if (C == 0) break;
+            FEM_TRY(pool.get(&cand.types, 2 * C));
+            FEM_TRY(pool.get(&cand.lo, C));
+            FEM_TRY(pool.get(&cand.hi, C));
+            FEM_TRY(pool.get(&cand.rec, C));
+            FEM_TRY(pool.get(&d_coffs, C + 1));
+            FEM_CUDA_TRY(cudaMemcpyAsync(d_coff_rec, c_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+            k_gen_level2<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(prev.types, prev.off, d_coff_rec, n_recs, d_blo,
+                                                                   d_bhi, nb, C, cand.types, cand.lo, cand.hi,
+                                                                   cand.rec, d_coffs);
+            S.kernel_launches++;
+        } else {
+            const int M = N - 1;
+            const int64_t F = prev.n;
+            if (F == 0) break;
+            int32_t *d_cnt, *d_tmp, *d_tot;
+            FEM_TRY(pool.get(&d_cnt, F + 1));
+            FEM_TRY(pool.get(&d_tmp, F / 1024 + 2));
+            FEM_TRY(pool.get(&d_tot, 2));
+            k_join_count<<<(unsigned)((F + B - 1) / B), B, 0, st>>>(prev.types, prev.lo, prev.hi, prev.rec, prev.off,
+                                                                   M, F, d_cnt);
+            FEM_TRY(scan_exclusive(st, d_cnt, F, d_tmp, d_tot, &S.kernel_launches));
+            int32_t Ct = 0;
+            FEM_CUDA_TRY(cudaMemcpyAsync(&Ct, d_tot, 4, cudaMemcpyDeviceToHost, st));
+            FEM_CUDA_TRY(cudaStreamSynchronize(st));
+            C = Ct;
+            S.kernel_launches++;
+            if (C == 0) break;
+            FEM_TRY(pool.get(&cand.types, (size_t)C * N));
+            FEM_TRY(pool.get(&cand.lo, (size_t)C * (N - 1)));
+            FEM_TRY(pool.get(&cand.hi, (size_t)C * (N - 1)));
+            FEM_TRY(pool.get(&cand.rec, C));
+            FEM_TRY(pool.get(&d_coffs, C + 1));
+            k_join_write<<<(unsigned)((F + B - 1) / B), B, 0, st>>>(prev.types, prev.lo, prev.hi, prev.rec, prev.off,
+                                                                   M, F, d_cnt, cand.types, cand.lo, cand.hi, cand.rec,
+                                                                   d_coffs, C);
+            k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(cand.rec, C, n_recs, d_coff_rec);
+            FEM_CUDA_TRY(cudaMemcpyAsync(c_off.data(), d_coff_rec, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
+            FEM_CUDA_TRY(cudaStreamSynchronize(st));
+            S.kernel_launches += 2;
+        }
+        cand.n = C;
+        FEM_TRY(pool.get(&cand.counts, C));
+        // ---- exact counting of every candidate of every recording
+        fem_stats cs{};
+        FEM_TRY(count_device(ctx, recs, C, d_coffs, cand.types, cand.lo, cand.hi, cand.rec, lo_vals, cand.counts,
+                             &cs));
+        S.kernel_launches += cs.kernel_launches;
+        S.candidates_counted += cs.candidates_counted;
+        S.candidates_pruned += cs.candidates_pruned;
+        S.fallback_recounts += cs.fallback_recounts;
+        S.relevant_events += cs.relevant_events;
+        S.count_kernel_ms += cs.count_kernel_ms;
+        for (int r = 0; r < n_recs; ++r) S.episode_events += (double)(c_off[r + 1] - c_off[r]) * (double)recs[r]->n;
+        // ---- threshold + compaction in canonical order
+        int32_t *d_fl, *d_tmp2, *d_tot2;
+        FEM_TRY(pool.get(&d_fl, C + 1));
+        FEM_TRY(pool.get(&d_tmp2, C / 1024 + 2));
+        FEM_TRY(pool.get(&d_tot2, 2));
+        k_thr_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(cand.counts, cand.rec, d_coff_rec, n_recs, prev.off, N,
+                                                              nb, d_thr, C, d_fl);
+        FEM_TRY(scan_exclusive(st, d_fl, C, d_tmp2, d_tot2, &S.kernel_launches));
+        int32_t Fn = 0;
+        FEM_CUDA_TRY(cudaMemcpyAsync(&Fn, d_tot2, 4, cudaMemcpyDeviceToHost, st));
+        FEM_CUDA_TRY(cudaStreamSynchronize(st));
+        DevLevel next;
+        next.N = N;
+        next.n = Fn;
+        FEM_TRY(pool.get(&next.types, (size_t)Fn * N));
+        FEM_TRY(pool.get(&next.lo, (size_t)Fn * (N - 1)));
+        FEM_TRY(pool.get(&next.hi, (size_t)Fn * (N - 1)));
+        FEM_TRY(pool.get(&next.rec, Fn));
+        FEM_TRY(pool.get(&next.counts, Fn));
+        FEM_TRY(pool.get(&next.off, n_recs + 1));
+        k_thr_write<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_fl, cand.counts, cand.types, cand.lo, cand.hi,
+                                                              cand.rec, d_coff_rec, n_recs, prev.off, N, nb, d_thr, N, C,
+                                                              next.types, next.lo, next.hi, next.rec, next.counts);
+        k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(next.rec, next.n, n_recs, next.off);
+        S.kernel_launches += 3;
+        next.h_off.resize(n_recs + 1);
+        FEM_CUDA_TRY(cudaMemcpyAsync(next.h_off.data(), next.off, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
+        FEM_TRY(sync_status(ctx));
+        FEM_TRY(copy_level_to_host(ctx, next, res, N));
+        S.levels = N;
+        prev = next;
+        if (Fn == 0) break;
+    }
+    return FEM_OK;
+}
+
+}  // namespace
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" int fem_mine_levelwise(fem_ctx *ctx, const fem_stream *const *recs, int n_recs, const int32_t *bin_lo,
+                                  const int32_t *bin_hi, int n_bins, const uint32_t *threshold, int max_size,
+                                  fem_result **out) {
+    if (!ctx || !recs || n_recs < 1 || !out || max_size < 1 || max_size > FEM_MAX_NODES || !threshold)
+        return FEM_ERR_INVAL;
+    if (n_bins < 0 || (n_bins > 0 && (!bin_lo || !bin_hi)) || (max_size > 1 && n_bins < 1)) return FEM_ERR_INVAL;
+    *out = nullptr;
+    std::vector<std::pair<int32_t, int32_t>> bins;
+    for (int b = 0; b < n_bins; ++b) {
+        if (bin_lo[b] < 0 || bin_lo[b] >= bin_hi[b]) return FEM_ERR_INVAL;
+        bins.push_back({bin_lo[b], bin_hi[b]});
+    }
+    std::sort(bins.begin(), bins.end());
+    bins.erase(std::unique(bins.begin(), bins.end()), bins.end());
+    std::vector<int32_t> blo, bhi;
+    for (auto &b : bins) {
+        blo.push_back(b.first);
+        bhi.push_back(b.second);
+    }
+    std::vector<fem_stream *> rv;
+    std::vector<uint32_t> thr(threshold, threshold + n_recs);
+    for (int r = 0; r < n_recs; ++r) {
+        if (!recs[r] || recs[r]->ctx != ctx) return FEM_ERR_INVAL;
+        rv.push_back(const_cast<fem_stream *>(recs[r]));
+    }
+    fem_result *res = new (std::nothrow) fem_result();
+    if (!res) return FEM_ERR_NOMEM;
+    res->n_recs = n_recs;
+    res->max_size = max_size;
+    res->lv.assign(n_recs, std::vector<fem_result::Level>(max_size + 1));
+    int st;
+    const double t0 = now_s();
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        cudaSetDevice(ctx->device);
+        st = mine_impl(ctx, rv, blo, bhi, thr, max_size, res);
+        if (st == FEM_OK) st = sync_status(ctx);
+    }
+    if (st != FEM_OK) {
+        delete res;
+        return st;
+    }
+    res->stats.total_ms = (now_s() - t0) * 1e3;
+    ctx->last = res->stats;
+    *out = res;
+    return FEM_OK;
+}
+
+extern "C" int fem_result_level(const fem_result *r, int rec, int level, int64_t *n_out, const int64_t **offs,
+                                const uint16_t **types, const int32_t **lo, const int32_t **hi,
+                                const uint32_t **counts) {
+    if (!r || rec < 0 || rec >= r->n_recs || level < 1 || level > r->max_size || !n_out) return FEM_ERR_INVAL;
+    const fem_result::Level &L = r->lv[rec][level];
+    *n_out = (int64_t)L.counts.size();
+    if (offs) *offs = L.offs.data();
+    if (types) *types = L.types.data();
+    if (lo) *lo = L.lo.data();
+    if (hi) *hi = L.hi.data();
+    if (counts) *counts = L.counts.data();
+    return FEM_OK;
+}
+
+extern "C" int fem_result_stats(const fem_result *r, fem_stats *out) {
+    if (!r || !out) return FEM_ERR_INVAL;
+    *out = r->stats;
+    return FEM_OK;
+}
+
+extern "C" void fem_result_free(fem_result *r) { delete r; }

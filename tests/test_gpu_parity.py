@@ -1,0 +1,283 @@
+"""GPU parity: the CUDA library through its C ABI against the CPU oracle.
+
+Counts are integers, so every comparison is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fb():
+    from paper_0905_2203_gb300 import build as b
+    b.build()
+    from paper_0905_2203_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(fb):
+    c = fb.Context(0)
+    yield c
+    c.close()
+
+
+def oracle_counts(ty, tm, offs, ct, lo, hi):
+    c, _ = oracle.count_many(ty, tm, offs, ct, lo, hi)
+    return c.astype(np.int64)
+
+
+def gpu_counts(fb, ctx, st, offs, ct, lo, hi):
+    return ctx.count_episodes(st, fb.Cands(offs, ct, lo, hi)).astype(np.int64)
+
+
+def test_version_and_symbols(fb):
+    assert "sm_103a" in fb.version()
+
+
+def test_level1_frequency(fb, ctx):
+    s, _ = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    f = st.freq()
+    for a in range(s.n_types):
+        assert f[a] == oracle.count_fsm(s.types, s.times, [a], [], [])
+    st.free()
+
+
+def test_stream_validation_errors(fb, ctx):
+    ty = np.array([0, 1, 0], np.uint16)
+    with pytest.raises(fb.FemError) as e:
+        ctx.load_stream(ty, np.array([0, 2, 1], np.int32), 2)
+    assert e.value.status == fb.FEM_ERR_UNSORTED
+    ok = ctx.load_stream(np.array([0, 1, 0], np.uint16), np.array([0, 1, 1], np.int32), 2)  # ties, distinct types
+    ok.free()
+    with pytest.raises(fb.FemError) as e:
+        ctx.load_stream(np.array([0, 1, 0], np.uint16), np.array([0, 1, 0], np.int32), 2)
+    assert e.value.status == fb.FEM_ERR_UNSORTED
+    with pytest.raises(fb.FemError) as e:
+        ctx.load_stream(np.array([0, 1, 1], np.uint16), np.array([0, 5, 5], np.int32), 2)
+    assert e.value.status == fb.FEM_ERR_DUP
+    with pytest.raises(fb.FemError) as e:
+        ctx.load_stream(np.array([0, 2], np.uint16), np.array([0, 1], np.int32), 2)
+    assert e.value.status == fb.FEM_ERR_INVAL
+    with pytest.raises(fb.FemError) as e:
+        ctx.load_stream(np.array([0, 1], np.uint16), np.array([-3, 1], np.int32), 2)
+    assert e.value.status == fb.FEM_ERR_RANGE
+
+
+def test_candidate_validation_errors(fb, ctx):
+    s, _ = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    bad = [
+        (np.array([0, 2]), np.array([0, 1]), np.array([5]), np.array([5])),   # lo == hi
+        (np.array([0, 2]), np.array([0, 1]), np.array([-1]), np.array([5])),  # lo < 0
+        (np.array([0, 2]), np.array([0, 40]), np.array([0]), np.array([5])),  # type >= n_types
+    ]
+    for offs, ct, lo, hi in bad:
+        with pytest.raises(fb.FemError) as e:
+            ctx.count_episodes(st, fb.Cands(offs, ct, lo, hi))
+        assert e.value.status == fb.FEM_ERR_INVAL
+    st.free()
+
+
+def test_golden_cases_on_gpu(fb, ctx):
+    from golden_io import all_cases
+    for name, ty, tm, (E, lo, hi), expect in all_cases():
+        st = ctx.load_stream(ty, tm, int(max(ty.max(initial=0), max(E)) + 1))
+        offs = np.array([0, len(E)], np.int64)
+        got = ctx.count_episodes(st, fb.Cands(offs, np.array(E, np.uint16), np.array(lo, np.int32),
+                                              np.array(hi, np.int32)))
+        assert int(got[0]) == expect, name
+        st.free()
+
+
+@pytest.mark.parametrize("segments,lanes,tile", [(0, 0, 0), (1, 32, 256), (7, 64, 512), (64, 256, 1024),
+                                                  (300, 96, 4096)])
+def test_random_tiny_streams(fb, ctx, segments, lanes, tile):
+    """Many random episodes (sizes 1-6, lower bounds 0..6) over random streams
+    with frequent equal times, under several segment / CTA / tile settings."""
+    r = synth.Rng(99, segments + 7)
+    ctx.set_tuning(lanes_per_cta=lanes, segments=segments, tile_events=tile)
+    try:
+        for trial in range(6):
+            n_types = int(r.integers(2, 7, 1)[0])
+            n = int(r.integers(50, 5000, 1)[0])
+            ty, tm = synth.tiny_random_stream(1000 + trial, n, n_types, int(r.integers(n // 3 + 5, 3 * n, 1)[0]))
+            nc = 700
+            sizes = r.integers(1, 6, nc)
+            offs = np.zeros(nc + 1, np.int64)
+            offs[1:] = np.cumsum(sizes)
+            ct = r.integers(0, n_types - 1, int(offs[-1])).astype(np.uint16)
+            ne = int(offs[-1]) - nc
+            lo = r.integers(0, 6, ne).astype(np.int32)
+            hi = (lo + r.integers(1, 12, ne)).astype(np.int32)
+            st = ctx.load_stream(ty, tm, n_types)
+            got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+            want = oracle_counts(ty, tm, offs, ct, lo, hi)
+            bad = np.nonzero(got != want)[0]
+            assert bad.size == 0, (trial, bad[:5], got[bad[:5]], want[bad[:5]])
+            st.free()
+    finally:
+        ctx.reset_tuning()
+
+
+def test_c1_random_candidates(fb, ctx):
+    s, _ = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    offs, ct, lo, hi = synth.random_candidates(7, 3000, s.n_types, 2, 8, [(0, 5), (3, 9), (0, 20)],
+                                               s.chains, 0.2)
+    assert np.array_equal(gpu_counts(fb, ctx, st, offs, ct, lo, hi), oracle_counts(s.types, s.times, offs, ct, lo, hi))
+    st.free()
+
+
+def test_plain_path_matches_oracle(fb, ctx):
+    s, _ = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    offs, ct, lo, hi = synth.random_candidates(8, 800, s.n_types, 1, 6, [(0, 5), (3, 9)], s.chains, 0.2)
+    got = ctx.count_episodes_plain(st, fb.Cands(offs, ct, lo, hi)).astype(np.int64)
+    assert np.array_equal(got, oracle_counts(s.types, s.times, offs, ct, lo, hi))
+    st.free()
+
+
+def test_upper_bound_is_relaxed_count(fb, ctx):
+    s, _ = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    offs, ct, lo, hi = synth.random_candidates(9, 600, s.n_types, 2, 5, [(2, 5), (3, 9)], s.chains, 0.3)
+    ub = ctx.upper_bound(st, fb.Cands(offs, ct, lo, hi)).astype(np.int64)
+    exact = oracle_counts(s.types, s.times, offs, ct, lo, hi)
+    relaxed = oracle_counts(s.types, s.times, offs, ct, np.zeros_like(lo), hi)
+    assert np.all(ub >= exact)
+    assert np.array_equal(ub, relaxed)
+    st.free()
+
+
+def test_bursty_stream_mixed_sizes(fb, ctx):
+    """Network bursts (dense windows) with sizes 2-8 and the 4-bin set."""
+    s = synth.bursty_60(0xFE0003, 150_000)
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    offs, ct, lo, hi = synth.random_candidates(0xFE0003, 3000, 60, 2, 8, synth.BINS_4, s.chains, 0.05)
+    got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+    want = oracle_counts(s.types, s.times, offs, ct, lo, hi)
+    assert np.array_equal(got, want)
+    assert want.max() > 0
+    st.free()
+
+
+def test_edge_cases(fb, ctx):
+    # empty stream
+    st = ctx.load_stream(np.zeros(0, np.uint16), np.zeros(0, np.int32), 3)
+    got = ctx.count_episodes(st, fb.Cands(np.array([0, 2, 3]), np.array([0, 1, 2], np.uint16),
+                                          np.array([0], np.int32), np.array([4], np.int32)))
+    assert got.tolist() == [0, 0]
+    st.free()
+    # zero candidates
+    s, _ = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    got = ctx.count_episodes(st, fb.Cands(np.array([0], np.int64), np.zeros(0, np.uint16),
+                                          np.zeros(0, np.int32), np.zeros(0, np.int32)))
+    assert got.size == 0
+    # maximum episode size, repeated types, single event stream
+    E = np.array([3, 3, 7, 3] * 4, np.uint16)
+    offs = np.array([0, 16], np.int64)
+    lo = np.zeros(15, np.int32)
+    hi = np.full(15, 40, np.int32)
+    got = ctx.count_episodes(st, fb.Cands(offs, E, lo, hi))
+    assert int(got[0]) == oracle.count_fsm(s.types, s.times, E, lo, hi)
+    st.free()
+    st = ctx.load_stream(np.array([2], np.uint16), np.array([0], np.int32), 3)
+    got = ctx.count_episodes(st, fb.Cands(np.array([0, 1, 3]), np.array([2, 2, 1], np.uint16),
+                                          np.array([0], np.int32), np.array([1], np.int32)))
+    assert got.tolist() == [1, 0]
+    st.free()
+
+
+def test_device_pointers_with_torch(fb, ctx):
+    torch = pytest.importorskip("torch")
+    s, _ = synth.c1_tiny()
+    dev = torch.device("cuda:0")
+    st = ctx.load_stream(torch.from_numpy(s.types.view(np.int16)).to(dev),
+                         torch.from_numpy(s.times).to(dev), s.n_types)
+    offs, ct, lo, hi = synth.random_candidates(12, 400, s.n_types, 2, 4, [(0, 5)], s.chains, 0.3)
+    c = fb.Cands(torch.from_numpy(offs).to(dev), torch.from_numpy(ct.view(np.int16)).to(dev),
+                 torch.from_numpy(lo).to(dev), torch.from_numpy(hi).to(dev))
+    out = torch.zeros(400, dtype=torch.int32, device=dev)
+    ctx.count_episodes(st, c, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert np.array_equal(got, oracle_counts(s.types, s.times, offs, ct, lo, hi))
+    st.free()
+
+
+def test_count_batch_multi_recording(fb, ctx):
+    recs = synth.c4_recordings(0xFE0004, n_rec=6, n_lo=2e3, n_hi=6e4)
+    streams = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
+    offs_l, ct_l, lo_l, hi_l, rid = [], [], [], [], []
+    base = 0
+    r = synth.Rng(3, 3)
+    order = r.integers(0, len(recs) - 1, 1200)
+    per = {}
+    for k, (s, cfg) in enumerate(recs):
+        per[k] = synth.random_candidates(40 + k, 200, 60, 2, 6, synth.BINS_4, s.chains, 0.3)
+    # interleave recordings in the candidate order
+    cursor = {k: 0 for k in per}
+    offs = [0]
+    for k in order:
+        o, t, l, h = per[k]
+        c = cursor[k] % 200
+        cursor[k] += 1
+        a, b = int(o[c]), int(o[c + 1])
+        ct_l.extend(t[a:b]); lo_l.extend(l[a - c:b - c - 1]); hi_l.extend(h[a - c:b - c - 1])
+        offs.append(offs[-1] + b - a)
+        rid.append(k)
+    offs = np.array(offs, np.int64)
+    ct = np.array(ct_l, np.uint16); lo = np.array(lo_l, np.int32); hi = np.array(hi_l, np.int32)
+    rid = np.array(rid, np.uint32)
+    got = ctx.count_batch(streams, fb.Cands(offs, ct, lo, hi), rid).astype(np.int64)
+    for k, (s, _) in enumerate(recs):
+        idx = np.nonzero(rid == k)[0]
+        sub_offs = [0]
+        st_, sl, sh = [], [], []
+        for c in idx:
+            a, b = int(offs[c]), int(offs[c + 1])
+            st_.extend(ct[a:b]); sl.extend(lo[a - c:b - c - 1]); sh.extend(hi[a - c:b - c - 1])
+            sub_offs.append(sub_offs[-1] + b - a)
+        want = oracle_counts(s.types, s.times, np.array(sub_offs), np.array(st_, np.uint16),
+                             np.array(sl, np.int32), np.array(sh, np.int32))
+        assert np.array_equal(got[idx], want), k
+    for st in streams:
+        st.free()
+
+
+def _mine_compare(fb, ctx, streams_np, bins, thrs, max_size):
+    streams = [ctx.load_stream(s.types, s.times, s.n_types) for s in streams_np]
+    res = ctx.mine_levelwise(streams, bins, thrs, max_size)
+    for k, s in enumerate(streams_np):
+        want = oracle.mine_levelwise(s.types, s.times, s.n_types, bins, thrs[k], max_size)
+        for N in range(1, max_size + 1):
+            eps, counts = res.level(k, N)
+            assert list(zip(eps, counts)) == want[N], (k, N)
+    st = res.stats()
+    res.free()
+    for x in streams:
+        x.free()
+    return st
+
+
+def test_mine_levelwise_c1(fb, ctx):
+    s, cfg = synth.c1_tiny()
+    _mine_compare(fb, ctx, [s], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
+
+
+def test_mine_levelwise_c2_short(fb, ctx):
+    s, cfg = synth.c2_mid(duration_s=60.0)
+    thr = int(0.0025 * s.n)
+    _mine_compare(fb, ctx, [s], cfg["bins"], [thr], cfg["max_size"])
+
+
+def test_mine_levelwise_multi_recording(fb, ctx):
+    recs = synth.c4_recordings(0xFE0004, n_rec=5, n_lo=5e3, n_hi=4e4)
+    _mine_compare(fb, ctx, [s for s, _ in recs], synth.BINS_4, [cfg["threshold"] for _, cfg in recs], 5)
