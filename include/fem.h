@@ -87,6 +87,9 @@ typedef struct {
     int segments;         /* stream segments per recording (>= 1) */
     int tile_events;      /* events per shared-memory stage (multiple of 256) */
     int prepass;          /* 1 = run the upper-bound pre-pass, -1 = never */
+    int plain_path;       /* 1 = count with the one-thread-per-episode plain
+                             path (comparison baseline) instead of the tiled
+                             kernels */
 } fem_tuning;
 
 /* Per-call statistics filled by the counting / mining calls. */

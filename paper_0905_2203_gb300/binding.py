@@ -49,7 +49,8 @@ class fem_cands(ctypes.Structure):
 
 
 class fem_tuning(ctypes.Structure):
-    _fields_ = [("lanes_per_cta", I32), ("segments", I32), ("tile_events", I32), ("prepass", I32)]
+    _fields_ = [("lanes_per_cta", I32), ("segments", I32), ("tile_events", I32), ("prepass", I32),
+                ("plain_path", I32)]
 
 
 class fem_stats(ctypes.Structure):
@@ -183,8 +184,8 @@ class Context:
         except Exception:
             pass
 
-    def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0):
-        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass)
+    def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0, plain_path=0):
+        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path)
         check(fem_ctx_set_tuning(self.h, ctypes.byref(t)), "fem_ctx_set_tuning")
 
     def reset_tuning(self):

@@ -1252,7 +1252,7 @@ int count_device(fem_ctx *ctx, const std::vector<fem_stream *> &recs, int64_t n_
     CountCall cc;
     cc.ctx = ctx;
     cc.recs = recs;
-    cc.mode = 0;
+    cc.mode = ctx->tuning.plain_path == 1 ? 1 : 0;
     cc.n_cand = n_cand;
     cc.offs = offs;
     cc.types = types;
