@@ -94,7 +94,11 @@ typedef struct {
 
 /* Per-call statistics filled by the counting / mining calls. */
 typedef struct {
-    double episode_events;      /* sum over counted (episode, recording) of n */
+    double episode_events;      /* sum over resolved (episode, recording) of n:
+                                   every candidate is resolved over its whole
+                                   recording, by the exact count or, in
+                                   mining, by the upper-bound pre-pass */
+    double counted_episode_events; /* the part resolved by the exact count */
     double relevant_events;     /* sum over counted episodes of sum_k freq(E_k) */
     int64_t candidates_counted; /* exact counts computed */
     int64_t candidates_pruned;  /* dropped by the upper-bound pre-pass */

@@ -54,7 +54,8 @@ class fem_tuning(ctypes.Structure):
 
 
 class fem_stats(ctypes.Structure):
-    _fields_ = [("episode_events", ctypes.c_double), ("relevant_events", ctypes.c_double),
+    _fields_ = [("episode_events", ctypes.c_double), ("counted_episode_events", ctypes.c_double),
+                ("relevant_events", ctypes.c_double),
                 ("candidates_counted", I64), ("candidates_pruned", I64),
                 ("fallback_recounts", I64), ("kernel_launches", I64),
                 ("count_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double),

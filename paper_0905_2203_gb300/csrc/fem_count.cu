@@ -36,14 +36,16 @@
 
 namespace fem {
 
-constexpr int kBucketNode = 5;   // NMAX classes: 2, 4, 8, 16 (+ N == 1)
-constexpr int kBucketRing = 5;   // ring classes: 4, 8, 16, 32, 64
+constexpr int kBucketNode = 4;   // NMAX classes: 2, 4, 8, 16
+constexpr int kBucketRing = 6;   // ring classes: R <= 2, 4, 8, 16, 32, 64
 constexpr int kBucketN1 = kBucketNode * kBucketRing;      // 1-node episodes
 constexpr int kBucketPlain = kBucketN1 + 1;               // global-memory path
 constexpr int kBuckets = kBucketPlain + 1;
 
 __host__ __device__ inline int nmax_of_class(int c) { return c == 0 ? 2 : c == 1 ? 4 : c == 2 ? 8 : 16; }
-__host__ __device__ inline int ring_of_class(int c) { return 4 << c; }
+__host__ __device__ inline int ring_of_class(int c) { return 2 << c; }
+// Largest register-ring capacity compiled for each NMAX class (0 = none).
+__host__ __device__ inline int max_reg_ring(int nclass) { return nclass == 0 ? 8 : nclass == 1 ? 4 : nclass == 2 ? 2 : 0; }
 
 struct RecInfo {
     const uint16_t *type;
@@ -71,127 +73,214 @@ struct TiledArgs {
     const int32_t *clo;
     const int32_t *chi;
     const int32_t *slot2cand;
-    int R;
+    int R;                // ring capacity (shared-memory rings only)
     int K;
     int T;
     int relaxed;
+    int small_alpha;      // every type < 128: the warp filter lives in registers
     int32_t *rec;         // records, kRecWords each
     int *status;
 };
 
 // ---------------------------------------------------------------------------
-// Per-lane machine state (registers; every array index is a compile-time
-// constant after unrolling).
+// Per-node rings of (time, latest start) entries, newest first.  Node 0's
+// latest start is its own time, so it stores times only.
+//
+// Register rings: R entries per node held as a shift register (every index a
+// compile-time constant after unrolling).
+template <int NMAX, int R>
+struct Rings {
+    int32_t t[NMAX - 1][R];
+    int32_t L[NMAX > 2 ? NMAX - 2 : 1][R];
+
+    __device__ __forceinline__ void init(int32_t *, int32_t *, int, int) {
+#pragma unroll
+        for (int k = 0; k < NMAX - 1; ++k)
+#pragma unroll
+            for (int r = 0; r < R; ++r) t[k][r] = INT32_MIN;
+#pragma unroll
+        for (int k = 0; k < (NMAX > 2 ? NMAX - 2 : 1); ++k)
+#pragma unroll
+            for (int r = 0; r < R; ++r) L[k][r] = 0;
+    }
+
+    // Dropping the oldest entry is safe if it is empty, expired for every
+    // query at time >= tt, or if the next-older entry is already past its
+    // lower bound (so the oldest can never again be the newest eligible one).
+    __device__ __forceinline__ void push(int k, int32_t tt, int32_t LL, int32_t lo, int32_t hi, int &flags) {
+        const int32_t o1 = t[k][R - 1], o2 = t[k][R - 2];
+        if (o1 != INT32_MIN && o1 >= tt - hi && o2 >= tt - lo) flags |= kMetaRingOverflow;
+#pragma unroll
+        for (int r = R - 1; r > 0; --r) {
+            t[k][r] = t[k][r - 1];
+            if (k > 0) L[k > 0 ? k - 1 : 0][r] = L[k > 0 ? k - 1 : 0][r - 1];
+        }
+        t[k][0] = tt;
+        if (k > 0) L[k > 0 ? k - 1 : 0][0] = LL;
+    }
+
+    // Newest entry already past its lower bound at time tt; valid when within
+    // the upper bound.  Returns its latest start through LL.
+    __device__ __forceinline__ bool query(int k, int32_t tt, int32_t lo, int32_t hi, int32_t &LL) const {
+        const int32_t elig = tt - lo;
+        int32_t tp = INT32_MIN, lp = 0;
+        bool found = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const bool c = !found && (t[k][r] < elig);
+            if (c) {
+                tp = t[k][r];
+                lp = (k == 0) ? t[k][r] : L[k > 0 ? k - 1 : 0][r];
+            }
+            found = found || c;
+        }
+        LL = lp;
+        return found && tp >= tt - hi;
+    }
+};
+
+// Shared-memory rings (R chosen at launch): entry r of node k of this lane at
+// base[(k * R + r) * K]; a per-node head index in registers.
 template <int NMAX>
-struct Lane {
+struct Rings<NMAX, 0> {
+    int32_t *rt;
+    int32_t *rl;
+    int R, K;
+    int head[NMAX - 1];
+
+    __device__ __forceinline__ void init(int32_t *rt_, int32_t *rl_, int R_, int K_) {
+        rt = rt_;
+        rl = rl_;
+        R = R_;
+        K = K_;
+#pragma unroll
+        for (int k = 0; k < NMAX - 1; ++k) head[k] = 0;
+        for (int k = 0; k < NMAX - 1; ++k)
+            for (int r = 0; r < R; ++r) rt[(k * R + r) * K] = INT32_MIN;
+    }
+
+    __device__ __forceinline__ void push(int k, int32_t tt, int32_t LL, int32_t lo, int32_t hi, int &flags) {
+        const int h = head[k];
+        int32_t *bt = rt + (k * R) * K;
+        int32_t *bl = rl + (k * R) * K;
+        const int h2 = (h + 1 == R) ? 0 : h + 1;
+        const int32_t o1 = bt[h * K];
+        const int32_t o2 = bt[h2 * K];
+        if (o1 != INT32_MIN && o1 >= tt - hi && o2 >= tt - lo) flags |= kMetaRingOverflow;
+        bt[h * K] = tt;
+        bl[h * K] = LL;
+        head[k] = h2;
+    }
+
+    __device__ __forceinline__ bool query(int k, int32_t tt, int32_t lo, int32_t hi, int32_t &LL) const {
+        const int32_t *bt = rt + (k * R) * K;
+        const int32_t *bl = rl + (k * R) * K;
+        const int32_t elig = tt - lo;
+        int idx = head[k];
+        for (int i = 0; i < R; ++i) {
+            idx = (idx == 0) ? R - 1 : idx - 1;
+            const int32_t tp = bt[idx * K];
+            if (tp < elig) {
+                LL = bl[idx * K];
+                return tp >= tt - hi;
+            }
+        }
+        return false;
+    }
+};
+
+// Per-lane machine: the episode, its rings, and Algorithm 1 per entry class.
+template <int NMAX, int RR>
+struct Machine {
     int N;
-    uint32_t E[NMAX];
-    int32_t lo[NMAX];
-    int32_t hi[NMAX];
-    int head[NMAX];
+    uint32_t E[NMAX];        // 0xFFFFFFFF beyond N (and for idle lanes)
+    int32_t lo[NMAX - 1];
+    int32_t hi[NMAX - 1];
+    Rings<NMAX, RR> rings;
     int32_t cthr[kClasses];
     int32_t cprev[kClasses];
     uint32_t ccnt[kClasses];
     int ncls;
+    uint32_t live;           // classes not merged into class 0 (bit 0 = class 0)
     int32_t M;
     int open;
     int flags;
-};
 
-// Ring of node k for this lane: entry r at base[(k * R + r) * K].
-template <int NMAX>
-__device__ __forceinline__ void ring_push(Lane<NMAX> &st, int k, int32_t *rt, int32_t *rl, int R,
-                                          int K, int32_t t, int32_t L) {
-    const int h = st.head[k];
-    int32_t *bt = rt + (k * R) * K;
-    int32_t *bl = rl + (k * R) * K;
-    const int h2 = (h + 1 == R) ? 0 : h + 1;
-    const int32_t old = bt[h * K];
-    const int32_t old2 = bt[h2 * K];
-    // Dropping `old` is safe if it is empty, expired for every query at
-    // time >= t, or if the next-older entry is already past its lower bound.
-    if (old != INT32_MIN && old >= t - st.hi[k] && old2 >= t - st.lo[k]) st.flags |= kMetaRingOverflow;
-    bt[h * K] = t;
-    bl[h * K] = L;
-    st.head[k] = h2;
-}
-
-// Newest entry of node k past its lower bound at time t; valid if it is
-// within the upper bound.  Returns its latest start through L.
-template <int NMAX>
-__device__ __forceinline__ bool ring_query(const Lane<NMAX> &st, int k, const int32_t *rt,
-                                           const int32_t *rl, int R, int K, int32_t t, int32_t &L) {
-    const int32_t *bt = rt + (k * R) * K;
-    const int32_t *bl = rl + (k * R) * K;
-    const int32_t elig = t - st.lo[k];
-    const int32_t expire = t - st.hi[k];
-    int idx = st.head[k];
-    for (int i = 0; i < R; ++i) {
-        idx = (idx == 0) ? R - 1 : idx - 1;
-        const int32_t tp = bt[idx * K];
-        if (tp < elig) {
-            if (tp >= expire) {
-                L = bl[idx * K];
-                return true;
+    // Algorithm 1 step for an end event at time t whose latest start is Lq,
+    // for every entry class of this (episode, segment) machine; a new class
+    // is opened while no occurrence has started inside the segment yet.
+    // A class whose last selection equals class 0's has the same future: it
+    // is merged (its count kept as an offset from class 0's), so the steady
+    // state is a single comparison.
+    __device__ __forceinline__ void greedy_end(int32_t t, int32_t Lq, int32_t Tp) {
+        if (!open && live == 1u) {
+            if (Lq > cprev[0]) {
+                ccnt[0] += 1;
+                cprev[0] = t;
             }
-            return false;
+            return;
         }
-    }
-    return false;
-}
-
-// Algorithm 1 step for an end event at time t whose latest start is Lq, for
-// every entry class of this (episode, segment) machine.
-template <int NMAX>
-__device__ __forceinline__ void greedy_end(Lane<NMAX> &st, int32_t t, int32_t Lq, int32_t Tp) {
 #pragma unroll
-    for (int j = 0; j < kClasses; ++j)
-        if (j < st.ncls && Lq > st.cprev[j]) {
-            st.ccnt[j] += 1;
-            st.cprev[j] = t;
-        }
-    if (st.open && Lq > st.M) {
-        if (st.ncls < kClasses) {
+        for (int j = 0; j < kClasses; ++j)
+            if (((live >> j) & 1u) && Lq > cprev[j]) {
+                ccnt[j] += 1;
+                cprev[j] = t;
+            }
+        if (open && Lq > M) {
+            if (ncls < kClasses) {
 #pragma unroll
-            for (int j = 0; j < kClasses; ++j)
-                if (j == st.ncls) {
-                    st.cthr[j] = Lq;
-                    st.ccnt[j] = 1;
-                    st.cprev[j] = t;
-                }
-            st.ncls += 1;
-        } else {
-            st.flags |= kMetaClassOverflow;
-        }
-        st.M = Lq;
-        if (Lq >= Tp) st.open = 0;
-    }
-}
-
-// One event (type ety, time et) offered to this lane's episode.  Nodes are
-// visited last to first; an entry pushed at time et can never serve a query
-// at the same time (0 <= lo), so the order only mirrors the serial algorithm.
-template <int NMAX>
-__device__ __forceinline__ void lane_step(Lane<NMAX> &st, uint32_t ety, int32_t et, bool in_seg,
-                                          int32_t Tp, int32_t *rt, int32_t *rl, int R, int K) {
-#pragma unroll
-    for (int k = NMAX - 1; k >= 0; --k) {
-        if (k < st.N && st.E[k] == ety) {
-            if (k == 0) {
-                ring_push(st, 0, rt, rl, R, K, et, et);
+                for (int j = 0; j < kClasses; ++j)
+                    if (j == ncls) {
+                        cthr[j] = Lq;
+                        ccnt[j] = 1;
+                        cprev[j] = t;
+                    }
+                live |= 1u << ncls;
+                ncls += 1;
             } else {
+                flags |= kMetaClassOverflow;
+            }
+            M = Lq;
+            if (Lq >= Tp) open = 0;
+        }
+#pragma unroll
+        for (int j = 1; j < kClasses; ++j)
+            if (((live >> j) & 1u) && cprev[j] == cprev[0]) {
+                ccnt[j] -= ccnt[0];  // offset from class 0 from here on
+                live &= ~(1u << j);
+            }
+    }
+
+    // Final per-class (count, last selection): merged classes follow class 0.
+    __device__ __forceinline__ void finish() {
+#pragma unroll
+        for (int j = 1; j < kClasses; ++j)
+            if (j < ncls && !((live >> j) & 1u)) {
+                ccnt[j] += ccnt[0];
+                cprev[j] = cprev[0];
+            }
+    }
+
+    // One event offered to this lane's episode.  Nodes are visited last to
+    // first; an entry pushed at time et never serves a query at the same time
+    // (0 <= lo), so the order only mirrors the serial algorithm.
+    __device__ __forceinline__ void step(uint32_t ety, int32_t et, bool in_seg, int32_t Tp) {
+#pragma unroll
+        for (int k = NMAX - 1; k >= 1; --k) {
+            if (E[k] == ety) {
                 int32_t Lq;
-                if (ring_query(st, k - 1, rt, rl, R, K, et, Lq)) {
-                    if (k == st.N - 1) {
-                        if (in_seg) greedy_end(st, et, Lq, Tp);
+                if (rings.query(k - 1, et, lo[k - 1], hi[k - 1], Lq)) {
+                    if (k == N - 1) {
+                        if (in_seg) greedy_end(et, Lq, Tp);
                     } else {
-                        ring_push(st, k, rt, rl, R, K, et, Lq);
+                        rings.push(k, et, Lq, lo[k], hi[k], flags);
                     }
                 }
             }
         }
+        if (E[0] == ety) rings.push(0, et, et, lo[0], hi[0], flags);
     }
-}
+};
 
 __device__ __forceinline__ int64_t lower_bound_time(const int32_t *tm, int64_t lo, int64_t hi, int64_t v) {
     while (lo < hi) {
@@ -204,6 +293,10 @@ __device__ __forceinline__ int64_t lower_bound_time(const int32_t *tm, int64_t l
     return lo;
 }
 
+__device__ __forceinline__ int clampi(int64_t v, int lo, int hi) {
+    return v < lo ? lo : (v > hi ? hi : (int)v);
+}
+
 // ---------------------------------------------------------------------------
 // The tiled kernel.  One CTA = one work item: up to K episodes (one per lane
 // of W = K/32 compute warps) of one recording, over one segment.  A producer
@@ -211,10 +304,11 @@ __device__ __forceinline__ int64_t lower_bound_time(const int32_t *tm, int64_t l
 // stages with 1-D bulk copies; every compute warp reads each stage, filters
 // events by its warp's union of episode types (bitmap + ballot), and offers
 // the surviving events, in order, to its 32 machines.
-template <int NMAX>
-__global__ void __launch_bounds__(kMaxWarps * 32 + 32) k_count_tiled(TiledArgs a) {
+template <int NMAX, int RR>
+__global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ? 3 : NMAX <= 4 ? 2 : 1))
+    k_count_tiled(TiledArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int K = a.K, T = a.T, R = a.R;
+    const int K = a.K, T = a.T;
     const int W = K >> 5;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -227,7 +321,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32) k_count_tiled(TiledArgs a
     int32_t *s_time = reinterpret_cast<int32_t *>(s_type + kStages * T);
     uint32_t *s_bm = reinterpret_cast<uint32_t *>(s_time + kStages * T);
     int32_t *s_rt = reinterpret_cast<int32_t *>(s_bm + W * kBitmapWords);
-    int32_t *s_rl = s_rt + (NMAX - 1) * R * K;
+    int32_t *s_rl = s_rt + (RR == 0 ? (NMAX - 1) * a.R * K : 0);
 
     __shared__ unsigned long long s_maxsh;
     __shared__ long long s_range[4];  // i_begin, seg_b, seg_e, Tp
@@ -235,18 +329,19 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32) k_count_tiled(TiledArgs a
 
     const bool compute = warp < W;
     const bool active = compute && tid < item.nslots;
-    Lane<NMAX> st;
+    Machine<NMAX, RR> st;
     st.N = 0;
     st.ncls = 0;
+    st.live = 0;
     st.M = INT32_MIN;
     st.open = 1;
     st.flags = 0;
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k) {
-        st.E[k] = 0xFFFFFFFFu;
+    for (int k = 0; k < NMAX; ++k) st.E[k] = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < NMAX - 1; ++k) {
         st.lo[k] = 0;
         st.hi[k] = 0;
-        st.head[k] = 0;
     }
 #pragma unroll
     for (int j = 0; j < kClasses; ++j) {
@@ -255,14 +350,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32) k_count_tiled(TiledArgs a
         st.ccnt[j] = 0;
     }
     int64_t sumhi = 0;
-    int slot = 0, cand = 0;
+    int slot = 0;
     if (tid == 0) {
         s_maxsh = 0;
         s_abort = 0;
     }
     if (active) {
         slot = item.slot0 + tid;
-        cand = a.slot2cand[slot];
+        const int cand = a.slot2cand[slot];
         const int64_t o = a.offs[cand];
         const int N = (int)(a.offs[cand + 1] - o);
         const int64_t eo = o - cand;
@@ -278,9 +373,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32) k_count_tiled(TiledArgs a
         }
     }
     if (compute) {
+        st.rings.init(s_rt + tid, s_rl + tid, a.R, K);
         for (int i = lane; i < kBitmapWords; i += 32) s_bm[warp * kBitmapWords + i] = 0;
-        for (int k = 0; k < NMAX - 1; ++k)
-            for (int r = 0; r < R; ++r) s_rt[(k * R + r) * K + tid] = INT32_MIN;
     }
     __syncthreads();
     if (active) {
@@ -349,9 +443,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32) k_count_tiled(TiledArgs a
         }
         __syncwarp();
     } else {
-        int32_t *rt = s_rt + tid;
-        int32_t *rl = s_rl + tid;
         const uint32_t *bm = s_bm + warp * kBitmapWords;
+        // the warp's filter in registers when every type is below 128
+        const uint32_t w0 = bm[0], w1 = bm[1], w2 = bm[2], w3 = bm[3];
+        const bool small = a.small_alpha != 0;
         for (int64_t k = 0; k < ntiles; ++k) {
             const int s = (int)(k % kStages);
             if (!dev::mbar_wait(&full[s], (uint32_t)((k / kStages) & 1), kMaxPoll, kMaxNs)) {
@@ -360,27 +455,36 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32) k_count_tiled(TiledArgs a
                 break;
             }
             const int64_t gbase = i_al + k * T;
+            const int lo_c = clampi(i_begin - gbase, 0, T);
+            const int hi_c = clampi(seg_e - gbase, 0, T);
+            const int sg_c = clampi(seg_b - gbase, 0, T);
             const uint16_t *tt = s_type + s * T;
             const int32_t *tm = s_time + s * T;
-            for (int c = 0; c < T; c += 32) {
-                const int64_t gi = gbase + c + lane;
-                const uint32_t ty = tt[c + lane];
-                const uint32_t word = bm[(ty >> 5) & (kBitmapWords - 1)];
-                const bool rel = (gi >= i_begin) && (gi < seg_e) && ((word >> (ty & 31)) & 1u);
+            for (int c = lo_c & ~31; c < hi_c; c += 32) {
+                const int idx = c + lane;
+                const uint32_t ty = tt[idx];
+                uint32_t word;
+                if (small) {
+                    const uint32_t q = ty >> 5;
+                    word = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : q == 3 ? w3 : 0u;
+                } else {
+                    word = bm[(ty >> 5) & (kBitmapWords - 1)];
+                }
+                const bool rel = ((word >> (ty & 31)) & 1u) && idx >= lo_c && idx < hi_c;
                 uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
                 while (m) {
                     const int b = __ffs(m) - 1;
                     m &= m - 1;
                     const uint32_t ety = __shfl_sync(0xFFFFFFFFu, ty, b);
                     const int32_t et = tm[c + b];
-                    const bool in_seg = (gbase + c + b) >= seg_b;
-                    if (active) lane_step<NMAX>(st, ety, et, in_seg, Tp, rt, rl, R, K);
+                    st.step(ety, et, (c + b) >= sg_c, Tp);
                 }
             }
             __syncwarp();
             if (lane == 0) dev::mbar_arrive(&empty[s]);
         }
         if (active) {
+            st.finish();
             int32_t *r = a.rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P + item.p) * kRecWords;
             r[0] = st.ncls | st.flags;
 #pragma unroll
@@ -609,7 +713,7 @@ __global__ void k_prep(PrepArgs a) {
         bucket = kBucketPlain;
     } else {
         const int nc = N <= 2 ? 0 : N <= 4 ? 1 : N <= 8 ? 2 : 3;
-        const int rc = R <= 4 ? 0 : R <= 8 ? 1 : R <= 16 ? 2 : R <= 32 ? 3 : 4;
+        const int rc = R <= 2 ? 0 : R <= 4 ? 1 : R <= 8 ? 2 : R <= 16 ? 3 : R <= 32 ? 4 : 5;
         bucket = nc * kBucketRing + rc;
     }
     a.key[i] = bucket * a.n_recs + rec;
@@ -762,63 +866,51 @@ __global__ void k_segments(const int32_t *__restrict__ tm, int64_t n, int P, int
 
 // ---------------------------------------------------------------------------
 // Host driver.
-struct RecHost {
-    fem_stream *s;
-};
-
-template <int NMAX>
-static size_t tiled_smem(int K, int R, int T) {
-    return 128 + (size_t)kStages * T * 6 + (size_t)(K / 32) * kBitmapWords * 4 +
-           (size_t)2 * (NMAX - 1) * R * K * 4;
+// Register-ring capacity compiled for (nclass, R); 0 = shared-memory rings.
+static int reg_ring_for(int nclass, int R) {
+    const int cap = max_reg_ring(nclass);
+    for (int r = 2; r <= cap; r *= 2)
+        if (R <= r) return r;
+    return 0;
 }
 
 static size_t tiled_smem_rt(int nclass, int K, int R, int T) {
-    switch (nclass) {
-        case 0: return tiled_smem<2>(K, R, T);
-        case 1: return tiled_smem<4>(K, R, T);
-        case 2: return tiled_smem<8>(K, R, T);
-        default: return tiled_smem<16>(K, R, T);
-    }
+    const int nmax = nmax_of_class(nclass);
+    const int rr = reg_ring_for(nclass, R);
+    return 128 + (size_t)kStages * T * 6 + (size_t)(K / 32) * kBitmapWords * 4 +
+           (rr ? 0 : (size_t)2 * (nmax - 1) * R * K * 4);
+}
+
+typedef void (*TiledFn)(TiledArgs);
+
+static TiledFn tiled_fn(int nclass, int rr) {
+#define FEM_TF(NM, R_) \
+    if (nmax_of_class(nclass) == NM && rr == R_) return k_count_tiled<NM, R_>;
+    FEM_TF(2, 2) FEM_TF(2, 4) FEM_TF(2, 8) FEM_TF(2, 0)
+    FEM_TF(4, 2) FEM_TF(4, 4) FEM_TF(4, 0)
+    FEM_TF(8, 2) FEM_TF(8, 0)
+    FEM_TF(16, 0)
+#undef FEM_TF
+    return nullptr;
 }
 
 static int launch_tiled(fem_ctx *ctx, int nclass, int n_items, int K, int R, int T, const TiledArgs &a) {
     const size_t sm = tiled_smem_rt(nclass, K, R, T);
-    const dim3 grid(n_items), block(K + 32);
-    cudaError_t e = cudaSuccess;
-    switch (nclass) {
-        case 0:
-            e = cudaFuncSetAttribute(k_count_tiled<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e == cudaSuccess) k_count_tiled<2><<<grid, block, sm, ctx->stream>>>(a);
-            break;
-        case 1:
-            e = cudaFuncSetAttribute(k_count_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e == cudaSuccess) k_count_tiled<4><<<grid, block, sm, ctx->stream>>>(a);
-            break;
-        case 2:
-            e = cudaFuncSetAttribute(k_count_tiled<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e == cudaSuccess) k_count_tiled<8><<<grid, block, sm, ctx->stream>>>(a);
-            break;
-        default:
-            e = cudaFuncSetAttribute(k_count_tiled<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e == cudaSuccess) k_count_tiled<16><<<grid, block, sm, ctx->stream>>>(a);
-            break;
-    }
-    if (e != cudaSuccess) return FEM_ERR_CUDA;
+    TiledFn f = tiled_fn(nclass, reg_ring_for(nclass, R));
+    if (!f) return FEM_ERR_CUDA;
+    if (cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return FEM_ERR_CUDA;
+    f<<<dim3(n_items), dim3(K + 32), sm, ctx->stream>>>(a);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 
-static int occupancy_tiled(int nclass, int K, size_t sm) {
+static int occupancy_tiled(int nclass, int K, int R, size_t sm) {
     int blocks = 0;
-    switch (nclass) {
-        case 0: cudaFuncSetAttribute(k_count_tiled<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_count_tiled<2>, K + 32, sm); break;
-        case 1: cudaFuncSetAttribute(k_count_tiled<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_count_tiled<4>, K + 32, sm); break;
-        case 2: cudaFuncSetAttribute(k_count_tiled<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_count_tiled<8>, K + 32, sm); break;
-        default: cudaFuncSetAttribute(k_count_tiled<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_count_tiled<16>, K + 32, sm); break;
+    TiledFn f = tiled_fn(nclass, reg_ring_for(nclass, R));
+    if (f) {
+        cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, f, K + 32, sm);
     }
     cudaGetLastError();
     return std::max(blocks, 1);
@@ -946,6 +1038,9 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     FEM_CUDA_TRY(cudaMemcpyAsync(&relv, mb + o_rel, 8, cudaMemcpyDeviceToHost, ctx->stream));
     FEM_TRY(sync_status(ctx));
     key_off[n_keys] = (int32_t)n_work;
+    if (force_segments == 0)
+        for (int k = 0; k < n_keys; ++k)
+            cc.stats.counted_episode_events += (double)(key_off[k + 1] - key_off[k]) * (double)cc.recs[k % n_recs]->n;
     cc.stats.relevant_events += (double)relv;
 
     // --- launches per bucket
@@ -985,7 +1080,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         pl.slot_begin = sb;
         pl.n_slots = se - sb;
         const size_t sm = tiled_smem_rt(pl.nclass, K, pl.R, T);
-        const int occ = occupancy_tiled(pl.nclass, K, sm);
+        const int occ = occupancy_tiled(pl.nclass, K, pl.R, sm);
         // segments: aim for ~4 CTAs per resident slot across the bucket
         const int64_t desired = (int64_t)4 * ctx->n_sm * occ;
         int64_t blocks_total = 0;
@@ -1077,6 +1172,9 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         ta.K = pl.K;
         ta.T = T;
         ta.relaxed = cc.mode == 2;
+        ta.small_alpha = 1;
+        for (auto *rs : cc.recs)
+            if (rs->n_types > 128) ta.small_alpha = 0;
         ta.rec = static_cast<int32_t *>(p_rec);
         ta.status = ctx->d_status;
         FEM_TRY(launch_tiled(ctx, pl.nclass, (int)pl.items.size(), pl.K, pl.R, T, ta));
@@ -1226,19 +1324,7 @@ static int count_entry(fem_ctx *ctx, const fem_stream *const *recs, int n_recs, 
     FEM_TRY(run_count(cc, nullptr, c->n_cand, 0));
     FEM_TRY(copy_out(ctx, counts, cc.counts, 4 * c->n_cand, out_is_device));
     FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    // statistics: episode-events = sum over candidates of its recording's n
-    double ee = 0;
-    if (n_recs == 1) {
-        ee = (double)c->n_cand * (double)recs[0]->n;
-    } else {
-        std::vector<uint32_t> rid(c->n_cand);
-        if (c->ptr_is_device)
-            cudaMemcpy(rid.data(), rec_id, 4 * c->n_cand, cudaMemcpyDeviceToHost);
-        else
-            std::memcpy(rid.data(), rec_id, 4 * c->n_cand);
-        for (auto r : rid) ee += (double)recs[r]->n;
-    }
-    cc.stats.episode_events = ee;
+    cc.stats.episode_events = cc.stats.counted_episode_events;
     cc.stats.count_kernel_ms = cc.count_ms;
     cc.stats.total_ms = (now_s() - t0) * 1e3;
     ctx->last = cc.stats;
@@ -1248,7 +1334,8 @@ static int count_entry(fem_ctx *ctx, const fem_stream *const *recs, int n_recs, 
 // Counting of device-resident candidates (used by the level-wise miner).
 int count_device(fem_ctx *ctx, const std::vector<fem_stream *> &recs, int64_t n_cand, const int64_t *offs,
                  const uint16_t *types, const int32_t *lo, const int32_t *hi, const uint32_t *cand_rec,
-                 const std::vector<int32_t> &lo_vals, uint32_t *counts, fem_stats *stats) {
+                 const std::vector<int32_t> &lo_vals, const int32_t *order, int64_t n_order, uint32_t *counts,
+                 fem_stats *stats) {
     CountCall cc;
     cc.ctx = ctx;
     cc.recs = recs;
@@ -1261,7 +1348,10 @@ int count_device(fem_ctx *ctx, const std::vector<fem_stream *> &recs, int64_t n_
     cc.cand_rec = cand_rec;
     cc.counts = counts;
     cc.lo_vals = lo_vals;
-    if (n_cand > 0) FEM_TRY(run_count(cc, nullptr, n_cand, 0));
+    // `order` (optional) lists every candidate once, in the order the
+    // counting kernels should hold them (lane neighbours share types).
+    const int64_t n_work = order ? n_order : n_cand;
+    if (n_work > 0) FEM_TRY(run_count(cc, order, n_work, 0));
     cc.stats.count_kernel_ms = cc.count_ms;
     *stats = cc.stats;
     return FEM_OK;

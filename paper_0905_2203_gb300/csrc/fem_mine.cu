@@ -11,9 +11,9 @@
 //
 // Candidate generation (readings of a point the paper leaves open):
 //   level 2: every ordered pair (a, b) of distinct frequent types with every
-//            bin.  They are counted in (a, b, bin) order so that the episodes
-//            a warp holds share their types (a narrow type filter), and
-//            compacted back in canonical (a, bin, b) order.
+//            bin, generated in canonical (a, bin, b) order and counted in a
+//            tiled order (a few first types x a few second types x all bins
+//            per warp) so that the episodes a warp holds share their types.
 //   level N: alpha, beta frequent (N-1)-episodes of one recording with
 //            alpha[2..] = beta[..N-2] (types and bins) give alpha + beta's last
 //            edge and node, provided that node's type is not already in alpha.
@@ -68,8 +68,8 @@ __global__ void k_level1_write(const int32_t *flags_scanned, const uint32_t *con
     }
 }
 
-// Level 2 candidates of recording r: local index i = ((ia*(F-1)) + jb)*nb + bin
-// (count order); b = jb < ia ? jb : jb + 1.
+// Level 2 candidates of recording r in canonical order: local index
+// i = ((ia * nb) + bin) * (F-1) + jb, second type b = jb < ia ? jb : jb + 1.
 __global__ void k_gen_level2(const uint16_t *ftypes, const int64_t *f_off, const int64_t *c_off, int n_recs,
                              const int32_t *bin_lo, const int32_t *bin_hi, int nb, int64_t total,
                              uint16_t *ctypes, int32_t *clo, int32_t *chi, uint32_t *crec, int64_t *coffs) {
@@ -83,9 +83,9 @@ __global__ void k_gen_level2(const uint16_t *ftypes, const int64_t *f_off, const
     const int r = lo_r;
     const int64_t i = g - c_off[r];
     const int64_t F = f_off[r + 1] - f_off[r];
-    const int64_t bin = i % nb;
-    const int64_t q = i / nb;
-    const int64_t ia = q / (F - 1), jb = q % (F - 1);
+    const int64_t jb = i % (F - 1);
+    const int64_t q = i / (F - 1);
+    const int64_t bin = q % nb, ia = q / nb;
     const int64_t ib = jb < ia ? jb : jb + 1;
     ctypes[2 * g] = ftypes[f_off[r] + ia];
     ctypes[2 * g + 1] = ftypes[f_off[r] + ib];
@@ -96,13 +96,114 @@ __global__ void k_gen_level2(const uint16_t *ftypes, const int64_t *f_off, const
     if (g == total - 1) coffs[total] = 2 * total;
 }
 
-// Canonical index -> count index for level 2 of recording r.
-__device__ __forceinline__ int64_t canon_to_count2(int64_t i, int64_t F, int nb) {
-    // canonical i = ((ia * nb) + bin) * (F-1) + jb
-    const int64_t jb = i % (F - 1);
-    const int64_t q = i / (F - 1);
-    const int64_t bin = q % nb, ia = q / nb;
-    return ((ia * (F - 1)) + jb) * nb + bin;
+// Counting order for level 2: the (first type, second type) grid is cut into
+// tiles of At x Bt pairs, each tile's pairs with all their bins adjacent, so
+// the 32 episodes of a warp span about At first types and Bt second types
+// (a narrow per-warp type filter).  flags[g] marks grid cells that are real
+// candidates (a != b, inside the grid); perm receives canonical indices.
+__device__ __forceinline__ int64_t l2_cell_canon(int64_t q, int64_t F, int nb, int At, int Bt, bool &valid) {
+    const int64_t TB = (F + Bt - 1) / Bt;
+    const int64_t per_tile = (int64_t)At * Bt * nb;
+    const int64_t tile = q / per_tile, w = q % per_tile;
+    const int64_t ta = tile / TB, tb = tile % TB;
+    const int64_t bin = w % nb, pr = w / nb;
+    const int64_t a = ta * At + pr / Bt, b = tb * Bt + pr % Bt;
+    valid = a < F && b < F && a != b;
+    return (a * nb + bin) * (F - 1) + (b < a ? b : b - 1);
+}
+
+__global__ void k_perm2_flags(const int64_t *f_off, const int64_t *g_off, int n_recs, int nb, int At, int Bt,
+                              int64_t total, int32_t *flags) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int lo_r = 0, hi_r = n_recs;
+    while (hi_r - lo_r > 1) {
+        const int mid = (lo_r + hi_r) >> 1;
+        if (g_off[mid] <= g) lo_r = mid; else hi_r = mid;
+    }
+    const int64_t F = f_off[lo_r + 1] - f_off[lo_r];
+    bool valid;
+    l2_cell_canon(g - g_off[lo_r], F, nb, At, Bt, valid);
+    flags[g] = valid ? 1 : 0;
+}
+
+__global__ void k_perm2_write(const int32_t *pos, const int64_t *f_off, const int64_t *g_off, const int64_t *c_off,
+                              int n_recs, int nb, int At, int Bt, int64_t total, int32_t *perm) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int lo_r = 0, hi_r = n_recs;
+    while (hi_r - lo_r > 1) {
+        const int mid = (lo_r + hi_r) >> 1;
+        if (g_off[mid] <= g) lo_r = mid; else hi_r = mid;
+    }
+    const int64_t F = f_off[lo_r + 1] - f_off[lo_r];
+    bool valid;
+    const int64_t canon = l2_cell_canon(g - g_off[lo_r], F, nb, At, Bt, valid);
+    if (valid) perm[pos[g]] = (int32_t)(c_off[lo_r] + canon);
+}
+
+// Upper-bound pre-pass for level 2 (anti-monotonicity, section "Temporal
+// Data Mining"): non-overlapped occurrences of a -(lo,hi]-> b end at distinct
+// b-events, each with an a-event inside (t - hi, ... t - lo] before it, so
+//     count(a, b, bin) <= UB(a, b, bin) = #{ b-events with an a-event in the
+//                                            bin's window }.
+// One pass over the stream: every event j looks back over the widest bin
+// window and marks, per bin, which types occur (a per-thread bitset in shared
+// memory dedupes repeated types), then adds one to UB(a, type_j, bin) for
+// every marked (a, bin).  The table is per recording: ub[rec][a][b][bin].
+__global__ void k_pair_ub(const uint16_t *__restrict__ ty, const int32_t *__restrict__ tm, int64_t n,
+                          uint32_t n_types, const int32_t *__restrict__ blo, const int32_t *__restrict__ bhi, int nb,
+                          int32_t hi_max, int words, uint32_t *__restrict__ ub) {
+    extern __shared__ uint32_t bits[];
+    uint32_t *my = bits + threadIdx.x * words;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        for (int w = 0; w < words; ++w) my[w] = 0;
+        const int32_t t = tm[j];
+        const uint32_t b = ty[j];
+        const int64_t lim = (int64_t)t - hi_max;
+        for (int64_t i = j - 1; i >= 0 && (int64_t)tm[i] >= lim; --i) {
+            const int32_t d = t - tm[i];
+            if (d <= 0) continue;
+            const uint32_t a = ty[i];
+            if (a == b) continue;
+            for (int k = 0; k < nb; ++k) {
+                if (blo[k] < d && d <= bhi[k]) {
+                    const uint32_t bit = a * (uint32_t)nb + (uint32_t)k;
+                    const uint32_t m = 1u << (bit & 31);
+                    if (!(my[bit >> 5] & m)) {
+                        my[bit >> 5] |= m;
+                        atomicAdd(&ub[((size_t)a * n_types + b) * nb + k], 1u);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Keeps, in counting order, the level-2 candidates whose bound exceeds the
+// threshold; pruned candidates get count 0 (they can never pass).
+__global__ void k_prune2_flags(const int32_t *order, int64_t C, const uint16_t *ct, const int32_t *clo,
+                               const int32_t *chi, const uint32_t *crec, const uint32_t *const *ub,
+                               const uint32_t *n_types, const int32_t *blo, const int32_t *bhi, int nb,
+                               const uint32_t *thr, int32_t *flags, uint32_t *counts) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const int64_t c = order[i];
+    const uint32_t r = crec[c];
+    int k = 0;
+    while (k < nb && !(blo[k] == clo[c] && bhi[k] == chi[c])) ++k;
+    const uint32_t a = ct[2 * c], b = ct[2 * c + 1], nt = n_types[r];
+    const uint32_t u = ub[r][((size_t)a * nt + b) * nb + k];
+    const bool keep = u > thr[r];
+    flags[i] = keep ? 1 : 0;
+    if (!keep) counts[c] = 0;
+}
+
+__global__ void k_prune2_write(const int32_t *pos, const int32_t *flags_copy, const int32_t *order, int64_t C,
+                               int32_t *kept) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    if (flags_copy[i]) kept[pos[i]] = order[i];
 }
 
 // Level N >= 3 join, CountScanWrite style: count partners per alpha, scan,
@@ -158,50 +259,28 @@ __global__ void k_join_write(const uint16_t *ft, const int32_t *fl, const int32_
 }
 
 // Threshold: flags in canonical order (count > threshold, strict).
-__global__ void k_thr_flags(const uint32_t *counts, const uint32_t *crec, const int64_t *c_off, int n_recs,
-                            const int64_t *f_prev_off, int level, int nb, const uint32_t *thr, int64_t total,
+__global__ void k_thr_flags(const uint32_t *counts, const uint32_t *crec, const uint32_t *thr, int64_t total,
                             int32_t *flags) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= total) return;
-    int64_t ci = i;
-    if (level == 2) {
-        int lo_r = 0, hi_r = n_recs;
-        while (hi_r - lo_r > 1) {
-            const int mid = (lo_r + hi_r) >> 1;
-            if (c_off[mid] <= i) lo_r = mid; else hi_r = mid;
-        }
-        const int64_t F = f_prev_off[lo_r + 1] - f_prev_off[lo_r];
-        ci = c_off[lo_r] + canon_to_count2(i - c_off[lo_r], F, nb);
-    }
-    flags[i] = counts[ci] > thr[crec[ci]] ? 1 : 0;
+    flags[i] = counts[i] > thr[crec[i]] ? 1 : 0;
 }
 
 __global__ void k_thr_write(const int32_t *pos, const uint32_t *counts, const uint16_t *ct, const int32_t *cl,
-                            const int32_t *ch, const uint32_t *crec, const int64_t *c_off, int n_recs,
-                            const int64_t *f_prev_off, int level, int nb, const uint32_t *thr, int N, int64_t total,
+                            const int32_t *ch, const uint32_t *crec, const uint32_t *thr, int N, int64_t total,
                             uint16_t *ft, int32_t *fl, int32_t *fh, uint32_t *frec, uint32_t *fcnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= total) return;
-    int64_t ci = i;
-    if (level == 2) {
-        int lo_r = 0, hi_r = n_recs;
-        while (hi_r - lo_r > 1) {
-            const int mid = (lo_r + hi_r) >> 1;
-            if (c_off[mid] <= i) lo_r = mid; else hi_r = mid;
-        }
-        const int64_t F = f_prev_off[lo_r + 1] - f_prev_off[lo_r];
-        ci = c_off[lo_r] + canon_to_count2(i - c_off[lo_r], F, nb);
-    }
-    const uint32_t r = crec[ci];
-    if (!(counts[ci] > thr[r])) return;
+    const uint32_t r = crec[i];
+    if (!(counts[i] > thr[r])) return;
     const int64_t o = pos[i];
-    for (int k = 0; k < N; ++k) ft[o * N + k] = ct[ci * N + k];
+    for (int k = 0; k < N; ++k) ft[o * N + k] = ct[i * N + k];
     for (int k = 0; k < N - 1; ++k) {
-        fl[o * (N - 1) + k] = cl[ci * (N - 1) + k];
-        fh[o * (N - 1) + k] = ch[ci * (N - 1) + k];
+        fl[o * (N - 1) + k] = cl[i * (N - 1) + k];
+        fh[o * (N - 1) + k] = ch[i * (N - 1) + k];
     }
     frec[o] = r;
-    fcnt[o] = counts[ci];
+    fcnt[o] = counts[i];
 }
 
 // Per-recording offsets of a rec-sorted array.
@@ -219,7 +298,8 @@ __global__ void k_rec_offsets(const uint32_t *rec, int64_t n, int n_recs, int64_
 // Counting entry shared with fem_count.cu (mode 0, device candidate arrays).
 int count_device(fem_ctx *ctx, const std::vector<fem_stream *> &recs, int64_t n_cand, const int64_t *offs,
                  const uint16_t *types, const int32_t *lo, const int32_t *hi, const uint32_t *cand_rec,
-                 const std::vector<int32_t> &lo_vals, uint32_t *counts, fem_stats *stats);
+                 const std::vector<int32_t> &lo_vals, const int32_t *order, int64_t n_order, uint32_t *counts,
+                 fem_stats *stats);
 
 namespace {
 
@@ -358,6 +438,7 @@ int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::ve
         cand.N = N;
         int64_t *d_coffs = nullptr;
         int64_t *d_coff_rec = nullptr;
+        int32_t *d_order = nullptr;  // counting order (level 2) or null
         FEM_TRY(pool.get(&d_coff_rec, n_recs + 1));
         if (N == 2) {
             C = c_off[n_recs];
@@ -372,6 +453,29 @@ int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::ve
                                                                    d_bhi, nb, C, cand.types, cand.lo, cand.hi,
                                                                    cand.rec, d_coffs);
             S.kernel_launches++;
+            // counting order: tiles of At x Bt type pairs with all bins
+            const int pairs = std::max(1, 32 / std::max(1, nb));
+            const int At = pairs >= 32 ? 8 : pairs >= 8 ? 4 : pairs >= 2 ? 2 : 1;
+            const int Bt = std::max(1, pairs / At);
+            std::vector<int64_t> g_off(n_recs + 1, 0);
+            for (int r = 0; r < n_recs; ++r) {
+                const int64_t F = prev.h_off[r + 1] - prev.h_off[r];
+                const int64_t cells = (F >= 2) ? ((F + At - 1) / At) * ((F + Bt - 1) / Bt) * (int64_t)At * Bt * nb : 0;
+                g_off[r + 1] = g_off[r] + cells;
+            }
+            const int64_t G = g_off[n_recs];
+            int64_t *d_goff;
+            int32_t *d_gfl, *d_gtmp;
+            FEM_TRY(pool.get(&d_goff, n_recs + 1));
+            FEM_TRY(pool.get(&d_gfl, G + 1));
+            FEM_TRY(pool.get(&d_gtmp, G / 1024 + 2));
+            FEM_TRY(pool.get(&d_order, C));
+            FEM_CUDA_TRY(cudaMemcpyAsync(d_goff, g_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+            k_perm2_flags<<<(unsigned)((G + B - 1) / B), B, 0, st>>>(prev.off, d_goff, n_recs, nb, At, Bt, G, d_gfl);
+            FEM_TRY(scan_exclusive(st, d_gfl, G, d_gtmp, nullptr, &S.kernel_launches));
+            k_perm2_write<<<(unsigned)((G + B - 1) / B), B, 0, st>>>(d_gfl, prev.off, d_goff, d_coff_rec, n_recs, nb, At,
+                                                                    Bt, G, d_order);
+            S.kernel_launches += 2;
         } else {
             const int M = N - 1;
             const int64_t F = prev.n;
@@ -404,15 +508,69 @@ int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::ve
         }
         cand.n = C;
         FEM_TRY(pool.get(&cand.counts, C));
+        int64_t C_exact = C;  // candidates left for the exact count
+        if (N == 2 && ctx->tuning.prepass != -1) {
+            int32_t hi_max = 0;
+            for (int k = 0; k < nb; ++k) hi_max = std::max(hi_max, bhi[k]);
+            bool ok = nb <= 8;
+            for (int r = 0; r < n_recs && ok; ++r) ok = recs[r]->n_types <= 1024;
+            if (ok) {
+                std::vector<const uint32_t *> ubp(n_recs);
+                for (int r = 0; r < n_recs; ++r) {
+                    const uint32_t nt = recs[r]->n_types;
+                    uint32_t *u;
+                    FEM_TRY(pool.get(&u, (size_t)nt * nt * nb));
+                    FEM_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(uint32_t) * (size_t)nt * nt * nb, st));
+                    const int words = (int)((nt * (uint32_t)nb + 31) / 32);
+                    int threads = std::min(256, (int)(48 * 1024 / (4 * words)) / 32 * 32);
+                    threads = std::max(threads, 32);
+                    if (recs[r]->n > 0 && (prev.h_off[r + 1] - prev.h_off[r]) >= 2) {
+                        const int64_t blocks = std::min<int64_t>((recs[r]->n + threads - 1) / threads, 8 * ctx->n_sm);
+                        k_pair_ub<<<(unsigned)blocks, threads, (size_t)threads * words * 4, st>>>(
+                            recs[r]->d_type, recs[r]->d_time, recs[r]->n, nt, d_blo, d_bhi, nb, hi_max, words, u);
+                        S.kernel_launches++;
+                    }
+                    ubp[r] = u;
+                }
+                const uint32_t **d_ubp;
+                uint32_t *d_nt;
+                int32_t *d_pf, *d_pf2, *d_ptmp, *d_ptot, *d_kept;
+                FEM_TRY(pool.get(&d_ubp, n_recs));
+                FEM_TRY(pool.get(&d_nt, n_recs));
+                FEM_TRY(pool.get(&d_pf, C + 1));
+                FEM_TRY(pool.get(&d_pf2, C + 1));
+                FEM_TRY(pool.get(&d_ptmp, C / 1024 + 2));
+                FEM_TRY(pool.get(&d_ptot, 2));
+                FEM_TRY(pool.get(&d_kept, C));
+                std::vector<uint32_t> nth(n_recs);
+                for (int r = 0; r < n_recs; ++r) nth[r] = recs[r]->n_types;
+                FEM_CUDA_TRY(cudaMemcpyAsync(d_ubp, ubp.data(), sizeof(void *) * n_recs, cudaMemcpyHostToDevice, st));
+                FEM_CUDA_TRY(cudaMemcpyAsync(d_nt, nth.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
+                k_prune2_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_order, C, cand.types, cand.lo, cand.hi,
+                                                                         cand.rec, d_ubp, d_nt, d_blo, d_bhi, nb, d_thr,
+                                                                         d_pf, cand.counts);
+                FEM_CUDA_TRY(cudaMemcpyAsync(d_pf2, d_pf, 4 * C, cudaMemcpyDeviceToDevice, st));
+                FEM_TRY(scan_exclusive(st, d_pf, C, d_ptmp, d_ptot, &S.kernel_launches));
+                k_prune2_write<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_pf, d_pf2, d_order, C, d_kept);
+                S.kernel_launches += 2;
+                int32_t kept = 0;
+                FEM_CUDA_TRY(cudaMemcpyAsync(&kept, d_ptot, 4, cudaMemcpyDeviceToHost, st));
+                FEM_CUDA_TRY(cudaStreamSynchronize(st));
+                C_exact = kept;
+                d_order = d_kept;
+                S.candidates_pruned += C - kept;
+            }
+        }
         // ---- exact counting of every candidate of every recording
         fem_stats cs{};
-        FEM_TRY(count_device(ctx, recs, C, d_coffs, cand.types, cand.lo, cand.hi, cand.rec, lo_vals, cand.counts,
-                             &cs));
+        FEM_TRY(count_device(ctx, recs, C, d_coffs, cand.types, cand.lo, cand.hi, cand.rec, lo_vals, d_order,
+                             C_exact, cand.counts, &cs));
         S.kernel_launches += cs.kernel_launches;
         S.candidates_counted += cs.candidates_counted;
         S.candidates_pruned += cs.candidates_pruned;
         S.fallback_recounts += cs.fallback_recounts;
         S.relevant_events += cs.relevant_events;
+        S.counted_episode_events += cs.counted_episode_events;
         S.count_kernel_ms += cs.count_kernel_ms;
         for (int r = 0; r < n_recs; ++r) S.episode_events += (double)(c_off[r + 1] - c_off[r]) * (double)recs[r]->n;
         // ---- threshold + compaction in canonical order
@@ -420,8 +578,7 @@ int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::ve
         FEM_TRY(pool.get(&d_fl, C + 1));
         FEM_TRY(pool.get(&d_tmp2, C / 1024 + 2));
         FEM_TRY(pool.get(&d_tot2, 2));
-        k_thr_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(cand.counts, cand.rec, d_coff_rec, n_recs, prev.off, N,
-                                                              nb, d_thr, C, d_fl);
+        k_thr_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(cand.counts, cand.rec, d_thr, C, d_fl);
         FEM_TRY(scan_exclusive(st, d_fl, C, d_tmp2, d_tot2, &S.kernel_launches));
         int32_t Fn = 0;
         FEM_CUDA_TRY(cudaMemcpyAsync(&Fn, d_tot2, 4, cudaMemcpyDeviceToHost, st));
@@ -436,8 +593,8 @@ int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::ve
         FEM_TRY(pool.get(&next.counts, Fn));
         FEM_TRY(pool.get(&next.off, n_recs + 1));
         k_thr_write<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_fl, cand.counts, cand.types, cand.lo, cand.hi,
-                                                              cand.rec, d_coff_rec, n_recs, prev.off, N, nb, d_thr, N, C,
-                                                              next.types, next.lo, next.hi, next.rec, next.counts);
+                                                              cand.rec, d_thr, N, C, next.types, next.lo, next.hi,
+                                                              next.rec, next.counts);
         k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(next.rec, next.n, n_recs, next.off);
         S.kernel_launches += 3;
         next.h_off.resize(n_recs + 1);

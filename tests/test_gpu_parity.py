@@ -281,3 +281,56 @@ def test_mine_levelwise_c2_short(fb, ctx):
 def test_mine_levelwise_multi_recording(fb, ctx):
     recs = synth.c4_recordings(0xFE0004, n_rec=5, n_lo=5e3, n_hi=4e4)
     _mine_compare(fb, ctx, [s for s, _ in recs], synth.BINS_4, [cfg["threshold"] for _, cfg in recs], 5)
+
+
+def test_large_alphabet_and_hashed_filter(fb, ctx):
+    """Alphabets above 128 types (shared-memory warp filter) and above 4096
+    (hashed filter bits): counts unchanged."""
+    for n_types in (300, 5000):
+        r = synth.Rng(n_types, 4)
+        ty, tm = synth.tiny_random_stream(n_types, 40000, n_types, 60000)
+        # concentrate on a few types so counts are non-trivial
+        hot = r.integers(0, n_types - 1, 12)
+        ty = np.where(r.uniform(ty.size) < 0.6, hot[r.integers(0, 11, ty.size)], ty).astype(np.uint16)
+        key = np.unique(tm.astype(np.int64) * 65536 + ty)
+        tm = (key // 65536).astype(np.int32)
+        ty = (key % 65536).astype(np.uint16)
+        nc = 1500
+        sizes = r.integers(2, 5, nc)
+        offs = np.zeros(nc + 1, np.int64)
+        offs[1:] = np.cumsum(sizes)
+        ct = hot[r.integers(0, 11, int(offs[-1]))].astype(np.uint16)
+        ne = int(offs[-1]) - nc
+        lo = r.integers(0, 20, ne).astype(np.int32)
+        hi = (lo + r.integers(1, 60, ne)).astype(np.int32)
+        st = ctx.load_stream(ty, tm, n_types)
+        got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+        want = oracle_counts(ty, tm, offs, ct, lo, hi)
+        assert np.array_equal(got, want), n_types
+        assert want.max() > 0
+        st.free()
+
+
+def test_prepass_prunes_but_never_changes_results(fb, ctx):
+    """The level-2 upper-bound pre-pass drops candidates (C2-like stream) and
+    the frequent sets are identical with it disabled."""
+    s, cfg = synth.c2_mid(duration_s=40.0)
+    thr = int(0.0025 * s.n)
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    res = ctx.mine_levelwise([st], cfg["bins"], [thr], 4)
+    stats_on = res.stats()
+    on = [res.level(0, N) for N in range(1, 5)]
+    res.free()
+    ctx.set_tuning(prepass=-1)
+    try:
+        res = ctx.mine_levelwise([st], cfg["bins"], [thr], 4)
+        stats_off = res.stats()
+        off = [res.level(0, N) for N in range(1, 5)]
+        res.free()
+    finally:
+        ctx.reset_tuning()
+    assert on == off
+    assert stats_on["candidates_pruned"] > 0 and stats_off["candidates_pruned"] == 0
+    assert stats_on["episode_events"] == stats_off["episode_events"]
+    assert stats_on["counted_episode_events"] < stats_off["counted_episode_events"]
+    st.free()
