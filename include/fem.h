@@ -176,6 +176,34 @@ int fem_count_episodes_plain(fem_ctx *ctx, const fem_stream *s, const fem_cands 
 int fem_upper_bound(fem_ctx *ctx, const fem_stream *s, const fem_cands *c, uint32_t *ub,
                     int out_is_device);
 
+/* Counting without any memory allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * when they ask for a count -- code running inside an allocator or a memory
+ * pool callback, processes whose device memory is entirely reserved by
+ * another framework, or latency-bound loops where a cudaMalloc (which can
+ * synchronise the whole device) is not allowed.  It needs no context: every
+ * pointer is a DEVICE pointer owned by the caller (stream types[n] and
+ * times[n], candidate CSR as in fem_cands, counts[n_cand] output), and the
+ * work runs on `cuda_stream` (NULL = the legacy default stream) of the
+ * current device.  The call returns after the counts are written.
+ *   Scratch: one 16 MiB array declared at file scope in the library, present
+ *   on every GPU that has loaded it until the process exits.  Its device
+ *   address is looked up on the first call made on each device, so make that
+ *   first call before any stream capture.  All calls on a device share the
+ *   array, so calls that overlap on the GPU (different host threads or
+ *   streams) race and must be serialised by the caller.
+ *   Limits: n_cand * 30 <= 4,194,296 (about 139,800 episodes); each episode's
+ *   per-node ring holds min(32, 4,194,296 / (n_cand * (largest size - 1)))
+ *   timestamps.  FEM_ERR_NOMEM if n_cand is too large or if a burst in the
+ *   stream needs a longer ring than that (use fem_count_episodes then);
+ *   FEM_ERR_INVAL on a malformed candidate.  It performs no stream
+ *   validation: the stream must already satisfy fem_load_stream's rules.
+ * The counts are those of fem_count_episodes (one thread per episode, the
+ * serial state machine, rings in the static array). */
+int fem_count_episodes_noalloc(const uint16_t *types, const int32_t *times, int64_t n, const int64_t *offs,
+                               const uint16_t *ep_types, const int32_t *lo, const int32_t *hi, int64_t n_cand,
+                               uint32_t *counts, void *cuda_stream);
+
 /* ---- level-wise mining --------------------------------------------------- */
 
 /* Level-wise frequent-episode discovery (section "Temporal Data Mining"):

@@ -88,6 +88,7 @@ _SIGS = {
     "fem_count_batch": (I32, [VP, VP, I32, ctypes.POINTER(fem_cands), VP, VP, I32]),
     "fem_count_episodes_plain": (I32, [VP, VP, ctypes.POINTER(fem_cands), VP, I32]),
     "fem_upper_bound": (I32, [VP, VP, ctypes.POINTER(fem_cands), VP, I32]),
+    "fem_count_episodes_noalloc": (I32, [VP, VP, I64, VP, VP, VP, VP, I64, VP, VP]),
     "fem_mine_levelwise": (I32, [VP, VP, I32, VP, VP, I32, VP, I32, ctypes.POINTER(VP)]),
     "fem_result_level": (I32, [VP, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(VP),
                                ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.POINTER(VP),
@@ -315,6 +316,25 @@ class Result:
             self.free()
         except Exception:
             pass
+
+
+def count_episodes_noalloc(types, times, offs, ep_types, lo, hi, out, cuda_stream=None):
+    """Counts with no memory allocation (fem_count_episodes_noalloc): every
+    argument is a CUDA torch tensor owned by the caller; `out` (uint32 or
+    int32, n_cand) receives the counts.  For callers that cannot allocate
+    device memory at call time; see include/fem.h for the scratch limits and
+    the rule that overlapping calls on one device must be serialised."""
+    ptrs = []
+    for x, dt in ((types, np.uint16), (times, np.int32), (offs, np.int64), (ep_types, np.uint16),
+                  (lo, np.int32), (hi, np.int32), (out, np.uint32)):
+        p, dev, _ = _ptr(x, dt)
+        if not dev:
+            raise ValueError("fem_count_episodes_noalloc takes device tensors only")
+        ptrs.append(p)
+    st = VP(int(cuda_stream)) if cuda_stream else None
+    check(fem_count_episodes_noalloc(ptrs[0], ptrs[1], int(len(types)), ptrs[2], ptrs[3], ptrs[4], ptrs[5],
+                                     int(len(offs) - 1), ptrs[6], st), "fem_count_episodes_noalloc")
+    return out
 
 
 def version() -> str:
