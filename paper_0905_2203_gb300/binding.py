@@ -318,6 +318,46 @@ class Result:
             pass
 
 
+class Server:
+    """Serving loop for level-wise mining jobs (fem_server_*): admission by
+    device memory, device-resident streams, continuous batching."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_jobs: int = 16):
+        h = VP()
+        check(fem_server_create(device, hbm_budget_bytes, max_jobs, ctypes.byref(h)), "fem_server_create")
+        self.h = h
+
+    def submit(self, types, times, n_types: int, bins, threshold: int, max_size: int) -> int:
+        ty = np.ascontiguousarray(types, np.uint16)
+        tm = np.ascontiguousarray(times, np.int32)
+        blo = np.ascontiguousarray([b[0] for b in bins] or [0], np.int32)
+        bhi = np.ascontiguousarray([b[1] for b in bins] or [1], np.int32)
+        jid = U64()
+        check(fem_server_submit(self.h, VP(ty.ctypes.data), VP(tm.ctypes.data), len(ty), int(n_types),
+                                VP(blo.ctypes.data), VP(bhi.ctypes.data), len(bins), int(threshold),
+                                int(max_size), ctypes.byref(jid)), "fem_server_submit")
+        return int(jid.value)
+
+    def wait(self, job_id: int, timeout_ms: int = -1):
+        """(Result, info dict) of a finished job."""
+        h = VP()
+        info = fem_job_info()
+        st = fem_server_wait(self.h, int(job_id), int(timeout_ms), ctypes.byref(h), ctypes.byref(info))
+        check(st, "fem_server_wait")
+        return Result(h, 1, 0), info.as_dict()
+
+    def close(self):
+        if self.h:
+            fem_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def count_episodes_noalloc(types, times, offs, ep_types, lo, hi, out, cuda_stream=None):
     """Counts with no memory allocation (fem_count_episodes_noalloc): every
     argument is a CUDA torch tensor owned by the caller; `out` (uint32 or

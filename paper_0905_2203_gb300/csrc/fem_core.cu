@@ -306,13 +306,12 @@ extern "C" int fem_ctx_memory(const fem_ctx *ctx, size_t *used, size_t *budget) 
 
 // ---------------------------------------------------------------------------
 // C ABI: streams.
-extern "C" int fem_load_stream(fem_ctx *ctx, const uint16_t *types, const int32_t *times, int64_t n,
-                               uint32_t n_types, int ptr_is_device, fem_stream **out) {
+int fem::load_stream_unlocked(fem_ctx *ctx, const uint16_t *types, const int32_t *times, int64_t n,
+                              uint32_t n_types, int ptr_is_device, fem_stream **out) {
     if (!ctx || !out || n < 0 || n_types < 1 || n_types > 65536) return FEM_ERR_INVAL;
     if (n > 0 && (!types || !times)) return FEM_ERR_INVAL;
     if (n > (int64_t)INT32_MAX * 4) return FEM_ERR_INVAL;
     *out = nullptr;
-    std::lock_guard<std::mutex> g(ctx->mu);
     cudaSetDevice(ctx->device);
     fem_stream *s = new (std::nothrow) fem_stream();
     if (!s) return FEM_ERR_NOMEM;
@@ -363,10 +362,22 @@ extern "C" int fem_load_stream(fem_ctx *ctx, const uint16_t *types, const int32_
     return FEM_OK;
 }
 
+extern "C" int fem_load_stream(fem_ctx *ctx, const uint16_t *types, const int32_t *times, int64_t n,
+                               uint32_t n_types, int ptr_is_device, fem_stream **out) {
+    if (!ctx) return FEM_ERR_INVAL;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    return load_stream_unlocked(ctx, types, times, n, n_types, ptr_is_device, out);
+}
+
 extern "C" void fem_stream_free(fem_stream *s) {
     if (!s) return;
+    std::lock_guard<std::mutex> g(s->ctx->mu);
+    stream_free_unlocked(s);
+}
+
+void fem::stream_free_unlocked(fem_stream *s) {
+    if (!s) return;
     fem_ctx *ctx = s->ctx;
-    std::lock_guard<std::mutex> g(ctx->mu);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     const int64_t cap = s->n + kPadEvents;

@@ -109,6 +109,27 @@ enum Slot : int {
 };
 
 double now_s();
+
+// Level-wise mining of one recording as a step-wise state machine (used by
+// the serving loop): begin() runs level 1 and prepares level 2; the current
+// candidates of many groups are counted together by mg_count_batch; advance()
+// thresholds and prepares the next level.
+struct MineGroup;
+MineGroup *mg_create(fem_ctx *ctx, fem_stream *s, const std::vector<int32_t> &blo, const std::vector<int32_t> &bhi,
+                     uint32_t thr, int max_size, fem_result *res);
+int mg_begin(MineGroup *g);
+int mg_advance(MineGroup *g);
+bool mg_done(const MineGroup *g);
+const fem_stats &mg_stats(const MineGroup *g);
+void mg_destroy(MineGroup *g);
+int mg_count_batch(fem_ctx *ctx, const std::vector<MineGroup *> &gs);
+fem_result *result_new(int n_recs, int max_size);
+void result_set_stats(fem_result *r, const fem_stats &s);
+// Stream load without taking the context lock (caller holds it or owns the
+// context exclusively).
+int load_stream_unlocked(fem_ctx *ctx, const uint16_t *types, const int32_t *times, int64_t n, uint32_t n_types,
+                         int ptr_is_device, fem_stream **out);
+void stream_free_unlocked(fem_stream *s);
 // Exclusive scan of m int32 in place; tmp holds ceil(m / 1024) entries.
 int scan_exclusive(cudaStream_t st, int32_t *data, int64_t m, int32_t *tmp, int32_t *total, int64_t *launches);
 

@@ -21,6 +21,7 @@
 //            emits candidates in canonical order.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "fem_internal.cuh"
@@ -313,12 +314,19 @@ struct DevLevel {
     std::vector<int64_t> h_off;
 };
 
+// Device allocations released together (one level's arrays, or the group's
+// constants); freed after the stream has drained.
 struct Pool {
     fem_ctx *ctx;
     std::vector<std::pair<void *, size_t>> held;
-    ~Pool() {
+    explicit Pool(fem_ctx *c) : ctx(c) {}
+    Pool(const Pool &) = delete;
+    ~Pool() { release(); }
+    void release() {
+        if (held.empty()) return;
         cudaStreamSynchronize(ctx->stream);
         for (auto &h : held) dev_free(ctx, h.first, h.second);
+        held.clear();
     }
     template <typename T>
     int get(T **p, size_t n) {
@@ -331,7 +339,8 @@ struct Pool {
     }
 };
 
-int copy_level_to_host(fem_ctx *ctx, const DevLevel &L, fem_result *res, int level) {
+int copy_level_to_host(fem_ctx *ctx, const DevLevel &L, fem_result *res, const std::vector<int> &out_rec,
+                       int level) {
     const int N = L.N;
     std::vector<uint16_t> t(L.n * N);
     std::vector<int32_t> lo(L.n * (N - 1)), hi(L.n * (N - 1));
@@ -345,10 +354,14 @@ int copy_level_to_host(fem_ctx *ctx, const DevLevel &L, fem_result *res, int lev
         FEM_CUDA_TRY(cudaMemcpyAsync(c.data(), L.counts, 4 * c.size(), cudaMemcpyDeviceToHost, ctx->stream));
         FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     }
-    for (int r = 0; r < res->n_recs; ++r) {
-        fem_result::Level &out = res->lv[r][level];
+    for (size_t r = 0; r + 1 < L.h_off.size(); ++r) {
+        fem_result::Level &out = res->lv[out_rec[r]][level];
         const int64_t b = L.h_off[r], e = L.h_off[r + 1];
         out.offs.assign(1, 0);
+        out.types.clear();
+        out.lo.clear();
+        out.hi.clear();
+        out.counts.clear();
         for (int64_t i = b; i < e; ++i) {
             out.types.insert(out.types.end(), t.begin() + i * N, t.begin() + (i + 1) * N);
             if (N > 1) {
@@ -362,28 +375,67 @@ int copy_level_to_host(fem_ctx *ctx, const DevLevel &L, fem_result *res, int lev
     return FEM_OK;
 }
 
-int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
-              const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, int max_size, fem_result *res) {
-    const int n_recs = (int)recs.size();
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// One set of recordings mined in lock-step: every recording of the group is
+// at the same level.  begin() runs level 1 and prepares the level-2
+// candidates; after the candidates have been counted (by anyone: a counting
+// call of its own, or a launch shared with other groups), advance() applies
+// the threshold and prepares the next level's candidates.
+struct MineGroup {
+    fem_ctx *ctx = nullptr;
+    std::vector<fem_stream *> recs;
+    std::vector<int> out_rec;           // result slot of each recording
+    fem_result *res = nullptr;
+    std::vector<int32_t> blo, bhi, lo_vals;
+    std::vector<uint32_t> thr;
+    int max_size = 0;
+    int level = 0;                      // level of the current candidates; 0 when done
+    bool done = false;
+    fem_stats S{};
+
+    std::unique_ptr<Pool> pconst, pprev, pcand;
+    uint32_t *d_thr = nullptr;
+    int32_t *d_blo = nullptr, *d_bhi = nullptr;
+    DevLevel prev, cand;
+    int64_t *d_coffs = nullptr;         // CSR node offsets of the candidates
+    int64_t *d_coff_rec = nullptr;      // per-recording candidate offsets
+    int32_t *d_order = nullptr;         // counting order (level 2) or null
+    int64_t n_order = 0;                // candidates left for the exact count
+    std::vector<int64_t> c_off;         // host copy of d_coff_rec
+
+    int nrec() const { return (int)recs.size(); }
+
+    int begin();
+    int advance();
+
+  private:
+    int gen_level2();
+    int gen_join();
+    int finish_candidates();
+};
+
+int MineGroup::begin() {
+    const int n_recs = nrec();
     const int nb = (int)blo.size();
-    Pool pool{ctx};
     cudaStream_t st = ctx->stream;
-    fem_stats &S = res->stats;
     const int B = 256;
-    // constants on device
-    uint32_t *d_thr;
-    int32_t *d_blo, *d_bhi;
-    FEM_TRY(pool.get(&d_thr, n_recs));
-    FEM_TRY(pool.get(&d_blo, nb));
-    FEM_TRY(pool.get(&d_bhi, nb));
+    pconst.reset(new Pool(ctx));
+    pprev.reset(new Pool(ctx));
+    FEM_TRY(pconst->get(&d_thr, n_recs));
+    FEM_TRY(pconst->get(&d_blo, std::max(nb, 1)));
+    FEM_TRY(pconst->get(&d_bhi, std::max(nb, 1)));
     FEM_CUDA_TRY(cudaMemcpyAsync(d_thr, thr.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(d_blo, blo.data(), 4 * nb, cudaMemcpyHostToDevice, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(d_bhi, bhi.data(), 4 * nb, cudaMemcpyHostToDevice, st));
-    std::vector<int32_t> lo_vals(blo.begin(), blo.end());
+    if (nb > 0) {
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_blo, blo.data(), 4 * nb, cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_bhi, bhi.data(), 4 * nb, cudaMemcpyHostToDevice, st));
+    }
+    lo_vals = blo;
     std::sort(lo_vals.begin(), lo_vals.end());
     lo_vals.erase(std::unique(lo_vals.begin(), lo_vals.end()), lo_vals.end());
 
-    // ---- level 1
+    // ---- level 1: frequent types
     std::vector<uint32_t> nt_pre(n_recs + 1, 0);
     std::vector<const uint32_t *> freq_p(n_recs);
     for (int r = 0; r < n_recs; ++r) {
@@ -391,29 +443,29 @@ int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::ve
         freq_p[r] = recs[r]->d_freq;
     }
     const int64_t tot1 = nt_pre[n_recs];
+    Pool tmp(ctx);
     uint32_t *d_ntpre;
     const uint32_t **d_freqp;
-    int32_t *d_flags, *d_scan;
-    FEM_TRY(pool.get(&d_ntpre, n_recs + 1));
-    FEM_TRY(pool.get(&d_freqp, n_recs));
-    FEM_TRY(pool.get(&d_flags, tot1 + 1));
-    FEM_TRY(pool.get(&d_scan, tot1 / 1024 + 2));
+    int32_t *d_flags, *d_scan, *d_total;
+    FEM_TRY(tmp.get(&d_ntpre, n_recs + 1));
+    FEM_TRY(tmp.get(&d_freqp, n_recs));
+    FEM_TRY(tmp.get(&d_flags, tot1 + 1));
+    FEM_TRY(tmp.get(&d_scan, tot1 / 1024 + 2));
+    FEM_TRY(tmp.get(&d_total, 2));
     FEM_CUDA_TRY(cudaMemcpyAsync(d_ntpre, nt_pre.data(), 4 * (n_recs + 1), cudaMemcpyHostToDevice, st));
     FEM_CUDA_TRY(cudaMemcpyAsync(d_freqp, freq_p.data(), sizeof(void *) * n_recs, cudaMemcpyHostToDevice, st));
     k_level1_flags<<<(unsigned)((tot1 + B - 1) / B), B, 0, st>>>(d_freqp, d_ntpre, n_recs, d_thr, d_flags, tot1);
-    int32_t *d_total;
-    FEM_TRY(pool.get(&d_total, 2));
     FEM_TRY(scan_exclusive(st, d_flags, tot1, d_scan, d_total, &S.kernel_launches));
     int32_t F1 = 0;
     FEM_CUDA_TRY(cudaMemcpyAsync(&F1, d_total, 4, cudaMemcpyDeviceToHost, st));
     FEM_CUDA_TRY(cudaStreamSynchronize(st));
-    DevLevel prev;
+    prev = DevLevel{};
     prev.N = 1;
     prev.n = F1;
-    FEM_TRY(pool.get(&prev.types, F1));
-    FEM_TRY(pool.get(&prev.counts, F1));
-    FEM_TRY(pool.get(&prev.rec, F1));
-    FEM_TRY(pool.get(&prev.off, n_recs + 1));
+    FEM_TRY(pprev->get(&prev.types, F1));
+    FEM_TRY(pprev->get(&prev.counts, F1));
+    FEM_TRY(pprev->get(&prev.rec, F1));
+    FEM_TRY(pprev->get(&prev.off, n_recs + 1));
     k_level1_write<<<(unsigned)((tot1 + B - 1) / B), B, 0, st>>>(d_flags, d_freqp, d_ntpre, n_recs, d_thr, tot1,
                                                                 prev.types, prev.counts, prev.rec);
     k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(prev.rec, prev.n, n_recs, prev.off);
@@ -421,194 +473,389 @@ int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::ve
     prev.h_off.resize(n_recs + 1);
     FEM_CUDA_TRY(cudaMemcpyAsync(prev.h_off.data(), prev.off, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
     FEM_CUDA_TRY(cudaStreamSynchronize(st));
-    FEM_TRY(copy_level_to_host(ctx, prev, res, 1));
+    FEM_TRY(copy_level_to_host(ctx, prev, res, out_rec, 1));
     S.levels = 1;
-
-    for (int N = 2; N <= max_size; ++N) {
-        // ---- candidate generation
-        std::vector<int64_t> c_off(n_recs + 1, 0);
-        if (N == 2) {
-            for (int r = 0; r < n_recs; ++r) {
-                const int64_t F = prev.h_off[r + 1] - prev.h_off[r];
-                c_off[r + 1] = c_off[r] + (F >= 2 ? F * (F - 1) * nb : 0);
-            }
-        }
-        int64_t C = 0;
-        DevLevel cand;
-        cand.N = N;
-        int64_t *d_coffs = nullptr;
-        int64_t *d_coff_rec = nullptr;
-        int32_t *d_order = nullptr;  // counting order (level 2) or null
-        FEM_TRY(pool.get(&d_coff_rec, n_recs + 1));
-        if (N == 2) {
-            C = c_off[n_recs];
-            if (C == 0) break;
-            FEM_TRY(pool.get(&cand.types, 2 * C));
-            FEM_TRY(pool.get(&cand.lo, C));
-            FEM_TRY(pool.get(&cand.hi, C));
-            FEM_TRY(pool.get(&cand.rec, C));
-            FEM_TRY(pool.get(&d_coffs, C + 1));
-            FEM_CUDA_TRY(cudaMemcpyAsync(d_coff_rec, c_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
-            k_gen_level2<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(prev.types, prev.off, d_coff_rec, n_recs, d_blo,
-                                                                   d_bhi, nb, C, cand.types, cand.lo, cand.hi,
-                                                                   cand.rec, d_coffs);
-            S.kernel_launches++;
-            // counting order: tiles of At x Bt type pairs with all bins
-            const int pairs = std::max(1, 32 / std::max(1, nb));
-            const int At = pairs >= 32 ? 8 : pairs >= 8 ? 4 : pairs >= 2 ? 2 : 1;
-            const int Bt = std::max(1, pairs / At);
-            std::vector<int64_t> g_off(n_recs + 1, 0);
-            for (int r = 0; r < n_recs; ++r) {
-                const int64_t F = prev.h_off[r + 1] - prev.h_off[r];
-                const int64_t cells = (F >= 2) ? ((F + At - 1) / At) * ((F + Bt - 1) / Bt) * (int64_t)At * Bt * nb : 0;
-                g_off[r + 1] = g_off[r] + cells;
-            }
-            const int64_t G = g_off[n_recs];
-            int64_t *d_goff;
-            int32_t *d_gfl, *d_gtmp;
-            FEM_TRY(pool.get(&d_goff, n_recs + 1));
-            FEM_TRY(pool.get(&d_gfl, G + 1));
-            FEM_TRY(pool.get(&d_gtmp, G / 1024 + 2));
-            FEM_TRY(pool.get(&d_order, C));
-            FEM_CUDA_TRY(cudaMemcpyAsync(d_goff, g_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
-            k_perm2_flags<<<(unsigned)((G + B - 1) / B), B, 0, st>>>(prev.off, d_goff, n_recs, nb, At, Bt, G, d_gfl);
-            FEM_TRY(scan_exclusive(st, d_gfl, G, d_gtmp, nullptr, &S.kernel_launches));
-            k_perm2_write<<<(unsigned)((G + B - 1) / B), B, 0, st>>>(d_gfl, prev.off, d_goff, d_coff_rec, n_recs, nb, At,
-                                                                    Bt, G, d_order);
-            S.kernel_launches += 2;
-        } else {
-            const int M = N - 1;
-            const int64_t F = prev.n;
-            if (F == 0) break;
-            int32_t *d_cnt, *d_tmp, *d_tot;
-            FEM_TRY(pool.get(&d_cnt, F + 1));
-            FEM_TRY(pool.get(&d_tmp, F / 1024 + 2));
-            FEM_TRY(pool.get(&d_tot, 2));
-            k_join_count<<<(unsigned)((F + B - 1) / B), B, 0, st>>>(prev.types, prev.lo, prev.hi, prev.rec, prev.off,
-                                                                   M, F, d_cnt);
-            FEM_TRY(scan_exclusive(st, d_cnt, F, d_tmp, d_tot, &S.kernel_launches));
-            int32_t Ct = 0;
-            FEM_CUDA_TRY(cudaMemcpyAsync(&Ct, d_tot, 4, cudaMemcpyDeviceToHost, st));
-            FEM_CUDA_TRY(cudaStreamSynchronize(st));
-            C = Ct;
-            S.kernel_launches++;
-            if (C == 0) break;
-            FEM_TRY(pool.get(&cand.types, (size_t)C * N));
-            FEM_TRY(pool.get(&cand.lo, (size_t)C * (N - 1)));
-            FEM_TRY(pool.get(&cand.hi, (size_t)C * (N - 1)));
-            FEM_TRY(pool.get(&cand.rec, C));
-            FEM_TRY(pool.get(&d_coffs, C + 1));
-            k_join_write<<<(unsigned)((F + B - 1) / B), B, 0, st>>>(prev.types, prev.lo, prev.hi, prev.rec, prev.off,
-                                                                   M, F, d_cnt, cand.types, cand.lo, cand.hi, cand.rec,
-                                                                   d_coffs, C);
-            k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(cand.rec, C, n_recs, d_coff_rec);
-            FEM_CUDA_TRY(cudaMemcpyAsync(c_off.data(), d_coff_rec, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
-            FEM_CUDA_TRY(cudaStreamSynchronize(st));
-            S.kernel_launches += 2;
-        }
-        cand.n = C;
-        FEM_TRY(pool.get(&cand.counts, C));
-        int64_t C_exact = C;  // candidates left for the exact count
-        if (N == 2 && ctx->tuning.prepass != -1) {
-            int32_t hi_max = 0;
-            for (int k = 0; k < nb; ++k) hi_max = std::max(hi_max, bhi[k]);
-            bool ok = nb <= 8;
-            for (int r = 0; r < n_recs && ok; ++r) ok = recs[r]->n_types <= 1024;
-            if (ok) {
-                std::vector<const uint32_t *> ubp(n_recs);
-                for (int r = 0; r < n_recs; ++r) {
-                    const uint32_t nt = recs[r]->n_types;
-                    uint32_t *u;
-                    FEM_TRY(pool.get(&u, (size_t)nt * nt * nb));
-                    FEM_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(uint32_t) * (size_t)nt * nt * nb, st));
-                    const int words = (int)((nt * (uint32_t)nb + 31) / 32);
-                    int threads = std::min(256, (int)(48 * 1024 / (4 * words)) / 32 * 32);
-                    threads = std::max(threads, 32);
-                    if (recs[r]->n > 0 && (prev.h_off[r + 1] - prev.h_off[r]) >= 2) {
-                        const int64_t blocks = std::min<int64_t>((recs[r]->n + threads - 1) / threads, 8 * ctx->n_sm);
-                        k_pair_ub<<<(unsigned)blocks, threads, (size_t)threads * words * 4, st>>>(
-                            recs[r]->d_type, recs[r]->d_time, recs[r]->n, nt, d_blo, d_bhi, nb, hi_max, words, u);
-                        S.kernel_launches++;
-                    }
-                    ubp[r] = u;
-                }
-                const uint32_t **d_ubp;
-                uint32_t *d_nt;
-                int32_t *d_pf, *d_pf2, *d_ptmp, *d_ptot, *d_kept;
-                FEM_TRY(pool.get(&d_ubp, n_recs));
-                FEM_TRY(pool.get(&d_nt, n_recs));
-                FEM_TRY(pool.get(&d_pf, C + 1));
-                FEM_TRY(pool.get(&d_pf2, C + 1));
-                FEM_TRY(pool.get(&d_ptmp, C / 1024 + 2));
-                FEM_TRY(pool.get(&d_ptot, 2));
-                FEM_TRY(pool.get(&d_kept, C));
-                std::vector<uint32_t> nth(n_recs);
-                for (int r = 0; r < n_recs; ++r) nth[r] = recs[r]->n_types;
-                FEM_CUDA_TRY(cudaMemcpyAsync(d_ubp, ubp.data(), sizeof(void *) * n_recs, cudaMemcpyHostToDevice, st));
-                FEM_CUDA_TRY(cudaMemcpyAsync(d_nt, nth.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
-                k_prune2_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_order, C, cand.types, cand.lo, cand.hi,
-                                                                         cand.rec, d_ubp, d_nt, d_blo, d_bhi, nb, d_thr,
-                                                                         d_pf, cand.counts);
-                FEM_CUDA_TRY(cudaMemcpyAsync(d_pf2, d_pf, 4 * C, cudaMemcpyDeviceToDevice, st));
-                FEM_TRY(scan_exclusive(st, d_pf, C, d_ptmp, d_ptot, &S.kernel_launches));
-                k_prune2_write<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_pf, d_pf2, d_order, C, d_kept);
-                S.kernel_launches += 2;
-                int32_t kept = 0;
-                FEM_CUDA_TRY(cudaMemcpyAsync(&kept, d_ptot, 4, cudaMemcpyDeviceToHost, st));
-                FEM_CUDA_TRY(cudaStreamSynchronize(st));
-                C_exact = kept;
-                d_order = d_kept;
-                S.candidates_pruned += C - kept;
-            }
-        }
-        // ---- exact counting of every candidate of every recording
-        fem_stats cs{};
-        FEM_TRY(count_device(ctx, recs, C, d_coffs, cand.types, cand.lo, cand.hi, cand.rec, lo_vals, d_order,
-                             C_exact, cand.counts, &cs));
-        S.kernel_launches += cs.kernel_launches;
-        S.candidates_counted += cs.candidates_counted;
-        S.candidates_pruned += cs.candidates_pruned;
-        S.fallback_recounts += cs.fallback_recounts;
-        S.relevant_events += cs.relevant_events;
-        S.counted_episode_events += cs.counted_episode_events;
-        S.count_kernel_ms += cs.count_kernel_ms;
-        for (int r = 0; r < n_recs; ++r) S.episode_events += (double)(c_off[r + 1] - c_off[r]) * (double)recs[r]->n;
-        // ---- threshold + compaction in canonical order
-        int32_t *d_fl, *d_tmp2, *d_tot2;
-        FEM_TRY(pool.get(&d_fl, C + 1));
-        FEM_TRY(pool.get(&d_tmp2, C / 1024 + 2));
-        FEM_TRY(pool.get(&d_tot2, 2));
-        k_thr_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(cand.counts, cand.rec, d_thr, C, d_fl);
-        FEM_TRY(scan_exclusive(st, d_fl, C, d_tmp2, d_tot2, &S.kernel_launches));
-        int32_t Fn = 0;
-        FEM_CUDA_TRY(cudaMemcpyAsync(&Fn, d_tot2, 4, cudaMemcpyDeviceToHost, st));
-        FEM_CUDA_TRY(cudaStreamSynchronize(st));
-        DevLevel next;
-        next.N = N;
-        next.n = Fn;
-        FEM_TRY(pool.get(&next.types, (size_t)Fn * N));
-        FEM_TRY(pool.get(&next.lo, (size_t)Fn * (N - 1)));
-        FEM_TRY(pool.get(&next.hi, (size_t)Fn * (N - 1)));
-        FEM_TRY(pool.get(&next.rec, Fn));
-        FEM_TRY(pool.get(&next.counts, Fn));
-        FEM_TRY(pool.get(&next.off, n_recs + 1));
-        k_thr_write<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_fl, cand.counts, cand.types, cand.lo, cand.hi,
-                                                              cand.rec, d_thr, N, C, next.types, next.lo, next.hi,
-                                                              next.rec, next.counts);
-        k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(next.rec, next.n, n_recs, next.off);
-        S.kernel_launches += 3;
-        next.h_off.resize(n_recs + 1);
-        FEM_CUDA_TRY(cudaMemcpyAsync(next.h_off.data(), next.off, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
-        FEM_TRY(sync_status(ctx));
-        FEM_TRY(copy_level_to_host(ctx, next, res, N));
-        S.levels = N;
-        prev = next;
-        if (Fn == 0) break;
+    if (max_size < 2 || F1 < 2 || nb == 0) {
+        done = true;
+        level = 0;
+        return FEM_OK;
     }
+    level = 2;
+    FEM_TRY(gen_level2());
+    return finish_candidates();
+}
+
+int MineGroup::gen_level2() {
+    const int n_recs = nrec();
+    const int nb = (int)blo.size();
+    cudaStream_t st = ctx->stream;
+    const int B = 256;
+    pcand.reset(new Pool(ctx));
+    c_off.assign(n_recs + 1, 0);
+    for (int r = 0; r < n_recs; ++r) {
+        const int64_t F = prev.h_off[r + 1] - prev.h_off[r];
+        c_off[r + 1] = c_off[r] + (F >= 2 ? F * (F - 1) * nb : 0);
+    }
+    const int64_t C = c_off[n_recs];
+    cand = DevLevel{};
+    cand.N = 2;
+    cand.n = C;
+    d_order = nullptr;
+    n_order = C;
+    FEM_TRY(pcand->get(&d_coff_rec, n_recs + 1));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_coff_rec, c_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+    if (C == 0) return FEM_OK;
+    FEM_TRY(pcand->get(&cand.types, 2 * C));
+    FEM_TRY(pcand->get(&cand.lo, C));
+    FEM_TRY(pcand->get(&cand.hi, C));
+    FEM_TRY(pcand->get(&cand.rec, C));
+    FEM_TRY(pcand->get(&cand.counts, C));
+    FEM_TRY(pcand->get(&d_coffs, C + 1));
+    k_gen_level2<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(prev.types, prev.off, d_coff_rec, n_recs, d_blo, d_bhi,
+                                                           nb, C, cand.types, cand.lo, cand.hi, cand.rec, d_coffs);
+    S.kernel_launches++;
+    // counting order: tiles of At x Bt type pairs with all bins
+    const int pairs = std::max(1, 32 / std::max(1, nb));
+    const int At = pairs >= 32 ? 8 : pairs >= 8 ? 4 : pairs >= 2 ? 2 : 1;
+    const int Bt = std::max(1, pairs / At);
+    std::vector<int64_t> g_off(n_recs + 1, 0);
+    for (int r = 0; r < n_recs; ++r) {
+        const int64_t F = prev.h_off[r + 1] - prev.h_off[r];
+        const int64_t cells = (F >= 2) ? ((F + At - 1) / At) * ((F + Bt - 1) / Bt) * (int64_t)At * Bt * nb : 0;
+        g_off[r + 1] = g_off[r] + cells;
+    }
+    const int64_t G = g_off[n_recs];
+    Pool tmp(ctx);
+    int64_t *d_goff;
+    int32_t *d_gfl, *d_gtmp;
+    FEM_TRY(tmp.get(&d_goff, n_recs + 1));
+    FEM_TRY(tmp.get(&d_gfl, G + 1));
+    FEM_TRY(tmp.get(&d_gtmp, G / 1024 + 2));
+    FEM_TRY(pcand->get(&d_order, C));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_goff, g_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+    k_perm2_flags<<<(unsigned)((G + B - 1) / B), B, 0, st>>>(prev.off, d_goff, n_recs, nb, At, Bt, G, d_gfl);
+    FEM_TRY(scan_exclusive(st, d_gfl, G, d_gtmp, nullptr, &S.kernel_launches));
+    k_perm2_write<<<(unsigned)((G + B - 1) / B), B, 0, st>>>(d_gfl, prev.off, d_goff, d_coff_rec, n_recs, nb, At, Bt,
+                                                            G, d_order);
+    S.kernel_launches += 2;
+
+    // ---- upper-bound pre-pass
+    if (ctx->tuning.prepass == -1 || nb > 8) return FEM_OK;
+    for (int r = 0; r < n_recs; ++r)
+        if (recs[r]->n_types > 1024) return FEM_OK;
+    int32_t hi_max = 0;
+    for (int k = 0; k < nb; ++k) hi_max = std::max(hi_max, bhi[k]);
+    std::vector<const uint32_t *> ubp(n_recs);
+    for (int r = 0; r < n_recs; ++r) {
+        const uint32_t nt = recs[r]->n_types;
+        uint32_t *u;
+        FEM_TRY(tmp.get(&u, (size_t)nt * nt * nb));
+        FEM_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(uint32_t) * (size_t)nt * nt * nb, st));
+        const int words = (int)((nt * (uint32_t)nb + 31) / 32);
+        int threads = std::min(256, (int)(48 * 1024 / (4 * words)) / 32 * 32);
+        threads = std::max(threads, 32);
+        if (recs[r]->n > 0 && (prev.h_off[r + 1] - prev.h_off[r]) >= 2) {
+            const int64_t blocks = std::min<int64_t>((recs[r]->n + threads - 1) / threads, 8 * ctx->n_sm);
+            k_pair_ub<<<(unsigned)blocks, threads, (size_t)threads * words * 4, st>>>(
+                recs[r]->d_type, recs[r]->d_time, recs[r]->n, nt, d_blo, d_bhi, nb, hi_max, words, u);
+            S.kernel_launches++;
+        }
+        ubp[r] = u;
+    }
+    const uint32_t **d_ubp;
+    uint32_t *d_nt;
+    int32_t *d_pf, *d_pf2, *d_ptmp, *d_ptot, *d_kept;
+    FEM_TRY(tmp.get(&d_ubp, n_recs));
+    FEM_TRY(tmp.get(&d_nt, n_recs));
+    FEM_TRY(tmp.get(&d_pf, C + 1));
+    FEM_TRY(tmp.get(&d_pf2, C + 1));
+    FEM_TRY(tmp.get(&d_ptmp, C / 1024 + 2));
+    FEM_TRY(tmp.get(&d_ptot, 2));
+    FEM_TRY(pcand->get(&d_kept, C));
+    std::vector<uint32_t> nth(n_recs);
+    for (int r = 0; r < n_recs; ++r) nth[r] = recs[r]->n_types;
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_ubp, ubp.data(), sizeof(void *) * n_recs, cudaMemcpyHostToDevice, st));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_nt, nth.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
+    k_prune2_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_order, C, cand.types, cand.lo, cand.hi, cand.rec, d_ubp,
+                                                             d_nt, d_blo, d_bhi, nb, d_thr, d_pf, cand.counts);
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_pf2, d_pf, 4 * C, cudaMemcpyDeviceToDevice, st));
+    FEM_TRY(scan_exclusive(st, d_pf, C, d_ptmp, d_ptot, &S.kernel_launches));
+    k_prune2_write<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_pf, d_pf2, d_order, C, d_kept);
+    S.kernel_launches += 2;
+    int32_t kept = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&kept, d_ptot, 4, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    n_order = kept;
+    d_order = d_kept;
+    S.candidates_pruned += C - kept;
     return FEM_OK;
 }
 
-}  // namespace
+int MineGroup::gen_join() {
+    const int n_recs = nrec();
+    const int N = level;
+    const int M = N - 1;
+    cudaStream_t st = ctx->stream;
+    const int B = 256;
+    const int64_t F = prev.n;
+    pcand.reset(new Pool(ctx));
+    cand = DevLevel{};
+    cand.N = N;
+    d_order = nullptr;
+    c_off.assign(n_recs + 1, 0);
+    FEM_TRY(pcand->get(&d_coff_rec, n_recs + 1));
+    if (F == 0) {
+        cand.n = 0;
+        n_order = 0;
+        return FEM_OK;
+    }
+    Pool tmp(ctx);
+    int32_t *d_cnt, *d_tmp, *d_tot;
+    FEM_TRY(tmp.get(&d_cnt, F + 1));
+    FEM_TRY(tmp.get(&d_tmp, F / 1024 + 2));
+    FEM_TRY(tmp.get(&d_tot, 2));
+    k_join_count<<<(unsigned)((F + B - 1) / B), B, 0, st>>>(prev.types, prev.lo, prev.hi, prev.rec, prev.off, M, F,
+                                                           d_cnt);
+    FEM_TRY(scan_exclusive(st, d_cnt, F, d_tmp, d_tot, &S.kernel_launches));
+    int32_t Ct = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&Ct, d_tot, 4, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    S.kernel_launches++;
+    const int64_t C = Ct;
+    cand.n = C;
+    n_order = C;
+    if (C == 0) return FEM_OK;
+    FEM_TRY(pcand->get(&cand.types, (size_t)C * N));
+    FEM_TRY(pcand->get(&cand.lo, (size_t)C * (N - 1)));
+    FEM_TRY(pcand->get(&cand.hi, (size_t)C * (N - 1)));
+    FEM_TRY(pcand->get(&cand.rec, C));
+    FEM_TRY(pcand->get(&cand.counts, C));
+    FEM_TRY(pcand->get(&d_coffs, C + 1));
+    k_join_write<<<(unsigned)((F + B - 1) / B), B, 0, st>>>(prev.types, prev.lo, prev.hi, prev.rec, prev.off, M, F,
+                                                           d_cnt, cand.types, cand.lo, cand.hi, cand.rec, d_coffs, C);
+    k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(cand.rec, C, n_recs, d_coff_rec);
+    FEM_CUDA_TRY(cudaMemcpyAsync(c_off.data(), d_coff_rec, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    S.kernel_launches += 2;
+    return FEM_OK;
+}
+
+// Statistics of the candidates about to be counted; an empty candidate set
+// ends the group.
+int MineGroup::finish_candidates() {
+    if (cand.n == 0) {
+        done = true;
+        level = 0;
+        pcand.reset();
+        return FEM_OK;
+    }
+    for (int r = 0; r < nrec(); ++r) S.episode_events += (double)(c_off[r + 1] - c_off[r]) * (double)recs[r]->n;
+    return FEM_OK;
+}
+
+int MineGroup::advance() {
+    const int n_recs = nrec();
+    const int N = level;
+    cudaStream_t st = ctx->stream;
+    const int B = 256;
+    const int64_t C = cand.n;
+    std::unique_ptr<Pool> pnext(new Pool(ctx));
+    Pool tmp(ctx);
+    int32_t *d_fl, *d_tmp2, *d_tot2;
+    FEM_TRY(tmp.get(&d_fl, C + 1));
+    FEM_TRY(tmp.get(&d_tmp2, C / 1024 + 2));
+    FEM_TRY(tmp.get(&d_tot2, 2));
+    k_thr_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(cand.counts, cand.rec, d_thr, C, d_fl);
+    FEM_TRY(scan_exclusive(st, d_fl, C, d_tmp2, d_tot2, &S.kernel_launches));
+    int32_t Fn = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&Fn, d_tot2, 4, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    DevLevel next;
+    next.N = N;
+    next.n = Fn;
+    FEM_TRY(pnext->get(&next.types, (size_t)Fn * N));
+    FEM_TRY(pnext->get(&next.lo, (size_t)Fn * (N - 1)));
+    FEM_TRY(pnext->get(&next.hi, (size_t)Fn * (N - 1)));
+    FEM_TRY(pnext->get(&next.rec, Fn));
+    FEM_TRY(pnext->get(&next.counts, Fn));
+    FEM_TRY(pnext->get(&next.off, n_recs + 1));
+    k_thr_write<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_fl, cand.counts, cand.types, cand.lo, cand.hi, cand.rec,
+                                                          d_thr, N, C, next.types, next.lo, next.hi, next.rec,
+                                                          next.counts);
+    k_rec_offsets<<<(n_recs + 1 + 127) / 128, 128, 0, st>>>(next.rec, next.n, n_recs, next.off);
+    S.kernel_launches += 3;
+    next.h_off.resize(n_recs + 1);
+    FEM_CUDA_TRY(cudaMemcpyAsync(next.h_off.data(), next.off, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    FEM_TRY(copy_level_to_host(ctx, next, res, out_rec, N));
+    S.levels = N;
+    prev = next;
+    pprev = std::move(pnext);
+    pcand.reset();
+    if (Fn == 0 || N >= max_size) {
+        done = true;
+        level = 0;
+        return FEM_OK;
+    }
+    level = N + 1;
+    FEM_TRY(gen_join());
+    return finish_candidates();
+}
+
+// Counting of the candidates of one group with the library's counting path.
+static int count_group(MineGroup &g) {
+    fem_stats cs{};
+    FEM_TRY(count_device(g.ctx, g.recs, g.cand.n, g.d_coffs, g.cand.types, g.cand.lo, g.cand.hi, g.cand.rec, g.lo_vals,
+                         g.d_order, g.n_order, g.cand.counts, &cs));
+    g.S.kernel_launches += cs.kernel_launches;
+    g.S.candidates_counted += cs.candidates_counted;
+    g.S.fallback_recounts += cs.fallback_recounts;
+    g.S.relevant_events += cs.relevant_events;
+    g.S.count_kernel_ms += cs.count_kernel_ms;
+    g.S.counted_episode_events += cs.counted_episode_events;
+    return FEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Continuous batching: the current candidates of several groups (each at its
+// own level) are concatenated and counted in one counting call, then the
+// counts are handed back to each group.
+__global__ void k_fill_group(int64_t C, int N, int64_t cbase, int64_t nbase, int rbase, const uint32_t *grec,
+                             const int32_t *gorder, int64_t n_order, int64_t obase, int64_t *offs, uint32_t *rec,
+                             int32_t *order) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < C) {
+        offs[cbase + i] = nbase + i * N;
+        rec[cbase + i] = (uint32_t)rbase + grec[i];
+    }
+    if (i < n_order) order[obase + i] = (int32_t)(cbase + (gorder ? gorder[i] : i));
+}
+
+__global__ void k_set_last_offs(int64_t *offs, int64_t C, int64_t nodes) { offs[C] = nodes; }
+
+int mg_count_batch(fem_ctx *ctx, const std::vector<MineGroup *> &gs) {
+    cudaStream_t st = ctx->stream;
+    std::vector<fem_stream *> recs;
+    std::vector<int32_t> lo_vals;
+    int64_t C = 0, nodes = 0, edges = 0, norder = 0;
+    for (MineGroup *g : gs) {
+        if (g->done || g->cand.n == 0) continue;
+        recs.insert(recs.end(), g->recs.begin(), g->recs.end());
+        lo_vals.insert(lo_vals.end(), g->lo_vals.begin(), g->lo_vals.end());
+        C += g->cand.n;
+        nodes += g->cand.n * g->cand.N;
+        edges += g->cand.n * (g->cand.N - 1);
+        norder += g->n_order;
+    }
+    if (C == 0) return FEM_OK;
+    std::sort(lo_vals.begin(), lo_vals.end());
+    lo_vals.erase(std::unique(lo_vals.begin(), lo_vals.end()), lo_vals.end());
+    void *p[7];
+    FEM_TRY(scratch(ctx, kSlotMine0 + 0, 8 * (C + 1), &p[0]));
+    FEM_TRY(scratch(ctx, kSlotMine0 + 1, 2 * nodes, &p[1]));
+    FEM_TRY(scratch(ctx, kSlotMine0 + 2, 4 * std::max<int64_t>(edges, 1), &p[2]));
+    FEM_TRY(scratch(ctx, kSlotMine0 + 3, 4 * std::max<int64_t>(edges, 1), &p[3]));
+    FEM_TRY(scratch(ctx, kSlotMine0 + 4, 4 * C, &p[4]));
+    FEM_TRY(scratch(ctx, kSlotMine0 + 5, 4 * std::max<int64_t>(norder, 1), &p[5]));
+    FEM_TRY(scratch(ctx, kSlotMine0 + 6, 4 * C, &p[6]));
+    int64_t *offs = static_cast<int64_t *>(p[0]);
+    uint16_t *types = static_cast<uint16_t *>(p[1]);
+    int32_t *lo = static_cast<int32_t *>(p[2]), *hi = static_cast<int32_t *>(p[3]);
+    uint32_t *rec = static_cast<uint32_t *>(p[4]);
+    int32_t *order = static_cast<int32_t *>(p[5]);
+    uint32_t *counts = static_cast<uint32_t *>(p[6]);
+    int64_t cb = 0, nbse = 0, ebse = 0, ob = 0;
+    int rb = 0;
+    for (MineGroup *g : gs) {
+        if (g->done || g->cand.n == 0) continue;
+        const int64_t c = g->cand.n;
+        const int N = g->cand.N;
+        FEM_CUDA_TRY(cudaMemcpyAsync(types + nbse, g->cand.types, 2 * c * N, cudaMemcpyDeviceToDevice, st));
+        if (N > 1) {
+            FEM_CUDA_TRY(cudaMemcpyAsync(lo + ebse, g->cand.lo, 4 * c * (N - 1), cudaMemcpyDeviceToDevice, st));
+            FEM_CUDA_TRY(cudaMemcpyAsync(hi + ebse, g->cand.hi, 4 * c * (N - 1), cudaMemcpyDeviceToDevice, st));
+        }
+        // pruned candidates already hold their final count (0)
+        FEM_CUDA_TRY(cudaMemcpyAsync(counts + cb, g->cand.counts, 4 * c, cudaMemcpyDeviceToDevice, st));
+        const int64_t m = std::max(c, g->n_order);
+        k_fill_group<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c, N, cb, nbse, rb, g->cand.rec, g->d_order,
+                                                                  g->n_order, ob, offs, rec, order);
+        cb += c;
+        nbse += c * N;
+        ebse += c * (N - 1);
+        ob += g->n_order;
+        rb += g->nrec();
+    }
+    k_set_last_offs<<<1, 1, 0, st>>>(offs, C, nodes);
+    FEM_CUDA_TRY(cudaGetLastError());
+    fem_stats cs{};
+    FEM_TRY(count_device(ctx, recs, C, offs, types, lo, hi, rec, lo_vals, order, norder, counts, &cs));
+    cb = 0;
+    for (MineGroup *g : gs) {
+        if (g->done || g->cand.n == 0) continue;
+        FEM_CUDA_TRY(cudaMemcpyAsync(g->cand.counts, counts + cb, 4 * g->cand.n, cudaMemcpyDeviceToDevice, st));
+        g->S.kernel_launches += 2;
+        cb += g->cand.n;
+    }
+    // shared launch statistics are attributed to the first group
+    gs[0]->S.kernel_launches += cs.kernel_launches;
+    gs[0]->S.count_kernel_ms += cs.count_kernel_ms;
+    for (MineGroup *g : gs) g->S.candidates_counted += g->done ? 0 : g->n_order;
+    return sync_status(ctx);
+}
+
+MineGroup *mg_create(fem_ctx *ctx, fem_stream *s, const std::vector<int32_t> &blo, const std::vector<int32_t> &bhi,
+                     uint32_t thr, int max_size, fem_result *res) {
+    MineGroup *g = new (std::nothrow) MineGroup();
+    if (!g) return nullptr;
+    g->ctx = ctx;
+    g->recs = {s};
+    g->out_rec = {0};
+    g->res = res;
+    g->blo = blo;
+    g->bhi = bhi;
+    g->thr = {thr};
+    g->max_size = max_size;
+    return g;
+}
+int mg_begin(MineGroup *g) { return g->begin(); }
+int mg_advance(MineGroup *g) { return g->advance(); }
+bool mg_done(const MineGroup *g) { return g->done; }
+const fem_stats &mg_stats(const MineGroup *g) { return g->S; }
+void mg_destroy(MineGroup *g) { delete g; }
+
+fem_result *result_new(int n_recs, int max_size) {
+    fem_result *res = new (std::nothrow) fem_result();
+    if (!res) return nullptr;
+    res->n_recs = n_recs;
+    res->max_size = max_size;
+    res->lv.assign(n_recs, std::vector<fem_result::Level>(max_size + 1));
+    return res;
+}
+void result_set_stats(fem_result *r, const fem_stats &s) { r->stats = s; }
+
+static int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
+                     const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, int max_size,
+                     fem_result *res) {
+    MineGroup g;
+    g.ctx = ctx;
+    g.recs = recs;
+    for (int r = 0; r < (int)recs.size(); ++r) g.out_rec.push_back(r);
+    g.res = res;
+    g.blo = blo;
+    g.bhi = bhi;
+    g.thr = thr;
+    g.max_size = max_size;
+    int st = g.begin();
+    while (st == FEM_OK && !g.done) {
+        st = count_group(g);
+        if (st == FEM_OK) st = sync_status(ctx);
+        if (st == FEM_OK) st = g.advance();
+    }
+    res->stats = g.S;
+    return st;
+}
+
 }  // namespace fem
 
 using namespace fem;
