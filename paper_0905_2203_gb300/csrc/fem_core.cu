@@ -354,6 +354,14 @@ int fem::load_stream_unlocked(fem_ctx *ctx, const uint16_t *types, const int32_t
         cudaStreamSynchronize(ctx->stream) != cudaSuccess)
         return fail(FEM_ERR_CUDA);
     const int e = ctx->h_status[1];
+    if (n > 0 && e == 0) {
+        int32_t tt[2] = {0, 0};
+        if (cudaMemcpy(&tt[0], s->d_time, 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&tt[1], s->d_time + n - 1, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(FEM_ERR_CUDA);
+        s->t_first = tt[0];
+        s->t_last = tt[1];
+    }
     if (e & 1) return fail(FEM_ERR_INVAL);
     if (e & 2) return fail(FEM_ERR_RANGE);
     if (e & 4) return fail(FEM_ERR_UNSORTED);

@@ -485,51 +485,78 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ?
         }
         if (active) {
             st.finish();
-            int32_t *r = a.rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P + item.p) * kRecWords;
-            r[0] = st.ncls | st.flags;
-#pragma unroll
-            for (int j = 0; j < kClasses; ++j) {
-                r[1 + j] = st.cthr[j];
-                r[1 + kClasses + j] = (int32_t)st.ccnt[j];
-                r[1 + 2 * kClasses + j] = st.cprev[j];
-            }
+            int4 *r = reinterpret_cast<int4 *>(a.rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P + item.p) *
+                                                          kRecWords);
+            r[0] = make_int4(st.ncls | st.flags, st.cthr[0], st.cthr[1], st.cthr[2]);
+            r[1] = make_int4(st.cthr[3], (int32_t)st.ccnt[0], (int32_t)st.ccnt[1], (int32_t)st.ccnt[2]);
+            r[2] = make_int4((int32_t)st.ccnt[3], st.cprev[0], st.cprev[1], st.cprev[2]);
+            r[3] = make_int4(st.cprev[3], 0, 0, 0);
         }
     }
 }
 
-// Concat step: per episode, walk its segments in order with the running end x
-// of the last selected occurrence (minus infinity before the first).
+// Concat step: per episode (one warp), walk its segments in order with the
+// running end x of the last selected occurrence (minus infinity before the
+// first).  The lanes load 32 segment records at a time; the walk itself is a
+// short sequential loop over values broadcast from the lane that holds them.
 __global__ void k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
                          const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec,
                          int slot_begin, int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list,
                          int *fb_count) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_slots) return;
-    const int slot = slot_begin + i;
+    const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wi >= n_slots) return;
+    const int slot = slot_begin + wi;
     const int cand = slot2cand[slot];
     const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
     const RecInfo ri = rinfo[r_id];
-    const int32_t *r = rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P) * kRecWords;
+    const int4 *base = reinterpret_cast<const int4 *>(rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P) *
+                                                      kRecWords);
     int64_t x = INT64_MIN;
     uint32_t total = 0;
     bool bad = false;
-    for (int p = 0; p < ri.P; ++p, r += kRecWords) {
-        const int meta = r[0];
-        if (meta & (kMetaRingOverflow | kMetaClassOverflow)) bad = true;
-        const int ncls = meta & 0xFF;
-        for (int j = 0; j < ncls; ++j) {
-            if (x < (int64_t)r[1 + j]) {
-                total += (uint32_t)r[1 + kClasses + j];
-                x = r[1 + 2 * kClasses + j];
-                break;
+    for (int p0 = 0; p0 < ri.P; p0 += 32) {
+        int4 q0 = make_int4(0, 0, 0, 0), q1 = q0, q2 = q0, q3 = q0;
+        if (p0 + lane < ri.P) {
+            const int4 *r = base + (int64_t)(p0 + lane) * (kRecWords / 4);
+            q0 = r[0];
+            q1 = r[1];
+            q2 = r[2];
+            q3 = r[3];
+        }
+        const int m = min(32, ri.P - p0);
+        for (int q = 0; q < m; ++q) {
+            const int meta = __shfl_sync(0xFFFFFFFFu, q0.x, q);
+            const int thr0 = __shfl_sync(0xFFFFFFFFu, q0.y, q), thr1 = __shfl_sync(0xFFFFFFFFu, q0.z, q);
+            const int thr2 = __shfl_sync(0xFFFFFFFFu, q0.w, q), thr3 = __shfl_sync(0xFFFFFFFFu, q1.x, q);
+            const int c0 = __shfl_sync(0xFFFFFFFFu, q1.y, q), c1 = __shfl_sync(0xFFFFFFFFu, q1.z, q);
+            const int c2 = __shfl_sync(0xFFFFFFFFu, q1.w, q), c3 = __shfl_sync(0xFFFFFFFFu, q2.x, q);
+            const int l0 = __shfl_sync(0xFFFFFFFFu, q2.y, q), l1 = __shfl_sync(0xFFFFFFFFu, q2.z, q);
+            const int l2 = __shfl_sync(0xFFFFFFFFu, q2.w, q), l3 = __shfl_sync(0xFFFFFFFFu, q3.x, q);
+            if (meta & (kMetaRingOverflow | kMetaClassOverflow)) bad = true;
+            const int ncls = meta & 0xFF;
+            if (ncls > 0 && x < (int64_t)thr0) {
+                total += (uint32_t)c0;
+                x = l0;
+            } else if (ncls > 1 && x < (int64_t)thr1) {
+                total += (uint32_t)c1;
+                x = l1;
+            } else if (ncls > 2 && x < (int64_t)thr2) {
+                total += (uint32_t)c2;
+                x = l2;
+            } else if (ncls > 3 && x < (int64_t)thr3) {
+                total += (uint32_t)c3;
+                x = l3;
             }
         }
     }
-    if (bad) {
-        const int q = atomicAdd(fb_count, 1);
-        fb_list[q] = cand;
-    } else {
-        counts[cand] = total;
+    if (lane == 0) {
+        if (bad) {
+            const int q = atomicAdd(fb_count, 1);
+            fb_list[q] = cand;
+        } else {
+            counts[cand] = total;
+        }
     }
 }
 
@@ -673,6 +700,7 @@ __global__ void k_prep(PrepArgs a) {
     const int64_t eo = o - c;
     bool bad = (rec < 0 || rec >= a.n_recs || N < 1 || N > FEM_MAX_NODES);
     int R = 2;
+    int64_t sumhi = 0;
     unsigned long long relv = 0;
     if (!bad) {
         const uint32_t nt = a.n_types[rec];
@@ -690,6 +718,7 @@ __global__ void k_prep(PrepArgs a) {
                     bad = true;
                     break;
                 }
+                sumhi += h;
                 const int32_t lq = (a.mode == 2) ? 0 : l;
                 uint32_t d = dens_lookup(a, rec, lq, ty);
                 if (d == kDensUnknown || d == 0) d = freq[ty] > 0 ? freq[ty] : 1;
@@ -720,6 +749,7 @@ __global__ void k_prep(PrepArgs a) {
     a.ring[i] = R;
     atomicMax(&a.bucket_maxR[bucket], R);
     atomicMax(&a.bucket_maxR[kBuckets + bucket], (int)N);
+    atomicMax(&a.bucket_maxR[2 * kBuckets + bucket], (int)(sumhi > INT32_MAX ? INT32_MAX : sumhi));
     atomicAdd(a.relevant, relv);
 }
 
@@ -963,7 +993,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     };
     const size_t o_lo = carve(lov.size() * 4), o_nt = carve(n_recs * 4),
                  o_dp = carve(dens_h.size() * sizeof(void *)), o_ri = carve(n_recs * sizeof(RecInfo)),
-                 o_bm = carve(2 * kBuckets * 4), o_rel = carve(8), o_fb = carve(8);
+                 o_bm = carve(3 * kBuckets * 4), o_rel = carve(8), o_fb = carve(8);
     void *misc = nullptr;
     FEM_TRY(scratch(ctx, kSlotMisc, off, &misc));
     char *mb = static_cast<char *>(misc);
@@ -978,7 +1008,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                                  cudaMemcpyHostToDevice, ctx->stream));
     FEM_CUDA_TRY(cudaMemcpyAsync(mb + o_ri, ri_h.data(), n_recs * sizeof(RecInfo), cudaMemcpyHostToDevice,
                                  ctx->stream));
-    FEM_CUDA_TRY(cudaMemsetAsync(mb + o_bm, 0, 2 * kBuckets * 4, ctx->stream));
+    FEM_CUDA_TRY(cudaMemsetAsync(mb + o_bm, 0, 3 * kBuckets * 4, ctx->stream));
     FEM_CUDA_TRY(cudaMemsetAsync(mb + o_rel, 0, 8, ctx->stream));
     FEM_CUDA_TRY(cudaMemsetAsync(mb + o_fb, 0, 8, ctx->stream));
 
@@ -1030,11 +1060,11 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         FEM_CUDA_TRY(cudaGetLastError());
     }
     std::vector<int32_t> key_off(n_keys + 1, 0);
-    std::vector<int32_t> bmax(2 * kBuckets, 0);
+    std::vector<int32_t> bmax(3 * kBuckets, 0);
     unsigned long long relv = 0;
     if (n_work > 0)
         FEM_CUDA_TRY(cudaMemcpyAsync(key_off.data(), d_keyoff, 4 * n_keys, cudaMemcpyDeviceToHost, ctx->stream));
-    FEM_CUDA_TRY(cudaMemcpyAsync(bmax.data(), mb + o_bm, 2 * kBuckets * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    FEM_CUDA_TRY(cudaMemcpyAsync(bmax.data(), mb + o_bm, 3 * kBuckets * 4, cudaMemcpyDeviceToHost, ctx->stream));
     FEM_CUDA_TRY(cudaMemcpyAsync(&relv, mb + o_rel, 8, cudaMemcpyDeviceToHost, ctx->stream));
     FEM_TRY(sync_status(ctx));
     key_off[n_keys] = (int32_t)n_work;
@@ -1072,7 +1102,9 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         pl.nclass = b / kBucketRing;
         pl.R = std::max(bmax[b], 2);
         const int nmax = nmax_of_class(pl.nclass);
-        int K = ctx->tuning.lanes_per_cta > 0 ? ctx->tuning.lanes_per_cta : 256;
+        // lanes per CTA: up to 256, but no wider than the bucket needs
+        int K = ctx->tuning.lanes_per_cta > 0 ? ctx->tuning.lanes_per_cta
+                                              : std::min(256, ((se - sb) + 31) / 32 * 32);
         while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > 100 * 1024) K -= 32;
         while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > (size_t)ctx->smem_optin - 2048) K -= 32;
         (void)nmax;
@@ -1081,6 +1113,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         pl.n_slots = se - sb;
         const size_t sm = tiled_smem_rt(pl.nclass, K, pl.R, T);
         const int occ = occupancy_tiled(pl.nclass, K, pl.R, sm);
+        const int64_t max_sumhi = bmax[2 * kBuckets + b];
         // segments: aim for ~4 CTAs per resident slot across the bucket
         const int64_t desired = (int64_t)4 * ctx->n_sm * occ;
         int64_t blocks_total = 0;
@@ -1105,8 +1138,12 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                 // explicit request: allow short segments (down to ~16 events)
                 P = std::max(1, std::min<int>(ctx->tuning.segments, (int)std::max<int64_t>(1, s->n / 16)));
             } else if (c > 0) {
-                P = (int)std::max<double>(1.0, std::min<double>((double)s->n / seg_len, (double)s->n / 4096.0));
-                P = std::max(1, std::min<int>(P, (int)std::max<int64_t>(1, s->n / 256)));
+                // shortest useful segment: 1024 events, and at least 8 halos
+                // (the halo is sum(hi) of time at the stream's mean rate)
+                const double span = std::max(1.0, (double)s->t_last - (double)s->t_first);
+                const double halo_ev = (double)s->n * (double)max_sumhi / span;
+                const double min_seg = std::max(1024.0, 8.0 * halo_ev);
+                P = (int)std::max<double>(1.0, std::min<double>((double)s->n / seg_len, (double)s->n / min_seg));
             }
             pl.ri[r] = RecInfo{s->d_type, s->d_time, s->n, nullptr, P, ks, recbase, s->d_freq};
             if (c > 0) {
@@ -1178,7 +1215,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         ta.rec = static_cast<int32_t *>(p_rec);
         ta.status = ctx->d_status;
         FEM_TRY(launch_tiled(ctx, pl.nclass, (int)pl.items.size(), pl.K, pl.R, T, ta));
-        k_stitch<<<(pl.n_slots + 255) / 256, 256, 0, ctx->stream>>>(ta.rec, d_ri, d_perm, cc.cand_rec,
+        k_stitch<<<(pl.n_slots + 7) / 8, 256, 0, ctx->stream>>>(ta.rec, d_ri, d_perm, cc.cand_rec,
                                                                    pl.slot_begin, pl.n_slots, cc.counts, fb_list,
                                                                    d_fbc);
         cc.stats.kernel_launches += 2;

@@ -17,7 +17,7 @@ namespace fem {
 // ---------------------------------------------------------------------------
 // Constants of the counting kernels.
 constexpr int kClasses = 4;              // entry classes kept per (episode, segment)
-constexpr int kRecWords = 1 + 3 * kClasses;  // meta, thr[H], cnt[H], last[H]
+constexpr int kRecWords = 16;            // meta, thr[H], cnt[H], last[H], pad (64 B, int4-aligned)
 constexpr int kMaxWarps = 8;             // compute warps per CTA
 constexpr int kBitmapWords = 128;        // per-warp type filter: 4096 bits
 constexpr int kStages = 4;               // shared-memory tile ring depth
@@ -68,6 +68,7 @@ struct fem_stream {
     int32_t *d_time = nullptr;    // n + kPadEvents entries
     uint32_t *d_freq = nullptr;   // n_types
     size_t bytes = 0;
+    int32_t t_first = 0, t_last = 0;  // first and last event time (n > 0)
     std::map<int32_t, uint32_t *> dens;  // lo -> per-type max events in a closed window of length lo
 };
 
