@@ -90,6 +90,10 @@ typedef struct {
     int plain_path;       /* 1 = count with the one-thread-per-episode plain
                              path (comparison baseline) instead of the tiled
                              kernels */
+    int autotune;         /* 1 = time a few launch configurations (lanes per
+                             CTA, tile size, segment count) the first time a
+                             workload signature is seen and keep the fastest
+                             in the context's tuning cache */
 } fem_tuning;
 
 /* Per-call statistics filled by the counting / mining calls. */
@@ -123,6 +127,13 @@ int fem_ctx_set_tuning(fem_ctx *ctx, const fem_tuning *t);    /* NULL resets */
 int fem_ctx_last_stats(const fem_ctx *ctx, fem_stats *out);  /* of the last call */
 /* Bytes currently held on the device by the context (streams + scratch). */
 int fem_ctx_memory(const fem_ctx *ctx, size_t *used, size_t *budget);
+/* Backs the context's autotuner cache with a JSON file: entries in `path` (if
+ * it exists) are loaded now, and every new choice is written back.  The file
+ * maps a workload signature ("n<size class>.r<ring class>.c<log2 episodes>.
+ * e<log2 events>.m<recordings>") to [lanes_per_cta, tile_events,
+ * segment multiplier].  NULL detaches the file (the cache stays in memory).
+ * FEM_ERR_INVAL if the file exists but cannot be parsed. */
+int fem_ctx_set_autotune_cache(fem_ctx *ctx, const char *path);
 
 /* ---- streams ------------------------------------------------------------ */
 

@@ -50,7 +50,7 @@ class fem_cands(ctypes.Structure):
 
 class fem_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_cta", I32), ("segments", I32), ("tile_events", I32), ("prepass", I32),
-                ("plain_path", I32)]
+                ("plain_path", I32), ("autotune", I32)]
 
 
 class fem_stats(ctypes.Structure):
@@ -80,6 +80,7 @@ _SIGS = {
     "fem_ctx_set_tuning": (I32, [VP, ctypes.POINTER(fem_tuning)]),
     "fem_ctx_last_stats": (I32, [VP, ctypes.POINTER(fem_stats)]),
     "fem_ctx_memory": (I32, [VP, ctypes.POINTER(SZ), ctypes.POINTER(SZ)]),
+    "fem_ctx_set_autotune_cache": (I32, [VP, ctypes.c_char_p]),
     "fem_load_stream": (I32, [VP, VP, VP, I64, U32, I32, ctypes.POINTER(VP)]),
     "fem_stream_free": (None, [VP]),
     "fem_stream_info": (I32, [VP, ctypes.POINTER(I64), ctypes.POINTER(U32)]),
@@ -186,12 +187,16 @@ class Context:
         except Exception:
             pass
 
-    def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0, plain_path=0):
-        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path)
+    def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0, plain_path=0, autotune=0):
+        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path, autotune)
         check(fem_ctx_set_tuning(self.h, ctypes.byref(t)), "fem_ctx_set_tuning")
 
     def reset_tuning(self):
         check(fem_ctx_set_tuning(self.h, None), "fem_ctx_set_tuning")
+
+    def set_autotune_cache(self, path):
+        check(fem_ctx_set_autotune_cache(self.h, None if path is None else str(path).encode()),
+              "fem_ctx_set_autotune_cache")
 
     def last_stats(self) -> dict:
         s = fem_stats()

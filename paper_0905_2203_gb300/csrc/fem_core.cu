@@ -2,7 +2,11 @@
 // level-1 counts) and the window-density tables that size the per-node rings.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 
 #include "fem_internal.cuh"
 
@@ -11,6 +15,71 @@ namespace fem {
 double now_s() {
     using namespace std::chrono;
     return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+static int ilog2_ceil(int64_t v) {
+    int k = 0;
+    while (((int64_t)1 << k) < v && k < 62) ++k;
+    return k;
+}
+
+std::string tune_key(int nclass, int rclass, int64_t n_slots, int64_t n_events, int n_recs) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "n%d.r%d.c%d.e%d.m%d", nclass, rclass, ilog2_ceil(n_slots),
+                  ilog2_ceil(n_events), n_recs > 1 ? 2 : 1);
+    return buf;
+}
+
+bool tune_lookup(fem_ctx *ctx, const std::string &key, TuneVal *out) {
+    auto it = ctx->tune.find(key);
+    if (it == ctx->tune.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+static void tune_save(fem_ctx *ctx) {
+    if (ctx->tune_path.empty()) return;
+    const std::string tmp = ctx->tune_path + ".tmp";
+    {
+        std::ofstream f(tmp);
+        if (!f) return;
+        f << "{\n";
+        size_t i = 0;
+        for (auto &kv : ctx->tune) {
+            f << "  \"" << kv.first << "\": [" << kv.second.K << ", " << kv.second.T << ", " << kv.second.seg_mult
+              << "]" << (++i < ctx->tune.size() ? "," : "") << "\n";
+        }
+        f << "}\n";
+    }
+    std::rename(tmp.c_str(), ctx->tune_path.c_str());
+}
+
+void tune_store(fem_ctx *ctx, const std::string &key, const TuneVal &v) {
+    ctx->tune[key] = v;
+    tune_save(ctx);
+}
+
+// Parses {"key": [K, T, m], ...}; returns false on malformed text.
+static bool tune_parse(const std::string &text, std::map<std::string, TuneVal> *out) {
+    size_t i = text.find('{');
+    if (i == std::string::npos) return false;
+    for (;;) {
+        const size_t q0 = text.find('"', i);
+        if (q0 == std::string::npos) break;
+        const size_t q1 = text.find('"', q0 + 1);
+        const size_t b0 = text.find('[', q1);
+        const size_t b1 = text.find(']', b0);
+        if (q1 == std::string::npos || b0 == std::string::npos || b1 == std::string::npos) return false;
+        TuneVal v{};
+        if (std::sscanf(text.substr(b0 + 1, b1 - b0 - 1).c_str(), "%d , %d , %lf", &v.K, &v.T, &v.seg_mult) != 3)
+            return false;
+        if (v.K < 32 || v.K > kMaxWarps * 32 || v.K % 32 || v.T < 256 || v.T > kMaxTile || v.T % 256 ||
+            !(v.seg_mult > 0.0 && v.seg_mult < 64.0))
+            return false;
+        (*out)[text.substr(q0 + 1, q1 - q0 - 1)] = v;
+        i = b1 + 1;
+    }
+    return true;
 }
 
 int dev_alloc(fem_ctx *ctx, void **p, size_t bytes) {
@@ -288,6 +357,26 @@ extern "C" int fem_ctx_set_tuning(fem_ctx *ctx, const fem_tuning *t) {
         t->tile_events > kMaxTile)
         return FEM_ERR_INVAL;
     ctx->tuning = *t;
+    return FEM_OK;
+}
+
+extern "C" int fem_ctx_set_autotune_cache(fem_ctx *ctx, const char *path) {
+    if (!ctx) return FEM_ERR_INVAL;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!path) {
+        ctx->tune_path.clear();
+        return FEM_OK;
+    }
+    std::ifstream f(path);
+    if (f) {
+        std::stringstream ss;
+        ss << f.rdbuf();
+        std::map<std::string, TuneVal> m;
+        if (!tune_parse(ss.str(), &m)) return FEM_ERR_INVAL;
+        for (auto &kv : m) ctx->tune[kv.first] = kv.second;
+    }
+    ctx->tune_path = path;
+    tune_save(ctx);
     return FEM_OK;
 }
 

@@ -1074,40 +1074,29 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     cc.stats.relevant_events += (double)relv;
 
     // --- launches per bucket
-    const int T = ctx->tuning.tile_events > 0 ? ctx->tuning.tile_events : 1024;
-    int64_t records_needed = 0;
+    const int T_def = ctx->tuning.tile_events > 0 ? ctx->tuning.tile_events : 1024;
     struct Plan {
         int bucket;
-        int K, R, nclass;
+        int K, R, nclass, T;
         std::vector<RecInfo> ri;
         std::vector<WorkItem> items;
-        std::vector<int64_t> seg_off;
         int slot_begin, n_slots;
+        int64_t records;
     };
-    std::vector<Plan> plans;
-    std::vector<int> plain_buckets, n1_buckets;
-    for (int b = 0; b < kBuckets; ++b) {
+    bool small_alpha = true;
+    for (auto *rs : cc.recs)
+        if (rs->n_types > 128) small_alpha = false;
+    // Builds the plan of bucket b for a given CTA width, tile and segment
+    // multiplier (records start at recbase).
+    auto make_plan = [&](int b, int K, int T, double seg_mult, int64_t recbase) {
         const int sb = key_off[b * n_recs], se = key_off[(b + 1) * n_recs];
-        if (se <= sb) continue;
-        if (b == kBucketN1) {
-            n1_buckets.push_back(b);
-            continue;
-        }
-        if (b == kBucketPlain) {
-            plain_buckets.push_back(b);
-            continue;
-        }
         Plan pl;
         pl.bucket = b;
         pl.nclass = b / kBucketRing;
         pl.R = std::max(bmax[b], 2);
-        const int nmax = nmax_of_class(pl.nclass);
-        // lanes per CTA: up to 256, but no wider than the bucket needs
-        int K = ctx->tuning.lanes_per_cta > 0 ? ctx->tuning.lanes_per_cta
-                                              : std::min(256, ((se - sb) + 31) / 32 * 32);
+        pl.T = T;
         while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > 100 * 1024) K -= 32;
         while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > (size_t)ctx->smem_optin - 2048) K -= 32;
-        (void)nmax;
         pl.K = K;
         pl.slot_begin = sb;
         pl.n_slots = se - sb;
@@ -1116,17 +1105,14 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         const int64_t max_sumhi = bmax[2 * kBuckets + b];
         // segments: aim for ~4 CTAs per resident slot across the bucket
         const int64_t desired = (int64_t)4 * ctx->n_sm * occ;
-        int64_t blocks_total = 0;
         double work = 0;
         for (int r = 0; r < n_recs; ++r) {
             const int c = key_off[b * n_recs + r + 1] - key_off[b * n_recs + r];
-            if (c <= 0) continue;
-            blocks_total += (c + K - 1) / K;
-            work += (double)((c + K - 1) / K) * (double)cc.recs[r]->n;
+            if (c > 0) work += (double)((c + K - 1) / K) * (double)cc.recs[r]->n;
         }
-        const double seg_len = std::max(1.0, work / (double)std::max<int64_t>(desired, 1));
+        const double seg_len = std::max(1.0, work / (double)std::max<int64_t>(desired, 1)) / seg_mult;
         pl.ri.resize(n_recs);
-        int64_t recbase = records_needed;
+        int64_t rb = recbase;
         for (int r = 0; r < n_recs; ++r) {
             const int ks = key_off[b * n_recs + r], ke = key_off[b * n_recs + r + 1];
             const int c = ke - ks;
@@ -1145,43 +1131,20 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                 const double min_seg = std::max(1024.0, 8.0 * halo_ev);
                 P = (int)std::max<double>(1.0, std::min<double>((double)s->n / seg_len, (double)s->n / min_seg));
             }
-            pl.ri[r] = RecInfo{s->d_type, s->d_time, s->n, nullptr, P, ks, recbase, s->d_freq};
+            pl.ri[r] = RecInfo{s->d_type, s->d_time, s->n, nullptr, P, ks, rb, s->d_freq};
             if (c > 0) {
                 for (int cb = 0; cb < c; cb += K)
                     for (int p = 0; p < P; ++p) pl.items.push_back(WorkItem{r, ks + cb, std::min(K, c - cb), p});
-                recbase += (int64_t)c * P;
+                rb += (int64_t)c * P;
             }
         }
-        records_needed = recbase;
-        (void)blocks_total;
-        plans.push_back(std::move(pl));
-    }
-    // records + segments scratch
-    void *p_rec = nullptr;
-    if (records_needed > 0) FEM_TRY(scratch(ctx, kSlotRecords, (size_t)records_needed * kRecWords * 4, &p_rec));
-    int64_t seg_total = 0;
-    for (auto &pl : plans)
-        for (auto &r : pl.ri) seg_total += r.P + 1;
-    void *p_seg = nullptr;
-    FEM_TRY(scratch(ctx, kSlotSeg, sizeof(int64_t) * std::max<int64_t>(seg_total, 1), &p_seg));
-    int64_t *d_seg = static_cast<int64_t *>(p_seg);
-    // items + rinfo tables
-    size_t tab_bytes = 0;
-    for (auto &pl : plans) tab_bytes += pl.items.size() * sizeof(WorkItem) + pl.ri.size() * sizeof(RecInfo) + 512;
-    void *p_tab = nullptr;
-    FEM_TRY(scratch(ctx, kSlotRecTab, std::max<size_t>(tab_bytes, 256), &p_tab));
-    char *tab = static_cast<char *>(p_tab);
+        pl.records = rb - recbase;
+        return pl;
+    };
+    // Uploads a plan's tables and launches its tiled kernel (no stitch).
     int64_t segpos = 0;
     size_t tabpos = 0;
-    int32_t *fb_list = nullptr;
-    void *p_fb = nullptr;
-    FEM_TRY(scratch(ctx, kSlotFallback, sizeof(int32_t) * std::max<int64_t>(n_work, 1), &p_fb));
-    fb_list = static_cast<int32_t *>(p_fb);
-    int *d_fbc = reinterpret_cast<int *>(mb + o_fb);
-    const RecInfo *d_ri_plain = reinterpret_cast<const RecInfo *>(mb + o_ri);
-
-    cudaEventRecord(ctx->ev0, ctx->stream);
-    for (auto &pl : plans) {
+    auto launch_plan = [&](Plan &pl, int32_t *rec_base, int64_t *d_seg, char *tab, RecInfo **d_ri_out) -> int {
         for (int r = 0; r < n_recs; ++r) {
             pl.ri[r].seg = d_seg + segpos;
             k_segments<<<(pl.ri[r].P + 1 + 127) / 128, 128, 0, ctx->stream>>>(cc.recs[r]->d_time, cc.recs[r]->n,
@@ -1207,18 +1170,135 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         ta.slot2cand = d_perm;
         ta.R = pl.R;
         ta.K = pl.K;
-        ta.T = T;
+        ta.T = pl.T;
         ta.relaxed = cc.mode == 2;
-        ta.small_alpha = 1;
-        for (auto *rs : cc.recs)
-            if (rs->n_types > 128) ta.small_alpha = 0;
-        ta.rec = static_cast<int32_t *>(p_rec);
+        ta.small_alpha = small_alpha ? 1 : 0;
+        ta.rec = rec_base;
         ta.status = ctx->d_status;
-        FEM_TRY(launch_tiled(ctx, pl.nclass, (int)pl.items.size(), pl.K, pl.R, T, ta));
-        k_stitch<<<(pl.n_slots + 7) / 8, 256, 0, ctx->stream>>>(ta.rec, d_ri, d_perm, cc.cand_rec,
-                                                                   pl.slot_begin, pl.n_slots, cc.counts, fb_list,
-                                                                   d_fbc);
-        cc.stats.kernel_launches += 2;
+        FEM_TRY(launch_tiled(ctx, pl.nclass, (int)pl.items.size(), pl.K, pl.R, pl.T, ta));
+        cc.stats.kernel_launches++;
+        *d_ri_out = d_ri;
+        return FEM_OK;
+    };
+    // Per-plan scratch sizes (tables and segments) for a plan.
+    auto tab_need = [&](const Plan &pl) {
+        return pl.items.size() * sizeof(WorkItem) + pl.ri.size() * sizeof(RecInfo) + 512;
+    };
+    auto seg_need = [&](const Plan &pl) {
+        int64_t t = 0;
+        for (auto &r : pl.ri) t += r.P + 1;
+        return t;
+    };
+
+    std::vector<Plan> plans;
+    std::vector<int> plain_buckets, n1_buckets;
+    int64_t records_needed = 0;
+    for (int b = 0; b < kBuckets; ++b) {
+        const int sb = key_off[b * n_recs], se = key_off[(b + 1) * n_recs];
+        if (se <= sb) continue;
+        if (b == kBucketN1) {
+            n1_buckets.push_back(b);
+            continue;
+        }
+        if (b == kBucketPlain) {
+            plain_buckets.push_back(b);
+            continue;
+        }
+        // lanes per CTA: up to 256, but no wider than the bucket needs
+        int K = ctx->tuning.lanes_per_cta > 0 ? ctx->tuning.lanes_per_cta : std::min(256, ((se - sb) + 31) / 32 * 32);
+        int T = T_def;
+        double seg_mult = 1.0;
+        const bool tunable = force_segments == 0 && ctx->tuning.lanes_per_cta == 0 && ctx->tuning.segments == 0 &&
+                             ctx->tuning.tile_events == 0;
+        if (tunable) {
+            int64_t nmax_ev = 0;
+            for (int r = 0; r < n_recs; ++r)
+                if (key_off[b * n_recs + r + 1] > key_off[b * n_recs + r]) nmax_ev = std::max(nmax_ev, cc.recs[r]->n);
+            const std::string key = tune_key(b / kBucketRing, b % kBucketRing, se - sb, nmax_ev, n_recs);
+            TuneVal tv;
+            if (tune_lookup(ctx, key, &tv)) {
+                K = tv.K;
+                T = tv.T;
+                seg_mult = tv.seg_mult;
+            } else if (ctx->tuning.autotune == 1) {
+                // Coordinate search over CTA width, tile and segment
+                // multiplier, each trial one timed launch of this bucket.
+                auto trial = [&](int k, int t, double m, float *ms) -> int {
+                    Plan pl = make_plan(b, k, t, m, 0);
+                    void *pr = nullptr, *ps = nullptr, *pt = nullptr;
+                    FEM_TRY(scratch(ctx, kSlotRecords, (size_t)std::max<int64_t>(pl.records, 1) * kRecWords * 4, &pr));
+                    FEM_TRY(scratch(ctx, kSlotSeg, sizeof(int64_t) * seg_need(pl), &ps));
+                    FEM_TRY(scratch(ctx, kSlotRecTab, tab_need(pl), &pt));
+                    segpos = 0;
+                    tabpos = 0;
+                    RecInfo *dri = nullptr;
+                    cudaEventRecord(ctx->ev0, ctx->stream);
+                    FEM_TRY(launch_plan(pl, static_cast<int32_t *>(pr), static_cast<int64_t *>(ps),
+                                        static_cast<char *>(pt), &dri));
+                    cudaEventRecord(ctx->ev1, ctx->stream);
+                    FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
+                    cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1);
+                    return FEM_OK;
+                };
+                const int kmax = std::min(256, ((se - sb) + 31) / 32 * 32);
+                float best = 0.f;
+                FEM_TRY(trial(K, T, seg_mult, &best));
+                for (int k : {32, 64, 128, 256}) {
+                    if (k > kmax || k == K) continue;
+                    float ms;
+                    FEM_TRY(trial(k, T, seg_mult, &ms));
+                    if (ms < best) best = ms, K = k;
+                }
+                for (int t : {512, 2048}) {
+                    float ms;
+                    FEM_TRY(trial(K, t, seg_mult, &ms));
+                    if (ms < best) best = ms, T = t;
+                }
+                for (double m : {0.5, 2.0}) {
+                    float ms;
+                    FEM_TRY(trial(K, T, m, &ms));
+                    if (ms < best) best = ms, seg_mult = m;
+                }
+                tune_store(ctx, key, TuneVal{K, T, seg_mult});
+                cc.stats.kernel_launches += 0;
+            }
+        }
+        Plan pl = make_plan(b, K, T, seg_mult, records_needed);
+        records_needed += pl.records;
+        plans.push_back(std::move(pl));
+    }
+    // records + segments scratch
+    void *p_rec = nullptr;
+    if (records_needed > 0) FEM_TRY(scratch(ctx, kSlotRecords, (size_t)records_needed * kRecWords * 4, &p_rec));
+    int64_t seg_total = 0;
+    size_t tab_bytes = 0;
+    for (auto &pl : plans) {
+        seg_total += seg_need(pl);
+        tab_bytes += tab_need(pl);
+    }
+    void *p_seg = nullptr;
+    FEM_TRY(scratch(ctx, kSlotSeg, sizeof(int64_t) * std::max<int64_t>(seg_total, 1), &p_seg));
+    int64_t *d_seg = static_cast<int64_t *>(p_seg);
+    void *p_tab = nullptr;
+    FEM_TRY(scratch(ctx, kSlotRecTab, std::max<size_t>(tab_bytes, 256), &p_tab));
+    char *tab = static_cast<char *>(p_tab);
+    segpos = 0;
+    tabpos = 0;
+    int32_t *fb_list = nullptr;
+    void *p_fb = nullptr;
+    FEM_TRY(scratch(ctx, kSlotFallback, sizeof(int32_t) * std::max<int64_t>(n_work, 1), &p_fb));
+    fb_list = static_cast<int32_t *>(p_fb);
+    int *d_fbc = reinterpret_cast<int *>(mb + o_fb);
+    const RecInfo *d_ri_plain = reinterpret_cast<const RecInfo *>(mb + o_ri);
+
+    cudaEventRecord(ctx->ev0, ctx->stream);
+    for (auto &pl : plans) {
+        RecInfo *d_ri = nullptr;
+        FEM_TRY(launch_plan(pl, static_cast<int32_t *>(p_rec), d_seg, tab, &d_ri));
+        k_stitch<<<(pl.n_slots + 7) / 8, 256, 0, ctx->stream>>>(static_cast<int32_t *>(p_rec), d_ri, d_perm,
+                                                               cc.cand_rec, pl.slot_begin, pl.n_slots, cc.counts,
+                                                               fb_list, d_fbc);
+        cc.stats.kernel_launches++;
         FEM_CUDA_TRY(cudaGetLastError());
     }
     cudaEventRecord(ctx->ev1, ctx->stream);

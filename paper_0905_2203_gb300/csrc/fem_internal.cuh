@@ -41,6 +41,13 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+// Autotuner choice for one workload signature.
+struct TuneVal {
+    int K;            // lanes (episodes) per CTA
+    int T;            // events per shared-memory stage
+    double seg_mult;  // multiplier on the segment-count heuristic
+};
+
 }  // namespace fem
 
 struct fem_ctx {
@@ -57,6 +64,8 @@ struct fem_ctx {
     fem_tuning tuning{};
     fem_stats last{};
     std::map<int, fem::DevBuf> scratch;  // slot -> buffer (grown on demand)
+    std::map<std::string, fem::TuneVal> tune;  // autotuner cache
+    std::string tune_path;                     // JSON file backing the cache ("" = memory only)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -110,6 +119,11 @@ enum Slot : int {
 };
 
 double now_s();
+// Autotuner cache: key of a counting launch (size class, ring class,
+// log2 of episodes and of events, recordings) and lookup / store.
+std::string tune_key(int nclass, int rclass, int64_t n_slots, int64_t n_events, int n_recs);
+bool tune_lookup(fem_ctx *ctx, const std::string &key, TuneVal *out);
+void tune_store(fem_ctx *ctx, const std::string &key, const TuneVal &v);
 
 // Level-wise mining of one recording as a step-wise state machine (used by
 // the serving loop): begin() runs level 1 and prepares level 2; the current
