@@ -95,6 +95,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def aggregate_over_ranks(local_ms: float, local_units: float, world: int, device=None):
+    """Replica aggregation: every rank did `local_units` episode-events in
+    `local_ms`; the job's time is the slowest rank's, and its throughput is
+    all ranks' work over that time.  Uses the process group of the caller
+    (NCCL on GPUs, gloo in the CPU tests)."""
+    if world <= 1:
+        return local_ms, local_units / (local_ms / 1e3)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms, local_units], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    t_max = float(mx[0].item())
+    return t_max, float(sm[1].item()) / (t_max / 1e3)
+
+
 def workload(name: str):
     if name == "c2":
         s, cfg = synth.c2_mid()
@@ -223,12 +241,7 @@ def run_ours(args, rank, world, local_rank):
     rel = sum(x["relevant_events"] for x in stats)
     cnt_ms = sum(x["count_kernel_ms"] for x in stats)
     launches = sum(x["kernel_launches"] for x in stats)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ee * world / (t_max / 1e3)
+    t_max, value = aggregate_over_ranks(ms, ee, world, dev)
 
     if args.quick:
         if rank == 0:

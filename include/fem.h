@@ -20,8 +20,8 @@
  *   - A context is used by one host thread at a time (calls on one context
  *     are serialised by an internal mutex); different contexts are
  *     independent.
- *   - Times are int32 ticks >= 0 (the tick is the caller's unit); types are
- *     uint16 ids < n_types.
+ *   - Times are int32 ticks in [0, 2^31 - 2] (the tick is the caller's
+ *     unit); types are uint16 ids < n_types.
  *
  * Episode semantics (section "Temporal Data Mining")
  *   An N-node episode is E_1 -(lo_1,hi_1]-> E_2 ... -> E_N.  An occurrence is a
@@ -48,7 +48,7 @@ extern "C" {
                                   [1, FEM_MAX_NODES], bad handle */
 #define FEM_ERR_UNSORTED -2    /* stream times decrease somewhere */
 #define FEM_ERR_DUP -3         /* two events with the same (type, time) */
-#define FEM_ERR_RANGE -4       /* a time < 0 */
+#define FEM_ERR_RANGE -4       /* a time < 0 or = 2^31 - 1 */
 #define FEM_ERR_NOMEM -5       /* the context's device-memory budget (or the
                                   device) cannot hold the request */
 #define FEM_ERR_TIMEOUT -6     /* a device-side wait gave up after its
@@ -91,9 +91,12 @@ typedef struct {
                              path (comparison baseline) instead of the tiled
                              kernels */
     int autotune;         /* 1 = time a few launch configurations (lanes per
-                             CTA, tile size, segment count) the first time a
-                             workload signature is seen and keep the fastest
-                             in the context's tuning cache */
+                             CTA, tile size, segment count, kernel) the first
+                             time a workload signature is seen and keep the
+                             fastest in the context's tuning cache */
+    int kernel;           /* 0 = choose per launch, 1 = always the tiled
+                             shared-memory broadcast kernel, 2 = the sparse
+                             per-type-list kernel where it applies */
 } fem_tuning;
 
 /* Per-call statistics filled by the counting / mining calls. */
@@ -108,6 +111,9 @@ typedef struct {
     int64_t candidates_pruned;  /* dropped by the upper-bound pre-pass */
     int64_t fallback_recounts;  /* episodes recounted unsegmented */
     int64_t kernel_launches;    /* library kernels launched by the call */
+    int64_t sparse_launches;    /* counting launches that used the sparse
+                                   per-type-list kernel (the rest used the
+                                   tiled broadcast kernel) */
     double count_kernel_ms;     /* device time of the exact-count kernels */
     double total_ms;            /* wall time of the call */
     int levels;                 /* mining: deepest level reached */
@@ -131,7 +137,7 @@ int fem_ctx_memory(const fem_ctx *ctx, size_t *used, size_t *budget);
  * it exists) are loaded now, and every new choice is written back.  The file
  * maps a workload signature ("n<size class>.r<ring class>.c<log2 episodes>.
  * e<log2 events>.m<recordings>") to [lanes_per_cta, tile_events,
- * segment multiplier].  NULL detaches the file (the cache stays in memory).
+ * segment multiplier, kernel (1 tiled, 2 sparse)].  NULL detaches the file (the cache stays in memory).
  * FEM_ERR_INVAL if the file exists but cannot be parsed. */
 int fem_ctx_set_autotune_cache(fem_ctx *ctx, const char *path);
 
@@ -143,7 +149,8 @@ int fem_ctx_set_autotune_cache(fem_ctx *ctx, const char *path);
  * frequency).
  *   types[n], times[n]  host or device (ptr_is_device); caller keeps them
  *   n >= 0, n_types in [1, 65536]
- * Errors: FEM_ERR_INVAL (type >= n_types), FEM_ERR_RANGE (time < 0),
+ * Errors: FEM_ERR_INVAL (type >= n_types), FEM_ERR_RANGE (time < 0 or
+ * time = 2^31 - 1),
  * FEM_ERR_UNSORTED, FEM_ERR_DUP (a repeated (type, time) would make two
  * events count once), FEM_ERR_NOMEM. */
 int fem_load_stream(fem_ctx *ctx, const uint16_t *types, const int32_t *times, int64_t n,

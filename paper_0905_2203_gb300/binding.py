@@ -50,14 +50,14 @@ class fem_cands(ctypes.Structure):
 
 class fem_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_cta", I32), ("segments", I32), ("tile_events", I32), ("prepass", I32),
-                ("plain_path", I32), ("autotune", I32)]
+                ("plain_path", I32), ("autotune", I32), ("kernel", I32)]
 
 
 class fem_stats(ctypes.Structure):
     _fields_ = [("episode_events", ctypes.c_double), ("counted_episode_events", ctypes.c_double),
                 ("relevant_events", ctypes.c_double),
                 ("candidates_counted", I64), ("candidates_pruned", I64),
-                ("fallback_recounts", I64), ("kernel_launches", I64),
+                ("fallback_recounts", I64), ("kernel_launches", I64), ("sparse_launches", I64),
                 ("count_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
                 ("levels", I32)]
 
@@ -187,8 +187,9 @@ class Context:
         except Exception:
             pass
 
-    def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0, plain_path=0, autotune=0):
-        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path, autotune)
+    def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0, plain_path=0, autotune=0,
+                   kernel=0):
+        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path, autotune, kernel)
         check(fem_ctx_set_tuning(self.h, ctypes.byref(t)), "fem_ctx_set_tuning")
 
     def reset_tuning(self):

@@ -47,7 +47,7 @@ static void tune_save(fem_ctx *ctx) {
         size_t i = 0;
         for (auto &kv : ctx->tune) {
             f << "  \"" << kv.first << "\": [" << kv.second.K << ", " << kv.second.T << ", " << kv.second.seg_mult
-              << "]" << (++i < ctx->tune.size() ? "," : "") << "\n";
+              << ", " << kv.second.kernel << "]" << (++i < ctx->tune.size() ? "," : "") << "\n";
         }
         f << "}\n";
     }
@@ -71,8 +71,10 @@ static bool tune_parse(const std::string &text, std::map<std::string, TuneVal> *
         const size_t b1 = text.find(']', b0);
         if (q1 == std::string::npos || b0 == std::string::npos || b1 == std::string::npos) return false;
         TuneVal v{};
-        if (std::sscanf(text.substr(b0 + 1, b1 - b0 - 1).c_str(), "%d , %d , %lf", &v.K, &v.T, &v.seg_mult) != 3)
-            return false;
+        v.kernel = 1;
+        const int got = std::sscanf(text.substr(b0 + 1, b1 - b0 - 1).c_str(), "%d , %d , %lf , %d", &v.K, &v.T,
+                                    &v.seg_mult, &v.kernel);
+        if (got < 3 || (v.kernel != 1 && v.kernel != 2)) return false;
         if (v.K < 32 || v.K > kMaxWarps * 32 || v.K % 32 || v.T < 256 || v.T > kMaxTile || v.T % 256 ||
             !(v.seg_mult > 0.0 && v.seg_mult < 64.0))
             return false;
@@ -170,7 +172,7 @@ __global__ void k_validate(const uint16_t *__restrict__ ty, const int32_t *__res
         const uint16_t a = ty[i];
         const int32_t t = tm[i];
         if (a >= n_types) e |= 1;
-        if (t < 0) e |= 2;
+        if (t < 0 || t == INT32_MAX) e |= 2;
         if (i > 0) {
             const int32_t tp = tm[i - 1];
             if (tp > t) e |= 4;
@@ -354,7 +356,7 @@ extern "C" int fem_ctx_set_tuning(fem_ctx *ctx, const fem_tuning *t) {
     if (t->lanes_per_cta < 0 || (t->lanes_per_cta % 32) != 0 || t->lanes_per_cta > kMaxWarps * 32)
         return FEM_ERR_INVAL;
     if (t->segments < 0 || t->tile_events < 0 || (t->tile_events % 256) != 0 ||
-        t->tile_events > kMaxTile)
+        t->tile_events > kMaxTile || t->kernel < 0 || t->kernel > 2)
         return FEM_ERR_INVAL;
     ctx->tuning = *t;
     return FEM_OK;
@@ -482,6 +484,8 @@ void fem::stream_free_unlocked(fem_stream *s) {
     dev_free(ctx, s->d_time, sizeof(int32_t) * cap);
     dev_free(ctx, s->d_freq, sizeof(uint32_t) * s->n_types);
     for (auto &kv : s->dens) dev_free(ctx, kv.second, sizeof(uint32_t) * s->n_types);
+    if (s->d_toff) dev_free(ctx, s->d_toff, sizeof(int64_t) * (s->n_types + 1));
+    if (s->d_ttime) dev_free(ctx, s->d_ttime, sizeof(int32_t) * std::max<int64_t>(s->n, 1));
     delete s;
 }
 

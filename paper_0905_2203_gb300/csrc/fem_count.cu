@@ -56,6 +56,8 @@ struct RecInfo {
     int slot_first;       // first launch slot of this recording in the bucket
     int64_t recbase;      // first record index of this recording
     const uint32_t *freq;
+    const int64_t *toff;  // per-type event lists (sparse kernel only)
+    const int32_t *ttime;
 };
 
 struct WorkItem {
@@ -305,7 +307,7 @@ __device__ __forceinline__ int clampi(int64_t v, int lo, int hi) {
 // events by its warp's union of episode types (bitmap + ballot), and offers
 // the surviving events, in order, to its 32 machines.
 template <int NMAX, int RR>
-__global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ? 3 : NMAX <= 4 ? 2 : 1))
+__global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ? 3 : NMAX == 2 ? 2 : 1))
     k_count_tiled(TiledArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int K = a.K, T = a.T;
@@ -487,23 +489,35 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ?
             st.finish();
             int4 *r = reinterpret_cast<int4 *>(a.rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P + item.p) *
                                                           kRecWords);
-            r[0] = make_int4(st.ncls | st.flags, st.cthr[0], st.cthr[1], st.cthr[2]);
-            r[1] = make_int4(st.cthr[3], (int32_t)st.ccnt[0], (int32_t)st.ccnt[1], (int32_t)st.ccnt[2]);
-            r[2] = make_int4((int32_t)st.ccnt[3], st.cprev[0], st.cprev[1], st.cprev[2]);
-            r[3] = make_int4(st.cprev[3], 0, 0, 0);
+            int32_t w[kRecWords];
+            w[0] = st.ncls | st.flags;
+#pragma unroll
+            for (int j = 0; j < kClasses; ++j) {
+                w[1 + j] = st.cthr[j];
+                w[1 + kClasses + j] = (int32_t)st.ccnt[j];
+                w[1 + 2 * kClasses + j] = st.cprev[j];
+            }
+#pragma unroll
+            for (int j = 1 + 3 * kClasses; j < kRecWords; ++j) w[j] = 0;
+#pragma unroll
+            for (int q = 0; q < kRecWords / 4; ++q) r[q] = make_int4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
     }
 }
 
 // Concat step: per episode (one warp), walk its segments in order with the
 // running end x of the last selected occurrence (minus infinity before the
-// first).  The lanes load 32 segment records at a time; the walk itself is a
-// short sequential loop over values broadcast from the lane that holds them.
-__global__ void k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
-                         const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec,
-                         int slot_begin, int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list,
-                         int *fb_count) {
-    const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// first).  The warp stages 32 segment records at a time in shared memory
+// (coalesced 16-byte loads); the walk reads them back as broadcasts.
+constexpr int kStitchWarps = 4;
+
+__global__ void __launch_bounds__(kStitchWarps * 32)
+    k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
+             const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
+             int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count) {
+    __shared__ __align__(16) int32_t buf[kStitchWarps][32 * kRecWords];
+    const int w = threadIdx.x >> 5;
+    const int wi = blockIdx.x * kStitchWarps + w;
     const int lane = threadIdx.x & 31;
     if (wi >= n_slots) return;
     const int slot = slot_begin + wi;
@@ -512,41 +526,27 @@ __global__ void k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restr
     const RecInfo ri = rinfo[r_id];
     const int4 *base = reinterpret_cast<const int4 *>(rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P) *
                                                       kRecWords);
+    int4 *sb = reinterpret_cast<int4 *>(buf[w]);
     int64_t x = INT64_MIN;
     uint32_t total = 0;
     bool bad = false;
     for (int p0 = 0; p0 < ri.P; p0 += 32) {
-        int4 q0 = make_int4(0, 0, 0, 0), q1 = q0, q2 = q0, q3 = q0;
-        if (p0 + lane < ri.P) {
-            const int4 *r = base + (int64_t)(p0 + lane) * (kRecWords / 4);
-            q0 = r[0];
-            q1 = r[1];
-            q2 = r[2];
-            q3 = r[3];
-        }
         const int m = min(32, ri.P - p0);
+        const int nvec = m * (kRecWords / 4);
+        __syncwarp();
+        for (int v = lane; v < nvec; v += 32) sb[v] = base[(int64_t)p0 * (kRecWords / 4) + v];
+        __syncwarp();
         for (int q = 0; q < m; ++q) {
-            const int meta = __shfl_sync(0xFFFFFFFFu, q0.x, q);
-            const int thr0 = __shfl_sync(0xFFFFFFFFu, q0.y, q), thr1 = __shfl_sync(0xFFFFFFFFu, q0.z, q);
-            const int thr2 = __shfl_sync(0xFFFFFFFFu, q0.w, q), thr3 = __shfl_sync(0xFFFFFFFFu, q1.x, q);
-            const int c0 = __shfl_sync(0xFFFFFFFFu, q1.y, q), c1 = __shfl_sync(0xFFFFFFFFu, q1.z, q);
-            const int c2 = __shfl_sync(0xFFFFFFFFu, q1.w, q), c3 = __shfl_sync(0xFFFFFFFFu, q2.x, q);
-            const int l0 = __shfl_sync(0xFFFFFFFFu, q2.y, q), l1 = __shfl_sync(0xFFFFFFFFu, q2.z, q);
-            const int l2 = __shfl_sync(0xFFFFFFFFu, q2.w, q), l3 = __shfl_sync(0xFFFFFFFFu, q3.x, q);
+            const int32_t *r = buf[w] + q * kRecWords;
+            const int meta = r[0];
             if (meta & (kMetaRingOverflow | kMetaClassOverflow)) bad = true;
             const int ncls = meta & 0xFF;
-            if (ncls > 0 && x < (int64_t)thr0) {
-                total += (uint32_t)c0;
-                x = l0;
-            } else if (ncls > 1 && x < (int64_t)thr1) {
-                total += (uint32_t)c1;
-                x = l1;
-            } else if (ncls > 2 && x < (int64_t)thr2) {
-                total += (uint32_t)c2;
-                x = l2;
-            } else if (ncls > 3 && x < (int64_t)thr3) {
-                total += (uint32_t)c3;
-                x = l3;
+            for (int j = 0; j < ncls; ++j) {
+                if (x < (int64_t)r[1 + j]) {
+                    total += (uint32_t)r[1 + kClasses + j];
+                    x = r[1 + 2 * kClasses + j];
+                    break;
+                }
             }
         }
     }
@@ -774,7 +774,7 @@ __global__ void k_part_count(const int32_t *__restrict__ key, int64_t n, int n_k
 
 __global__ void k_part_scatter(const int32_t *__restrict__ key, int64_t n, int n_keys, int64_t nblk,
                                const int32_t *__restrict__ blk, const int32_t *__restrict__ subset,
-                               int32_t *__restrict__ out) {
+                               int32_t *__restrict__ out, int32_t *__restrict__ out_key) {
     extern __shared__ int32_t run[];
     const int lane = threadIdx.x;
     for (int k = lane; k < n_keys; k += 32) run[k] = blk[(int64_t)k * nblk + blockIdx.x];
@@ -791,6 +791,7 @@ __global__ void k_part_scatter(const int32_t *__restrict__ key, int64_t n, int n
         __syncwarp();
         if (k >= 0) {
             out[pos] = subset ? subset[i] : (int32_t)i;
+            if (out_key) out_key[pos] = k;
             if (rank == 0) run[k] += __popc(peers);
         }
         __syncwarp();
@@ -896,6 +897,302 @@ __global__ void k_segments(const int32_t *__restrict__ tm, int64_t n, int P, int
 
 // ---------------------------------------------------------------------------
 // Host driver.
+// ---------------------------------------------------------------------------
+// Sparse counting kernel: one thread per (episode, segment).  Instead of
+// reading every event of the segment, the thread merges, in time order, the
+// per-type event lists of its episode's node types (the per-type index lists
+// of section "Parallel Local Tracking"), so it touches only the events its
+// episode can use.  The machine (rings, Algorithm 1 per entry class, halo)
+// and the records are those of the tiled kernel; k_stitch reads both.
+struct SparseArgs {
+    const RecInfo *rinfo;
+    int n_recs;
+    int64_t rec_first;    // first record index of this plan
+    int64_t n_threads;    // records of this plan = sum over recordings of c_r * P_r
+    const int64_t *offs;
+    const uint16_t *ctypes;
+    const int32_t *clo;
+    const int32_t *chi;
+    const int32_t *slot2cand;
+    int relaxed;
+    int R;                // ring capacity (shared-memory rings only)
+    int32_t *rec;
+};
+
+// RR > 0: register rings; RR == 0: shared-memory rings of a.R entries per
+// node (64-thread blocks; node k entry r of thread i at (k*R + r)*64 + i).
+template <int NMAX, int RR>
+__global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs a) {
+    extern __shared__ int32_t s_ring[];
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= a.n_threads) return;
+    const int64_t tr = a.rec_first + t;
+    int lo_r = 0, hi_r = a.n_recs;  // last recording whose records start at or before tr
+    while (hi_r - lo_r > 1) {
+        const int mid = (lo_r + hi_r) >> 1;
+        if (a.rinfo[mid].recbase <= tr) lo_r = mid; else hi_r = mid;
+    }
+    const RecInfo ri = a.rinfo[lo_r];
+    const int64_t local = tr - ri.recbase;
+    const int slot = ri.slot_first + (int)(local / ri.P);
+    const int p = (int)(local % ri.P);
+    const int cand = a.slot2cand[slot];
+    const int64_t o = a.offs[cand];
+    const int N = (int)(a.offs[cand + 1] - o);
+    const int64_t eo = o - cand;
+
+    Machine<NMAX, RR> st;
+    st.N = N;
+    st.ncls = 0;
+    st.live = 0;
+    st.M = INT32_MIN;
+    st.open = 1;
+    st.flags = 0;
+    int64_t sumhi = 0;
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) st.E[k] = k < N ? (uint32_t)a.ctypes[o + k] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < NMAX - 1; ++k) {
+        st.lo[k] = (k < N - 1) ? (a.relaxed ? 0 : a.clo[eo + k]) : 0;
+        st.hi[k] = (k < N - 1) ? a.chi[eo + k] : 0;
+        sumhi += st.hi[k];
+    }
+#pragma unroll
+    for (int j = 0; j < kClasses; ++j) {
+        st.cthr[j] = 0;
+        st.cprev[j] = 0;
+        st.ccnt[j] = 0;
+    }
+    if (RR == 0)
+        st.rings.init(s_ring + threadIdx.x, s_ring + (NMAX - 1) * a.R * blockDim.x + threadIdx.x, a.R, blockDim.x);
+    else
+        st.rings.init(nullptr, nullptr, 0, 0);
+
+    const int64_t seg_b = ri.seg[p], seg_e = ri.seg[p + 1];
+    int32_t Tp = 0;
+    int32_t head[NMAX];
+    int32_t cur[NMAX], end[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+        head[k] = INT32_MAX;
+        cur[k] = 0;
+        end[k] = 0;
+    }
+    if (seg_b < seg_e) {
+        Tp = ri.time[seg_b];
+        const int64_t haloT = (p == 0) ? INT64_MIN : (int64_t)Tp - sumhi;
+        const int32_t Tend = (seg_e < ri.n) ? ri.time[seg_e] : INT32_MAX;
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            if (k >= N) continue;
+            bool first = true;  // a repeated type is merged once
+#pragma unroll
+            for (int j = 0; j < k; ++j)
+                if (st.E[j] == st.E[k]) first = false;
+            if (!first) continue;
+            const int64_t b0 = ri.toff[st.E[k]], b1 = ri.toff[st.E[k] + 1];
+            int64_t lo_i = b0, hi_i = b1;  // first time >= haloT
+            while (lo_i < hi_i) {
+                const int64_t mid = (lo_i + hi_i) >> 1;
+                if ((int64_t)ri.ttime[mid] < haloT) lo_i = mid + 1; else hi_i = mid;
+            }
+            int64_t e_i = b1;
+            if (seg_e < ri.n) {  // first time >= Tend
+                int64_t l2 = lo_i, h2 = b1;
+                while (l2 < h2) {
+                    const int64_t mid = (l2 + h2) >> 1;
+                    if (ri.ttime[mid] < Tend) l2 = mid + 1; else h2 = mid;
+                }
+                e_i = l2;
+            }
+            cur[k] = (int32_t)lo_i;
+            end[k] = (int32_t)e_i;
+            head[k] = lo_i < e_i ? ri.ttime[lo_i] : INT32_MAX;
+        }
+        for (;;) {
+            int32_t best = INT32_MAX;
+            int bk = -1;
+#pragma unroll
+            for (int k = 0; k < NMAX; ++k)
+                if (head[k] < best) {
+                    best = head[k];
+                    bk = k;
+                }
+            if (bk < 0) break;
+            uint32_t ety = 0;
+#pragma unroll
+            for (int k = 0; k < NMAX; ++k)
+                if (k == bk) {
+                    ety = st.E[k];
+                    cur[k] += 1;
+                    head[k] = cur[k] < end[k] ? ri.ttime[cur[k]] : INT32_MAX;
+                }
+            st.step(ety, best, best >= Tp, Tp);
+        }
+    }
+    st.finish();
+    int4 *r = reinterpret_cast<int4 *>(a.rec + tr * kRecWords);
+    int32_t w[kRecWords];
+    w[0] = st.ncls | st.flags;
+#pragma unroll
+    for (int j = 0; j < kClasses; ++j) {
+        w[1 + j] = st.cthr[j];
+        w[1 + kClasses + j] = (int32_t)st.ccnt[j];
+        w[1 + 2 * kClasses + j] = st.cprev[j];
+    }
+#pragma unroll
+    for (int j = 1 + 3 * kClasses; j < kRecWords; ++j) w[j] = 0;
+#pragma unroll
+    for (int q = 0; q < kRecWords / 4; ++q) r[q] = make_int4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+}
+
+// Cost inputs for choosing between the tiled and the sparse kernel, per
+// bucket: for each group of 32 consecutive slots (one warp of the tiled
+// kernel), the events whose type some lane uses (what the tiled warp reads),
+// and the largest per-episode event count (what the slowest sparse lane reads).
+__global__ void k_group_stats(const int32_t *__restrict__ perm, const int32_t *__restrict__ slot_key, int64_t n_work,
+                              int n_recs, const int64_t *__restrict__ offs, const uint16_t *__restrict__ ctypes,
+                              const RecInfo *__restrict__ rinfo, unsigned long long *dense_units,
+                              unsigned long long *sparse_units) {
+    __shared__ uint32_t bm[4][kBitmapWords];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = blockIdx.x * 4 + w;
+    const int64_t slot = g * 32 + lane;
+    for (int i = lane; i < kBitmapWords; i += 32) bm[w][i] = 0;
+    __syncwarp();
+    unsigned long long cov = 0, rel = 0;
+    int b = -1;
+    if (slot < n_work) {
+        const int cand = perm[slot];
+        const int key = slot_key[slot];
+        b = key / n_recs;
+        const uint32_t *freq = rinfo[key % n_recs].freq;
+        for (int64_t q = offs[cand]; q < offs[cand + 1]; ++q) {
+            const uint32_t ty = ctypes[q];
+            const uint32_t f = freq[ty];
+            rel += f;
+            const uint32_t bit = 1u << (ty & 31);
+            const uint32_t old = atomicOr(&bm[w][(ty >> 5) & (kBitmapWords - 1)], bit);
+            if (!(old & bit)) cov += f;
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        cov += __shfl_down_sync(0xFFFFFFFFu, cov, d);
+        const unsigned long long o = __shfl_down_sync(0xFFFFFFFFu, rel, d);
+        rel = o > rel ? o : rel;
+    }
+    const int b0 = __shfl_sync(0xFFFFFFFFu, b, 0);
+    if (lane == 0 && b0 >= 0) {
+        atomicAdd(&dense_units[b0], cov);
+        atomicAdd(&sparse_units[b0], rel);
+    }
+}
+
+// Per-type event lists of a stream: a stable partition of the event indices
+// by type, then the times gathered in that order.
+__global__ void k_widen_types(const uint16_t *__restrict__ ty, int64_t n, int32_t *__restrict__ key) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        key[i] = ty[i];
+}
+
+__global__ void k_gather_ttime(const int32_t *__restrict__ perm, const int32_t *__restrict__ tm, int64_t n,
+                               int32_t *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = tm[perm[i]];
+}
+
+__global__ void k_toff(const int32_t *__restrict__ keyoff, int n_types, int64_t n, int64_t *__restrict__ toff) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n_types) toff[a] = keyoff[a];
+    if (a == n_types) toff[a] = n;
+}
+
+// Temporary device allocations freed together (after the stream drains).
+struct TmpDev {
+    fem_ctx *ctx;
+    std::vector<std::pair<void *, size_t>> held;
+    explicit TmpDev(fem_ctx *c) : ctx(c) {}
+    ~TmpDev() {
+        if (held.empty()) return;
+        cudaStreamSynchronize(ctx->stream);
+        for (auto &h : held) dev_free(ctx, h.first, h.second);
+    }
+    template <typename T>
+    int get(T **p, size_t n) {
+        void *q = nullptr;
+        const size_t b = std::max<size_t>(n, 1) * sizeof(T);
+        FEM_TRY(dev_alloc(ctx, &q, b));
+        held.push_back({q, b});
+        *p = static_cast<T *>(q);
+        return FEM_OK;
+    }
+};
+
+int stream_bytype(fem_ctx *ctx, fem_stream *s) {
+    if (s->d_ttime) return FEM_OK;
+    if (s->n_types > 8192 || s->n > INT32_MAX / 2) return FEM_ERR_INVAL;
+    const int64_t n = s->n;
+    void *p1 = nullptr, *p2 = nullptr;
+    FEM_TRY(dev_alloc(ctx, &p1, sizeof(int64_t) * (s->n_types + 1)));
+    const int st2 = dev_alloc(ctx, &p2, sizeof(int32_t) * std::max<int64_t>(n, 1));
+    if (st2 != FEM_OK) {
+        dev_free(ctx, p1, sizeof(int64_t) * (s->n_types + 1));
+        return st2;
+    }
+    int64_t *toff = static_cast<int64_t *>(p1);
+    int32_t *ttime = static_cast<int32_t *>(p2);
+    const int n_keys = (int)s->n_types;
+    const int64_t nblk = std::max<int64_t>(1, (n + kPartBlock - 1) / kPartBlock);
+    const int64_t tab_n = (int64_t)n_keys * nblk;
+    TmpDev tmp(ctx);
+    int32_t *key, *perm, *blk, *stmp, *koff;
+    int st = tmp.get(&key, std::max<int64_t>(n, 1));
+    if (st == FEM_OK) st = tmp.get(&perm, std::max<int64_t>(n, 1));
+    if (st == FEM_OK) st = tmp.get(&blk, tab_n);
+    if (st == FEM_OK) st = tmp.get(&stmp, tab_n / kScanBlock + 2);
+    if (st == FEM_OK) st = tmp.get(&koff, n_keys + 1);
+    if (st != FEM_OK) {
+        dev_free(ctx, p1, sizeof(int64_t) * (s->n_types + 1));
+        dev_free(ctx, p2, sizeof(int32_t) * std::max<int64_t>(n, 1));
+        return st;
+    }
+    cudaStream_t cs = ctx->stream;
+    if (n > 0) {
+        const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 8 * ctx->n_sm);
+        k_widen_types<<<g, 256, 0, cs>>>(s->d_type, n, key);
+        k_part_count<<<(unsigned)nblk, 256, n_keys * 4, cs>>>(key, n, n_keys, nblk, blk);
+        FEM_TRY(scan_exclusive(cs, blk, tab_n, stmp, nullptr, nullptr));
+        k_part_scatter<<<(unsigned)nblk, 32, n_keys * 4, cs>>>(key, n, n_keys, nblk, blk, nullptr, perm, nullptr);
+        k_gather_keyoff<<<(n_keys + 255) / 256, 256, 0, cs>>>(blk, n_keys, nblk, koff);
+        k_gather_ttime<<<g, 256, 0, cs>>>(perm, s->d_time, n, ttime);
+        k_toff<<<(n_keys + 1 + 255) / 256, 256, 0, cs>>>(koff, n_keys, n, toff);
+    } else {
+        FEM_CUDA_TRY(cudaMemsetAsync(toff, 0, sizeof(int64_t) * (s->n_types + 1), cs));
+    }
+    FEM_CUDA_TRY(cudaGetLastError());
+    FEM_CUDA_TRY(cudaStreamSynchronize(cs));
+    s->d_toff = toff;
+    s->d_ttime = ttime;
+    s->bytes += sizeof(int64_t) * (s->n_types + 1) + sizeof(int32_t) * n;
+    return FEM_OK;
+}
+
+typedef void (*SparseFn)(SparseArgs);
+
+// Shared memory of a sparse block with shared-memory rings (64 threads).
+static size_t sparse_smem(int nclass, int R) { return (size_t)2 * (nmax_of_class(nclass) - 1) * R * 64 * 4; }
+
+static SparseFn sparse_fn(int nclass, int rr) {
+#define FEM_SF(NM, R_) \
+    if (nmax_of_class(nclass) == NM && rr == R_) return k_count_sparse<NM, R_>;
+    FEM_SF(2, 2) FEM_SF(2, 4) FEM_SF(2, 8) FEM_SF(2, 0)
+    FEM_SF(4, 2) FEM_SF(4, 4) FEM_SF(4, 0)
+    FEM_SF(8, 2) FEM_SF(8, 0)
+    FEM_SF(16, 0)
+#undef FEM_SF
+    return nullptr;
+}
+
 // Register-ring capacity compiled for (nclass, R); 0 = shared-memory rings.
 static int reg_ring_for(int nclass, int R) {
     const int cap = max_reg_ring(nclass);
@@ -959,6 +1256,7 @@ struct CountCall {
     uint32_t *counts = nullptr;          // device, n_cand
     std::vector<int32_t> lo_vals;        // distinct lo values (host)
     int mode = 0;                        // 0 exact, 1 plain, 2 relaxed
+    double seg_div = 1.0;                // fallback rounds divide the segment count
     fem_stats stats{};
     float count_ms = 0.f;
 };
@@ -993,14 +1291,15 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     };
     const size_t o_lo = carve(lov.size() * 4), o_nt = carve(n_recs * 4),
                  o_dp = carve(dens_h.size() * sizeof(void *)), o_ri = carve(n_recs * sizeof(RecInfo)),
-                 o_bm = carve(3 * kBuckets * 4), o_rel = carve(8), o_fb = carve(8);
+                 o_bm = carve(3 * kBuckets * 4), o_rel = carve(8), o_fb = carve(8),
+                 o_units = carve(2 * kBuckets * 8);
     void *misc = nullptr;
     FEM_TRY(scratch(ctx, kSlotMisc, off, &misc));
     char *mb = static_cast<char *>(misc);
     std::vector<RecInfo> ri_h(n_recs);
     for (int r = 0; r < n_recs; ++r) {
         ri_h[r] = RecInfo{cc.recs[r]->d_type, cc.recs[r]->d_time, cc.recs[r]->n, nullptr, 1, 0, 0,
-                          cc.recs[r]->d_freq};
+                          cc.recs[r]->d_freq, nullptr, nullptr};
     }
     FEM_CUDA_TRY(cudaMemcpyAsync(mb + o_lo, lov.data(), lov.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     FEM_CUDA_TRY(cudaMemcpyAsync(mb + o_nt, nt_h.data(), n_recs * 4, cudaMemcpyHostToDevice, ctx->stream));
@@ -1011,12 +1310,14 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     FEM_CUDA_TRY(cudaMemsetAsync(mb + o_bm, 0, 3 * kBuckets * 4, ctx->stream));
     FEM_CUDA_TRY(cudaMemsetAsync(mb + o_rel, 0, 8, ctx->stream));
     FEM_CUDA_TRY(cudaMemsetAsync(mb + o_fb, 0, 8, ctx->stream));
+    FEM_CUDA_TRY(cudaMemsetAsync(mb + o_units, 0, 2 * kBuckets * 8, ctx->stream));
 
     // --- prep
     void *p_key, *p_perm, *p_blk;
-    FEM_TRY(scratch(ctx, kSlotPrep, sizeof(int32_t) * std::max<int64_t>(n_work, 1) * 2, &p_key));
+    FEM_TRY(scratch(ctx, kSlotPrep, sizeof(int32_t) * std::max<int64_t>(n_work, 1) * 3, &p_key));
     int32_t *d_key = static_cast<int32_t *>(p_key);
     int32_t *d_ring = d_key + std::max<int64_t>(n_work, 1);
+    int32_t *d_slotkey = d_ring + std::max<int64_t>(n_work, 1);
     FEM_TRY(scratch(ctx, kSlotPerm, sizeof(int32_t) * std::max<int64_t>(n_work, 1), &p_perm));
     int32_t *d_perm = static_cast<int32_t *>(p_perm);
     const int pb = 256;
@@ -1054,9 +1355,13 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         k_part_count<<<(unsigned)nblk, 256, n_keys * 4, ctx->stream>>>(d_key, n_work, n_keys, nblk, d_blk);
         FEM_TRY(scan_exclusive(ctx->stream, d_blk, tab_n, d_scan_tmp, nullptr, &cc.stats.kernel_launches));
         k_part_scatter<<<(unsigned)nblk, 32, n_keys * 4, ctx->stream>>>(d_key, n_work, n_keys, nblk, d_blk,
-                                                                        subset, d_perm);
+                                                                        subset, d_perm, d_slotkey);
         k_gather_keyoff<<<(n_keys + 255) / 256, 256, 0, ctx->stream>>>(d_blk, n_keys, nblk, d_keyoff);
-        cc.stats.kernel_launches += 4;
+        unsigned long long *units = reinterpret_cast<unsigned long long *>(mb + o_units);
+        k_group_stats<<<(unsigned)((n_work + 127) / 128), 128, 0, ctx->stream>>>(
+            d_perm, d_slotkey, n_work, n_recs, cc.offs, cc.types, reinterpret_cast<const RecInfo *>(mb + o_ri), units,
+            units + kBuckets);
+        cc.stats.kernel_launches += 5;
         FEM_CUDA_TRY(cudaGetLastError());
     }
     std::vector<int32_t> key_off(n_keys + 1, 0);
@@ -1066,6 +1371,8 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         FEM_CUDA_TRY(cudaMemcpyAsync(key_off.data(), d_keyoff, 4 * n_keys, cudaMemcpyDeviceToHost, ctx->stream));
     FEM_CUDA_TRY(cudaMemcpyAsync(bmax.data(), mb + o_bm, 3 * kBuckets * 4, cudaMemcpyDeviceToHost, ctx->stream));
     FEM_CUDA_TRY(cudaMemcpyAsync(&relv, mb + o_rel, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<unsigned long long> units_h(2 * kBuckets, 0);
+    FEM_CUDA_TRY(cudaMemcpyAsync(units_h.data(), mb + o_units, 2 * kBuckets * 8, cudaMemcpyDeviceToHost, ctx->stream));
     FEM_TRY(sync_status(ctx));
     key_off[n_keys] = (int32_t)n_work;
     if (force_segments == 0)
@@ -1077,6 +1384,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     const int T_def = ctx->tuning.tile_events > 0 ? ctx->tuning.tile_events : 1024;
     struct Plan {
         int bucket;
+        bool sparse;
         int K, R, nclass, T;
         std::vector<RecInfo> ri;
         std::vector<WorkItem> items;
@@ -1086,31 +1394,46 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     bool small_alpha = true;
     for (auto *rs : cc.recs)
         if (rs->n_types > 128) small_alpha = false;
-    // Builds the plan of bucket b for a given CTA width, tile and segment
-    // multiplier (records start at recbase).
-    auto make_plan = [&](int b, int K, int T, double seg_mult, int64_t recbase) {
+    // Builds the plan of bucket b: tiled (CTA width K, tile T) or sparse, with
+    // a multiplier on the segment-count heuristic; records start at recbase.
+    auto make_plan = [&](int b, bool sparse, int K, int T, double seg_mult, int64_t recbase) {
         const int sb = key_off[b * n_recs], se = key_off[(b + 1) * n_recs];
         Plan pl;
         pl.bucket = b;
+        pl.sparse = sparse;
         pl.nclass = b / kBucketRing;
         pl.R = std::max(bmax[b], 2);
         pl.T = T;
-        while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > 100 * 1024) K -= 32;
-        while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > (size_t)ctx->smem_optin - 2048) K -= 32;
+        if (!sparse) {
+            while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > 100 * 1024) K -= 32;
+            while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > (size_t)ctx->smem_optin - 2048) K -= 32;
+        }
         pl.K = K;
         pl.slot_begin = sb;
         pl.n_slots = se - sb;
-        const size_t sm = tiled_smem_rt(pl.nclass, K, pl.R, T);
-        const int occ = occupancy_tiled(pl.nclass, K, pl.R, sm);
         const int64_t max_sumhi = bmax[2 * kBuckets + b];
-        // segments: aim for ~4 CTAs per resident slot across the bucket
-        const int64_t desired = (int64_t)4 * ctx->n_sm * occ;
-        double work = 0;
-        for (int r = 0; r < n_recs; ++r) {
-            const int c = key_off[b * n_recs + r + 1] - key_off[b * n_recs + r];
-            if (c > 0) work += (double)((c + K - 1) / K) * (double)cc.recs[r]->n;
+        double seg_len;
+        if (sparse) {
+            // enough (episode, segment) threads to fill the GPU ~4 times
+            const double desired = 4.0 * ctx->n_sm * 2048.0;
+            double work = 0;
+            for (int r = 0; r < n_recs; ++r) {
+                const int c = key_off[b * n_recs + r + 1] - key_off[b * n_recs + r];
+                work += (double)c * (double)cc.recs[r]->n;
+            }
+            seg_len = std::max(1.0, work / desired) / seg_mult;
+        } else {
+            const size_t sm = tiled_smem_rt(pl.nclass, K, pl.R, T);
+            const int occ = occupancy_tiled(pl.nclass, K, pl.R, sm);
+            // segments: aim for ~4 CTAs per resident slot across the bucket
+            const int64_t desired = (int64_t)4 * ctx->n_sm * occ;
+            double work = 0;
+            for (int r = 0; r < n_recs; ++r) {
+                const int c = key_off[b * n_recs + r + 1] - key_off[b * n_recs + r];
+                if (c > 0) work += (double)((c + K - 1) / K) * (double)cc.recs[r]->n;
+            }
+            seg_len = std::max(1.0, work / (double)std::max<int64_t>(desired, 1)) / seg_mult;
         }
-        const double seg_len = std::max(1.0, work / (double)std::max<int64_t>(desired, 1)) / seg_mult;
         pl.ri.resize(n_recs);
         int64_t rb = recbase;
         for (int r = 0; r < n_recs; ++r) {
@@ -1122,29 +1445,57 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                 P = force_segments;
             } else if (ctx->tuning.segments > 0) {
                 // explicit request: allow short segments (down to ~16 events)
-                P = std::max(1, std::min<int>(ctx->tuning.segments, (int)std::max<int64_t>(1, s->n / 16)));
+                P = std::max(1, std::min<int>((int)(ctx->tuning.segments / cc.seg_div),
+                                              (int)std::max<int64_t>(1, s->n / 16)));
             } else if (c > 0) {
                 // shortest useful segment: 1024 events, and at least 8 halos
                 // (the halo is sum(hi) of time at the stream's mean rate)
                 const double span = std::max(1.0, (double)s->t_last - (double)s->t_first);
                 const double halo_ev = (double)s->n * (double)max_sumhi / span;
                 const double min_seg = std::max(1024.0, 8.0 * halo_ev);
-                P = (int)std::max<double>(1.0, std::min<double>((double)s->n / seg_len, (double)s->n / min_seg));
+                P = (int)std::max<double>(1.0, std::min<double>((double)s->n / seg_len, (double)s->n / min_seg) /
+                                                   cc.seg_div);
             }
-            pl.ri[r] = RecInfo{s->d_type, s->d_time, s->n, nullptr, P, ks, rb, s->d_freq};
+            pl.ri[r] = RecInfo{s->d_type, s->d_time, s->n, nullptr, P, ks, rb, s->d_freq, s->d_toff, s->d_ttime};
             if (c > 0) {
-                for (int cb = 0; cb < c; cb += K)
-                    for (int p = 0; p < P; ++p) pl.items.push_back(WorkItem{r, ks + cb, std::min(K, c - cb), p});
+                if (!sparse)
+                    for (int cb = 0; cb < c; cb += K)
+                        for (int p = 0; p < P; ++p) pl.items.push_back(WorkItem{r, ks + cb, std::min(K, c - cb), p});
                 rb += (int64_t)c * P;
             }
         }
         pl.records = rb - recbase;
+        // Records take kRecWords words per (episode, segment): keep a plan's
+        // records within a quarter of the context's free budget by using
+        // fewer segments (never fewer than one).
+        const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+        const double cap = std::max<double>((double)pl.n_slots, (double)free_b / 4.0 / (kRecWords * 4.0));
+        if (force_segments == 0 && (double)pl.records > cap) {
+            const double f = cap / (double)pl.records;
+            pl.items.clear();
+            rb = recbase;
+            for (int r = 0; r < n_recs; ++r) {
+                const int ks = key_off[b * n_recs + r], c = key_off[b * n_recs + r + 1] - ks;
+                const int P = std::max(1, (int)(pl.ri[r].P * f));
+                pl.ri[r].P = P;
+                pl.ri[r].recbase = rb;
+                if (c > 0) {
+                    if (!sparse)
+                        for (int cb = 0; cb < c; cb += K)
+                            for (int p = 0; p < P; ++p) pl.items.push_back(WorkItem{r, ks + cb, std::min(K, c - cb), p});
+                    rb += (int64_t)c * P;
+                }
+            }
+            pl.records = rb - recbase;
+        }
         return pl;
     };
-    // Uploads a plan's tables and launches its tiled kernel (no stitch).
+    // Uploads a plan's tables and launches its counting kernel (no stitch).
+    // `limit` > 0 launches only that many work items / threads (autotuner).
     int64_t segpos = 0;
     size_t tabpos = 0;
-    auto launch_plan = [&](Plan &pl, int32_t *rec_base, int64_t *d_seg, char *tab, RecInfo **d_ri_out) -> int {
+    auto launch_plan = [&](Plan &pl, int32_t *rec_base, int64_t *d_seg, char *tab, RecInfo **d_ri_out,
+                           int64_t limit) -> int {
         for (int r = 0; r < n_recs; ++r) {
             pl.ri[r].seg = d_seg + segpos;
             k_segments<<<(pl.ri[r].P + 1 + 127) / 128, 128, 0, ctx->stream>>>(cc.recs[r]->d_time, cc.recs[r]->n,
@@ -1154,10 +1505,38 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         }
         RecInfo *d_ri = reinterpret_cast<RecInfo *>(tab + tabpos);
         tabpos += (pl.ri.size() * sizeof(RecInfo) + 255) & ~size_t(255);
-        WorkItem *d_items = reinterpret_cast<WorkItem *>(tab + tabpos);
-        tabpos += (pl.items.size() * sizeof(WorkItem) + 255) & ~size_t(255);
         FEM_CUDA_TRY(cudaMemcpyAsync(d_ri, pl.ri.data(), pl.ri.size() * sizeof(RecInfo), cudaMemcpyHostToDevice,
                                      ctx->stream));
+        *d_ri_out = d_ri;
+        if (pl.sparse) {
+            SparseArgs sa{};
+            sa.rinfo = d_ri;
+            sa.n_recs = n_recs;
+            sa.rec_first = pl.ri.empty() ? 0 : pl.ri[0].recbase;
+            sa.n_threads = limit > 0 ? std::min(limit, pl.records) : pl.records;
+            sa.offs = cc.offs;
+            sa.ctypes = cc.types;
+            sa.clo = cc.lo;
+            sa.chi = cc.hi;
+            sa.slot2cand = d_perm;
+            sa.relaxed = cc.mode == 2;
+            sa.rec = rec_base;
+            sa.R = pl.R;
+            const int rr = reg_ring_for(pl.nclass, pl.R);
+            SparseFn f = sparse_fn(pl.nclass, rr);
+            if (!f) return FEM_ERR_CUDA;
+            const int bs = rr ? 128 : 64;
+            const size_t sm = rr ? 0 : sparse_smem(pl.nclass, pl.R);
+            if (sm > 48 * 1024 &&
+                cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+                return FEM_ERR_CUDA;
+            if (sa.n_threads > 0) f<<<(unsigned)((sa.n_threads + bs - 1) / bs), bs, sm, ctx->stream>>>(sa);
+            FEM_CUDA_TRY(cudaGetLastError());
+            cc.stats.kernel_launches++;
+            return FEM_OK;
+        }
+        WorkItem *d_items = reinterpret_cast<WorkItem *>(tab + tabpos);
+        tabpos += (pl.items.size() * sizeof(WorkItem) + 255) & ~size_t(255);
         FEM_CUDA_TRY(cudaMemcpyAsync(d_items, pl.items.data(), pl.items.size() * sizeof(WorkItem),
                                      cudaMemcpyHostToDevice, ctx->stream));
         TiledArgs ta{};
@@ -1175,9 +1554,9 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         ta.small_alpha = small_alpha ? 1 : 0;
         ta.rec = rec_base;
         ta.status = ctx->d_status;
-        FEM_TRY(launch_tiled(ctx, pl.nclass, (int)pl.items.size(), pl.K, pl.R, pl.T, ta));
+        const int64_t n_items = limit > 0 ? std::min<int64_t>(limit, pl.items.size()) : (int64_t)pl.items.size();
+        FEM_TRY(launch_tiled(ctx, pl.nclass, (int)n_items, pl.K, pl.R, pl.T, ta));
         cc.stats.kernel_launches++;
-        *d_ri_out = d_ri;
         return FEM_OK;
     };
     // Per-plan scratch sizes (tables and segments) for a plan.
@@ -1188,6 +1567,14 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         int64_t t = 0;
         for (auto &r : pl.ri) t += r.P + 1;
         return t;
+    };
+    // Work units a plan launches (tiled: CTAs; sparse: threads) and a sample
+    // of about two waves for timing trials.
+    auto units_of = [&](const Plan &pl) { return pl.sparse ? pl.records : (int64_t)pl.items.size(); };
+    auto sample_of = [&](const Plan &pl) -> int64_t {
+        if (pl.sparse) return (int64_t)2 * ctx->n_sm * 2048;
+        const size_t sm = tiled_smem_rt(pl.nclass, pl.K, pl.R, pl.T);
+        return (int64_t)2 * ctx->n_sm * occupancy_tiled(pl.nclass, pl.K, pl.R, sm);
     };
 
     std::vector<Plan> plans;
@@ -1204,27 +1591,52 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             plain_buckets.push_back(b);
             continue;
         }
+        const int nclass = b / kBucketRing;
+        const int R = std::max(bmax[b], 2);
+        // the sparse kernel needs register rings and per-type lists
+        bool sparse_ok = sparse_fn(nclass, reg_ring_for(nclass, R)) != nullptr &&
+                         (reg_ring_for(nclass, R) > 0 || sparse_smem(nclass, R) <= (size_t)ctx->smem_optin - 1024);
+        for (int r = 0; r < n_recs && sparse_ok; ++r)
+            if (key_off[b * n_recs + r + 1] > key_off[b * n_recs + r] && cc.recs[r]->n_types > 8192)
+                sparse_ok = false;
+        // cost model: the tiled warp pays for every event whose type one of
+        // its lanes uses (~64 issue slots each) plus the filter scan; a sparse
+        // warp pays for the longest merged list among its lanes
+        double nbar = 0;
+        for (int r = 0; r < n_recs; ++r)
+            if (key_off[b * n_recs + r + 1] > key_off[b * n_recs + r]) nbar = std::max(nbar, (double)cc.recs[r]->n);
+        const double groups = std::ceil((se - sb) / 32.0);
+        const double cost_dense = (double)units_h[b] * 64.0 + groups * nbar / 32.0 * 12.0;
+        const double cost_sparse = (double)units_h[kBuckets + b] * (4.0 * nmax_of_class(nclass) + 40.0);
+        bool sparse = sparse_ok && cost_sparse < cost_dense;
+        if (ctx->tuning.kernel == 1) sparse = false;
+        if (ctx->tuning.kernel == 2) sparse = sparse_ok;
         // lanes per CTA: up to 256, but no wider than the bucket needs
         int K = ctx->tuning.lanes_per_cta > 0 ? ctx->tuning.lanes_per_cta : std::min(256, ((se - sb) + 31) / 32 * 32);
         int T = T_def;
         double seg_mult = 1.0;
-        const bool tunable = force_segments == 0 && ctx->tuning.lanes_per_cta == 0 && ctx->tuning.segments == 0 &&
-                             ctx->tuning.tile_events == 0;
+        const bool tunable = force_segments == 0 && cc.seg_div == 1.0 && ctx->tuning.lanes_per_cta == 0 &&
+                             ctx->tuning.segments == 0 && ctx->tuning.tile_events == 0 && ctx->tuning.kernel == 0;
         if (tunable) {
             int64_t nmax_ev = 0;
             for (int r = 0; r < n_recs; ++r)
                 if (key_off[b * n_recs + r + 1] > key_off[b * n_recs + r]) nmax_ev = std::max(nmax_ev, cc.recs[r]->n);
-            const std::string key = tune_key(b / kBucketRing, b % kBucketRing, se - sb, nmax_ev, n_recs);
+            const std::string key = tune_key(nclass, b % kBucketRing, se - sb, nmax_ev, n_recs);
             TuneVal tv;
             if (tune_lookup(ctx, key, &tv)) {
                 K = tv.K;
                 T = tv.T;
                 seg_mult = tv.seg_mult;
+                sparse = (tv.kernel == 2) && sparse_ok;
             } else if (ctx->tuning.autotune == 1) {
-                // Coordinate search over CTA width, tile and segment
-                // multiplier, each trial one timed launch of this bucket.
-                auto trial = [&](int k, int t, double m, float *ms) -> int {
-                    Plan pl = make_plan(b, k, t, m, 0);
+                // Coordinate search; each trial times about two waves of the
+                // bucket's work and scales to the whole launch.
+                if (sparse_ok)
+                    for (int r = 0; r < n_recs; ++r)
+                        if (key_off[b * n_recs + r + 1] > key_off[b * n_recs + r])
+                            FEM_TRY(stream_bytype(ctx, cc.recs[r]));
+                auto trial = [&](bool sp, int k, int t, double m, float *cost) -> int {
+                    Plan pl = make_plan(b, sp, k, t, m, 0);
                     void *pr = nullptr, *ps = nullptr, *pt = nullptr;
                     FEM_TRY(scratch(ctx, kSlotRecords, (size_t)std::max<int64_t>(pl.records, 1) * kRecWords * 4, &pr));
                     FEM_TRY(scratch(ctx, kSlotSeg, sizeof(int64_t) * seg_need(pl), &ps));
@@ -1232,38 +1644,65 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                     segpos = 0;
                     tabpos = 0;
                     RecInfo *dri = nullptr;
+                    const int64_t lim = std::min(units_of(pl), sample_of(pl));
                     cudaEventRecord(ctx->ev0, ctx->stream);
                     FEM_TRY(launch_plan(pl, static_cast<int32_t *>(pr), static_cast<int64_t *>(ps),
-                                        static_cast<char *>(pt), &dri));
+                                        static_cast<char *>(pt), &dri, lim));
                     cudaEventRecord(ctx->ev1, ctx->stream);
                     FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
-                    cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+                    *cost = ms * (float)((double)units_of(pl) / (double)std::max<int64_t>(lim, 1));
                     return FEM_OK;
                 };
                 const int kmax = std::min(256, ((se - sb) + 31) / 32 * 32);
                 float best = 0.f;
-                FEM_TRY(trial(K, T, seg_mult, &best));
+                FEM_TRY(trial(false, K, T, seg_mult, &best));
                 for (int k : {32, 64, 128, 256}) {
                     if (k > kmax || k == K) continue;
-                    float ms;
-                    FEM_TRY(trial(k, T, seg_mult, &ms));
-                    if (ms < best) best = ms, K = k;
+                    float c;
+                    FEM_TRY(trial(false, k, T, seg_mult, &c));
+                    if (c < best) best = c, K = k;
                 }
                 for (int t : {512, 2048}) {
-                    float ms;
-                    FEM_TRY(trial(K, t, seg_mult, &ms));
-                    if (ms < best) best = ms, T = t;
+                    float c;
+                    FEM_TRY(trial(false, K, t, seg_mult, &c));
+                    if (c < best) best = c, T = t;
                 }
                 for (double m : {0.5, 2.0}) {
-                    float ms;
-                    FEM_TRY(trial(K, T, m, &ms));
-                    if (ms < best) best = ms, seg_mult = m;
+                    float c;
+                    FEM_TRY(trial(false, K, T, m, &c));
+                    if (c < best) best = c, seg_mult = m;
                 }
-                tune_store(ctx, key, TuneVal{K, T, seg_mult});
-                cc.stats.kernel_launches += 0;
+                sparse = false;
+                if (sparse_ok) {
+                    double sm_best = 1.0;
+                    float cs = 0.f;
+                    FEM_TRY(trial(true, K, T, 1.0, &cs));
+                    for (double m : {0.25, 4.0}) {
+                        float c;
+                        FEM_TRY(trial(true, K, T, m, &c));
+                        if (c < cs) cs = c, sm_best = m;
+                    }
+                    if (cs < best) {
+                        sparse = true;
+                        seg_mult = sm_best;
+                    }
+                }
+                tune_store(ctx, key, TuneVal{K, T, seg_mult, sparse ? 2 : 1});
             }
         }
-        Plan pl = make_plan(b, K, T, seg_mult, records_needed);
+        // the per-type lists cost 4 B per event (plus 8 B transient): without
+        // room for them the tiled kernel does the work
+        for (int r = 0; r < n_recs && sparse; ++r)
+            if (key_off[b * n_recs + r + 1] > key_off[b * n_recs + r]) {
+                const int sb2 = stream_bytype(ctx, cc.recs[r]);
+                if (sb2 == FEM_ERR_NOMEM)
+                    sparse = false;
+                else if (sb2 != FEM_OK)
+                    return sb2;
+            }
+        Plan pl = make_plan(b, sparse, K, T, seg_mult, records_needed);
         records_needed += pl.records;
         plans.push_back(std::move(pl));
     }
@@ -1294,10 +1733,12 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     cudaEventRecord(ctx->ev0, ctx->stream);
     for (auto &pl : plans) {
         RecInfo *d_ri = nullptr;
-        FEM_TRY(launch_plan(pl, static_cast<int32_t *>(p_rec), d_seg, tab, &d_ri));
-        k_stitch<<<(pl.n_slots + 7) / 8, 256, 0, ctx->stream>>>(static_cast<int32_t *>(p_rec), d_ri, d_perm,
-                                                               cc.cand_rec, pl.slot_begin, pl.n_slots, cc.counts,
-                                                               fb_list, d_fbc);
+        FEM_TRY(launch_plan(pl, static_cast<int32_t *>(p_rec), d_seg, tab, &d_ri, 0));
+        if (pl.sparse)
+            cc.stats.sparse_launches++;
+        k_stitch<<<(pl.n_slots + kStitchWarps - 1) / kStitchWarps, kStitchWarps * 32, 0, ctx->stream>>>(
+            static_cast<int32_t *>(p_rec), d_ri, d_perm, cc.cand_rec, pl.slot_begin, pl.n_slots, cc.counts, fb_list,
+            d_fbc);
         cc.stats.kernel_launches++;
         FEM_CUDA_TRY(cudaGetLastError());
     }
@@ -1330,8 +1771,8 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     }
     cc.stats.candidates_counted += n_work - fbc;
     if (fbc > 0) {
-        // Exact recount of the (episode) machines that ran out of entry classes:
-        // one segment, so no entry class is ever needed beyond the first.
+        // Exact recount of the episodes whose machines ran out of entry
+        // classes at some segment boundary.
         cc.stats.fallback_recounts += fbc;
         void *p_sub = nullptr;
         FEM_TRY(scratch(ctx, kSlotScanTmp, sizeof(int32_t) * fbc, &p_sub));
@@ -1343,7 +1784,13 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         void *p_keep = nullptr;
         FEM_TRY(dev_alloc(ctx, &p_keep, sizeof(int32_t) * fbc));
         cudaMemcpyAsync(p_keep, hsub.data(), sizeof(int32_t) * fbc, cudaMemcpyHostToDevice, ctx->stream);
-        const int st = count_core(cc, static_cast<int32_t *>(p_keep), fbc, 1);
+        // Each round divides the segment count by 8 (fewer boundaries, so
+        // fewer entry classes); after a few rounds a single segment remains,
+        // which never needs more than one class.
+        const double saved = cc.seg_div;
+        cc.seg_div *= 8.0;
+        const int st = count_core(cc, static_cast<int32_t *>(p_keep), fbc, cc.seg_div >= 4096.0 ? 1 : 0);
+        cc.seg_div = saved;
         cudaStreamSynchronize(ctx->stream);
         dev_free(ctx, p_keep, sizeof(int32_t) * fbc);
         return st;

@@ -16,8 +16,8 @@ namespace fem {
 
 // ---------------------------------------------------------------------------
 // Constants of the counting kernels.
-constexpr int kClasses = 4;              // entry classes kept per (episode, segment)
-constexpr int kRecWords = 16;            // meta, thr[H], cnt[H], last[H], pad (64 B, int4-aligned)
+constexpr int kClasses = 6;              // entry classes kept per (episode, segment)
+constexpr int kRecWords = 20;            // meta, thr[H], cnt[H], last[H], pad (80 B, int4-aligned)
 constexpr int kMaxWarps = 8;             // compute warps per CTA
 constexpr int kBitmapWords = 128;        // per-warp type filter: 4096 bits
 constexpr int kStages = 4;               // shared-memory tile ring depth
@@ -46,6 +46,7 @@ struct TuneVal {
     int K;            // lanes (episodes) per CTA
     int T;            // events per shared-memory stage
     double seg_mult;  // multiplier on the segment-count heuristic
+    int kernel;       // 1 tiled, 2 sparse
 };
 
 }  // namespace fem
@@ -78,6 +79,8 @@ struct fem_stream {
     uint32_t *d_freq = nullptr;   // n_types
     size_t bytes = 0;
     int32_t t_first = 0, t_last = 0;  // first and last event time (n > 0)
+    int64_t *d_toff = nullptr;    // per-type event lists (built on first use): offsets [n_types + 1]
+    int32_t *d_ttime = nullptr;   // times grouped by type, ascending within a type [n]
     std::map<int32_t, uint32_t *> dens;  // lo -> per-type max events in a closed window of length lo
 };
 
@@ -107,6 +110,8 @@ int sync_status(fem_ctx *ctx);
 // Copy helpers honouring host/device pointers.
 int copy_in(fem_ctx *ctx, void *dst_dev, const void *src, size_t bytes, int src_is_device);
 int copy_out(fem_ctx *ctx, void *dst, const void *src_dev, size_t bytes, int dst_is_device);
+// Per-type event lists of a stream (built on first use, kept in the stream).
+int stream_bytype(fem_ctx *ctx, fem_stream *s);
 // Density table for one lo (computed on first use, cached in the stream).
 int stream_density(fem_ctx *ctx, fem_stream *s, int32_t lo, uint32_t **d_dens);
 

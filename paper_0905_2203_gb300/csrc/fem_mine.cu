@@ -708,6 +708,7 @@ static int count_group(MineGroup &g) {
     FEM_TRY(count_device(g.ctx, g.recs, g.cand.n, g.d_coffs, g.cand.types, g.cand.lo, g.cand.hi, g.cand.rec, g.lo_vals,
                          g.d_order, g.n_order, g.cand.counts, &cs));
     g.S.kernel_launches += cs.kernel_launches;
+    g.S.sparse_launches += cs.sparse_launches;
     g.S.candidates_counted += cs.candidates_counted;
     g.S.fallback_recounts += cs.fallback_recounts;
     g.S.relevant_events += cs.relevant_events;
@@ -799,6 +800,7 @@ int mg_count_batch(fem_ctx *ctx, const std::vector<MineGroup *> &gs) {
     }
     // shared launch statistics are attributed to the first group
     gs[0]->S.kernel_launches += cs.kernel_launches;
+    gs[0]->S.sparse_launches += cs.sparse_launches;
     gs[0]->S.count_kernel_ms += cs.count_kernel_ms;
     for (MineGroup *g : gs) g->S.candidates_counted += g->done ? 0 : g->n_order;
     return sync_status(ctx);

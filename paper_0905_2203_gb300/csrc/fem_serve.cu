@@ -40,6 +40,7 @@ struct Job {
     fem_job_info info{};
     int status = FEM_OK;
     bool done = false;
+    int requeues = 0;
 };
 
 }  // namespace
@@ -63,7 +64,8 @@ namespace {
 // padding), level-2 candidate arrays and the pair-bound table (both at most
 // quadratic in the alphabet), and a fixed allowance for the rest.
 size_t estimate_job_bytes(int64_t n, uint32_t n_types, int nb) {
-    const size_t stream = (size_t)(n + fem::kPadEvents) * 6;
+    // stream (6 B/event) + per-type lists (4 B/event kept, 8 B/event while built)
+    const size_t stream = (size_t)(n + fem::kPadEvents) * 18;
     const size_t pairs = (size_t)n_types * n_types * (size_t)std::max(nb, 1);
     return stream + pairs * 48 + (size_t)16 * 1024 * 1024;
 }
@@ -93,6 +95,28 @@ void finish_job(fem_server *srv, Job *j, int status) {
     srv->cv_done.notify_all();
 }
 
+// Releases a job's device state and puts it back at the head of the queue:
+// it ran out of device memory next to other resident jobs and will be
+// retried once memory has been freed.
+void requeue_job(fem_server *srv, Job *j) {
+    if (j->g) {
+        fem::mg_destroy(j->g);
+        j->g = nullptr;
+    }
+    if (j->s) {
+        fem::stream_free_unlocked(j->s);
+        j->s = nullptr;
+    }
+    if (j->res) {
+        fem_result_free(j->res);
+        j->res = nullptr;
+    }
+    j->status = FEM_OK;
+    j->requeues++;
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->pending.push_front(j);
+}
+
 // Uploads and starts one job (level 1, level-2 candidates).
 int start_job(fem_server *srv, Job *j) {
     fem_ctx *ctx = srv->ctx;
@@ -118,6 +142,9 @@ void worker_loop(fem_server *srv) {
             while (!srv->pending.empty() && (int)(srv->active.size() + admit.size()) < srv->max_jobs) {
                 Job *j = srv->pending.front();
                 const bool empty = srv->active.empty() && admit.empty();
+                // a job that ran out of memory next to others re-enters only
+                // when at most one other job is resident
+                if (j->requeues > 0 && srv->active.size() + admit.size() > 1) break;
                 if (!empty && ctx->used.load() + planned + j->mem_est > ctx->budget) break;
                 srv->pending.pop_front();
                 planned += j->mem_est;
@@ -129,7 +156,9 @@ void worker_loop(fem_server *srv) {
             for (Job *j : admit) {
                 j->info.admit_s = fem::now_s();
                 const int st = start_job(srv, j);
-                if (st != FEM_OK) {
+                if (st == FEM_ERR_NOMEM && !srv->active.empty()) {
+                    requeue_job(srv, j);
+                } else if (st != FEM_OK) {
                     finish_job(srv, j, st);
                 } else if (fem::mg_done(j->g)) {
                     finish_job(srv, j, FEM_OK);
@@ -141,11 +170,25 @@ void worker_loop(fem_server *srv) {
             std::vector<fem::MineGroup *> gs;
             for (Job *j : srv->active) gs.push_back(j->g);
             int st = fem::mg_count_batch(ctx, gs);
+            if (st == FEM_ERR_NOMEM && gs.size() > 1) {
+                // the batch does not fit next to the resident jobs: count the
+                // jobs one at a time (each job then fails or succeeds alone)
+                st = FEM_OK;
+                for (auto *g1 : gs) {
+                    const int s1 = fem::mg_count_batch(ctx, {g1});
+                    if (s1 != FEM_OK) {
+                        for (Job *j : srv->active)
+                            if (j->g == g1) j->status = s1;
+                    }
+                }
+            }
             std::vector<Job *> still;
             for (Job *j : srv->active) {
-                int sj = st;
+                int sj = st != FEM_OK ? st : j->status;
                 if (sj == FEM_OK) sj = fem::mg_advance(j->g);
-                if (sj != FEM_OK) {
+                if (sj == FEM_ERR_NOMEM && srv->active.size() > 1 && j->requeues < 64) {
+                    requeue_job(srv, j);
+                } else if (sj != FEM_OK) {
                     finish_job(srv, j, sj);
                 } else if (fem::mg_done(j->g)) {
                     const fem_stats &S = fem::mg_stats(j->g);

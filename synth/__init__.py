@@ -273,48 +273,46 @@ def random_candidates(seed: int, n_cand: int, n_types: int, size_lo: int, size_h
                       bins, planted=(), planted_frac: float = 0.0):
     """CSR candidate set: sizes uniform in [size_lo, size_hi], distinct random
     types, each edge a bin chosen uniformly; a fraction are contiguous
-    sub-episodes of the planted chains (with the chain's own bins when the
-    chain records them, else random bins)."""
+    sub-episodes of the planted chains (padded with random distinct types when
+    the chain is shorter than the drawn size)."""
     rng = Rng(seed, 11)
     sizes = rng.integers(size_lo, size_hi, n_cand)
     offs = np.zeros(n_cand + 1, np.int64)
     offs[1:] = np.cumsum(sizes)
     total = int(offs[-1])
-    types = np.zeros(total, np.uint16)
-    lo = np.zeros(total - n_cand, np.int32)
-    hi = np.zeros(total - n_cand, np.int32)
-    bins = list(bins)
-    u_plant = rng.uniform(n_cand)
-    for c in range(n_cand):
-        N = int(sizes[c])
-        o, eo = int(offs[c]), int(offs[c]) - c
-        if planted and u_plant[c] < planted_frac:
-            ch = planted[int(rng.integers(0, len(planted) - 1, 1)[0])]
-            neurons = ch["neurons"]
-            if len(neurons) >= 2:
-                N2 = min(N, len(neurons))
-                st = int(rng.integers(0, len(neurons) - N2, 1)[0])
-                seq = neurons[st:st + N2]
-                # pad with random distinct types if the chain is shorter
-                extra = [int(x) for x in np.argsort(rng.uniform(n_types)) if int(x) not in seq]
-                seq = list(seq) + extra[: N - N2]
-                types[o:o + N] = seq
-                for k in range(N - 1):
-                    b = bins[int(rng.integers(0, len(bins) - 1, 1)[0])]
-                    lo[eo + k], hi[eo + k] = b
-                continue
-        perm = np.argsort(rng.uniform(n_types))[:N]
-        types[o:o + N] = perm
-        pick = rng.integers(0, len(bins) - 1, N - 1)
-        for k in range(N - 1):
-            lo[eo + k], hi[eo + k] = bins[int(pick[k])]
+    bins = np.asarray(list(bins), np.int64).reshape(-1, 2)
+    # distinct random types per candidate: the first N of a random permutation
+    order = np.argsort(rng.uniform(n_cand * n_types).reshape(n_cand, n_types), axis=1)
+    nmax = int(sizes.max()) if n_cand else 0
+    seq = order[:, :max(nmax, 1)].copy()
+    planted = [list(ch["neurons"]) for ch in planted if len(ch["neurons"]) >= 2]
+    if planted and planted_frac > 0:
+        u = rng.uniform(n_cand)
+        pick = rng.integers(0, len(planted) - 1, n_cand)
+        start_u = rng.uniform(n_cand)
+        for c in np.nonzero(u < planted_frac)[0]:
+            ch = planted[int(pick[c])]
+            N = int(sizes[c])
+            N2 = min(N, len(ch))
+            st = int(np.floor(start_u[c] * (len(ch) - N2 + 1)))
+            head = ch[st:st + N2]
+            rest = [int(x) for x in order[c] if int(x) not in head][: N - N2]
+            seq[c, :N] = head + rest
+    col = np.arange(max(nmax, 1))[None, :]
+    types = seq[col < sizes[:, None]].astype(np.uint16)
+    n_edges = total - n_cand
+    pickb = rng.integers(0, len(bins) - 1, n_edges)
+    lo = bins[pickb, 0].astype(np.int32)
+    hi = bins[pickb, 1].astype(np.int32)
     return offs, types, lo, hi
 
 
 def c3_batched(seed: int = 0xFE0003, n_events: int = 4_000_000, n_cand: int = 200_000):
     """One bursty 60-type stream (10 us ticks) and 200k candidates of sizes
     2-8 with edges drawn from the 4-bin set; 5% planted-chain sub-episodes."""
-    s = bursty_60(seed, n_events)
+    s = bursty_60(seed, int(n_events * 1.05))
+    # generated until n events: keep the time-ordered prefix of exactly n_events
+    s.types, s.times = s.types[:n_events].copy(), s.times[:n_events].copy()
     offs, types, lo, hi = random_candidates(seed, n_cand, 60, 2, 8, BINS_4, s.chains, 0.05)
     return s, (offs, types, lo, hi)
 

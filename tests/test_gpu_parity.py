@@ -67,6 +67,9 @@ def test_stream_validation_errors(fb, ctx):
     with pytest.raises(fb.FemError) as e:
         ctx.load_stream(np.array([0, 1], np.uint16), np.array([-3, 1], np.int32), 2)
     assert e.value.status == fb.FEM_ERR_RANGE
+    with pytest.raises(fb.FemError) as e:
+        ctx.load_stream(np.array([0, 1], np.uint16), np.array([5, 2**31 - 1], np.int32), 2)
+    assert e.value.status == fb.FEM_ERR_RANGE
 
 
 def test_candidate_validation_errors(fb, ctx):
@@ -95,13 +98,15 @@ def test_golden_cases_on_gpu(fb, ctx):
         st.free()
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("segments,lanes,tile", [(0, 0, 0), (1, 32, 256), (7, 64, 512), (64, 256, 1024),
                                                   (300, 96, 4096)])
-def test_random_tiny_streams(fb, ctx, segments, lanes, tile):
+def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
     """Many random episodes (sizes 1-6, lower bounds 0..6) over random streams
-    with frequent equal times, under several segment / CTA / tile settings."""
+    with frequent equal times, under several segment / CTA / tile settings,
+    with the tiled (1) and the sparse (2) counting kernel."""
     r = synth.Rng(99, segments + 7)
-    ctx.set_tuning(lanes_per_cta=lanes, segments=segments, tile_events=tile)
+    ctx.set_tuning(lanes_per_cta=lanes, segments=segments, tile_events=tile, kernel=kernel)
     try:
         for trial in range(6):
             n_types = int(r.integers(2, 7, 1)[0])
@@ -155,13 +160,18 @@ def test_upper_bound_is_relaxed_count(fb, ctx):
     st.free()
 
 
-def test_bursty_stream_mixed_sizes(fb, ctx):
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_bursty_stream_mixed_sizes(fb, ctx, kernel):
     """Network bursts (dense windows) with sizes 2-8 and the 4-bin set."""
     s = synth.bursty_60(0xFE0003, 150_000)
     st = ctx.load_stream(s.types, s.times, s.n_types)
     offs, ct, lo, hi = synth.random_candidates(0xFE0003, 3000, 60, 2, 8, synth.BINS_4, s.chains, 0.05)
-    got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
     want = oracle_counts(s.types, s.times, offs, ct, lo, hi)
+    ctx.set_tuning(kernel=kernel)
+    try:
+        got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+    finally:
+        ctx.reset_tuning()
     assert np.array_equal(got, want)
     assert want.max() > 0
     st.free()
