@@ -97,6 +97,9 @@ typedef struct {
     int kernel;           /* 0 = choose per launch, 1 = always the tiled
                              shared-memory broadcast kernel, 2 = the sparse
                              per-type-list kernel where it applies */
+    int level_graph;      /* mining: 0 = run levels >= 3 as one captured CUDA
+                             graph where it applies, -1 = level by level
+                             from the host */
 } fem_tuning;
 
 /* Per-call statistics filled by the counting / mining calls. */
@@ -117,6 +120,8 @@ typedef struct {
     double count_kernel_ms;     /* device time of the exact-count kernels */
     double total_ms;            /* wall time of the call */
     int levels;                 /* mining: deepest level reached */
+    int graph_tails;            /* mining: 1 if levels >= 3 ran as one
+                                   captured CUDA graph */
 } fem_stats;
 
 /* ---- context ----------------------------------------------------------- */

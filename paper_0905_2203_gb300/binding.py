@@ -50,7 +50,7 @@ class fem_cands(ctypes.Structure):
 
 class fem_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_cta", I32), ("segments", I32), ("tile_events", I32), ("prepass", I32),
-                ("plain_path", I32), ("autotune", I32), ("kernel", I32)]
+                ("plain_path", I32), ("autotune", I32), ("kernel", I32), ("level_graph", I32)]
 
 
 class fem_stats(ctypes.Structure):
@@ -59,7 +59,7 @@ class fem_stats(ctypes.Structure):
                 ("candidates_counted", I64), ("candidates_pruned", I64),
                 ("fallback_recounts", I64), ("kernel_launches", I64), ("sparse_launches", I64),
                 ("count_kernel_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
-                ("levels", I32)]
+                ("levels", I32), ("graph_tails", I32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -188,8 +188,8 @@ class Context:
             pass
 
     def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0, plain_path=0, autotune=0,
-                   kernel=0):
-        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path, autotune, kernel)
+                   kernel=0, level_graph=0):
+        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path, autotune, kernel, level_graph)
         check(fem_ctx_set_tuning(self.h, ctypes.byref(t)), "fem_ctx_set_tuning")
 
     def reset_tuning(self):

@@ -336,6 +336,7 @@ extern "C" void fem_ctx_destroy(fem_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    graph_cache_clear(ctx);
     for (auto &kv : ctx->scratch) dev_free(ctx, kv.second.p, kv.second.cap);
     ctx->scratch.clear();
     dev_free(ctx, ctx->d_status, sizeof(int) * 4);
@@ -478,6 +479,7 @@ void fem::stream_free_unlocked(fem_stream *s) {
     if (!s) return;
     fem_ctx *ctx = s->ctx;
     cudaSetDevice(ctx->device);
+    graph_cache_forget(ctx, s);
     cudaStreamSynchronize(ctx->stream);
     const int64_t cap = s->n + kPadEvents;
     dev_free(ctx, s->d_type, sizeof(uint16_t) * cap);

@@ -47,19 +47,6 @@ __host__ __device__ inline int ring_of_class(int c) { return 2 << c; }
 // Largest register-ring capacity compiled for each NMAX class (0 = none).
 __host__ __device__ inline int max_reg_ring(int nclass) { return nclass == 0 ? 8 : nclass == 1 ? 4 : nclass == 2 ? 2 : 0; }
 
-struct RecInfo {
-    const uint16_t *type;
-    const int32_t *time;
-    int64_t n;
-    const int64_t *seg;   // P + 1 segment starts (device)
-    int P;
-    int slot_first;       // first launch slot of this recording in the bucket
-    int64_t recbase;      // first record index of this recording
-    const uint32_t *freq;
-    const int64_t *toff;  // per-type event lists (sparse kernel only)
-    const int32_t *ttime;
-};
-
 struct WorkItem {
     int rec;
     int slot0;
@@ -514,12 +501,13 @@ constexpr int kStitchWarps = 4;
 __global__ void __launch_bounds__(kStitchWarps * 32)
     k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
              const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
-             int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count) {
+             int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
+             const int32_t *d_n_slots = nullptr) {
     __shared__ __align__(16) int32_t buf[kStitchWarps][32 * kRecWords];
     const int w = threadIdx.x >> 5;
     const int wi = blockIdx.x * kStitchWarps + w;
     const int lane = threadIdx.x & 31;
-    if (wi >= n_slots) return;
+    if (wi >= (d_n_slots ? *d_n_slots : n_slots)) return;
     const int slot = slot_begin + wi;
     const int cand = slot2cand[slot];
     const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
@@ -880,19 +868,43 @@ int scan_exclusive(cudaStream_t st, int32_t *data, int64_t m, int32_t *tmp, int3
     return FEM_OK;
 }
 
+// Segment boundaries: boundary p sits near p*n/P, at the largest gap
+// between consecutive event times within +-w events of it (a quiet spot, so
+// few occurrences span the boundary and few entry classes are needed); a
+// boundary always falls where the time changes.
 __global__ void k_segments(const int32_t *__restrict__ tm, int64_t n, int P, int64_t *__restrict__ seg) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p > P) return;
     int64_t b;
-    if (p == 0)
+    if (p == 0) {
         b = 0;
-    else if (p == P)
+    } else if (p == P) {
         b = n;
-    else {
-        b = (int64_t)((__int128)n * p / P);
-        while (b < n && b > 0 && tm[b] == tm[b - 1]) ++b;
+    } else {
+        const int64_t nom = (int64_t)((__int128)n * p / P);
+        const int64_t seg_len = n / P;
+        const int64_t w = seg_len / 4 < 4096 ? seg_len / 4 : 4096;
+        const int64_t lo = nom - w > 1 ? nom - w : 1;
+        const int64_t hi = nom + w < n - 1 ? nom + w : n - 1;
+        b = nom;
+        int64_t best = -1;
+        for (int64_t i = lo; i <= hi; ++i) {
+            const int64_t gap = (int64_t)tm[i] - tm[i - 1];
+            if (gap > best) {
+                best = gap;
+                b = i;
+            }
+        }
+        if (best <= 0)
+            while (b < n && b > 0 && tm[b] == tm[b - 1]) ++b;
     }
     seg[p] = b;
+}
+
+int launch_segments(cudaStream_t st, const int32_t *time, int64_t n, int P, int64_t *seg) {
+    k_segments<<<(P + 1 + 127) / 128, 128, 0, st>>>(time, n, P, seg);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -909,6 +921,7 @@ struct SparseArgs {
     int n_recs;
     int64_t rec_first;    // first record index of this plan
     int64_t n_threads;    // records of this plan = sum over recordings of c_r * P_r
+    const int64_t *d_n_threads;  // if set, the thread count is read from device memory
     const int64_t *offs;
     const uint16_t *ctypes;
     const int32_t *clo;
@@ -925,7 +938,7 @@ template <int NMAX, int RR>
 __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs a) {
     extern __shared__ int32_t s_ring[];
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= a.n_threads) return;
+    if (t >= (a.d_n_threads ? *a.d_n_threads : a.n_threads)) return;
     const int64_t tr = a.rec_first + t;
     int lo_r = 0, hi_r = a.n_recs;  // last recording whose records start at or before tr
     while (hi_r - lo_r > 1) {
@@ -1192,6 +1205,45 @@ static SparseFn sparse_fn(int nclass, int rr) {
 #undef FEM_SF
     return nullptr;
 }
+
+// Device-sized counting for captured graphs: the sparse kernel with
+// shared-memory rings of R entries over up to cap_threads (episode, segment)
+// threads, then the stitch over up to cap_slots episodes; the live sizes are
+// read from device memory.
+int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int n_recs, const int64_t *d_n_threads,
+                     int64_t cap_threads, const int64_t *offs, const uint16_t *ctypes, const int32_t *clo,
+                     const int32_t *chi, const int32_t *slot2cand, const uint32_t *cand_rec, int32_t *rec,
+                     const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count) {
+    const int nclass = nmax == 2 ? 0 : nmax == 4 ? 1 : nmax == 8 ? 2 : 3;
+    SparseFn f = sparse_fn(nclass, 0);
+    if (!f) return FEM_ERR_CUDA;
+    SparseArgs sa{};
+    sa.rinfo = rinfo;
+    sa.n_recs = n_recs;
+    sa.rec_first = 0;
+    sa.n_threads = cap_threads;
+    sa.d_n_threads = d_n_threads;
+    sa.offs = offs;
+    sa.ctypes = ctypes;
+    sa.clo = clo;
+    sa.chi = chi;
+    sa.slot2cand = slot2cand;
+    sa.relaxed = 0;
+    sa.R = R;
+    sa.rec = rec;
+    const size_t sm = sparse_smem(nclass, R);
+    if (sm > 48 * 1024 &&
+        cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return FEM_ERR_CUDA;
+    if (cap_threads > 0) f<<<(unsigned)((cap_threads + 63) / 64), 64, sm, st>>>(sa);
+    if (cap_slots > 0)
+        k_stitch<<<(unsigned)((cap_slots + kStitchWarps - 1) / kStitchWarps), kStitchWarps * 32, 0, st>>>(
+            rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots, counts, fb_list, fb_count, d_n_slots);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+size_t sparse_smem_bytes(int nmax, int R) { return (size_t)2 * (nmax - 1) * R * 64 * 4; }
 
 // Register-ring capacity compiled for (nclass, R); 0 = shared-memory rings.
 static int reg_ring_for(int nclass, int R) {

@@ -41,6 +41,34 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+// One recording as seen by a counting launch.
+struct RecInfo {
+    const uint16_t *type;
+    const int32_t *time;
+    int64_t n;
+    const int64_t *seg;   // P + 1 segment starts (device)
+    int P;
+    int slot_first;       // first launch slot of this recording in the bucket
+    int64_t recbase;      // first record index of this recording
+    const uint32_t *freq;
+    const int64_t *toff;  // per-type event lists (sparse kernel only)
+    const int32_t *ttime;
+};
+
+// Results of the graph-captured tail (levels >= 3) of level-wise mining.
+struct TailLevel {
+    int N = 0;
+    int64_t C = 0;                    // candidates counted at this level
+    std::vector<int64_t> coff;        // per-recording candidate offsets
+    std::vector<uint16_t> types;      // frequent episodes, fixed stride N
+    std::vector<int32_t> lo, hi;
+    std::vector<uint32_t> rec, counts;
+};
+struct TailResult {
+    std::vector<TailLevel> levels;
+};
+struct GraphTail;
+
 // Autotuner choice for one workload signature.
 struct TuneVal {
     int K;            // lanes (episodes) per CTA
@@ -66,6 +94,7 @@ struct fem_ctx {
     fem_stats last{};
     std::map<int, fem::DevBuf> scratch;  // slot -> buffer (grown on demand)
     std::map<std::string, fem::TuneVal> tune;  // autotuner cache
+    std::map<std::string, fem::GraphTail *> graphs;  // captured mining tails
     std::string tune_path;                     // JSON file backing the cache ("" = memory only)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -145,6 +174,20 @@ void mg_destroy(MineGroup *g);
 int mg_count_batch(fem_ctx *ctx, const std::vector<MineGroup *> &gs);
 fem_result *result_new(int n_recs, int max_size);
 void result_set_stats(fem_result *r, const fem_stats &s);
+int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int n_recs, const int64_t *d_n_threads,
+                     int64_t cap_threads, const int64_t *offs, const uint16_t *ctypes, const int32_t *clo,
+                     const int32_t *chi, const int32_t *slot2cand, const uint32_t *cand_rec, int32_t *rec,
+                     const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count);
+size_t sparse_smem_bytes(int nmax, int R);
+// Segment boundaries (P + 1 entries) of a stream cut into P segments at time changes.
+int launch_segments(cudaStream_t st, const int32_t *time, int64_t n, int P, int64_t *seg);
+int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
+                   const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, const std::vector<int32_t> &lo_vals,
+                   int max_size, int64_t F2, const uint16_t *f2_types, const int32_t *f2_lo, const int32_t *f2_hi,
+                   const uint32_t *f2_rec, const uint32_t *f2_counts, const std::vector<int64_t> &f2_off,
+                   TailResult *out, bool *used);
+void graph_cache_clear(fem_ctx *ctx);
+void graph_cache_forget(fem_ctx *ctx, const fem_stream *s);
 // Stream load without taking the context lock (caller holds it or owns the
 // context exclusively).
 int load_stream_unlocked(fem_ctx *ctx, const uint16_t *types, const int32_t *times, int64_t n, uint32_t n_types,

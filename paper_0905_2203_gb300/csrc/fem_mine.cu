@@ -409,6 +409,7 @@ struct MineGroup {
 
     int begin();
     int advance();
+    int graph_tail();
 
   private:
     int gen_level2();
@@ -702,6 +703,56 @@ int MineGroup::advance() {
     return finish_candidates();
 }
 
+// Levels 3..max_size through the captured graph (fem_graph.cu), starting
+// from the level-2 frequent set; when it does not apply or reports a flag the
+// group simply continues level by level.
+int MineGroup::graph_tail() {
+    TailResult tr;
+    bool used = false;
+    FEM_TRY(run_graph_tail(ctx, recs, blo, bhi, thr, lo_vals, max_size, prev.n, prev.types, prev.lo, prev.hi, prev.rec,
+                           prev.counts, prev.h_off, &tr, &used));
+    if (!used) return FEM_OK;
+    // the level-3 candidates the host path had prepared are superseded
+    const int n_recs = nrec();
+    for (const TailLevel &tl : tr.levels) {
+        const int N = tl.N;
+        if (tl.C == 0) break;
+        S.levels = N;
+        S.candidates_counted += tl.C;
+        for (int r = 0; r < n_recs; ++r) {
+            const double cr = (double)(tl.coff[r + 1] - tl.coff[r]);
+            S.episode_events += cr * (double)recs[r]->n;
+            S.counted_episode_events += cr * (double)recs[r]->n;
+        }
+        std::vector<int64_t> off(n_recs + 1, 0);
+        for (uint32_t r : tl.rec) off[r + 1]++;
+        for (int r = 0; r < n_recs; ++r) off[r + 1] += off[r];
+        for (int r = 0; r < n_recs; ++r) {
+            fem_result::Level &out = res->lv[out_rec[r]][N];
+            out.offs.assign(1, 0);
+            out.types.clear();
+            out.lo.clear();
+            out.hi.clear();
+            out.counts.clear();
+            for (int64_t i = off[r]; i < off[r + 1]; ++i) {
+                out.types.insert(out.types.end(), tl.types.begin() + i * N, tl.types.begin() + (i + 1) * N);
+                out.lo.insert(out.lo.end(), tl.lo.begin() + i * (N - 1), tl.lo.begin() + (i + 1) * (N - 1));
+                out.hi.insert(out.hi.end(), tl.hi.begin() + i * (N - 1), tl.hi.begin() + (i + 1) * (N - 1));
+                out.counts.push_back(tl.counts[i]);
+                out.offs.push_back((int64_t)out.types.size());
+            }
+        }
+    }
+    S.graph_tails += 1;
+    // the episode-events of the level-3 candidates were added when they were
+    // prepared on the host; the graph recounted them, so remove that share
+    for (int r = 0; r < n_recs; ++r) S.episode_events -= (double)(c_off[r + 1] - c_off[r]) * (double)recs[r]->n;
+    done = true;
+    level = 0;
+    pcand.reset();
+    return FEM_OK;
+}
+
 // Counting of the candidates of one group with the library's counting path.
 static int count_group(MineGroup &g) {
     fem_stats cs{};
@@ -853,6 +904,9 @@ static int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
         st = count_group(g);
         if (st == FEM_OK) st = sync_status(ctx);
         if (st == FEM_OK) st = g.advance();
+        // after level 2, the remaining levels run as one captured graph
+        if (st == FEM_OK && !g.done && g.level == 3 && ctx->tuning.level_graph != -1 && ctx->tuning.plain_path != 1)
+            st = g.graph_tail();
     }
     res->stats = g.S;
     return st;

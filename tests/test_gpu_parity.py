@@ -344,3 +344,41 @@ def test_prepass_prunes_but_never_changes_results(fb, ctx):
     assert stats_on["episode_events"] == stats_off["episode_events"]
     assert stats_on["counted_episode_events"] < stats_off["counted_episode_events"]
     st.free()
+
+
+@pytest.mark.parametrize("which", ["c2", "multi"])
+def test_level_graph_equals_host_path(fb, ctx, which):
+    """Levels >= 3 run as one captured CUDA graph; results equal the
+    level-by-level host path, and a repeated call reuses the cached graph."""
+    if which == "c2":
+        s, cfg = synth.c2_mid(duration_s=80.0)
+        streams_np, thrs, bins, L = [s], [int(0.0025 * s.n)], cfg["bins"], cfg["max_size"]
+    else:
+        recs = synth.c4_recordings(0xFE0004, n_rec=5, n_lo=5e3, n_hi=6e4)
+        streams_np = [x for x, _ in recs]
+        thrs = [c["threshold"] for _, c in recs]
+        bins, L = synth.BINS_4, 6
+    streams = [ctx.load_stream(x.types, x.times, x.n_types) for x in streams_np]
+
+    def run():
+        res = ctx.mine_levelwise(streams, bins, thrs, L)
+        out = [[res.level(k, N) for N in range(1, L + 1)] for k in range(len(streams))]
+        st = res.stats()
+        res.free()
+        return out, st
+
+    g1, s1 = run()
+    g2, s2 = run()
+    ctx.set_tuning(level_graph=-1)
+    try:
+        h, sh = run()
+    finally:
+        ctx.reset_tuning()
+    assert g1 == h and g2 == h
+    assert sh["graph_tails"] == 0
+    if max(sh["levels"], 0) >= 3:
+        assert s1["graph_tails"] == 1 and s2["graph_tails"] == 1
+        assert s1["levels"] == sh["levels"]
+        assert abs(s1["episode_events"] - sh["episode_events"]) < 1e-6 * sh["episode_events"]
+    for x in streams:
+        x.free()
