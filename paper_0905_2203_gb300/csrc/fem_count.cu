@@ -505,9 +505,9 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
              const int32_t *d_n_slots = nullptr) {
     __shared__ __align__(16) int32_t buf[kStitchWarps][32 * kRecWords];
     const int w = threadIdx.x >> 5;
-    const int wi = blockIdx.x * kStitchWarps + w;
     const int lane = threadIdx.x & 31;
-    if (wi >= (d_n_slots ? *d_n_slots : n_slots)) return;
+    const int n_live = d_n_slots ? *d_n_slots : n_slots;
+    for (int wi = blockIdx.x * kStitchWarps + w; wi < n_live; wi += gridDim.x * kStitchWarps) {
     const int slot = slot_begin + wi;
     const int cand = slot2cand[slot];
     const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
@@ -545,6 +545,7 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
         } else {
             counts[cand] = total;
         }
+    }
     }
 }
 
@@ -901,6 +902,26 @@ __global__ void k_segments(const int32_t *__restrict__ tm, int64_t n, int P, int
     seg[p] = b;
 }
 
+int stream_segments(fem_ctx *ctx, fem_stream *s, int P, const int64_t **seg) {
+    auto it = s->segs.find(P);
+    if (it != s->segs.end()) {
+        *seg = it->second;
+        return FEM_OK;
+    }
+    if (s->segs.size() >= 64) {  // bound the cache
+        cudaStreamSynchronize(ctx->stream);
+        for (auto &kv : s->segs) dev_free(ctx, kv.second, sizeof(int64_t) * (kv.first + 1));
+        s->segs.clear();
+    }
+    void *p = nullptr;
+    FEM_TRY(dev_alloc(ctx, &p, sizeof(int64_t) * (P + 1)));
+    k_segments<<<(P + 1 + 127) / 128, 128, 0, ctx->stream>>>(s->d_time, s->n, P, static_cast<int64_t *>(p));
+    FEM_CUDA_TRY(cudaGetLastError());
+    s->segs[P] = static_cast<int64_t *>(p);
+    *seg = static_cast<int64_t *>(p);
+    return FEM_OK;
+}
+
 int launch_segments(cudaStream_t st, const int32_t *time, int64_t n, int P, int64_t *seg) {
     k_segments<<<(P + 1 + 127) / 128, 128, 0, st>>>(time, n, P, seg);
     FEM_CUDA_TRY(cudaGetLastError());
@@ -937,8 +958,9 @@ struct SparseArgs {
 template <int NMAX, int RR>
 __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs a) {
     extern __shared__ int32_t s_ring[];
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (a.d_n_threads ? *a.d_n_threads : a.n_threads)) return;
+    const int64_t n_thr = a.d_n_threads ? *a.d_n_threads : a.n_threads;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_thr;
+         t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t tr = a.rec_first + t;
     int lo_r = 0, hi_r = a.n_recs;  // last recording whose records start at or before tr
     while (hi_r - lo_r > 1) {
@@ -1057,6 +1079,7 @@ __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs 
     for (int j = 1 + 3 * kClasses; j < kRecWords; ++j) w[j] = 0;
 #pragma unroll
     for (int q = 0; q < kRecWords / 4; ++q) r[q] = make_int4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    }
 }
 
 // Cost inputs for choosing between the tiled and the sparse kernel, per
@@ -1235,10 +1258,18 @@ int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int
     if (sm > 48 * 1024 &&
         cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return FEM_ERR_CUDA;
-    if (cap_threads > 0) f<<<(unsigned)((cap_threads + 63) / 64), 64, sm, st>>>(sa);
+    // grid-stride launches sized to what the GPU holds at once (the live
+    // sizes are only known on the device)
+    int dev = 0, nsm = 0, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 64, sm);
+    const int64_t gs = std::min<int64_t>((cap_threads + 63) / 64, (int64_t)std::max(1, nsm) * std::max(1, per_sm));
+    if (cap_threads > 0) f<<<(unsigned)gs, 64, sm, st>>>(sa);
+    const int64_t gst = std::min<int64_t>((cap_slots + kStitchWarps - 1) / kStitchWarps, (int64_t)std::max(1, nsm) * 8);
     if (cap_slots > 0)
-        k_stitch<<<(unsigned)((cap_slots + kStitchWarps - 1) / kStitchWarps), kStitchWarps * 32, 0, st>>>(
-            rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots, counts, fb_list, fb_count, d_n_slots);
+        k_stitch<<<(unsigned)gst, kStitchWarps * 32, 0, st>>>(rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots,
+                                                            counts, fb_list, fb_count, d_n_slots);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
@@ -1507,6 +1538,8 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                 const double min_seg = std::max(1024.0, 8.0 * halo_ev);
                 P = (int)std::max<double>(1.0, std::min<double>((double)s->n / seg_len, (double)s->n / min_seg) /
                                                    cc.seg_div);
+                // each segment adds one record the stitch walks per episode
+                if (sparse) P = std::min(P, 512);
             }
             pl.ri[r] = RecInfo{s->d_type, s->d_time, s->n, nullptr, P, ks, rb, s->d_freq, s->d_toff, s->d_ttime};
             if (c > 0) {
@@ -1549,11 +1582,10 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     auto launch_plan = [&](Plan &pl, int32_t *rec_base, int64_t *d_seg, char *tab, RecInfo **d_ri_out,
                            int64_t limit) -> int {
         for (int r = 0; r < n_recs; ++r) {
-            pl.ri[r].seg = d_seg + segpos;
-            k_segments<<<(pl.ri[r].P + 1 + 127) / 128, 128, 0, ctx->stream>>>(cc.recs[r]->d_time, cc.recs[r]->n,
-                                                                             pl.ri[r].P, d_seg + segpos);
-            cc.stats.kernel_launches++;
-            segpos += pl.ri[r].P + 1;
+            const int64_t *sg = nullptr;
+            FEM_TRY(stream_segments(ctx, cc.recs[r], pl.ri[r].P, &sg));
+            pl.ri[r].seg = sg;
+            (void)d_seg;
         }
         RecInfo *d_ri = reinterpret_cast<RecInfo *>(tab + tabpos);
         tabpos += (pl.ri.size() * sizeof(RecInfo) + 255) & ~size_t(255);

@@ -110,7 +110,8 @@ struct fem_stream {
     int32_t t_first = 0, t_last = 0;  // first and last event time (n > 0)
     int64_t *d_toff = nullptr;    // per-type event lists (built on first use): offsets [n_types + 1]
     int32_t *d_ttime = nullptr;   // times grouped by type, ascending within a type [n]
-    std::map<int32_t, uint32_t *> dens;  // lo -> per-type max events in a closed window of length lo
+    std::map<int32_t, uint32_t *> dens;
+    std::map<int, int64_t *> segs;    // P -> segment boundaries (P + 1), cached  // lo -> per-type max events in a closed window of length lo
 };
 
 namespace fem {
@@ -139,6 +140,8 @@ int sync_status(fem_ctx *ctx);
 // Copy helpers honouring host/device pointers.
 int copy_in(fem_ctx *ctx, void *dst_dev, const void *src, size_t bytes, int src_is_device);
 int copy_out(fem_ctx *ctx, void *dst, const void *src_dev, size_t bytes, int dst_is_device);
+// Segment boundaries of a stream cut into P segments (cached per P).
+int stream_segments(fem_ctx *ctx, fem_stream *s, int P, const int64_t **seg);
 // Per-type event lists of a stream (built on first use, kept in the stream).
 int stream_bytype(fem_ctx *ctx, fem_stream *s);
 // Density table for one lo (computed on first use, cached in the stream).
