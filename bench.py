@@ -193,6 +193,71 @@ def cpu_baseline_leg(s, cfg):
                       f"serial state-machine counter on {used} threads, {dt:.1f} s"}
 
 
+def c3_leg(ctx, tstream, flush, steps: int = 2):
+    """Batched counting: one 4M-event bursty 60-type stream and 200k
+    candidates (sizes 2-8, 4-bin intervals), one count_episodes call per
+    step, stream resident; episode-events/s over all 200k x 4M pairs."""
+    import torch
+    from paper_0905_2203_gb300 import binding as fb
+    s, (offs, ct, lo, hi) = synth.c3_batched()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    cands = fb.Cands(offs, ct, lo, hi)
+    ctx.set_tuning()  # default kernel choice, no autotuning trials here
+    ctx.count_episodes(st, cands)  # warm-up: builds per-type lists and densities
+    ms, rel, kms, sp = 0.0, 0.0, 0.0, 0
+    for k in range(steps):
+        flush.fill_(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(tstream)
+        ctx.count_episodes(st, cands)
+        b.record(tstream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        S = ctx.last_stats()
+        rel += S["relevant_events"]
+        kms += S["count_kernel_ms"]
+        sp += S["sparse_launches"]
+    st.free()
+    ctx.set_tuning(autotune=1)
+    n_c = len(offs) - 1
+    return {"workload": f"one bursty 60-type stream, n={s.n}, {n_c} candidates sizes 2-8, 4 bins",
+            "value": n_c * s.n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "relevant_events_per_s": rel / (kms / 1e3) if kms else None,
+            "sparse_launches_per_step": sp / steps}
+
+
+def run_case(name: str):
+    """Small fixed invocations used for ncu captures (no timing line):
+    c2_level2_tiled -- one C2 mining pass with the pre-pass off and the tiled
+                       kernel forced (level 2 counts all 55k candidates);
+    c3_mid_sparse   -- one count of 20k episodes (sizes 2-8) over a 1M-event
+                       bursty stream with the sparse kernel forced;
+    c2_mining       -- one default C2 mining pass."""
+    import torch
+    from paper_0905_2203_gb300 import binding as fb
+    ctx = fb.Context(0)
+    if name in ("c2_level2_tiled", "c2_mining"):
+        s, cfg = synth.c2_mid()
+        st = ctx.load_stream(s.types, s.times, s.n_types)
+        if name == "c2_level2_tiled":
+            ctx.set_tuning(prepass=-1, kernel=1)
+        res = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
+        print(json.dumps({"case": name, "stats": res.stats()}))
+        res.free()
+    elif name == "c3_mid_sparse":
+        s = synth.bursty_60(0xFE0003, 1_000_000)
+        offs, ct, lo, hi = synth.random_candidates(0xFE0003, 20000, 60, 2, 8, synth.BINS_4, s.chains, 0.05)
+        st = ctx.load_stream(s.types, s.times, s.n_types)
+        ctx.set_tuning(kernel=2)
+        ctx.count_episodes(st, fb.Cands(offs, ct, lo, hi))
+        print(json.dumps({"case": name, "stats": ctx.last_stats()}))
+    else:
+        raise SystemExit(f"unknown case {name}")
+    torch.cuda.synchronize()
+    st.free()
+    ctx.close()
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -205,6 +270,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_stream(tstream)
     ctx = fb.Context(local_rank, 0, tstream.cuda_stream)
     st = ctx.load_stream(s.types, s.times, s.n_types)
+    # autotuner on: its timing trials run during the warm-up steps
+    ctx.set_tuning(autotune=1)
     bins, thr, max_size = cfg["bins"], cfg["threshold"], cfg["max_size"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
 
@@ -251,6 +318,9 @@ def run_ours(args, rank, world, local_rank):
         ctx.close()
         return
 
+    sparse_launches = sum(x["sparse_launches"] for x in stats)
+    graph_tails = sum(x["graph_tails"] for x in stats)
+
     # --- plain per-level GPU path (comparison): same step, one thread per episode
     ctx.set_tuning(plain_path=1)
     step()
@@ -265,7 +335,7 @@ def run_ours(args, rank, world, local_rank):
     pe[1].record(tstream)
     torch.cuda.synchronize()
     p_ms = pe[0].elapsed_time(pe[1])
-    ctx.reset_tuning()
+    ctx.set_tuning(autotune=1)
     plain_value = sum(x["episode_events"] for x in pst) / (p_ms / 1e3)
 
     # --- end to end through the C ABI from host buffers
@@ -295,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_steps = max(1, min(args.steps, 5))
     e2e_value = e2e_ee * world / (e2e_ms / 1e3)
 
+    c3 = None if args.no_c3 else c3_leg(ctx, tstream, flush)
     if rank != 0:
         return
     peaks = _peaks()
@@ -339,6 +410,9 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(6 * s.n),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / e2e_steps},
         "gpu_launches": int(launches),
+        "kernels": {"sparse_launches_per_step": sparse_launches / args.steps,
+                    "graph_tail_steps": graph_tails},
+        "c3_batched_counting": c3,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -356,9 +430,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="skip the batched-counting (C3) leg")
     ap.add_argument("--quick", action="store_true",
                     help="time the tiled path only (no plain-path, e2e or CPU legs); for profiling")
+    ap.add_argument("--case", default=None,
+                    help="run one small fixed invocation for profiling (c2_level2_tiled, c3_mid_sparse, c2_mining)")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

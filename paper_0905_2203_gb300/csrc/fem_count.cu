@@ -134,24 +134,46 @@ template <int NMAX>
 struct Rings<NMAX, 0> {
     int32_t *rt;
     int32_t *rl;
-    int R, K;
+    int K;
+    int cap[NMAX - 1];       // entries of node k's ring
+    int off[NMAX - 1];       // first entry of node k's ring in this lane's slab
     int head[NMAX - 1];
 
+    // Uniform rings: R entries per node.
     __device__ __forceinline__ void init(int32_t *rt_, int32_t *rl_, int R_, int K_) {
         rt = rt_;
         rl = rl_;
-        R = R_;
         K = K_;
 #pragma unroll
-        for (int k = 0; k < NMAX - 1; ++k) head[k] = 0;
-        for (int k = 0; k < NMAX - 1; ++k)
-            for (int r = 0; r < R; ++r) rt[(k * R + r) * K] = INT32_MIN;
+        for (int k = 0; k < NMAX - 1; ++k) {
+            head[k] = 0;
+            cap[k] = R_;
+            off[k] = k * R_;
+        }
+        for (int e = 0; e < (NMAX - 1) * R_; ++e) rt[e * K] = INT32_MIN;
+    }
+
+    // Rings sized per node (cap[] already set, at least 2 each); their sum
+    // must fit the lane's slab.
+    __device__ __forceinline__ void init_var(int32_t *rt_, int32_t *rl_, int K_) {
+        rt = rt_;
+        rl = rl_;
+        K = K_;
+        int o = 0;
+#pragma unroll
+        for (int k = 0; k < NMAX - 1; ++k) {
+            head[k] = 0;
+            off[k] = o;
+            o += cap[k];
+        }
+        for (int e = 0; e < o; ++e) rt[e * K] = INT32_MIN;
     }
 
     __device__ __forceinline__ void push(int k, int32_t tt, int32_t LL, int32_t lo, int32_t hi, int &flags) {
         const int h = head[k];
-        int32_t *bt = rt + (k * R) * K;
-        int32_t *bl = rl + (k * R) * K;
+        const int R = cap[k];
+        int32_t *bt = rt + off[k] * K;
+        int32_t *bl = rl + off[k] * K;
         const int h2 = (h + 1 == R) ? 0 : h + 1;
         const int32_t o1 = bt[h * K];
         const int32_t o2 = bt[h2 * K];
@@ -162,8 +184,9 @@ struct Rings<NMAX, 0> {
     }
 
     __device__ __forceinline__ bool query(int k, int32_t tt, int32_t lo, int32_t hi, int32_t &LL) const {
-        const int32_t *bt = rt + (k * R) * K;
-        const int32_t *bl = rl + (k * R) * K;
+        const int R = cap[k];
+        const int32_t *bt = rt + off[k] * K;
+        const int32_t *bl = rl + off[k] * K;
         const int32_t elig = tt - lo;
         int idx = head[k];
         for (int i = 0; i < R; ++i) {
@@ -689,6 +712,7 @@ __global__ void k_prep(PrepArgs a) {
     const int64_t eo = o - c;
     bool bad = (rec < 0 || rec >= a.n_recs || N < 1 || N > FEM_MAX_NODES);
     int R = 2;
+    int64_t slab = 0;  // sum over nodes of the ring sizes
     int64_t sumhi = 0;
     unsigned long long relv = 0;
     if (!bad) {
@@ -713,6 +737,7 @@ __global__ void k_prep(PrepArgs a) {
                 if (d == kDensUnknown || d == 0) d = freq[ty] > 0 ? freq[ty] : 1;
                 const uint32_t need = d >= 0x7FFFFFFEu ? 0x7FFFFFFFu : d + 1;
                 if ((int)need > R) R = (int)need;
+                slab += need < 2 ? 2 : need;
             }
         }
     }
@@ -739,6 +764,7 @@ __global__ void k_prep(PrepArgs a) {
     atomicMax(&a.bucket_maxR[bucket], R);
     atomicMax(&a.bucket_maxR[kBuckets + bucket], (int)N);
     atomicMax(&a.bucket_maxR[2 * kBuckets + bucket], (int)(sumhi > INT32_MAX ? INT32_MAX : sumhi));
+    atomicMax(&a.bucket_maxR[3 * kBuckets + bucket], (int)(slab > INT32_MAX ? INT32_MAX : slab));
     atomicAdd(a.relevant, relv);
 }
 
@@ -949,12 +975,21 @@ struct SparseArgs {
     const int32_t *chi;
     const int32_t *slot2cand;
     int relaxed;
-    int R;                // ring capacity (shared-memory rings only)
+    int R;                // ring capacity (shared-memory rings, uniform mode)
     int32_t *rec;
+    // per-node ring sizes (shared-memory rings, sized mode): window density
+    // tables [rec * n_lo + j] for the distinct lower bounds lo_vals[j]; each
+    // thread's rings share a slab of `slab` entries
+    const uint32_t *const *dens;
+    const int32_t *lo_vals;
+    int n_lo;
+    int slab;
 };
 
-// RR > 0: register rings; RR == 0: shared-memory rings of a.R entries per
-// node (64-thread blocks; node k entry r of thread i at (k*R + r)*64 + i).
+// RR > 0: register rings.  RR == 0: shared-memory rings in 64-thread blocks,
+// entry e of thread i's slab at e*64 + i -- either R entries per node
+// (uniform mode) or, when density tables are given, each node's ring sized
+// to its own window density + 1 inside a slab of a.slab entries.
 template <int NMAX, int RR>
 __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs a) {
     extern __shared__ int32_t s_ring[];
@@ -998,10 +1033,39 @@ __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs 
         st.cprev[j] = 0;
         st.ccnt[j] = 0;
     }
-    if (RR == 0)
+    bool slab_overflow = false;
+    if constexpr (RR == 0) {
+    if (a.dens) {
+        int used = 0;
+#pragma unroll
+        for (int k = 0; k < NMAX - 1; ++k) {
+            int c = 2;
+            if (k < N - 1) {
+                const int32_t l = a.relaxed ? 0 : st.lo[k];
+                int j = 0;
+                while (j < a.n_lo && a.lo_vals[j] != l) ++j;
+                uint32_t d = j < a.n_lo ? a.dens[lo_r * a.n_lo + j][st.E[k]] : 0xFFFFFFFFu;
+                if (d == 0xFFFFFFFFu || d == 0) d = ri.freq[st.E[k]] > 0 ? ri.freq[st.E[k]] : 1;
+                c = d >= 0x7FFFFFFEu ? 0x7FFFFFFF : (int)d + 1;
+            } else {
+                c = 0;
+            }
+            st.rings.cap[k] = c < 2 && k < N - 1 ? 2 : c;
+            used += st.rings.cap[k];
+            if (used > a.slab) slab_overflow = true;
+        }
+        if (slab_overflow) {
+#pragma unroll
+            for (int k = 0; k < NMAX - 1; ++k) st.rings.cap[k] = 0;
+        }
+        st.rings.init_var(s_ring + threadIdx.x, s_ring + a.slab * blockDim.x + threadIdx.x, blockDim.x);
+    } else {
         st.rings.init(s_ring + threadIdx.x, s_ring + (NMAX - 1) * a.R * blockDim.x + threadIdx.x, a.R, blockDim.x);
-    else
+    }
+    } else {
         st.rings.init(nullptr, nullptr, 0, 0);
+    }
+    if (slab_overflow) st.flags |= kMetaRingOverflow;
 
     const int64_t seg_b = ri.seg[p], seg_e = ri.seg[p + 1];
     int32_t Tp = 0;
@@ -1013,7 +1077,7 @@ __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs 
         cur[k] = 0;
         end[k] = 0;
     }
-    if (seg_b < seg_e) {
+    if (seg_b < seg_e && !slab_overflow) {
         Tp = ri.time[seg_b];
         const int64_t haloT = (p == 0) ? INT64_MIN : (int64_t)Tp - sumhi;
         const int32_t Tend = (seg_e < ri.n) ? ri.time[seg_e] : INT32_MAX;
@@ -1340,6 +1404,7 @@ struct CountCall {
     std::vector<int32_t> lo_vals;        // distinct lo values (host)
     int mode = 0;                        // 0 exact, 1 plain, 2 relaxed
     double seg_div = 1.0;                // fallback rounds divide the segment count
+    bool force_tiled = false;            // last fallback round: tiled kernel, one segment
     fem_stats stats{};
     float count_ms = 0.f;
 };
@@ -1374,7 +1439,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     };
     const size_t o_lo = carve(lov.size() * 4), o_nt = carve(n_recs * 4),
                  o_dp = carve(dens_h.size() * sizeof(void *)), o_ri = carve(n_recs * sizeof(RecInfo)),
-                 o_bm = carve(3 * kBuckets * 4), o_rel = carve(8), o_fb = carve(8),
+                 o_bm = carve(4 * kBuckets * 4), o_rel = carve(8), o_fb = carve(8),
                  o_units = carve(2 * kBuckets * 8);
     void *misc = nullptr;
     FEM_TRY(scratch(ctx, kSlotMisc, off, &misc));
@@ -1390,7 +1455,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                                  cudaMemcpyHostToDevice, ctx->stream));
     FEM_CUDA_TRY(cudaMemcpyAsync(mb + o_ri, ri_h.data(), n_recs * sizeof(RecInfo), cudaMemcpyHostToDevice,
                                  ctx->stream));
-    FEM_CUDA_TRY(cudaMemsetAsync(mb + o_bm, 0, 3 * kBuckets * 4, ctx->stream));
+    FEM_CUDA_TRY(cudaMemsetAsync(mb + o_bm, 0, 4 * kBuckets * 4, ctx->stream));
     FEM_CUDA_TRY(cudaMemsetAsync(mb + o_rel, 0, 8, ctx->stream));
     FEM_CUDA_TRY(cudaMemsetAsync(mb + o_fb, 0, 8, ctx->stream));
     FEM_CUDA_TRY(cudaMemsetAsync(mb + o_units, 0, 2 * kBuckets * 8, ctx->stream));
@@ -1448,11 +1513,11 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         FEM_CUDA_TRY(cudaGetLastError());
     }
     std::vector<int32_t> key_off(n_keys + 1, 0);
-    std::vector<int32_t> bmax(3 * kBuckets, 0);
+    std::vector<int32_t> bmax(4 * kBuckets, 0);
     unsigned long long relv = 0;
     if (n_work > 0)
         FEM_CUDA_TRY(cudaMemcpyAsync(key_off.data(), d_keyoff, 4 * n_keys, cudaMemcpyDeviceToHost, ctx->stream));
-    FEM_CUDA_TRY(cudaMemcpyAsync(bmax.data(), mb + o_bm, 3 * kBuckets * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    FEM_CUDA_TRY(cudaMemcpyAsync(bmax.data(), mb + o_bm, 4 * kBuckets * 4, cudaMemcpyDeviceToHost, ctx->stream));
     FEM_CUDA_TRY(cudaMemcpyAsync(&relv, mb + o_rel, 8, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<unsigned long long> units_h(2 * kBuckets, 0);
     FEM_CUDA_TRY(cudaMemcpyAsync(units_h.data(), mb + o_units, 2 * kBuckets * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1469,6 +1534,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         int bucket;
         bool sparse;
         int K, R, nclass, T;
+        int slab;         // largest sum of per-node ring sizes in the bucket
         std::vector<RecInfo> ri;
         std::vector<WorkItem> items;
         int slot_begin, n_slots;
@@ -1486,6 +1552,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         pl.sparse = sparse;
         pl.nclass = b / kBucketRing;
         pl.R = std::max(bmax[b], 2);
+        pl.slab = std::max(bmax[3 * kBuckets + b], 2);
         pl.T = T;
         if (!sparse) {
             while (K > 32 && tiled_smem_rt(pl.nclass, K, pl.R, T) > 100 * 1024) K -= 32;
@@ -1610,7 +1677,14 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             SparseFn f = sparse_fn(pl.nclass, rr);
             if (!f) return FEM_ERR_CUDA;
             const int bs = rr ? 128 : 64;
-            const size_t sm = rr ? 0 : sparse_smem(pl.nclass, pl.R);
+            // shared-memory rings sized per node inside a slab per thread;
+            // episodes whose rings exceed the slab fall back (flagged)
+            const int slab = std::max(2, std::min(pl.slab, 128));
+            sa.dens = reinterpret_cast<const uint32_t *const *>(mb + o_dp);
+            sa.lo_vals = reinterpret_cast<const int32_t *>(mb + o_lo);
+            sa.n_lo = (int)lov.size();
+            sa.slab = slab;
+            const size_t sm = rr ? 0 : (size_t)2 * slab * 64 * 4;
             if (sm > 48 * 1024 &&
                 cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
                 return FEM_ERR_CUDA;
@@ -1678,8 +1752,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         const int nclass = b / kBucketRing;
         const int R = std::max(bmax[b], 2);
         // the sparse kernel needs register rings and per-type lists
-        bool sparse_ok = sparse_fn(nclass, reg_ring_for(nclass, R)) != nullptr &&
-                         (reg_ring_for(nclass, R) > 0 || sparse_smem(nclass, R) <= (size_t)ctx->smem_optin - 1024);
+        bool sparse_ok = sparse_fn(nclass, reg_ring_for(nclass, R)) != nullptr && !cc.force_tiled;
         for (int r = 0; r < n_recs && sparse_ok; ++r)
             if (key_off[b * n_recs + r + 1] > key_off[b * n_recs + r] && cc.recs[r]->n_types > 8192)
                 sparse_ok = false;
@@ -1871,10 +1944,17 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         // Each round divides the segment count by 8 (fewer boundaries, so
         // fewer entry classes); after a few rounds a single segment remains,
         // which never needs more than one class.
+        // The last round runs the tiled kernel on one segment, where neither
+        // entry classes nor rings (sized from the stream's densities) can
+        // overflow.
         const double saved = cc.seg_div;
+        const bool saved_ft = cc.force_tiled;
         cc.seg_div *= 8.0;
-        const int st = count_core(cc, static_cast<int32_t *>(p_keep), fbc, cc.seg_div >= 4096.0 ? 1 : 0);
+        const bool last = cc.seg_div >= 4096.0;
+        if (last) cc.force_tiled = true;
+        const int st = count_core(cc, static_cast<int32_t *>(p_keep), fbc, last ? 1 : 0);
         cc.seg_div = saved;
+        cc.force_tiled = saved_ft;
         cudaStreamSynchronize(ctx->stream);
         dev_free(ctx, p_keep, sizeof(int32_t) * fbc);
         return st;

@@ -447,7 +447,9 @@ int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const st
     std::vector<int32_t> c2(kCtr, 0);
     c2[1] = (int32_t)F2;
     FEM_CUDA_TRY(cudaMemcpyAsync(g->ctr + 2 * kCtr, c2.data(), 4 * kCtr, cudaMemcpyHostToDevice, st));
+    cudaEventRecord(ctx->ev0, st);
     FEM_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+    cudaEventRecord(ctx->ev1, st);
     std::vector<int32_t> ctr((size_t)(max_size + 1) * kCtr);
     std::vector<int64_t> coff((size_t)(max_size + 1) * (n_recs + 1));
     FEM_CUDA_TRY(cudaMemcpyAsync(ctr.data(), g->ctr, 4 * ctr.size(), cudaMemcpyDeviceToHost, st));
@@ -457,6 +459,9 @@ int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const st
         const int32_t *c = &ctr[(size_t)N * kCtr];
         if (c[2] != 0 || c[3] != 0) return FEM_OK;  // flagged: redo on the host path
     }
+    float gms = 0.f;
+    cudaEventElapsedTime(&gms, ctx->ev0, ctx->ev1);
+    out->graph_ms = gms;
     // results
     out->levels.clear();
     for (int N = 3; N <= max_size; ++N) {

@@ -66,6 +66,7 @@ struct TailLevel {
 };
 struct TailResult {
     std::vector<TailLevel> levels;
+    float graph_ms = 0.f;             // device time of the graph launch
 };
 struct GraphTail;
 
