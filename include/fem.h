@@ -96,7 +96,9 @@ typedef struct {
                              fastest in the context's tuning cache */
     int kernel;           /* 0 = choose per launch, 1 = always the tiled
                              shared-memory broadcast kernel, 2 = the sparse
-                             per-type-list kernel where it applies */
+                             per-type-list kernel where it applies, 3 = the
+                             sparse kernel with per-node branching instead of
+                             its node-uniform variant (comparison) */
     int level_graph;      /* mining: 0 = run levels >= 3 as one captured CUDA
                              graph where it applies, -1 = level by level
                              from the host */

@@ -1146,6 +1146,234 @@ __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs 
     }
 }
 
+// Node-uniform sparse kernel (shared-memory rings sized per node).  Every
+// lane handles its next event with the same instruction sequence whatever
+// node the event belongs to: the node's ring offset, size, head and bounds
+// live in a small per-thread header in shared memory, so the update indexes
+// them instead of branching per node (lanes of a warp are usually at
+// different nodes).  Thread i's words are strided by the block size:
+// header word w at w*64 + i, ring times at (H + e)*64 + i, ring starts at
+// (H + slab + e)*64 + i, with H = 5*(NMAX-1).
+template <int NMAX>
+__global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
+    extern __shared__ int32_t s_u[];
+    constexpr int HW = 5 * (NMAX - 1);
+    const int bd = blockDim.x;
+    int32_t *hdr = s_u + threadIdx.x;                 // [w * bd]
+    int32_t *rT = s_u + HW * bd + threadIdx.x;        // [e * bd]
+    int32_t *rL = s_u + (HW + a.slab) * bd + threadIdx.x;
+    // header fields of node k: off, cap, head, lo, hi
+#define H_OFF(k) hdr[(5 * (k) + 0) * bd]
+#define H_CAP(k) hdr[(5 * (k) + 1) * bd]
+#define H_HEAD(k) hdr[(5 * (k) + 2) * bd]
+#define H_LO(k) hdr[(5 * (k) + 3) * bd]
+#define H_HI(k) hdr[(5 * (k) + 4) * bd]
+    const int64_t n_thr = a.d_n_threads ? *a.d_n_threads : a.n_threads;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_thr; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t tr = a.rec_first + t;
+        int lo_r = 0, hi_r = a.n_recs;
+        while (hi_r - lo_r > 1) {
+            const int mid = (lo_r + hi_r) >> 1;
+            if (a.rinfo[mid].recbase <= tr) lo_r = mid; else hi_r = mid;
+        }
+        const RecInfo ri = a.rinfo[lo_r];
+        const int64_t local = tr - ri.recbase;
+        const int slot = ri.slot_first + (int)(local / ri.P);
+        const int p = (int)(local % ri.P);
+        const int cand = a.slot2cand[slot];
+        const int64_t o = a.offs[cand];
+        const int N = (int)(a.offs[cand + 1] - o);
+        const int64_t eo = o - cand;
+
+        Machine<NMAX, 0> st;  // entry classes only (its rings are unused here)
+        st.N = N;
+        st.ncls = 0;
+        st.live = 0;
+        st.M = INT32_MIN;
+        st.open = 1;
+        st.flags = 0;
+#pragma unroll
+        for (int j = 0; j < kClasses; ++j) {
+            st.cthr[j] = 0;
+            st.cprev[j] = 0;
+            st.ccnt[j] = 0;
+        }
+        uint32_t E[NMAX];
+        int64_t sumhi = 0;
+        int used = 0;
+        bool slab_overflow = false;
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) E[k] = k < N ? (uint32_t)a.ctypes[o + k] : 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < NMAX - 1; ++k) {
+            if (k >= N - 1) continue;
+            const int32_t l = a.relaxed ? 0 : a.clo[eo + k];
+            const int32_t h = a.chi[eo + k];
+            sumhi += h;
+            const int32_t lq = a.relaxed ? 0 : l;
+            int j = 0;
+            while (j < a.n_lo && a.lo_vals[j] != lq) ++j;
+            uint32_t d = j < a.n_lo ? a.dens[lo_r * a.n_lo + j][E[k]] : 0xFFFFFFFFu;
+            if (d == 0xFFFFFFFFu || d == 0) d = ri.freq[E[k]] > 0 ? ri.freq[E[k]] : 1;
+            const int c = d >= (uint32_t)a.slab ? a.slab + 1 : (int)d + 1;
+            H_OFF(k) = used;
+            H_CAP(k) = c;
+            H_HEAD(k) = 0;
+            H_LO(k) = l;
+            H_HI(k) = h;
+            used += c;
+            if (used > a.slab) slab_overflow = true;
+        }
+        if (!slab_overflow)
+            for (int e = 0; e < used; ++e) rT[e * bd] = INT32_MIN;
+        else
+            st.flags |= kMetaRingOverflow;
+
+        const int64_t seg_b = ri.seg[p], seg_e = ri.seg[p + 1];
+        int32_t Tp = 0;
+        int32_t head[NMAX];
+        int32_t cur[NMAX], end[NMAX];
+        uint32_t nodes[NMAX];  // nodes sharing the cursor's type (bit k = node k)
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            head[k] = INT32_MAX;
+            cur[k] = 0;
+            end[k] = 0;
+            nodes[k] = 0;
+        }
+        if (seg_b < seg_e && !slab_overflow) {
+            Tp = ri.time[seg_b];
+            const int64_t haloT = (p == 0) ? INT64_MIN : (int64_t)Tp - sumhi;
+            const int32_t Tend = (seg_e < ri.n) ? ri.time[seg_e] : INT32_MAX;
+#pragma unroll
+            for (int k = 0; k < NMAX; ++k) {
+                if (k >= N) continue;
+                bool first = true;
+#pragma unroll
+                for (int j = 0; j < k; ++j)
+                    if (E[j] == E[k]) first = false;
+                if (!first) continue;
+                uint32_t m = 0;
+#pragma unroll
+                for (int j = 0; j < NMAX; ++j)
+                    if (j < N && E[j] == E[k]) m |= 1u << j;
+                nodes[k] = m;
+                const int64_t b0 = ri.toff[E[k]], b1 = ri.toff[E[k] + 1];
+                int64_t lo_i = b0, hi_i = b1;
+                while (lo_i < hi_i) {
+                    const int64_t mid = (lo_i + hi_i) >> 1;
+                    if ((int64_t)ri.ttime[mid] < haloT) lo_i = mid + 1; else hi_i = mid;
+                }
+                int64_t e_i = b1;
+                if (seg_e < ri.n) {
+                    int64_t l2 = lo_i, h2 = b1;
+                    while (l2 < h2) {
+                        const int64_t mid = (l2 + h2) >> 1;
+                        if (ri.ttime[mid] < Tend) l2 = mid + 1; else h2 = mid;
+                    }
+                    e_i = l2;
+                }
+                cur[k] = (int32_t)lo_i;
+                end[k] = (int32_t)e_i;
+                head[k] = lo_i < e_i ? ri.ttime[lo_i] : INT32_MAX;
+            }
+            for (;;) {
+                int32_t tt = INT32_MAX;
+                int bk = -1;
+#pragma unroll
+                for (int k = 0; k < NMAX; ++k)
+                    if (head[k] < tt) {
+                        tt = head[k];
+                        bk = k;
+                    }
+                if (bk < 0) break;
+                uint32_t mask = 0;
+#pragma unroll
+                for (int k = 0; k < NMAX; ++k)
+                    if (k == bk) {
+                        mask = nodes[k];
+                        cur[k] += 1;
+                        head[k] = cur[k] < end[k] ? ri.ttime[cur[k]] : INT32_MAX;
+                    }
+                const bool in_seg = tt >= Tp;
+                // nodes of this type, last to first (one node unless the
+                // episode repeats a type)
+                while (mask) {
+                    const int k = 31 - __clz(mask);
+                    mask &= ~(1u << k);
+                    bool do_push = (k == 0) && (N > 1);
+                    bool do_end = false;
+                    int32_t L = tt;
+                    if (k > 0) {
+                        const int q = k - 1;
+                        const int32_t base = H_OFF(q), R = H_CAP(q);
+                        const int32_t elig = tt - H_LO(q), expire = tt - H_HI(q);
+                        int idx = H_HEAD(q);
+                        bool ok = false;
+                        for (int i = 0; i < R; ++i) {
+                            idx = (idx == 0) ? R - 1 : idx - 1;
+                            const int32_t tp = rT[(base + idx) * bd];
+                            if (tp < elig) {
+                                ok = tp >= expire;
+                                L = rL[(base + idx) * bd];
+                                break;
+                            }
+                        }
+                        if (ok) {
+                            if (k == N - 1)
+                                do_end = true;
+                            else
+                                do_push = true;
+                        }
+                    }
+                    if (do_end && in_seg) st.greedy_end(tt, L, Tp);
+                    if (do_push) {
+                        const int32_t base = H_OFF(k), R = H_CAP(k), h = H_HEAD(k);
+                        const int h2 = (h + 1 == R) ? 0 : h + 1;
+                        const int32_t o1 = rT[(base + h) * bd], o2 = rT[(base + h2) * bd];
+                        if (o1 != INT32_MIN && o1 >= tt - H_HI(k) && o2 >= tt - H_LO(k)) st.flags |= kMetaRingOverflow;
+                        rT[(base + h) * bd] = tt;
+                        rL[(base + h) * bd] = L;
+                        H_HEAD(k) = h2;
+                    }
+                }
+            }
+        }
+        st.finish();
+        int4 *r = reinterpret_cast<int4 *>(a.rec + tr * kRecWords);
+        int32_t w[kRecWords];
+        w[0] = st.ncls | st.flags;
+#pragma unroll
+        for (int j = 0; j < kClasses; ++j) {
+            w[1 + j] = st.cthr[j];
+            w[1 + kClasses + j] = (int32_t)st.ccnt[j];
+            w[1 + 2 * kClasses + j] = st.cprev[j];
+        }
+#pragma unroll
+        for (int j = 1 + 3 * kClasses; j < kRecWords; ++j) w[j] = 0;
+#pragma unroll
+        for (int q = 0; q < kRecWords / 4; ++q) r[q] = make_int4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    }
+#undef H_OFF
+#undef H_CAP
+#undef H_HEAD
+#undef H_LO
+#undef H_HI
+}
+
+// Shared memory of a node-uniform sparse block (64 threads, slab entries).
+static size_t sparse_u_smem(int nmax, int slab) { return (size_t)(5 * (nmax - 1) + 2 * slab) * 64 * 4; }
+
+typedef void (*SparseUFn)(SparseArgs);
+static SparseUFn sparse_u_fn(int nclass) {
+    switch (nclass) {
+        case 0: return k_count_sparse_u<2>;
+        case 1: return k_count_sparse_u<4>;
+        case 2: return k_count_sparse_u<8>;
+        default: return k_count_sparse_u<16>;
+    }
+}
+
 // Cost inputs for choosing between the tiled and the sparse kernel, per
 // bucket: for each group of 32 consecutive slots (one warp of the tiled
 // kernel), the events whose type some lane uses (what the tiled warp reads),
@@ -1684,6 +1912,19 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             sa.lo_vals = reinterpret_cast<const int32_t *>(mb + o_lo);
             sa.n_lo = (int)lov.size();
             sa.slab = slab;
+            if (!rr && ctx->tuning.kernel != 3) {
+                // node-uniform variant (rings and per-node data in shared memory)
+                SparseUFn fu = sparse_u_fn(pl.nclass);
+                const size_t smu = sparse_u_smem(nmax_of_class(pl.nclass), slab);
+                if (smu > 48 * 1024 &&
+                    cudaFuncSetAttribute((const void *)fu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smu) !=
+                        cudaSuccess)
+                    return FEM_ERR_CUDA;
+                if (sa.n_threads > 0) fu<<<(unsigned)((sa.n_threads + 63) / 64), 64, smu, ctx->stream>>>(sa);
+                FEM_CUDA_TRY(cudaGetLastError());
+                cc.stats.kernel_launches++;
+                return FEM_OK;
+            }
             const size_t sm = rr ? 0 : (size_t)2 * slab * 64 * 4;
             if (sm > 48 * 1024 &&
                 cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
@@ -1767,7 +2008,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         const double cost_sparse = (double)units_h[kBuckets + b] * (4.0 * nmax_of_class(nclass) + 40.0);
         bool sparse = sparse_ok && cost_sparse < cost_dense;
         if (ctx->tuning.kernel == 1) sparse = false;
-        if (ctx->tuning.kernel == 2) sparse = sparse_ok;
+        if (ctx->tuning.kernel >= 2) sparse = sparse_ok;
         // lanes per CTA: up to 256, but no wider than the bucket needs
         int K = ctx->tuning.lanes_per_cta > 0 ? ctx->tuning.lanes_per_cta : std::min(256, ((se - sb) + 31) / 32 * 32);
         int T = T_def;
