@@ -63,6 +63,11 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi's start-up (driver queries) must not overlap the timed
+            # steps: wait for its first sample before the caller starts timing.
+            t_end = time.time() + 15.0
+            while not self.rows and self.proc.poll() is None and time.time() < t_end:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -425,7 +430,7 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")

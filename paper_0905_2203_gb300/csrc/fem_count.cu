@@ -1528,9 +1528,10 @@ static SparseFn sparse_fn(int nclass, int rr) {
 int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int n_recs, const int64_t *d_n_threads,
                      int64_t cap_threads, const int64_t *offs, const uint16_t *ctypes, const int32_t *clo,
                      const int32_t *chi, const int32_t *slot2cand, const uint32_t *cand_rec, int32_t *rec,
-                     const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count) {
+                     const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count,
+                     const uint32_t *const *dens, const int32_t *lo_vals, int n_lo) {
     const int nclass = nmax == 2 ? 0 : nmax == 4 ? 1 : nmax == 8 ? 2 : 3;
-    SparseFn f = sparse_fn(nclass, 0);
+    SparseUFn f = sparse_u_fn(nclass);
     if (!f) return FEM_ERR_CUDA;
     SparseArgs sa{};
     sa.rinfo = rinfo;
@@ -1546,7 +1547,11 @@ int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int
     sa.relaxed = 0;
     sa.R = R;
     sa.rec = rec;
-    const size_t sm = sparse_smem(nclass, R);
+    sa.dens = dens;
+    sa.lo_vals = lo_vals;
+    sa.n_lo = n_lo;
+    sa.slab = (nmax - 1) * R;  // every node's ring fits R entries (checked by the caller)
+    const size_t sm = sparse_u_smem(nmax, sa.slab);
     if (sm > 48 * 1024 &&
         cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return FEM_ERR_CUDA;

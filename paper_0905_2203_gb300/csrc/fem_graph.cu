@@ -313,7 +313,8 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
     // smem attribute for the sparse kernels before capture
     for (int N = 3; N <= L; ++N) {
         const int nmax = N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : 16;
-        if (sparse_smem_bytes(nmax, kRingCap) > (size_t)ctx->smem_optin - 1024) return FEM_ERR_INVAL;
+        if ((size_t)(5 * (nmax - 1) + 2 * (nmax - 1) * kRingCap) * 64 * 4 > (size_t)ctx->smem_optin - 1024)
+            return FEM_ERR_INVAL;
     }
 
     // ---- capture levels 3..L
@@ -338,7 +339,7 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
         k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), kRingCap, cn);
         if (cst == FEM_OK)
             cst = launch_count_dev(st, nmax, kRingCap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch, iota,
-                                   crec, rec, cn, cap, counts, fb_list, cn + 3);
+                                   crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov, (int)lo_vals.size());
         k_g_thr_flags<<<gb, 256, 0, st>>>(counts, crec, g->d_thr, cn, cap, pos);
         if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
         k_g_thr_write<<<gb, 256, 0, st>>>(pos, counts, ct, cl, ch, crec, g->d_thr, N, cap, nf.types, nf.lo, nf.hi,

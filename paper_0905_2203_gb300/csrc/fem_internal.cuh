@@ -181,7 +181,8 @@ void result_set_stats(fem_result *r, const fem_stats &s);
 int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int n_recs, const int64_t *d_n_threads,
                      int64_t cap_threads, const int64_t *offs, const uint16_t *ctypes, const int32_t *clo,
                      const int32_t *chi, const int32_t *slot2cand, const uint32_t *cand_rec, int32_t *rec,
-                     const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count);
+                     const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count,
+                     const uint32_t *const *dens, const int32_t *lo_vals, int n_lo);
 size_t sparse_smem_bytes(int nmax, int R);
 // Segment boundaries (P + 1 entries) of a stream cut into P segments at time changes.
 int launch_segments(cudaStream_t st, const int32_t *time, int64_t n, int P, int64_t *seg);
