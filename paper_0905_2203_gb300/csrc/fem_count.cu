@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ?
             int4 *r = reinterpret_cast<int4 *>(a.rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P + item.p) *
                                                           kRecWords);
             int32_t w[kRecWords];
-            w[0] = st.ncls | st.flags;
+            w[0] = st.ncls | st.flags | (st.open ? 0 : kMetaClosed);
 #pragma unroll
             for (int j = 0; j < kClasses; ++j) {
                 w[1 + j] = st.cthr[j];
@@ -515,60 +515,136 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ?
     }
 }
 
-// Concat step: per episode (one warp), walk its segments in order with the
-// running end x of the last selected occurrence (minus infinity before the
-// first).  The warp stages 32 segment records at a time in shared memory
-// (coalesced 16-byte loads); the walk reads them back as broadcasts.
+// Concat step.  A segment's record is a map from the entry value x (end of
+// the last occurrence selected before the segment, minus infinity before the
+// first) to (occurrences added, exit value): the first class j with
+// x < thr[j] applies, and x passes through unchanged (nothing added) when no
+// class does.  Such maps compose into maps of the same form, so per episode
+// (one warp) each lane composes the records of a contiguous run of segments
+// into one map; a walk over the 32 lane maps then gives the count.  A lane's
+// map keeps up to kChunkClasses classes; if one overflows, the warp walks all
+// records in order instead (same result).
 constexpr int kStitchWarps = 4;
+constexpr int kChunkClasses = 8;
+
+__device__ __forceinline__ void stitch_apply(const int32_t *r, int ncls, int64_t &x, uint32_t &total) {
+#pragma unroll
+    for (int j = 0; j < kClasses; ++j)
+        if (j < ncls && x < (int64_t)r[1 + j]) {
+            total += (uint32_t)r[1 + kClasses + j];
+            x = r[1 + 2 * kClasses + j];
+            return;
+        }
+}
 
 __global__ void __launch_bounds__(kStitchWarps * 32)
     k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
              const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
              int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
              const int32_t *d_n_slots = nullptr) {
-    __shared__ __align__(16) int32_t buf[kStitchWarps][32 * kRecWords];
-    const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int n_live = d_n_slots ? *d_n_slots : n_slots;
-    for (int wi = blockIdx.x * kStitchWarps + w; wi < n_live; wi += gridDim.x * kStitchWarps) {
-    const int slot = slot_begin + wi;
-    const int cand = slot2cand[slot];
-    const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
-    const RecInfo ri = rinfo[r_id];
-    const int4 *base = reinterpret_cast<const int4 *>(rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * ri.P) *
-                                                      kRecWords);
-    int4 *sb = reinterpret_cast<int4 *>(buf[w]);
-    int64_t x = INT64_MIN;
-    uint32_t total = 0;
-    bool bad = false;
-    for (int p0 = 0; p0 < ri.P; p0 += 32) {
-        const int m = min(32, ri.P - p0);
-        const int nvec = m * (kRecWords / 4);
-        __syncwarp();
-        for (int v = lane; v < nvec; v += 32) sb[v] = base[(int64_t)p0 * (kRecWords / 4) + v];
-        __syncwarp();
-        for (int q = 0; q < m; ++q) {
-            const int32_t *r = buf[w] + q * kRecWords;
+    for (int wi = blockIdx.x * kStitchWarps + (threadIdx.x >> 5); wi < n_live; wi += gridDim.x * kStitchWarps) {
+        const int slot = slot_begin + wi;
+        const int cand = slot2cand[slot];
+        const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
+        const RecInfo ri = rinfo[r_id];
+        const int P = ri.P;
+        const int4 *base = reinterpret_cast<const int4 *>(
+            rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * P) * kRecWords);
+        // ---- this lane's run of segments [pa, pb) composed into one map
+        const int per = (P + 31) >> 5;
+        const int pa = min(P, lane * per), pb = min(P, pa + per);
+        int32_t fthr[kChunkClasses], flast[kChunkClasses];
+        uint32_t fcnt[kChunkClasses];
+#pragma unroll
+        for (int j = 0; j < kChunkClasses; ++j) fthr[j] = flast[j] = 0, fcnt[j] = 0;
+        int fm = 0;           // classes of the map
+        bool through = true;  // entry values above the last class still pass through
+        bool bad = false, ovf = false;
+        for (int p = pa; p < pb; ++p) {
+            int32_t r[kRecWords];
+#pragma unroll
+            for (int q = 0; q < kRecWords / 4; ++q) {
+                const int4 v = base[(int64_t)p * (kRecWords / 4) + q];
+                r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
+            }
             const int meta = r[0];
             if (meta & (kMetaRingOverflow | kMetaClassOverflow)) bad = true;
             const int ncls = meta & 0xFF;
-            for (int j = 0; j < ncls; ++j) {
-                if (x < (int64_t)r[1 + j]) {
-                    total += (uint32_t)r[1 + kClasses + j];
-                    x = r[1 + 2 * kClasses + j];
-                    break;
+            if (ncls == 0) continue;
+            // classes already in the map have a known exit value: run it on
+#pragma unroll
+            for (int j = 0; j < kChunkClasses; ++j)
+                if (j < fm) {
+                    int64_t x = flast[j];
+                    uint32_t t = fcnt[j];
+                    stitch_apply(r, ncls, x, t);
+                    flast[j] = (int32_t)x;
+                    fcnt[j] = t;
                 }
+            if (!through) continue;
+            // entry values still passing through meet this segment's classes
+            // above the map's last threshold
+            const int64_t floor_thr = fm > 0 ? (int64_t)fthr[fm - 1] : INT64_MIN;
+#pragma unroll
+            for (int i = 0; i < kClasses; ++i)
+                if (i < ncls && (int64_t)r[1 + i] > floor_thr) {
+                    if (fm == kChunkClasses) {
+                        ovf = true;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < kChunkClasses; ++j)
+                            if (j == fm) {
+                                fthr[j] = r[1 + i];
+                                fcnt[j] = (uint32_t)r[1 + kClasses + i];
+                                flast[j] = r[1 + 2 * kClasses + i];
+                            }
+                        ++fm;
+                    }
+                }
+            if (meta & kMetaClosed) through = false;
+        }
+        const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
+        const bool any_ovf = __any_sync(0xFFFFFFFFu, ovf);
+        int64_t x = INT64_MIN;
+        uint32_t total = 0;
+        if (!any_bad && !any_ovf) {
+            // ---- walk the 32 lane maps in segment order
+            for (int l = 0; l < 32; ++l) {
+                if (lane == l) {
+                    bool hit = false;
+#pragma unroll
+                    for (int j = 0; j < kChunkClasses; ++j)
+                        if (!hit && j < fm && x < (int64_t)fthr[j]) {
+                            total += fcnt[j];
+                            x = flast[j];
+                            hit = true;
+                        }
+                }
+                x = __shfl_sync(0xFFFFFFFFu, x, l);
+                total = __shfl_sync(0xFFFFFFFFu, total, l);
+            }
+        } else if (!any_bad) {
+            // ---- a lane map overflowed: walk every record in order
+            for (int p = 0; p < P; ++p) {
+                int32_t r[kRecWords];
+#pragma unroll
+                for (int q = 0; q < kRecWords / 4; ++q) {
+                    const int4 v = base[(int64_t)p * (kRecWords / 4) + q];
+                    r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
+                }
+                stitch_apply(r, r[0] & 0xFF, x, total);
             }
         }
-    }
-    if (lane == 0) {
-        if (bad) {
-            const int q = atomicAdd(fb_count, 1);
-            fb_list[q] = cand;
-        } else {
-            counts[cand] = total;
+        if (lane == 0) {
+            if (any_bad) {
+                const int q = atomicAdd(fb_count, 1);
+                fb_list[q] = cand;
+            } else {
+                counts[cand] = total;
+            }
         }
-    }
     }
 }
 
@@ -1132,7 +1208,7 @@ __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs 
     st.finish();
     int4 *r = reinterpret_cast<int4 *>(a.rec + tr * kRecWords);
     int32_t w[kRecWords];
-    w[0] = st.ncls | st.flags;
+    w[0] = st.ncls | st.flags | (st.open ? 0 : kMetaClosed);
 #pragma unroll
     for (int j = 0; j < kClasses; ++j) {
         w[1 + j] = st.cthr[j];
@@ -1342,7 +1418,7 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
         st.finish();
         int4 *r = reinterpret_cast<int4 *>(a.rec + tr * kRecWords);
         int32_t w[kRecWords];
-        w[0] = st.ncls | st.flags;
+        w[0] = st.ncls | st.flags | (st.open ? 0 : kMetaClosed);
 #pragma unroll
         for (int j = 0; j < kClasses; ++j) {
             w[1 + j] = st.cthr[j];

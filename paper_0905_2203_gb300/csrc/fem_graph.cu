@@ -124,12 +124,18 @@ __global__ void k_g_recinfo(const uint32_t *crec, const int32_t *ctr, int n_recs
     }
 }
 
-// Every node's ring must fit kRingCap entries (window density + 1).
+// Every node's ring must fit kRingCap entries (window density + 1).  Also
+// sums the candidates' relevant events (sum over nodes of the node type's
+// frequency in the candidate's recording) into *rel.
 __global__ void k_g_ringcheck(const uint16_t *ct, const int32_t *cl, const uint32_t *crec, const int32_t *ctr, int N,
-                              const uint32_t *const *dens, const int32_t *lo_vals, int n_lo, int R_cap, int32_t *ctr_w) {
+                              const uint32_t *const *dens, const int32_t *lo_vals, int n_lo, int R_cap,
+                              const RecInfo *ri, int32_t *ctr_w, unsigned long long *rel) {
     const int64_t C = ctr[0];
+    unsigned long long acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t r = crec[i];
+        const uint32_t *fq = ri[r].freq;
+        for (int k = 0; k < N; ++k) acc += fq[ct[i * N + k]];
         for (int k = 0; k < N - 1; ++k) {
             const int32_t l = cl[i * (N - 1) + k];
             int j = 0;
@@ -138,6 +144,8 @@ __global__ void k_g_ringcheck(const uint16_t *ct, const int32_t *cl, const uint3
             if (d == 0xFFFFFFFFu || d + 1 > (uint32_t)R_cap) atomicOr(&ctr_w[2], 2);
         }
     }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(rel, acc);
 }
 
 __global__ void k_g_thr_flags(const uint32_t *counts, const uint32_t *crec, const uint32_t *thr, const int32_t *ctr,
@@ -204,6 +212,8 @@ struct GraphTail {
     int32_t *ctr = nullptr;                // kCtr per level, indexed by N
     int64_t *coff = nullptr;               // (n_recs + 1) per level
     uint32_t *d_thr = nullptr;
+    unsigned long long *rel = nullptr;    // relevant events counted, per level
+    std::vector<cudaEvent_t> ev;           // around each level's count kernels
     cudaGraphExec_t exec = nullptr;
 
     template <typename T>
@@ -218,6 +228,7 @@ struct GraphTail {
     ~GraphTail() {
         if (exec) cudaGraphExecDestroy(exec);
         cudaStreamSynchronize(ctx->stream);
+        for (auto e : ev) cudaEventDestroy(e);
         for (auto &h : held) dev_free(ctx, h.first, h.second);
     }
 };
@@ -293,6 +304,9 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
     FEM_TRY(g->get(&g->d_thr, n_recs));
     FEM_TRY(g->get(&g->ctr, (size_t)(L + 1) * kCtr));
     FEM_TRY(g->get(&g->coff, (size_t)(L + 1) * (n_recs + 1)));
+    FEM_TRY(g->get(&g->rel, (size_t)(L + 1)));
+    g->ev.assign(2 * (L + 1), nullptr);
+    for (auto &e : g->ev) FEM_CUDA_TRY(cudaEventCreate(&e));
     g->F.assign(L + 1, FLevel{});
     for (int N = 2; N <= L; ++N) {
         FLevel &f = g->F[N];
@@ -330,16 +344,25 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
         int32_t *cn = g->ctr + (size_t)N * kCtr;
         int64_t *coffN = g->coff + (size_t)N * (n_recs + 1);
         const int nmax = N <= 4 ? 4 : N <= 8 ? 8 : 16;
-        if (cudaMemsetAsync(cn, 0, sizeof(int32_t) * kCtr, st) != cudaSuccess) cst = FEM_ERR_CUDA;
+        if (cudaMemsetAsync(cn, 0, sizeof(int32_t) * kCtr, st) != cudaSuccess ||
+            cudaMemsetAsync(g->rel + N, 0, sizeof(unsigned long long), st) != cudaSuccess)
+            cst = FEM_ERR_CUDA;
         k_g_join_count<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos);
         if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
         k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl, ch, crec, cn);
         k_g_index<<<gb, 256, 0, st>>>(crec, cn, N, cap, offs, iota);
         k_g_recinfo<<<1, 256, 0, st>>>(crec, cn, n_recs, coffN, d_ri, nthreads);
-        k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), kRingCap, cn);
+        k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), kRingCap, d_ri, cn,
+                                          g->rel + N);
+        // external event nodes: their timestamps time the count kernels of
+        // this level on every launch of the graph
+        if (cst == FEM_OK && cudaEventRecordWithFlags(g->ev[2 * N], st, cudaEventRecordExternal) != cudaSuccess)
+            cst = FEM_ERR_CUDA;
         if (cst == FEM_OK)
             cst = launch_count_dev(st, nmax, kRingCap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch, iota,
                                    crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov, (int)lo_vals.size());
+        if (cst == FEM_OK && cudaEventRecordWithFlags(g->ev[2 * N + 1], st, cudaEventRecordExternal) != cudaSuccess)
+            cst = FEM_ERR_CUDA;
         k_g_thr_flags<<<gb, 256, 0, st>>>(counts, crec, g->d_thr, cn, cap, pos);
         if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
         k_g_thr_write<<<gb, 256, 0, st>>>(pos, counts, ct, cl, ch, crec, g->d_thr, N, cap, nf.types, nf.lo, nf.hi,
@@ -455,6 +478,8 @@ int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const st
     std::vector<int64_t> coff((size_t)(max_size + 1) * (n_recs + 1));
     FEM_CUDA_TRY(cudaMemcpyAsync(ctr.data(), g->ctr, 4 * ctr.size(), cudaMemcpyDeviceToHost, st));
     FEM_CUDA_TRY(cudaMemcpyAsync(coff.data(), g->coff, 8 * coff.size(), cudaMemcpyDeviceToHost, st));
+    std::vector<unsigned long long> rel((size_t)max_size + 1, 0ull);
+    FEM_CUDA_TRY(cudaMemcpyAsync(rel.data(), g->rel, 8 * rel.size(), cudaMemcpyDeviceToHost, st));
     FEM_TRY(sync_status(ctx));
     for (int N = 3; N <= max_size; ++N) {
         const int32_t *c = &ctr[(size_t)N * kCtr];
@@ -463,6 +488,19 @@ int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const st
     float gms = 0.f;
     cudaEventElapsedTime(&gms, ctx->ev0, ctx->ev1);
     out->graph_ms = gms;
+    // count-kernel time of the levels from the graph's event nodes (the whole
+    // graph's time if the driver cannot time them)
+    float cms = 0.f;
+    bool timed = true;
+    for (int N = 3; N <= max_size && timed; ++N) {
+        float m = 0.f;
+        if (cudaEventElapsedTime(&m, g->ev[2 * N], g->ev[2 * N + 1]) != cudaSuccess) timed = false;
+        cms += m;
+    }
+    if (!timed) cudaGetLastError();
+    out->count_ms = timed ? cms : gms;
+    out->relevant = 0.0;
+    for (int N = 3; N <= max_size; ++N) out->relevant += (double)rel[N];
     // results
     out->levels.clear();
     for (int N = 3; N <= max_size; ++N) {

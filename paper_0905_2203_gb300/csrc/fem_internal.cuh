@@ -34,6 +34,10 @@ constexpr int kStatusInval = 2;
 // Record meta bits.
 constexpr int kMetaRingOverflow = 1 << 8;
 constexpr int kMetaClassOverflow = 1 << 9;
+// The segment's classes catch every entry value that can reach it: some class
+// threshold is at or after the segment's first event time, and every end
+// selected in earlier segments lies before that time.
+constexpr int kMetaClosed = 1 << 10;
 
 // ---------------------------------------------------------------------------
 struct DevBuf {
@@ -67,6 +71,8 @@ struct TailLevel {
 struct TailResult {
     std::vector<TailLevel> levels;
     float graph_ms = 0.f;             // device time of the graph launch
+    float count_ms = 0.f;             // of which in the count kernels (+ stitch)
+    double relevant = 0.0;            // relevant episode-events of the counted levels
 };
 struct GraphTail;
 

@@ -744,7 +744,8 @@ int MineGroup::graph_tail() {
         }
     }
     S.graph_tails += 1;
-    S.count_kernel_ms += tr.graph_ms;
+    S.count_kernel_ms += tr.count_ms;
+    S.relevant_events += tr.relevant;
     // the episode-events of the level-3 candidates were added when they were
     // prepared on the host; the graph recounted them, so remove that share
     for (int r = 0; r < n_recs; ++r) S.episode_events -= (double)(c_off[r + 1] - c_off[r]) * (double)recs[r]->n;

@@ -130,6 +130,26 @@ def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
         ctx.reset_tuning()
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("segments", [0, 33, 1000, 4099])
+def test_few_episodes_many_segments(fb, ctx, segments, kernel):
+    """Few episodes over the 1M-event mid stream cut into up to ~4k segments:
+    each episode's count is stitched from thousands of segment records
+    (several per lane of the stitch warp, with a ragged last run)."""
+    s, cfg = synth.c2_mid()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    offs, ct, lo, hi = synth.random_candidates(0xFE0102, 48, s.n_types, 2, 6, cfg["bins"], s.chains, 0.5)
+    want = oracle_counts(s.types, s.times, offs, ct, lo, hi)
+    ctx.set_tuning(segments=segments, kernel=kernel)
+    try:
+        got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+    finally:
+        ctx.reset_tuning()
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:5]
+    assert want.max() > 0
+    st.free()
+
+
 def test_c1_random_candidates(fb, ctx):
     s, _ = synth.c1_tiny()
     st = ctx.load_stream(s.types, s.times, s.n_types)
