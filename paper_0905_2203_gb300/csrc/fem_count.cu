@@ -1229,21 +1229,28 @@ __global__ void __launch_bounds__(RR == 0 ? 64 : 128) k_count_sparse(SparseArgs 
 // them instead of branching per node (lanes of a warp are usually at
 // different nodes).  Thread i's words are strided by the block size:
 // header word w at w*64 + i, ring times at (H + e)*64 + i, ring starts at
-// (H + slab + e)*64 + i, with H = 5*(NMAX-1).
+// (H + slab + e)*64 + i, with H = 6*(NMAX-1).
+//
+// A node's ring is a queue in time order: entries from the tail up to the
+// head are not yet past the node's lower bound; the entry just before the
+// tail is the newest one that is.  Queries of a node come in time order, so
+// the tail only moves forward and a query costs one comparison per entry
+// that becomes eligible plus one.
 template <int NMAX>
 __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
     extern __shared__ int32_t s_u[];
-    constexpr int HW = 5 * (NMAX - 1);
+    constexpr int HW = 6 * (NMAX - 1);
     const int bd = blockDim.x;
     int32_t *hdr = s_u + threadIdx.x;                 // [w * bd]
     int32_t *rT = s_u + HW * bd + threadIdx.x;        // [e * bd]
     int32_t *rL = s_u + (HW + a.slab) * bd + threadIdx.x;
-    // header fields of node k: off, cap, head, lo, hi
-#define H_OFF(k) hdr[(5 * (k) + 0) * bd]
-#define H_CAP(k) hdr[(5 * (k) + 1) * bd]
-#define H_HEAD(k) hdr[(5 * (k) + 2) * bd]
-#define H_LO(k) hdr[(5 * (k) + 3) * bd]
-#define H_HI(k) hdr[(5 * (k) + 4) * bd]
+    // header fields of node k: off, cap, head, lo, hi, tail
+#define H_OFF(k) hdr[(6 * (k) + 0) * bd]
+#define H_CAP(k) hdr[(6 * (k) + 1) * bd]
+#define H_HEAD(k) hdr[(6 * (k) + 2) * bd]
+#define H_LO(k) hdr[(6 * (k) + 3) * bd]
+#define H_HI(k) hdr[(6 * (k) + 4) * bd]
+#define H_TAIL(k) hdr[(6 * (k) + 5) * bd]
     const int64_t n_thr = a.d_n_threads ? *a.d_n_threads : a.n_threads;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_thr; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t tr = a.rec_first + t;
@@ -1295,6 +1302,7 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
             H_OFF(k) = used;
             H_CAP(k) = c;
             H_HEAD(k) = 0;
+            H_TAIL(k) = 0;
             H_LO(k) = l;
             H_HI(k) = h;
             used += c;
@@ -1307,12 +1315,15 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
 
         const int64_t seg_b = ri.seg[p], seg_e = ri.seg[p + 1];
         int32_t Tp = 0;
-        int32_t head[NMAX];
+        // head[k]: time at list cursor cur[k]; nxt[k]: the one after it,
+        // loaded one step early so that the merge does not wait on it
+        int32_t head[NMAX], nxt[NMAX];
         int32_t cur[NMAX], end[NMAX];
         uint32_t nodes[NMAX];  // nodes sharing the cursor's type (bit k = node k)
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) {
             head[k] = INT32_MAX;
+            nxt[k] = INT32_MAX;
             cur[k] = 0;
             end[k] = 0;
             nodes[k] = 0;
@@ -1352,6 +1363,7 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
                 cur[k] = (int32_t)lo_i;
                 end[k] = (int32_t)e_i;
                 head[k] = lo_i < e_i ? ri.ttime[lo_i] : INT32_MAX;
+                nxt[k] = lo_i + 1 < e_i ? ri.ttime[lo_i + 1] : INT32_MAX;
             }
             for (;;) {
                 int32_t tt = INT32_MAX;
@@ -1369,7 +1381,8 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
                     if (k == bk) {
                         mask = nodes[k];
                         cur[k] += 1;
-                        head[k] = cur[k] < end[k] ? ri.ttime[cur[k]] : INT32_MAX;
+                        head[k] = nxt[k];
+                        nxt[k] = cur[k] + 1 < end[k] ? ri.ttime[cur[k] + 1] : INT32_MAX;
                     }
                 const bool in_seg = tt >= Tp;
                 // nodes of this type, last to first (one node unless the
@@ -1382,19 +1395,15 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
                     int32_t L = tt;
                     if (k > 0) {
                         const int q = k - 1;
-                        const int32_t base = H_OFF(q), R = H_CAP(q);
+                        const int32_t base = H_OFF(q), R = H_CAP(q), hd = H_HEAD(q);
                         const int32_t elig = tt - H_LO(q), expire = tt - H_HI(q);
-                        int idx = H_HEAD(q);
-                        bool ok = false;
-                        for (int i = 0; i < R; ++i) {
-                            idx = (idx == 0) ? R - 1 : idx - 1;
-                            const int32_t tp = rT[(base + idx) * bd];
-                            if (tp < elig) {
-                                ok = tp >= expire;
-                                L = rL[(base + idx) * bd];
-                                break;
-                            }
-                        }
+                        int tl = H_TAIL(q);
+                        while (tl != hd && rT[(base + tl) * bd] < elig) tl = (tl + 1 == R) ? 0 : tl + 1;
+                        H_TAIL(q) = tl;
+                        const int le = (tl == 0) ? R - 1 : tl - 1;  // newest eligible entry
+                        const int32_t tp = rT[(base + le) * bd];
+                        const bool ok = tp != INT32_MIN && tp >= expire;
+                        if (ok) L = rL[(base + le) * bd];
                         if (ok) {
                             if (k == N - 1)
                                 do_end = true;
@@ -1404,13 +1413,21 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
                     }
                     if (do_end && in_seg) st.greedy_end(tt, L, Tp);
                     if (do_push) {
+                        // entries already past the lower bound at tt stay so
+                        // for every later query: retire them first, so the
+                        // queue holds only entries inside [tt - lo, tt]
+                        // (at most the window density, one less than the
+                        // ring) and a full ring means the density was wrong
                         const int32_t base = H_OFF(k), R = H_CAP(k), h = H_HEAD(k);
+                        const int32_t eg = tt - H_LO(k);
+                        int tl = H_TAIL(k);
+                        while (tl != h && rT[(base + tl) * bd] < eg) tl = (tl + 1 == R) ? 0 : tl + 1;
                         const int h2 = (h + 1 == R) ? 0 : h + 1;
-                        const int32_t o1 = rT[(base + h) * bd], o2 = rT[(base + h2) * bd];
-                        if (o1 != INT32_MIN && o1 >= tt - H_HI(k) && o2 >= tt - H_LO(k)) st.flags |= kMetaRingOverflow;
+                        if (h2 == tl) st.flags |= kMetaRingOverflow;
                         rT[(base + h) * bd] = tt;
                         rL[(base + h) * bd] = L;
                         H_HEAD(k) = h2;
+                        H_TAIL(k) = tl;
                     }
                 }
             }
@@ -1435,10 +1452,11 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
 #undef H_HEAD
 #undef H_LO
 #undef H_HI
+#undef H_TAIL
 }
 
 // Shared memory of a node-uniform sparse block (64 threads, slab entries).
-static size_t sparse_u_smem(int nmax, int slab) { return (size_t)(5 * (nmax - 1) + 2 * slab) * 64 * 4; }
+static size_t sparse_u_smem(int nmax, int slab) { return (size_t)(6 * (nmax - 1) + 2 * slab) * 64 * 4; }
 
 typedef void (*SparseUFn)(SparseArgs);
 static SparseUFn sparse_u_fn(int nclass) {
@@ -1601,7 +1619,7 @@ static SparseFn sparse_fn(int nclass, int rr) {
 // shared-memory rings of R entries over up to cap_threads (episode, segment)
 // threads, then the stitch over up to cap_slots episodes; the live sizes are
 // read from device memory.
-int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int n_recs, const int64_t *d_n_threads,
+int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo *rinfo, int n_recs, const int64_t *d_n_threads,
                      int64_t cap_threads, const int64_t *offs, const uint16_t *ctypes, const int32_t *clo,
                      const int32_t *chi, const int32_t *slot2cand, const uint32_t *cand_rec, int32_t *rec,
                      const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count,
@@ -1626,7 +1644,7 @@ int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int
     sa.dens = dens;
     sa.lo_vals = lo_vals;
     sa.n_lo = n_lo;
-    sa.slab = (nmax - 1) * R;  // every node's ring fits R entries (checked by the caller)
+    sa.slab = (nodes - 1) * R;  // every node's ring fits R entries (checked by the caller)
     const size_t sm = sparse_u_smem(nmax, sa.slab);
     if (sm > 48 * 1024 &&
         cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)

@@ -212,6 +212,7 @@ struct GraphTail {
     int32_t *ctr = nullptr;                // kCtr per level, indexed by N
     int64_t *coff = nullptr;               // (n_recs + 1) per level
     uint32_t *d_thr = nullptr;
+    int ring_cap = kRingCap;               // ring entries per node
     unsigned long long *rel = nullptr;    // relevant events counted, per level
     std::vector<cudaEvent_t> ev;           // around each level's count kernels
     cudaGraphExec_t exec = nullptr;
@@ -279,6 +280,19 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
         }
     }
     g->cap_threads = cap * Pmax;
+    // ring entries per node: the largest window density of any type + 1
+    // (capped at kRingCap; nodes needing more are flagged by the ring check)
+    uint32_t dmax = 1;
+    for (int r = 0; r < n_recs; ++r) {
+        std::vector<uint32_t> hd(g->recs[r]->n_types);
+        for (size_t j = 0; j < lo_vals.size(); ++j) {
+            FEM_CUDA_TRY(cudaMemcpyAsync(hd.data(), dens_h[(size_t)r * lo_vals.size() + j], 4 * hd.size(),
+                                         cudaMemcpyDeviceToHost, st));
+            FEM_CUDA_TRY(cudaStreamSynchronize(st));
+            for (uint32_t d : hd) dmax = std::max(dmax, d);
+        }
+    }
+    g->ring_cap = (int)std::min<uint32_t>(kRingCap, dmax + 1);
     RecInfo *d_ri;
     const uint32_t **d_dens;
     int32_t *d_lov, *pos, *fb_list, *iota, *rec;
@@ -327,7 +341,7 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
     // smem attribute for the sparse kernels before capture
     for (int N = 3; N <= L; ++N) {
         const int nmax = N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : 16;
-        if ((size_t)(5 * (nmax - 1) + 2 * (nmax - 1) * kRingCap) * 64 * 4 > (size_t)ctx->smem_optin - 1024)
+        if ((size_t)(6 * (nmax - 1) + 2 * (N - 1) * g->ring_cap) * 64 * 4 > (size_t)ctx->smem_optin - 1024)
             return FEM_ERR_INVAL;
     }
 
@@ -352,14 +366,14 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
         k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl, ch, crec, cn);
         k_g_index<<<gb, 256, 0, st>>>(crec, cn, N, cap, offs, iota);
         k_g_recinfo<<<1, 256, 0, st>>>(crec, cn, n_recs, coffN, d_ri, nthreads);
-        k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), kRingCap, d_ri, cn,
+        k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), g->ring_cap, d_ri, cn,
                                           g->rel + N);
         // external event nodes: their timestamps time the count kernels of
         // this level on every launch of the graph
         if (cst == FEM_OK && cudaEventRecordWithFlags(g->ev[2 * N], st, cudaEventRecordExternal) != cudaSuccess)
             cst = FEM_ERR_CUDA;
         if (cst == FEM_OK)
-            cst = launch_count_dev(st, nmax, kRingCap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch, iota,
+            cst = launch_count_dev(st, nmax, N, g->ring_cap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch, iota,
                                    crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov, (int)lo_vals.size());
         if (cst == FEM_OK && cudaEventRecordWithFlags(g->ev[2 * N + 1], st, cudaEventRecordExternal) != cudaSuccess)
             cst = FEM_ERR_CUDA;

@@ -184,7 +184,7 @@ void mg_destroy(MineGroup *g);
 int mg_count_batch(fem_ctx *ctx, const std::vector<MineGroup *> &gs);
 fem_result *result_new(int n_recs, int max_size);
 void result_set_stats(fem_result *r, const fem_stats &s);
-int launch_count_dev(cudaStream_t st, int nmax, int R, const RecInfo *rinfo, int n_recs, const int64_t *d_n_threads,
+int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo *rinfo, int n_recs, const int64_t *d_n_threads,
                      int64_t cap_threads, const int64_t *offs, const uint16_t *ctypes, const int32_t *clo,
                      const int32_t *chi, const int32_t *slot2cand, const uint32_t *cand_rec, int32_t *rec,
                      const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count,
