@@ -231,6 +231,186 @@ def c3_leg(ctx, tstream, flush, steps: int = 2):
             "sparse_launches_per_step": sp / steps}
 
 
+def _level_arrays(res, n_recs: int, max_size: int):
+    out = []
+    for r in range(n_recs):
+        for N in range(1, max_size + 1):
+            out.append(res.level(r, N))  # (episodes, counts), canonical order
+    return out
+
+
+def _same_levels(a, b) -> bool:
+    return len(a) == len(b) and all(x[0] == y[0] and x[1] == y[1] for x, y in zip(a, b))
+
+
+def _lat_summary(lat_s, ee, span_s):
+    lat = np.asarray(lat_s) * 1e3
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "episode_events_per_s": float(ee / span_s) if span_s > 0 else None}
+
+
+def serving_leg(n_jobs: int = 12, n_cap: int = 500_000, stress_n: int = 0, load: float = 0.7,
+                seed: int = 0xFE0005):
+    """Serving on a bounded sample of the job list (the first `n_jobs` jobs
+    with at most `n_cap` events, plus the stress job when stress_n > 0).
+    Arrivals are Poisson (seeded) at `load` x the served path's measured
+    capacity.  Three arms on the same arrival times:
+      served      -- the serving loop (admission by device memory, streams and
+                     candidates resident, ready levels of all admitted jobs
+                     counted together), live; latency = result ready - submit;
+      ours_fifo   -- the library's mine_levelwise, one job at a time;
+      plain_fifo  -- the plain per-level GPU path, one job at a time.
+    The FIFO arms' per-job service times (stream upload, mining, result read)
+    are measured on the GPU and queued first-in first-out on the arrival
+    times.  Every job's frequent episodes and counts must agree across arms."""
+    import torch
+    from paper_0905_2203_gb300 import binding as fb
+    jobs = [j for j in synth.serving_jobs(seed, stress_n=stress_n)]
+    stress = [j for j in jobs if j["n"] == stress_n] if stress_n else []
+    pick = [j for j in jobs if j["n"] <= n_cap][:n_jobs] + stress
+    data = [synth.make_job_stream(j) for j in pick]
+    K = len(pick)
+    srv = fb.Server(0, 0, 16)
+
+    def submit(i):
+        s, cfg = data[i]
+        return srv.submit(s.types, s.times, s.n_types, cfg["bins"], cfg["threshold"], cfg["max_size"])
+
+    def collect(ids):
+        lat, ee, arrays, sub, fin = [], 0.0, [], [], []
+        for i, jid in enumerate(ids):
+            res, info = srv.wait(jid)
+            lat.append(info["finish_s"] - info["submit_s"])
+            sub.append(info["submit_s"])
+            fin.append(info["finish_s"])
+            ee += res.stats()["episode_events"]
+            arrays.append(_level_arrays(res, 1, data[i][1]["max_size"]))
+            res.free()
+        return lat, ee, arrays, min(sub), max(fin)
+
+    # warm-up (kernel loading, first allocations), then capacity: all at once
+    collect([submit(0)])
+    _, ee_all, _, t_a, t_b = collect([submit(i) for i in range(K)])
+    capacity = K / max(t_b - t_a, 1e-9)
+    lam = load * capacity
+    u = synth.Rng(seed, 11).uniform(K)
+    arrive = np.cumsum(-np.log1p(-u) / lam)
+    t0 = time.perf_counter()
+    ids = []
+    for i in range(K):
+        d = t0 + arrive[i] - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        ids.append(submit(i))
+    lat_srv, ee_srv, arr_srv, t_a, t_b = collect(ids)
+    srv.close()
+
+    def fifo(plain: bool):
+        ctx = fb.Context(0)
+        if plain:
+            ctx.set_tuning(plain_path=1)
+        svc, arrays, ee = [], [], 0.0
+        for i in range(-1, K):  # i = -1: warm-up on the first job
+            s, cfg = data[max(i, 0)]
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st = ctx.load_stream(s.types, s.times, s.n_types)
+            res = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
+            a = _level_arrays(res, 1, cfg["max_size"])
+            e = res.stats()["episode_events"]
+            res.free()
+            st.free()
+            dt = time.perf_counter() - t
+            if i >= 0:
+                svc.append(dt)
+                arrays.append(a)
+                ee += e
+        ctx.close()
+        end, lat = 0.0, []
+        for i in range(K):
+            start = max(arrive[i], end)
+            end = start + svc[i]
+            lat.append(end - arrive[i])
+        return lat, ee, arrays, end - arrive[0], svc
+
+    lat_o, ee_o, arr_o, span_o, svc_o = fifo(False)
+    lat_p, ee_p, arr_p, span_p, svc_p = fifo(True)
+    parity = all(_same_levels(a, b) and _same_levels(a, c) for a, b, c in zip(arr_srv, arr_o, arr_p))
+    return {
+        "workload": f"serving sample: {K} jobs of the job list (n <= {n_cap}"
+                    + (f", plus the {stress_n}-event stress job" if stress else "") + "), "
+                    f"{int(sum(d[0].n for d in data))} events, 60-256 types, max size 4-8, 10 us ticks",
+        "arrivals": f"Poisson, {lam:.2f} jobs/s = {load} x served capacity ({capacity:.2f} jobs/s)",
+        "served": _lat_summary(lat_srv, ee_srv, t_b - t_a),
+        "ours_fifo": dict(_lat_summary(lat_o, ee_o, span_o), service_ms_mean=1e3 * float(np.mean(svc_o))),
+        "plain_fifo": dict(_lat_summary(lat_p, ee_p, span_p), service_ms_mean=1e3 * float(np.mean(svc_p))),
+        "parity_across_arms": bool(parity),
+        "note": "p99 over the sample's jobs (interpolated); FIFO arms queued on the same arrivals",
+    }
+
+
+def run_c4(args):
+    """Multi-recording batched mining on a bounded sample of the 256-recording
+    set (the first `--c4-recs` recordings): levels 1-6 of all of them in one
+    mine_levelwise call per step, against one call per recording and against
+    the plain per-level path; results must agree recording by recording."""
+    import torch
+    from paper_0905_2203_gb300 import binding as fb
+    recs = synth.c4_recordings()[: args.c4_recs]
+    ctx = fb.Context(0)
+    sts = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
+    bins = recs[0][1]["bins"]
+    thr = [c["threshold"] for _, c in recs]
+    max_size = recs[0][1]["max_size"]
+
+    def batched():
+        res = ctx.mine_levelwise(sts, bins, thr, max_size)
+        a = _level_arrays(res, len(sts), max_size)
+        ee = res.stats()["episode_events"]
+        res.free()
+        return a, ee
+
+    def per_rec():
+        out, ee = [], 0.0
+        for st, t in zip(sts, thr):
+            res = ctx.mine_levelwise([st], bins, [t], max_size)
+            out += _level_arrays(res, 1, max_size)
+            ee += res.stats()["episode_events"]
+            res.free()
+        return out, ee
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(steps):
+            a, ee = fn()
+        torch.cuda.synchronize()
+        return a, ee, (time.perf_counter() - t) / steps
+
+    a_b, ee_b, t_b = timed(batched, args.steps)
+    a_r, ee_r, t_r = timed(per_rec, max(1, args.steps // 2))
+    ctx.set_tuning(plain_path=1)
+    a_p, ee_p, t_p = timed(per_rec, 1)
+    n_tot = sum(s.n for s, _ in recs)
+    line = {"metric": METRIC, "value": ee_b / t_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"batched multi-recording mining: first {len(recs)} of the 256 60-channel "
+                                   f"recordings ({n_tot} events), levels 1-{max_size}, one call per step",
+                       "timing": "host wall clock around synchronised steps"},
+            "per_recording_calls": {"value": ee_r / t_r, "ms_per_step": 1e3 * t_r},
+            "plain_gpu": {"value": ee_p / t_p, "ms_per_step": 1e3 * t_p},
+            "parity_batched_vs_per_recording": _same_levels(a_b, a_r),
+            "parity_batched_vs_plain": _same_levels(a_b, a_p)}
+    for st in sts:
+        st.free()
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_case(name: str):
     """Small fixed invocations used for ncu captures (no timing line):
     c2_level2_tiled -- one C2 mining pass with the pre-pass off and the tiled
@@ -371,6 +551,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = e2e_ee * world / (e2e_ms / 1e3)
 
     c3 = None if args.no_c3 else c3_leg(ctx, tstream, flush)
+    serving = None if args.no_serving else serving_leg()
     if rank != 0:
         return
     peaks = _peaks()
@@ -418,6 +599,7 @@ def run_ours(args, rank, world, local_rank):
         "kernels": {"sparse_launches_per_step": sparse_launches / args.steps,
                     "graph_tail_steps": graph_tails},
         "c3_batched_counting": c3,
+        "serving": serving,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -436,6 +618,11 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-c3", action="store_true", help="skip the batched-counting (C3) leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency leg")
+    ap.add_argument("--c4-recs", type=int, default=32, help="recordings of the multi-recording set (--workload c4)")
+    ap.add_argument("--c5-jobs", type=int, default=40, help="jobs of the serving sample (--workload c5)")
+    ap.add_argument("--c5-cap", type=int, default=4_000_000, help="largest job of the serving sample (--workload c5)")
+    ap.add_argument("--c5-stress", type=int, default=0, help="add the stress job with this many events (--workload c5)")
     ap.add_argument("--quick", action="store_true",
                     help="time the tiled path only (no plain-path, e2e or CPU legs); for profiling")
     ap.add_argument("--case", default=None,
@@ -449,6 +636,15 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "c4":
+        if rank == 0:
+            run_c4(args)
+        return
+    if args.workload == "c5":
+        if rank == 0:
+            print(json.dumps({"workload": "c5", "serving": serving_leg(args.c5_jobs, args.c5_cap, args.c5_stress)}),
+                  flush=True)
         return
     if world > 1:
         import torch

@@ -527,21 +527,197 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ?
 constexpr int kStitchWarps = 4;
 constexpr int kChunkClasses = 8;
 
-__device__ __forceinline__ void stitch_apply(const int32_t *r, int ncls, int64_t &x, uint32_t &total) {
+// Entry values are times (>= 0) or minus infinity, held as INT32_MIN.
+__device__ __forceinline__ void stitch_apply(const int32_t (&r)[kRecWords], int ncls, int ncw, int32_t &x,
+                                             uint32_t &total) {
+    bool hit = false;
+    int32_t nx = x;
+    uint32_t add = 0;
 #pragma unroll
-    for (int j = 0; j < kClasses; ++j)
-        if (j < ncls && x < (int64_t)r[1 + j]) {
-            total += (uint32_t)r[1 + kClasses + j];
-            x = r[1 + 2 * kClasses + j];
-            return;
+    for (int j = 0; j < kClasses; ++j) {
+        if (j >= ncw) break;  // warp-uniform bound
+        if (!hit && j < ncls && x < r[1 + j]) {
+            add = (uint32_t)r[1 + kClasses + j];
+            nx = r[1 + 2 * kClasses + j];
+            hit = true;
+        }
+    }
+    x = nx;
+    total += add;
+}
+
+// One lane's map: the records of segments [pa, pb) composed in order.
+struct LaneMap {
+    int32_t thr[kChunkClasses], last[kChunkClasses];
+    uint32_t cnt[kChunkClasses];
+    int m;          // classes
+    int32_t top;    // last threshold (INT32_MIN without classes)
+    bool through;   // entry values above top pass through unchanged
+    bool bad;       // a record is flagged (ring or class overflow)
+    bool ovf;       // more than kChunkClasses classes
+};
+
+// Composes this lane's records [pa, pb); every lane of the warp calls it with
+// the same `per` (its trip count), so the warp-wide bounds below are safe.
+__device__ __forceinline__ void stitch_compose(const int4 *__restrict__ base, int pa, int pb, int per, LaneMap &f) {
+#pragma unroll
+    for (int j = 0; j < kChunkClasses; ++j) f.thr[j] = f.last[j] = 0, f.cnt[j] = 0;
+    f.m = 0;
+    f.bad = f.ovf = false;
+    f.top = INT32_MIN;
+    f.through = true;
+    // records are loaded one ahead of the one being composed
+    int4 nx[kRecWords / 4];
+#pragma unroll
+    for (int q = 0; q < kRecWords / 4; ++q)
+        nx[q] = pa < pb ? base[(int64_t)pa * (kRecWords / 4) + q] : make_int4(0, 0, 0, 0);
+    for (int i = 0; i < per; ++i) {
+        const int p = pa + i;
+        int32_t r[kRecWords];
+#pragma unroll
+        for (int q = 0; q < kRecWords / 4; ++q) {
+            const int4 v = nx[q];
+            r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
+        }
+        if (p + 1 < pb) {
+#pragma unroll
+            for (int q = 0; q < kRecWords / 4; ++q) nx[q] = base[(int64_t)(p + 1) * (kRecWords / 4) + q];
+        }
+        const int meta = p < pb ? r[0] : 0;
+        if (meta & (kMetaRingOverflow | kMetaClassOverflow)) f.bad = true;
+        const int ncls = meta & 0xFF;
+        const int ncw = __reduce_max_sync(0xFFFFFFFFu, ncls);
+        if (ncw == 0) continue;
+        const int fmw = __reduce_max_sync(0xFFFFFFFFu, f.m);
+        // classes already in the map have a known exit value: run it on
+#pragma unroll
+        for (int j = 0; j < kChunkClasses; ++j) {
+            if (j >= fmw) break;
+            if (j < f.m && ncls > 0) {
+                int32_t x = f.last[j];
+                uint32_t t = f.cnt[j];
+                stitch_apply(r, ncls, ncw, x, t);
+                f.last[j] = x;
+                f.cnt[j] = t;
+            }
+        }
+        if (!f.through || ncls == 0) continue;
+        // entry values still passing through meet this segment's classes
+        // above the map's last threshold
+        const int32_t floor_thr = f.top;
+#pragma unroll
+        for (int c = 0; c < kClasses; ++c) {
+            if (c >= ncls) break;
+            if (r[1 + c] > floor_thr) {
+                if (f.m == kChunkClasses) {
+                    f.ovf = true;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kChunkClasses; ++j)
+                        if (j == f.m) {
+                            f.thr[j] = r[1 + c];
+                            f.cnt[j] = (uint32_t)r[1 + kClasses + c];
+                            f.last[j] = r[1 + 2 * kClasses + c];
+                        }
+                    ++f.m;
+                    f.top = r[1 + c];
+                }
+            }
+        }
+        if (meta & kMetaClosed) f.through = false;
+    }
+}
+
+// x -> the lane map's (x', total += added): the first class with x < thr.
+__device__ __forceinline__ void lanemap_apply(const LaneMap &f, int32_t &x, uint32_t &total) {
+    bool hit = false;
+#pragma unroll
+    for (int j = 0; j < kChunkClasses; ++j)
+        if (!hit && j < f.m && x < f.thr[j]) {
+            total += f.cnt[j];
+            x = f.last[j];
+            hit = true;
         }
 }
 
+// a := a then b (the runs of a and b are adjacent, a's first).  a's classes
+// have known exits, which b maps on; entry values still passing through a
+// meet b's classes above a's last threshold.
+__device__ __forceinline__ void lanemap_then(LaneMap &a, const LaneMap &b) {
+#pragma unroll
+    for (int j = 0; j < kChunkClasses; ++j)
+        if (j < a.m) {
+            int32_t x = a.last[j];
+            uint32_t t = a.cnt[j];
+            lanemap_apply(b, x, t);
+            a.last[j] = x;
+            a.cnt[j] = t;
+        }
+    if (a.through) {
+#pragma unroll
+        for (int c = 0; c < kChunkClasses; ++c)
+            if (c < b.m && b.thr[c] > a.top) {
+                if (a.m == kChunkClasses) {
+                    a.ovf = true;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kChunkClasses; ++j)
+                        if (j == a.m) {
+                            a.thr[j] = b.thr[c];
+                            a.cnt[j] = b.cnt[c];
+                            a.last[j] = b.last[c];
+                        }
+                    ++a.m;
+                    a.top = b.thr[c];
+                }
+            }
+        a.through = b.through;
+    }
+    a.bad = a.bad || b.bad;
+    a.ovf = a.ovf || b.ovf;
+}
+
+// Tree composition of the warp's 32 lane maps (lane order); lane 0 ends with
+// the map of the warp's whole run.
+__device__ __forceinline__ void warp_compose(LaneMap &f, int lane) {
+#pragma unroll 1
+    for (int d = 1; d < 32; d <<= 1) {
+        LaneMap o;
+#pragma unroll
+        for (int j = 0; j < kChunkClasses; ++j) {
+            o.thr[j] = __shfl_down_sync(0xFFFFFFFFu, f.thr[j], d);
+            o.last[j] = __shfl_down_sync(0xFFFFFFFFu, f.last[j], d);
+            o.cnt[j] = __shfl_down_sync(0xFFFFFFFFu, f.cnt[j], d);
+        }
+        o.m = __shfl_down_sync(0xFFFFFFFFu, f.m, d);
+        o.top = __shfl_down_sync(0xFFFFFFFFu, f.top, d);
+        o.through = __shfl_down_sync(0xFFFFFFFFu, (int)f.through, d) != 0;
+        o.bad = __shfl_down_sync(0xFFFFFFFFu, (int)f.bad, d) != 0;
+        o.ovf = __shfl_down_sync(0xFFFFFFFFu, (int)f.ovf, d) != 0;
+        if ((lane & (2 * d - 1)) == 0 && lane + d < 32) lanemap_then(f, o);
+    }
+}
+
+// Every record of one episode in order (used when a lane map overflowed).
+__device__ void stitch_serial(const int4 *__restrict__ base, int P, int32_t &x, uint32_t &total) {
+    for (int p = 0; p < P; ++p) {
+        int32_t r[kRecWords];
+#pragma unroll
+        for (int q = 0; q < kRecWords / 4; ++q) {
+            const int4 v = base[(int64_t)p * (kRecWords / 4) + q];
+            r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
+        }
+        stitch_apply(r, r[0] & 0xFF, kClasses, x, total);
+    }
+}
+
+// One warp per episode, for episodes with at most max_P segments (the others
+// are left to k_stitch_block).
 __global__ void __launch_bounds__(kStitchWarps * 32)
     k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
              const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
              int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
-             const int32_t *d_n_slots = nullptr) {
+             const int32_t *d_n_slots = nullptr, int max_P = INT32_MAX) {
     const int lane = threadIdx.x & 31;
     const int n_live = d_n_slots ? *d_n_slots : n_slots;
     for (int wi = blockIdx.x * kStitchWarps + (threadIdx.x >> 5); wi < n_live; wi += gridDim.x * kStitchWarps) {
@@ -550,93 +726,22 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
         const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
         const RecInfo ri = rinfo[r_id];
         const int P = ri.P;
+        if (P > max_P) continue;
         const int4 *base = reinterpret_cast<const int4 *>(
             rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * P) * kRecWords);
-        // ---- this lane's run of segments [pa, pb) composed into one map
         const int per = (P + 31) >> 5;
         const int pa = min(P, lane * per), pb = min(P, pa + per);
-        int32_t fthr[kChunkClasses], flast[kChunkClasses];
-        uint32_t fcnt[kChunkClasses];
-#pragma unroll
-        for (int j = 0; j < kChunkClasses; ++j) fthr[j] = flast[j] = 0, fcnt[j] = 0;
-        int fm = 0;           // classes of the map
-        bool through = true;  // entry values above the last class still pass through
-        bool bad = false, ovf = false;
-        for (int p = pa; p < pb; ++p) {
-            int32_t r[kRecWords];
-#pragma unroll
-            for (int q = 0; q < kRecWords / 4; ++q) {
-                const int4 v = base[(int64_t)p * (kRecWords / 4) + q];
-                r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
-            }
-            const int meta = r[0];
-            if (meta & (kMetaRingOverflow | kMetaClassOverflow)) bad = true;
-            const int ncls = meta & 0xFF;
-            if (ncls == 0) continue;
-            // classes already in the map have a known exit value: run it on
-#pragma unroll
-            for (int j = 0; j < kChunkClasses; ++j)
-                if (j < fm) {
-                    int64_t x = flast[j];
-                    uint32_t t = fcnt[j];
-                    stitch_apply(r, ncls, x, t);
-                    flast[j] = (int32_t)x;
-                    fcnt[j] = t;
-                }
-            if (!through) continue;
-            // entry values still passing through meet this segment's classes
-            // above the map's last threshold
-            const int64_t floor_thr = fm > 0 ? (int64_t)fthr[fm - 1] : INT64_MIN;
-#pragma unroll
-            for (int i = 0; i < kClasses; ++i)
-                if (i < ncls && (int64_t)r[1 + i] > floor_thr) {
-                    if (fm == kChunkClasses) {
-                        ovf = true;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < kChunkClasses; ++j)
-                            if (j == fm) {
-                                fthr[j] = r[1 + i];
-                                fcnt[j] = (uint32_t)r[1 + kClasses + i];
-                                flast[j] = r[1 + 2 * kClasses + i];
-                            }
-                        ++fm;
-                    }
-                }
-            if (meta & kMetaClosed) through = false;
-        }
-        const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
-        const bool any_ovf = __any_sync(0xFFFFFFFFu, ovf);
-        int64_t x = INT64_MIN;
+        LaneMap f;
+        stitch_compose(base, pa, pb, per, f);
+        warp_compose(f, lane);
+        const bool any_bad = __shfl_sync(0xFFFFFFFFu, (int)f.bad, 0) != 0;
+        const bool any_ovf = __shfl_sync(0xFFFFFFFFu, (int)f.ovf, 0) != 0;
+        int32_t x = INT32_MIN;  // before the first occurrence
         uint32_t total = 0;
-        if (!any_bad && !any_ovf) {
-            // ---- walk the 32 lane maps in segment order
-            for (int l = 0; l < 32; ++l) {
-                if (lane == l) {
-                    bool hit = false;
-#pragma unroll
-                    for (int j = 0; j < kChunkClasses; ++j)
-                        if (!hit && j < fm && x < (int64_t)fthr[j]) {
-                            total += fcnt[j];
-                            x = flast[j];
-                            hit = true;
-                        }
-                }
-                x = __shfl_sync(0xFFFFFFFFu, x, l);
-                total = __shfl_sync(0xFFFFFFFFu, total, l);
-            }
-        } else if (!any_bad) {
-            // ---- a lane map overflowed: walk every record in order
-            for (int p = 0; p < P; ++p) {
-                int32_t r[kRecWords];
-#pragma unroll
-                for (int q = 0; q < kRecWords / 4; ++q) {
-                    const int4 v = base[(int64_t)p * (kRecWords / 4) + q];
-                    r[4 * q] = v.x, r[4 * q + 1] = v.y, r[4 * q + 2] = v.z, r[4 * q + 3] = v.w;
-                }
-                stitch_apply(r, r[0] & 0xFF, x, total);
-            }
-        }
+        if (!any_bad && !any_ovf)
+            lanemap_apply(f, x, total);  // lane 0's map of the whole episode
+        else if (!any_bad)
+            stitch_serial(base, P, x, total);
         if (lane == 0) {
             if (any_bad) {
                 const int q = atomicAdd(fb_count, 1);
@@ -645,6 +750,77 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
                 counts[cand] = total;
             }
         }
+    }
+}
+
+// One block per episode, for episodes with more than min_P segments: 256
+// lanes compose their runs, each warp composes its lanes' maps, and the
+// eight warp maps (shared memory) are applied in order.
+constexpr int kStitchBlock = 256;
+constexpr int kStitchSplit = 256;  // episodes with more segments take a block
+
+__global__ void __launch_bounds__(kStitchBlock)
+    k_stitch_block(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
+                   const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
+                   int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
+                   const int32_t *d_n_slots, int min_P) {
+    constexpr int W = kStitchBlock / 32;
+    __shared__ int32_t s_thr[W][kChunkClasses], s_last[W][kChunkClasses];
+    __shared__ uint32_t s_cnt[W][kChunkClasses];
+    __shared__ int s_m[W], s_flag[W];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_live = d_n_slots ? *d_n_slots : n_slots;
+    for (int wi = blockIdx.x; wi < n_live; wi += gridDim.x) {
+        const int slot = slot_begin + wi;
+        const int cand = slot2cand[slot];
+        const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
+        const RecInfo ri = rinfo[r_id];
+        const int P = ri.P;
+        if (P <= min_P) continue;  // block-uniform
+        const int4 *base = reinterpret_cast<const int4 *>(
+            rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * P) * kRecWords);
+        const int per = (P + kStitchBlock - 1) / kStitchBlock;
+        const int pa = min(P, tid * per), pb = min(P, pa + per);
+        LaneMap f;
+        stitch_compose(base, pa, pb, per, f);
+        warp_compose(f, lane);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < kChunkClasses; ++j) {
+                s_thr[warp][j] = f.thr[j];
+                s_last[warp][j] = f.last[j];
+                s_cnt[warp][j] = f.cnt[j];
+            }
+            s_m[warp] = f.m;
+            s_flag[warp] = (f.bad ? 1 : 0) | (f.ovf ? 2 : 0);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int fl = 0;
+            for (int w = 0; w < W; ++w) fl |= s_flag[w];
+            int32_t x = INT32_MIN;  // before the first occurrence
+            uint32_t total = 0;
+            if (fl == 0) {
+                for (int w = 0; w < W; ++w) {
+                    bool hit = false;
+                    for (int j = 0; j < s_m[w] && !hit; ++j)
+                        if (x < s_thr[w][j]) {
+                            total += s_cnt[w][j];
+                            x = s_last[w][j];
+                            hit = true;
+                        }
+                }
+            } else if (!(fl & 1)) {
+                stitch_serial(base, P, x, total);
+            }
+            if (fl & 1) {
+                const int q = atomicAdd(fb_count, 1);
+                fb_list[q] = cand;
+            } else {
+                counts[cand] = total;
+            }
+        }
+        __syncthreads();  // the maps are rewritten for the next episode
     }
 }
 
@@ -1601,9 +1777,6 @@ int stream_bytype(fem_ctx *ctx, fem_stream *s) {
 
 typedef void (*SparseFn)(SparseArgs);
 
-// Shared memory of a sparse block with shared-memory rings (64 threads).
-static size_t sparse_smem(int nclass, int R) { return (size_t)2 * (nmax_of_class(nclass) - 1) * R * 64 * 4; }
-
 static SparseFn sparse_fn(int nclass, int rr) {
 #define FEM_SF(NM, R_) \
     if (nmax_of_class(nclass) == NM && rr == R_) return k_count_sparse<NM, R_>;
@@ -1657,10 +1830,16 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 64, sm);
     const int64_t gs = std::min<int64_t>((cap_threads + 63) / 64, (int64_t)std::max(1, nsm) * std::max(1, per_sm));
     if (cap_threads > 0) f<<<(unsigned)gs, 64, sm, st>>>(sa);
+    // the live segment counts are only known on the device: both stitch
+    // kernels run, each taking the episodes on its side of kStitchSplit
     const int64_t gst = std::min<int64_t>((cap_slots + kStitchWarps - 1) / kStitchWarps, (int64_t)std::max(1, nsm) * 8);
-    if (cap_slots > 0)
+    const int64_t gsb = std::min<int64_t>(cap_slots, (int64_t)std::max(1, nsm) * 4);
+    if (cap_slots > 0) {
         k_stitch<<<(unsigned)gst, kStitchWarps * 32, 0, st>>>(rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots,
-                                                            counts, fb_list, fb_count, d_n_slots);
+                                                            counts, fb_list, fb_count, d_n_slots, kStitchSplit);
+        k_stitch_block<<<(unsigned)gsb, kStitchBlock, 0, st>>>(rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots,
+                                                               counts, fb_list, fb_count, d_n_slots, kStitchSplit);
+    }
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
@@ -2233,10 +2412,18 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         FEM_TRY(launch_plan(pl, static_cast<int32_t *>(p_rec), d_seg, tab, &d_ri, 0));
         if (pl.sparse)
             cc.stats.sparse_launches++;
+        int maxP = 1;
+        for (auto &r : pl.ri) maxP = std::max(maxP, r.P);
         k_stitch<<<(pl.n_slots + kStitchWarps - 1) / kStitchWarps, kStitchWarps * 32, 0, ctx->stream>>>(
             static_cast<int32_t *>(p_rec), d_ri, d_perm, cc.cand_rec, pl.slot_begin, pl.n_slots, cc.counts, fb_list,
-            d_fbc);
+            d_fbc, nullptr, kStitchSplit);
         cc.stats.kernel_launches++;
+        if (maxP > kStitchSplit) {
+            k_stitch_block<<<(unsigned)std::min<int64_t>(pl.n_slots, (int64_t)ctx->n_sm * 4), kStitchBlock, 0,
+                             ctx->stream>>>(static_cast<int32_t *>(p_rec), d_ri, d_perm, cc.cand_rec, pl.slot_begin,
+                                            pl.n_slots, cc.counts, fb_list, d_fbc, nullptr, kStitchSplit);
+            cc.stats.kernel_launches++;
+        }
         FEM_CUDA_TRY(cudaGetLastError());
     }
     cudaEventRecord(ctx->ev1, ctx->stream);

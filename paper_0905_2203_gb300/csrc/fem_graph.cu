@@ -26,7 +26,7 @@ namespace fem {
 namespace {
 
 constexpr int kRingCap = 16;      // shared-memory ring entries in the graph path
-constexpr int kMaxPerRec = 256;   // segments per recording
+constexpr int kMaxPerRec = 4096;  // finest segmentation of a recording
 
 // Counters per level: [0] candidates C, [1] frequent F, [2] flags, [3]
 // entry-class fallbacks (stitch), [4..5] padding.
@@ -101,8 +101,13 @@ __global__ void k_g_index(const uint32_t *crec, const int32_t *ctr, int N, int64
     }
 }
 
+// Per-level segmentation: the level's (candidate, segment) threads should
+// number about `target`, so a level with few candidates cuts its recordings
+// finely and one with many coarsely.  Segment boundaries are taken from the
+// recording's finest boundaries (pfine[r] segments, in segf) every s-th one.
 __global__ void k_g_recinfo(const uint32_t *crec, const int32_t *ctr, int n_recs, int64_t *coff, RecInfo *ri,
-                            int64_t *nthreads) {
+                            int64_t *nthreads, const int64_t *segf, const int32_t *pfine, int32_t *sstep,
+                            int64_t *segl, int64_t target) {
     const int64_t C = ctr[0];
     for (int r = threadIdx.x; r <= n_recs; r += blockDim.x) {
         int64_t lo = 0, hi = C;  // first candidate of recording >= r
@@ -114,13 +119,29 @@ __global__ void k_g_recinfo(const uint32_t *crec, const int32_t *ctr, int n_recs
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        double W = 0;  // episode-events of the level
+        for (int r = 0; r < n_recs; ++r) W += (double)(coff[r + 1] - coff[r]) * (double)ri[r].n;
+        const double seg_len = fmax(1.0, W / (double)target);
         int64_t base = 0;
         for (int r = 0; r < n_recs; ++r) {
+            const int pf = pfine[r];
+            const double want = fmin((double)pf, fmax(1.0, ceil((double)ri[r].n / seg_len)));
+            const int st = (pf + (int)want - 1) / (int)want;
+            const int P = (pf + st - 1) / st;
+            sstep[r] = st;
+            ri[r].P = P;
             ri[r].slot_first = (int)coff[r];
             ri[r].recbase = base;
-            base += (coff[r + 1] - coff[r]) * ri[r].P;
+            base += (coff[r + 1] - coff[r]) * P;
         }
         *nthreads = base;
+    }
+    __syncthreads();
+    for (int r = 0; r < n_recs; ++r) {
+        const int P = ri[r].P, st = sstep[r], pf = pfine[r];
+        const int64_t *f = segf + (size_t)r * (kMaxPerRec + 1);
+        int64_t *o = segl + (size_t)r * (kMaxPerRec + 1);
+        for (int p = threadIdx.x; p <= P; p += blockDim.x) o[p] = f[min(p * st, pf)];
     }
 }
 
@@ -213,6 +234,9 @@ struct GraphTail {
     int64_t *coff = nullptr;               // (n_recs + 1) per level
     uint32_t *d_thr = nullptr;
     int ring_cap = kRingCap;               // ring entries per node
+    int64_t *segf = nullptr, *segl = nullptr;  // finest / current level's segment starts
+    int32_t *pfine = nullptr, *sstep = nullptr;
+    int64_t target = 0;                    // (candidate, segment) threads per level
     unsigned long long *rel = nullptr;    // relevant events counted, per level
     std::vector<cudaEvent_t> ev;           // around each level's count kernels
     cudaGraphExec_t exec = nullptr;
@@ -244,10 +268,13 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
     for (auto h : bhi) hi_max = std::max(hi_max, h);
     // per-recording segment counts and boundaries, per-type lists, densities
     std::vector<RecInfo> ri_h(n_recs);
-    int64_t *segs = nullptr;
+    int64_t *segs = nullptr;  // finest boundaries per recording
     FEM_TRY(g->get(&segs, (size_t)n_recs * (kMaxPerRec + 1)));
+    FEM_TRY(g->get(&g->segl, (size_t)n_recs * (kMaxPerRec + 1)));
+    FEM_TRY(g->get(&g->pfine, n_recs));
+    FEM_TRY(g->get(&g->sstep, n_recs));
+    std::vector<int32_t> pfine_h(n_recs);
     const int64_t sumhi_max = (int64_t)(L - 1) * hi_max;
-    int Pmax = 1;
     std::vector<const uint32_t *> dens_h((size_t)n_recs * lo_vals.size());
     for (int r = 0; r < n_recs; ++r) {
         fem_stream *s = g->recs[r];
@@ -257,29 +284,25 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
             FEM_TRY(stream_density(ctx, s, lo_vals[j], &d));
             dens_h[(size_t)r * lo_vals.size() + j] = d;
         }
+        // finest segments: at least 256 events and twice the halo (sum of
+        // the upper bounds, in events at the recording's mean rate)
         const double span = std::max(1.0, (double)s->t_last - (double)s->t_first);
         const double halo_ev = (double)s->n * (double)sumhi_max / span;
-        const double min_seg = std::max(1024.0, 8.0 * halo_ev);
-        int P = (int)std::max(1.0, std::min<double>(kMaxPerRec, (double)s->n / min_seg));
-        Pmax = std::max(Pmax, P);
+        const double min_seg = std::max(256.0, 2.0 * halo_ev);
+        const int P = (int)std::max(1.0, std::min<double>(kMaxPerRec, (double)s->n / min_seg));
+        pfine_h[r] = P;
         FEM_TRY(launch_segments(st, s->d_time, s->n, P, segs + (size_t)r * (kMaxPerRec + 1)));
-        ri_h[r] = RecInfo{s->d_type, s->d_time, s->n, segs + (size_t)r * (kMaxPerRec + 1), P, 0, 0,
+        ri_h[r] = RecInfo{s->d_type, s->d_time, s->n, g->segl + (size_t)r * (kMaxPerRec + 1), 1, 0, 0,
                           s->d_freq, s->d_toff, s->d_ttime};
     }
-    // records: at most cap episodes x Pmax segments; keep within ~1/4 of the free budget
+    FEM_CUDA_TRY(cudaMemcpyAsync(g->pfine, pfine_h.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
+    g->segf = segs;
+    // (candidate, segment) threads per level: about two waves of the sparse
+    // kernel, never more than target + live candidates (one segment each)
+    g->target = (int64_t)2 * ctx->n_sm * 512;
+    g->cap_threads = g->target + cap;
     const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
-    const int64_t rec_cap = std::max<int64_t>(cap, (int64_t)(free_b / 4 / (kRecWords * 4)));
-    if ((int64_t)cap * Pmax > rec_cap) {
-        const double f = (double)rec_cap / ((double)cap * Pmax);
-        Pmax = 1;
-        for (int r = 0; r < n_recs; ++r) {
-            ri_h[r].P = std::max(1, (int)(ri_h[r].P * f));
-            FEM_TRY(launch_segments(st, g->recs[r]->d_time, g->recs[r]->n, ri_h[r].P,
-                                    segs + (size_t)r * (kMaxPerRec + 1)));
-            Pmax = std::max(Pmax, ri_h[r].P);
-        }
-    }
-    g->cap_threads = cap * Pmax;
+    if ((size_t)g->cap_threads * kRecWords * 4 > free_b / 4) return FEM_ERR_NOMEM;
     // ring entries per node: the largest window density of any type + 1
     // (capped at kRingCap; nodes needing more are flagged by the ring check)
     uint32_t dmax = 1;
@@ -365,7 +388,8 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
         if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
         k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl, ch, crec, cn);
         k_g_index<<<gb, 256, 0, st>>>(crec, cn, N, cap, offs, iota);
-        k_g_recinfo<<<1, 256, 0, st>>>(crec, cn, n_recs, coffN, d_ri, nthreads);
+        k_g_recinfo<<<1, 256, 0, st>>>(crec, cn, n_recs, coffN, d_ri, nthreads, g->segf, g->pfine, g->sstep,
+                                       g->segl, g->target);
         k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), g->ring_cap, d_ri, cn,
                                           g->rel + N);
         // external event nodes: their timestamps time the count kernels of
