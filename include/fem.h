@@ -99,9 +99,12 @@ typedef struct {
                              per-type-list kernel where it applies, 3 = the
                              sparse kernel with per-node branching instead of
                              its node-uniform variant (comparison) */
-    int level_graph;      /* mining: 0 = run levels >= 3 as one captured CUDA
-                             graph where it applies, -1 = level by level
-                             from the host */
+    int level_graph;      /* mining: 0 = run the levels as one captured CUDA
+                             graph where it applies (all levels when no
+                             other override is set and every alphabet has at
+                             least 16 types; otherwise levels >= 3 after a
+                             host-driven level 2), -1 = level by level from
+                             the host */
 } fem_tuning;
 
 /* Per-call statistics filled by the counting / mining calls. */
@@ -122,8 +125,9 @@ typedef struct {
     double count_kernel_ms;     /* device time of the exact-count kernels */
     double total_ms;            /* wall time of the call */
     int levels;                 /* mining: deepest level reached */
-    int graph_tails;            /* mining: 1 if levels >= 3 ran as one
-                                   captured CUDA graph */
+    int graph_tails;            /* mining: 1 if levels ran as one captured
+                                   CUDA graph (kernel_launches then counts its
+                                   kernel nodes) */
 } fem_stats;
 
 /* ---- context ----------------------------------------------------------- */
@@ -244,7 +248,9 @@ int fem_count_episodes_noalloc(const uint16_t *types, const int32_t *times, int6
  *   threshold[n_recs]      host array, per recording
  *   max_size               in [1, FEM_MAX_NODES]
  * All recordings' levels share one launch per step, and the levels are
- * chained in a captured CUDA graph.  *out receives a result (free with
+ * chained in a captured CUDA graph (fem_tuning.level_graph); a flag raised
+ * inside the graph (a capacity or ring-size overflow) makes the call redo the
+ * mining level by level, with the same results.  *out receives a result (free with
  * fem_result_free) whose episodes are in canonical order: size, then the
  * interleaved sequence (E_1, lo_1, hi_1, E_2, ..., lo_{N-1}, hi_{N-1}, E_N). */
 int fem_mine_levelwise(fem_ctx *ctx, const fem_stream *const *recs, int n_recs,

@@ -1,16 +1,22 @@
-// fem_graph.cu -- levels 3..max of level-wise mining chained in one captured
-// CUDA graph.
+// fem_graph.cu -- level-wise mining chained in one captured CUDA graph.
 //
-// After level 2 (which is host-driven: upper-bound pre-pass, choice of
-// counting kernel), every later level runs the same fixed sequence --
-// join (count, scan, write), candidate index, ring-capacity check, sparse
-// counting + stitch, threshold (flags, scan, write), per-recording offsets --
-// whose sizes live in device counters.  The sequence for all remaining
-// levels is captured once into a graph over fixed-capacity buffers and
-// launched with a single call; a level that keeps nothing leaves zero
-// counters behind, so the later levels' kernels exit at once.  Any capacity
-// overflow, ring-capacity miss or entry-class overflow sets a flag; the
-// caller then runs the host-driven path instead (same results).
+// Every level runs a fixed sequence of kernels whose sizes live in device
+// counters, so the levels need no host step in between:
+//   level 1   frequent types: flags, scan, write ("Temporal Data Mining":
+//             a 1-node count is the type's frequency);
+//   level 2   every ordered pair of distinct frequent types x bins, generated
+//             in canonical order; the upper-bound pre-pass (one stream pass)
+//             drops pairs that cannot pass; survivors compacted;
+//   level N   prefix/suffix join of level N-1 (count, scan, write);
+// then, for every level >= 2: candidate index, the level's segmentation
+// (chosen on the device from its candidate count), ring-capacity check,
+// sparse counting + stitch, threshold (flags, scan, write) and per-recording
+// offsets.  The sequence for levels `first`..max_size is captured once over
+// fixed-capacity buffers and launched with a single call; a level that keeps
+// nothing leaves zero counters behind and the later levels' kernels exit at
+// once.  A capacity overflow, ring-capacity miss or entry-class overflow sets
+// a flag; the caller then mines on the host-driven path (same results) and
+// the next capture of the same workload gets the capacity that was needed.
 // Graphs are cached per context for repeated calls with the same recordings
 // and parameters.
 #include <algorithm>
@@ -25,13 +31,187 @@ namespace fem {
 
 namespace {
 
-constexpr int kRingCap = 16;      // shared-memory ring entries in the graph path
+constexpr int kRingCap = 32;      // largest shared-memory ring in the graph path
 constexpr int kMaxPerRec = 4096;  // finest segmentation of a recording
 
-// Counters per level: [0] candidates C, [1] frequent F, [2] flags, [3]
-// entry-class fallbacks (stitch), [4..5] padding.
+// Counters per level: [0] candidates counted C, [1] frequent F, [2] flags,
+// [3] entry-class fallbacks (stitch), [4] candidates generated (level 2,
+// before the pre-pass), [5] candidates needed (a capacity overflow leaves
+// the true total here).
 constexpr int kCtr = 6;
+constexpr int kFlagCap = 1, kFlagRing = 2, kFlagFreq = 4, kFlagGen = 8;
 
+// Largest r with pre[r] <= i (pre: n + 1 non-decreasing offsets, pre[0] = 0).
+__device__ __forceinline__ int seg_of(const int64_t *pre, int n, int64_t i) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ---- level 1 ---------------------------------------------------------------
+// Frequent types of every recording, in type order: flags over the
+// concatenated type ranges (ntpre = prefix of n_types), then write.
+__global__ void k_g_l1_flags(const RecInfo *ri, const uint32_t *thr, const int64_t *ntpre, int n_recs, int64_t tot,
+                             int32_t *flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= tot; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t f = 0;
+        if (i < tot) {
+            const int r = seg_of(ntpre, n_recs, i);
+            f = ri[r].freq[i - ntpre[r]] > thr[r] ? 1 : 0;
+        }
+        flags[i] = f;
+    }
+}
+
+__global__ void k_g_l1_write(const int32_t *pos, const RecInfo *ri, const uint32_t *thr, const int64_t *ntpre,
+                             int n_recs, int64_t tot, uint16_t *ft, uint32_t *frec, uint32_t *fcnt, int32_t *ctr) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = seg_of(ntpre, n_recs, i);
+        const uint32_t a = (uint32_t)(i - ntpre[r]);
+        const uint32_t f = ri[r].freq[a];
+        if (f > thr[r]) {
+            const int64_t o = pos[i];
+            ft[o] = (uint16_t)a;
+            frec[o] = (uint32_t)r;
+            fcnt[o] = f;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr[0] = (int32_t)tot;
+        ctr[1] = pos[tot];
+    }
+}
+
+// ---- level 2 ---------------------------------------------------------------
+// Generated pairs per recording: F_r (F_r - 1) nb; offsets and total.
+__global__ void k_g_gen2_off(const int64_t *foff1, int n_recs, int nb, int64_t cap2, int64_t *coff2, int32_t *ctr) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int64_t s = 0;
+    coff2[0] = 0;
+    for (int r = 0; r < n_recs; ++r) {
+        const int64_t F = foff1[r + 1] - foff1[r];
+        s += F >= 2 ? F * (F - 1) * nb : 0;
+        coff2[r + 1] = s;
+    }
+    ctr[4] = (int32_t)(s < INT32_MAX ? s : INT32_MAX);
+    if (s > cap2) atomicOr(&ctr[2], kFlagGen);
+}
+
+// Pair c of recording r in canonical order (E1, bin, E2): the frequent types
+// of the recording are in type order and the bins sorted by (lo, hi).
+__global__ void k_g_gen2(const uint16_t *ft1, const int64_t *foff1, const int64_t *coff2, int n_recs,
+                         const int32_t *blo, const int32_t *bhi, int nb, int64_t cap2, uint16_t *gt, int32_t *glo,
+                         int32_t *ghi, uint32_t *grec) {
+    const int64_t C = min(coff2[n_recs], cap2);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const int r = seg_of(coff2, n_recs, c);
+        const int64_t local = c - coff2[r];
+        const int64_t F = foff1[r + 1] - foff1[r];
+        const int64_t per_i = (int64_t)nb * (F - 1);
+        const int64_t i = local / per_i, rem = local % per_i;
+        const int k = (int)(rem / (F - 1));
+        const int64_t jj = rem % (F - 1);
+        const int64_t j = jj < i ? jj : jj + 1;
+        gt[2 * c] = ft1[foff1[r] + i];
+        gt[2 * c + 1] = ft1[foff1[r] + j];
+        glo[c] = blo[k];
+        ghi[c] = bhi[k];
+        grec[c] = (uint32_t)r;
+    }
+}
+
+// Upper-bound pre-pass over all recordings (anti-monotonicity, "Temporal Data
+// Mining"): the non-overlapped occurrences of a -(lo,hi]-> b end at distinct
+// b-events, each with an a-event inside its window, so
+//     count(a, b, bin) <= UB = #{ b-events with an a-event in the window }.
+// One thread per event scans back over the widest window, marks each
+// (type, bin) once in a per-thread bitset and adds one to UB for it.
+__global__ void k_g_pair_ub(const RecInfo *ri, const int64_t *evpre, int n_recs, const uint32_t *nt,
+                            const int64_t *ub_off, const int32_t *blo, const int32_t *bhi, int nb, int32_t hi_max,
+                            int words, uint32_t *ub) {
+    extern __shared__ uint32_t bits[];
+    uint32_t *my = bits + threadIdx.x * words;
+    const int64_t tot = evpre[n_recs];
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot; g += (int64_t)gridDim.x * blockDim.x) {
+        const int r = seg_of(evpre, n_recs, g);
+        const int64_t j = g - evpre[r];
+        const uint16_t *ty = ri[r].type;
+        const int32_t *tm = ri[r].time;
+        const uint32_t ntr = nt[r];
+        const int wr = (int)((ntr * (uint32_t)nb + 31) / 32);
+        uint32_t *u = ub + ub_off[r];
+        for (int w = 0; w < wr; ++w) my[w] = 0;
+        const int32_t t = tm[j];
+        const uint32_t b = ty[j];
+        const int64_t lim = (int64_t)t - hi_max;
+        for (int64_t i = j - 1; i >= 0 && (int64_t)tm[i] >= lim; --i) {
+            const int32_t d = t - tm[i];
+            if (d <= 0) continue;
+            const uint32_t a = ty[i];
+            if (a == b) continue;
+            for (int k = 0; k < nb; ++k) {
+                if (blo[k] < d && d <= bhi[k]) {
+                    const uint32_t bit = a * (uint32_t)nb + (uint32_t)k;
+                    const uint32_t m = 1u << (bit & 31);
+                    if (!(my[bit >> 5] & m)) {
+                        my[bit >> 5] |= m;
+                        atomicAdd(&u[((size_t)a * ntr + b) * nb + k], 1u);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ bool g_keep2(int64_t c, const uint16_t *gt, const int32_t *glo, const int32_t *ghi,
+                                        const uint32_t *grec, const uint32_t *ub, const int64_t *ub_off,
+                                        const uint32_t *nt, const int32_t *blo, const int32_t *bhi, int nb,
+                                        const uint32_t *thr) {
+    if (!ub) return true;
+    const uint32_t r = grec[c];
+    int k = 0;
+    while (k < nb && !(blo[k] == glo[c] && bhi[k] == ghi[c])) ++k;
+    const uint32_t a = gt[2 * c], b = gt[2 * c + 1];
+    return ub[ub_off[r] + ((size_t)a * nt[r] + b) * nb + k] > thr[r];
+}
+
+__global__ void k_g_prune_flags(const uint16_t *gt, const int32_t *glo, const int32_t *ghi, const uint32_t *grec,
+                                const int32_t *ctr, int64_t cap2, const uint32_t *ub, const int64_t *ub_off,
+                                const uint32_t *nt, const int32_t *blo, const int32_t *bhi, int nb,
+                                const uint32_t *thr, int32_t *flags) {
+    const int64_t C = min((int64_t)ctr[4], cap2);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= cap2; c += (int64_t)gridDim.x * blockDim.x)
+        flags[c] = (c < C && g_keep2(c, gt, glo, ghi, grec, ub, ub_off, nt, blo, bhi, nb, thr)) ? 1 : 0;
+}
+
+__global__ void k_g_prune_write(const int32_t *pos, const uint16_t *gt, const int32_t *glo, const int32_t *ghi,
+                                const uint32_t *grec, int64_t cap2, const uint32_t *ub, const int64_t *ub_off,
+                                const uint32_t *nt, const int32_t *blo, const int32_t *bhi, int nb,
+                                const uint32_t *thr, int64_t cap, uint16_t *ct, int32_t *cl, int32_t *ch,
+                                uint32_t *crec, int32_t *ctr) {
+    const int64_t C = min((int64_t)ctr[4], cap2);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        if (!g_keep2(c, gt, glo, ghi, grec, ub, ub_off, nt, blo, bhi, nb, thr)) continue;
+        const int64_t o = pos[c];
+        if (o >= cap) continue;
+        ct[2 * o] = gt[2 * c];
+        ct[2 * o + 1] = gt[2 * c + 1];
+        cl[o] = glo[c];
+        ch[o] = ghi[c];
+        crec[o] = grec[c];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t total = pos[cap2];
+        ctr[0] = (int32_t)(total < cap ? total : cap);
+        ctr[5] = (int32_t)total;
+        if (total > cap) atomicOr(&ctr[2], kFlagCap);
+    }
+}
+
+// ---- level N >= 3: prefix/suffix join --------------------------------------
 __device__ __forceinline__ bool g_joins(const uint16_t *ft, const int32_t *fl, const int32_t *fh, int M, int64_t a,
                                         int64_t b) {
     for (int k = 1; k < M; ++k)
@@ -87,13 +267,15 @@ __global__ void k_g_join_write(const uint16_t *ft, const int32_t *fl, const int3
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t total = pos[cap];
         ctr[0] = (int32_t)(total < cap ? total : cap);
-        if (total > cap) atomicOr(&ctr[2], 1);
+        ctr[4] = ctr[0];
+        ctr[5] = (int32_t)(total < INT32_MAX ? total : INT32_MAX);
+        if (total > cap) atomicOr(&ctr[2], kFlagCap);
     }
 }
 
-// CSR offsets of the candidates, identity slot order, per-recording
-// candidate offsets, and the RecInfo fields that depend on them.
-__global__ void k_g_index(const uint32_t *crec, const int32_t *ctr, int N, int64_t cap, int64_t *offs, int32_t *iota) {
+// ---- every level >= 2 --------------------------------------------------------
+// CSR offsets of the candidates and the identity slot order.
+__global__ void k_g_index(const int32_t *ctr, int N, int64_t cap, int64_t *offs, int32_t *iota) {
     const int64_t C = ctr[0];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= cap; i += (int64_t)gridDim.x * blockDim.x) {
         if (i <= C) offs[i] = i * N;
@@ -145,8 +327,8 @@ __global__ void k_g_recinfo(const uint32_t *crec, const int32_t *ctr, int n_recs
     }
 }
 
-// Every node's ring must fit kRingCap entries (window density + 1).  Also
-// sums the candidates' relevant events (sum over nodes of the node type's
+// Every node's ring must fit R_cap entries (window density + 1).  Also sums
+// the candidates' relevant events (sum over nodes of the node type's
 // frequency in the candidate's recording) into *rel.
 __global__ void k_g_ringcheck(const uint16_t *ct, const int32_t *cl, const uint32_t *crec, const int32_t *ctr, int N,
                               const uint32_t *const *dens, const int32_t *lo_vals, int n_lo, int R_cap,
@@ -162,7 +344,7 @@ __global__ void k_g_ringcheck(const uint16_t *ct, const int32_t *cl, const uint3
             int j = 0;
             while (j < n_lo && lo_vals[j] != l) ++j;
             const uint32_t d = j < n_lo ? dens[r * n_lo + j][ct[i * N + k]] : 0xFFFFFFFFu;
-            if (d == 0xFFFFFFFFu || d + 1 > (uint32_t)R_cap) atomicOr(&ctr_w[2], 2);
+            if (d == 0xFFFFFFFFu || d + 1 > (uint32_t)R_cap) atomicOr(&ctr_w[2], kFlagRing);
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -196,7 +378,7 @@ __global__ void k_g_thr_write(const int32_t *pos, const uint32_t *counts, const 
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t total = pos[cap];
         ctr[1] = (int32_t)(total < cap ? total : cap);
-        if (total > cap) atomicOr(&ctr[2], 4);
+        if (total > cap) atomicOr(&ctr[2], kFlagFreq);
     }
 }
 
@@ -226,19 +408,22 @@ struct GraphTail {
     fem_ctx *ctx = nullptr;
     std::string key;
     std::vector<fem_stream *> recs;
-    int n_recs = 0, max_size = 0;
-    int64_t cap = 0, cap_threads = 0;
+    int n_recs = 0, max_size = 0, first = 3;
+    bool prepass = false;
+    int64_t cap = 0, cap2 = 0, cap_threads = 0;
     std::vector<std::pair<void *, size_t>> held;
-    std::vector<FLevel> F;                 // F[N] for N = 2..max_size
+    std::vector<FLevel> F;                 // F[N] for N = 1..max_size
     int32_t *ctr = nullptr;                // kCtr per level, indexed by N
-    int64_t *coff = nullptr;               // (n_recs + 1) per level
+    int64_t *coff = nullptr;               // (n_recs + 1) per level: counted candidates per recording
+    int64_t *coff2 = nullptr;              // generated level-2 candidates per recording
     uint32_t *d_thr = nullptr;
     int ring_cap = kRingCap;               // ring entries per node
     int64_t *segf = nullptr, *segl = nullptr;  // finest / current level's segment starts
     int32_t *pfine = nullptr, *sstep = nullptr;
     int64_t target = 0;                    // (candidate, segment) threads per level
-    unsigned long long *rel = nullptr;    // relevant events counted, per level
+    unsigned long long *rel = nullptr;     // relevant events counted, per level
     std::vector<cudaEvent_t> ev;           // around each level's count kernels
+    int64_t kernel_nodes = 0;              // kernel launches per run of the graph
     cudaGraphExec_t exec = nullptr;
 
     template <typename T>
@@ -258,15 +443,23 @@ struct GraphTail {
     }
 };
 
-static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::vector<int32_t> &bhi,
-                      const std::vector<uint32_t> &thr, const std::vector<int32_t> &lo_vals) {
+// Shared memory of the node-uniform sparse kernel for N-node episodes with
+// rings of R entries (the kernel's per-thread header + slab, 64 threads).
+static size_t graph_sparse_smem(int N, int R) {
+    const int nmax = N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : 16;
+    return (size_t)(6 * (nmax - 1) + 2 * (N - 1) * R) * 64 * 4;
+}
+
+static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std::vector<int32_t> &bhi,
+                       const std::vector<uint32_t> &thr, const std::vector<int32_t> &lo_vals) {
     fem_ctx *ctx = g->ctx;
     cudaStream_t st = ctx->stream;
-    const int n_recs = g->n_recs, L = g->max_size;
+    const int n_recs = g->n_recs, L = g->max_size, first = g->first;
+    const int nb = (int)blo.size();
     const int64_t cap = g->cap;
     int32_t hi_max = 0;
     for (auto h : bhi) hi_max = std::max(hi_max, h);
-    // per-recording segment counts and boundaries, per-type lists, densities
+    // per-recording segment boundaries, per-type lists, densities
     std::vector<RecInfo> ri_h(n_recs);
     int64_t *segs = nullptr;  // finest boundaries per recording
     FEM_TRY(g->get(&segs, (size_t)n_recs * (kMaxPerRec + 1)));
@@ -301,10 +494,9 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
     // kernel, never more than target + live candidates (one segment each)
     g->target = (int64_t)2 * ctx->n_sm * 512;
     g->cap_threads = g->target + cap;
-    const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
-    if ((size_t)g->cap_threads * kRecWords * 4 > free_b / 4) return FEM_ERR_NOMEM;
-    // ring entries per node: the largest window density of any type + 1
-    // (capped at kRingCap; nodes needing more are flagged by the ring check)
+    // ring entries per node: the largest window density of any type + 1; the
+    // graph does not apply when that exceeds kRingCap or what the deepest
+    // level's shared memory holds (such streams mine on the host-driven path)
     uint32_t dmax = 1;
     for (int r = 0; r < n_recs; ++r) {
         std::vector<uint32_t> hd(g->recs[r]->n_types);
@@ -315,98 +507,183 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
             for (uint32_t d : hd) dmax = std::max(dmax, d);
         }
     }
-    g->ring_cap = (int)std::min<uint32_t>(kRingCap, dmax + 1);
+    if (dmax + 1 > (uint32_t)kRingCap) return FEM_ERR_INVAL;
+    g->ring_cap = (int)dmax + 1;
+    for (int N = std::max(first, 2); N <= L; ++N)
+        if (graph_sparse_smem(N, g->ring_cap) > (size_t)ctx->smem_optin - 1024) return FEM_ERR_INVAL;
+    // level 1 / level 2 sizes
+    std::vector<int64_t> ntpre(n_recs + 1, 0), evpre(n_recs + 1, 0), ub_off(n_recs + 1, 0);
+    std::vector<uint32_t> nt_h(n_recs);
+    int64_t cap2 = 0;
+    uint32_t nt_max = 1;
+    for (int r = 0; r < n_recs; ++r) {
+        const int64_t nt = g->recs[r]->n_types;
+        nt_h[r] = (uint32_t)nt;
+        nt_max = std::max(nt_max, (uint32_t)nt);
+        ntpre[r + 1] = ntpre[r] + nt;
+        evpre[r + 1] = evpre[r] + g->recs[r]->n;
+        ub_off[r + 1] = ub_off[r] + nt * nt * nb;
+        cap2 += nt >= 2 ? nt * (nt - 1) * nb : 0;
+    }
+    g->cap2 = cap2;
+    const int64_t tot1 = ntpre[n_recs];
+    const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+    if ((size_t)g->cap_threads * kRecWords * 4 > free_b / 4) return FEM_ERR_NOMEM;
+    // pre-pass launch shape (a per-thread bitset of n_types x bins bits)
+    const int ub_words = (int)((nt_max * (uint32_t)std::max(nb, 1) + 31) / 32);
+    int ub_threads = std::max(32, std::min(256, (int)(48 * 1024 / (4 * ub_words)) / 32 * 32));
+    if ((size_t)ub_threads * ub_words * 4 > 48 * 1024) g->prepass = false;
+
     RecInfo *d_ri;
     const uint32_t **d_dens;
-    int32_t *d_lov, *pos, *fb_list, *iota, *rec;
+    int32_t *d_lov, *pos, *fb_list, *iota, *rec, *d_blo, *d_bhi;
     int64_t *offs, *nthreads;
     uint16_t *ct;
     int32_t *cl, *ch;
     uint32_t *crec, *counts;
     const int Nmax = L;
+    const int64_t scan_m = std::max<int64_t>(std::max<int64_t>(cap, tot1), first <= 2 ? cap2 : 0);
     FEM_TRY(g->get(&d_ri, n_recs));
     FEM_TRY(g->get(&d_dens, dens_h.size()));
     FEM_TRY(g->get(&d_lov, lo_vals.size()));
-    FEM_TRY(g->get(&pos, cap + 2));
+    FEM_TRY(g->get(&d_blo, std::max(nb, 1)));
+    FEM_TRY(g->get(&d_bhi, std::max(nb, 1)));
+    FEM_TRY(g->get(&pos, scan_m + 2));
     FEM_TRY(g->get(&fb_list, cap));
     FEM_TRY(g->get(&iota, cap));
     FEM_TRY(g->get(&rec, (size_t)g->cap_threads * kRecWords));
     FEM_TRY(g->get(&offs, cap + 1));
     FEM_TRY(g->get(&nthreads, 1));
     FEM_TRY(g->get(&ct, (size_t)cap * Nmax));
-    FEM_TRY(g->get(&cl, (size_t)cap * (Nmax - 1)));
-    FEM_TRY(g->get(&ch, (size_t)cap * (Nmax - 1)));
+    FEM_TRY(g->get(&cl, (size_t)cap * std::max(Nmax - 1, 1)));
+    FEM_TRY(g->get(&ch, (size_t)cap * std::max(Nmax - 1, 1)));
     FEM_TRY(g->get(&crec, cap));
     FEM_TRY(g->get(&counts, cap));
     FEM_TRY(g->get(&g->d_thr, n_recs));
     FEM_TRY(g->get(&g->ctr, (size_t)(L + 1) * kCtr));
     FEM_TRY(g->get(&g->coff, (size_t)(L + 1) * (n_recs + 1)));
+    FEM_TRY(g->get(&g->coff2, n_recs + 1));
     FEM_TRY(g->get(&g->rel, (size_t)(L + 1)));
     g->ev.assign(2 * (L + 1), nullptr);
     for (auto &e : g->ev) FEM_CUDA_TRY(cudaEventCreate(&e));
     g->F.assign(L + 1, FLevel{});
-    for (int N = 2; N <= L; ++N) {
+    for (int N = std::max(1, first - 1); N <= L; ++N) {
         FLevel &f = g->F[N];
-        FEM_TRY(g->get(&f.types, (size_t)cap * N));
-        FEM_TRY(g->get(&f.lo, (size_t)cap * (N - 1)));
-        FEM_TRY(g->get(&f.hi, (size_t)cap * (N - 1)));
-        FEM_TRY(g->get(&f.rec, cap));
-        FEM_TRY(g->get(&f.counts, cap));
+        const int64_t fc = N == 1 ? std::max<int64_t>(tot1, 1) : cap;
+        FEM_TRY(g->get(&f.types, (size_t)fc * N));
+        if (N > 1) {
+            FEM_TRY(g->get(&f.lo, (size_t)fc * (N - 1)));
+            FEM_TRY(g->get(&f.hi, (size_t)fc * (N - 1)));
+        }
+        FEM_TRY(g->get(&f.rec, fc));
+        FEM_TRY(g->get(&f.counts, fc));
         FEM_TRY(g->get(&f.foff, n_recs + 1));
+    }
+    // level-1 / level-2 inputs
+    int64_t *d_ntpre = nullptr, *d_evpre = nullptr, *d_uboff = nullptr;
+    uint32_t *d_nt = nullptr, *ub = nullptr;
+    uint16_t *gt = nullptr;
+    int32_t *glo = nullptr, *ghi = nullptr;
+    uint32_t *grec = nullptr;
+    if (first <= 2) {
+        FEM_TRY(g->get(&d_ntpre, n_recs + 1));
+        FEM_TRY(g->get(&d_evpre, n_recs + 1));
+        FEM_TRY(g->get(&d_uboff, n_recs + 1));
+        FEM_TRY(g->get(&d_nt, n_recs));
+        FEM_TRY(g->get(&gt, (size_t)2 * std::max<int64_t>(cap2, 1)));
+        FEM_TRY(g->get(&glo, std::max<int64_t>(cap2, 1)));
+        FEM_TRY(g->get(&ghi, std::max<int64_t>(cap2, 1)));
+        FEM_TRY(g->get(&grec, std::max<int64_t>(cap2, 1)));
+        if (g->prepass) FEM_TRY(g->get(&ub, std::max<int64_t>(ub_off[n_recs], 1)));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_ntpre, ntpre.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_evpre, evpre.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_uboff, ub_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_nt, nt_h.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
     }
     FEM_CUDA_TRY(cudaMemcpyAsync(d_ri, ri_h.data(), sizeof(RecInfo) * n_recs, cudaMemcpyHostToDevice, st));
     FEM_CUDA_TRY(cudaMemcpyAsync(d_dens, dens_h.data(), sizeof(void *) * dens_h.size(), cudaMemcpyHostToDevice, st));
     FEM_CUDA_TRY(cudaMemcpyAsync(d_lov, lo_vals.data(), 4 * lo_vals.size(), cudaMemcpyHostToDevice, st));
+    if (nb > 0) {
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_blo, blo.data(), 4 * nb, cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_bhi, bhi.data(), 4 * nb, cudaMemcpyHostToDevice, st));
+    }
     FEM_CUDA_TRY(cudaMemcpyAsync(g->d_thr, thr.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
     int32_t *scan_tmp;
-    FEM_TRY(g->get(&scan_tmp, (cap + 2) / 1024 + 2));
+    FEM_TRY(g->get(&scan_tmp, (scan_m + 2) / 1024 + 2));
     FEM_CUDA_TRY(cudaStreamSynchronize(st));
-    // smem attribute for the sparse kernels before capture
-    for (int N = 3; N <= L; ++N) {
-        const int nmax = N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : 16;
-        if ((size_t)(6 * (nmax - 1) + 2 * (N - 1) * g->ring_cap) * 64 * 4 > (size_t)ctx->smem_optin - 1024)
-            return FEM_ERR_INVAL;
-    }
 
-    // ---- capture levels 3..L
+    // ---- capture levels first..L
     const unsigned gb = (unsigned)std::min<int64_t>((cap + 256) / 256, 4 * ctx->n_sm);
+    const unsigned gb2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap2 + 256) / 256, 8 * ctx->n_sm));
+    const unsigned gb1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot1 + 256) / 256, 4 * ctx->n_sm));
+    const unsigned gbe = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((evpre[n_recs] + ub_threads - 1) / ub_threads, 8 * ctx->n_sm));
     cudaGraph_t graph = nullptr;
     FEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int cst = FEM_OK;
-    for (int N = 3; N <= L && cst == FEM_OK; ++N) {
-        const int M = N - 1;
-        const FLevel &pf = g->F[M];
-        FLevel &nf = g->F[N];
-        int32_t *cp = g->ctr + (size_t)M * kCtr;  // previous level's counters
+    auto ok = [&](cudaError_t e) {
+        if (cst == FEM_OK && e != cudaSuccess) cst = FEM_ERR_CUDA;
+    };
+    for (int N = first; N <= L && cst == FEM_OK; ++N) {
         int32_t *cn = g->ctr + (size_t)N * kCtr;
         int64_t *coffN = g->coff + (size_t)N * (n_recs + 1);
-        const int nmax = N <= 4 ? 4 : N <= 8 ? 8 : 16;
-        if (cudaMemsetAsync(cn, 0, sizeof(int32_t) * kCtr, st) != cudaSuccess ||
-            cudaMemsetAsync(g->rel + N, 0, sizeof(unsigned long long), st) != cudaSuccess)
-            cst = FEM_ERR_CUDA;
-        k_g_join_count<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos);
-        if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
-        k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl, ch, crec, cn);
-        k_g_index<<<gb, 256, 0, st>>>(crec, cn, N, cap, offs, iota);
-        k_g_recinfo<<<1, 256, 0, st>>>(crec, cn, n_recs, coffN, d_ri, nthreads, g->segf, g->pfine, g->sstep,
-                                       g->segl, g->target);
-        k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), g->ring_cap, d_ri, cn,
-                                          g->rel + N);
+        FLevel &nf = g->F[N];
+        ok(cudaMemsetAsync(cn, 0, sizeof(int32_t) * kCtr, st));
+        ok(cudaMemsetAsync(g->rel + N, 0, sizeof(unsigned long long), st));
+        if (N == 1) {
+            k_g_l1_flags<<<gb1, 256, 0, st>>>(d_ri, g->d_thr, d_ntpre, n_recs, tot1, pos);
+            if (cst == FEM_OK) cst = scan_exclusive(st, pos, tot1 + 1, scan_tmp, nullptr, nullptr);
+            k_g_l1_write<<<gb1, 256, 0, st>>>(pos, d_ri, g->d_thr, d_ntpre, n_recs, tot1, nf.types, nf.rec, nf.counts,
+                                              cn);
+            k_g_foff<<<1, 256, 0, st>>>(nf.rec, cn, n_recs, nf.foff);
+            ok(cudaGetLastError());
+            continue;
+        }
+        const int nmax = N <= 2 ? 2 : N <= 4 ? 4 : N <= 8 ? 8 : 16;
+        if (N == 2) {
+            const FLevel &f1 = g->F[1];
+            k_g_gen2_off<<<1, 32, 0, st>>>(f1.foff, n_recs, nb, cap2, g->coff2, cn);
+            k_g_gen2<<<gb2, 256, 0, st>>>(f1.types, f1.foff, g->coff2, n_recs, d_blo, d_bhi, nb, cap2, gt, glo, ghi,
+                                          grec);
+            if (g->prepass) {
+                ok(cudaMemsetAsync(ub, 0, sizeof(uint32_t) * std::max<int64_t>(ub_off[n_recs], 1), st));
+                k_g_pair_ub<<<gbe, ub_threads, (size_t)ub_threads * ub_words * 4, st>>>(
+                    d_ri, d_evpre, n_recs, d_nt, d_uboff, d_blo, d_bhi, nb, hi_max, ub_words, ub);
+            }
+            const uint32_t *ubp = g->prepass ? ub : nullptr;
+            k_g_prune_flags<<<gb2, 256, 0, st>>>(gt, glo, ghi, grec, cn, cap2, ubp, d_uboff, d_nt, d_blo, d_bhi, nb,
+                                                 g->d_thr, pos);
+            if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap2 + 1, scan_tmp, nullptr, nullptr);
+            k_g_prune_write<<<gb2, 256, 0, st>>>(pos, gt, glo, ghi, grec, cap2, ubp, d_uboff, d_nt, d_blo, d_bhi, nb,
+                                                 g->d_thr, cap, ct, cl, ch, crec, cn);
+        } else {
+            const int M = N - 1;
+            const FLevel &pf = g->F[M];
+            int32_t *cp = g->ctr + (size_t)M * kCtr;  // previous level's counters
+            k_g_join_count<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos);
+            if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
+            k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl, ch,
+                                               crec, cn);
+        }
+        k_g_index<<<gb, 256, 0, st>>>(cn, N, cap, offs, iota);
+        k_g_recinfo<<<1, 256, 0, st>>>(crec, cn, n_recs, coffN, d_ri, nthreads, g->segf, g->pfine, g->sstep, g->segl,
+                                       g->target);
+        k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), g->ring_cap, d_ri,
+                                          cn, g->rel + N);
         // external event nodes: their timestamps time the count kernels of
         // this level on every launch of the graph
-        if (cst == FEM_OK && cudaEventRecordWithFlags(g->ev[2 * N], st, cudaEventRecordExternal) != cudaSuccess)
-            cst = FEM_ERR_CUDA;
+        ok(cudaEventRecordWithFlags(g->ev[2 * N], st, cudaEventRecordExternal));
         if (cst == FEM_OK)
-            cst = launch_count_dev(st, nmax, N, g->ring_cap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch, iota,
-                                   crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov, (int)lo_vals.size());
-        if (cst == FEM_OK && cudaEventRecordWithFlags(g->ev[2 * N + 1], st, cudaEventRecordExternal) != cudaSuccess)
-            cst = FEM_ERR_CUDA;
+            cst = launch_count_dev(st, nmax, N, g->ring_cap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch,
+                                   iota, crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov,
+                                   (int)lo_vals.size());
+        ok(cudaEventRecordWithFlags(g->ev[2 * N + 1], st, cudaEventRecordExternal));
         k_g_thr_flags<<<gb, 256, 0, st>>>(counts, crec, g->d_thr, cn, cap, pos);
         if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
         k_g_thr_write<<<gb, 256, 0, st>>>(pos, counts, ct, cl, ch, crec, g->d_thr, N, cap, nf.types, nf.lo, nf.hi,
                                           nf.rec, nf.counts, cn);
         k_g_foff<<<1, 256, 0, st>>>(nf.rec, cn, n_recs, nf.foff);
-        if (cst == FEM_OK && cudaGetLastError() != cudaSuccess) cst = FEM_ERR_CUDA;
+        ok(cudaGetLastError());
     }
     const cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (cst != FEM_OK || ce != cudaSuccess) {
@@ -414,6 +691,17 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
         cudaGetLastError();
         return cst != FEM_OK ? cst : FEM_ERR_CUDA;
     }
+    // kernel nodes of the graph (reported as kernel launches per run)
+    size_t n_nodes = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &n_nodes) == cudaSuccess && n_nodes > 0) {
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        if (cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess)
+            for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++g->kernel_nodes;
+            }
+    }
+    cudaGetLastError();
     const cudaError_t ie = cudaGraphInstantiate(&g->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) {
@@ -424,14 +712,14 @@ static int build_tail(GraphTail *g, const std::vector<int32_t> &blo, const std::
     return FEM_OK;
 }
 
-static std::string tail_key(const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
-                            const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, int max_size,
-                            int64_t cap) {
+static std::string graph_key(const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
+                             const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, int max_size,
+                             int first, bool prepass) {
     std::ostringstream k;
     for (auto *s : recs) k << (const void *)s << ':' << s->n << ';';
     for (size_t i = 0; i < blo.size(); ++i) k << blo[i] << ',' << bhi[i] << ';';
     for (auto t : thr) k << t << ';';
-    k << max_size << '/' << cap;
+    k << max_size << '/' << first << '/' << (prepass ? 1 : 0);
     return k.str();
 }
 
@@ -445,6 +733,7 @@ void graph_cache_forget(fem_ctx *ctx, const fem_stream *s) {
         bool uses = false;
         for (auto *r : it->second->recs) uses = uses || r == s;
         if (uses) {
+            ctx->graph_cap.erase(it->first);
             delete it->second;
             it = ctx->graphs.erase(it);
         } else {
@@ -453,35 +742,43 @@ void graph_cache_forget(fem_ctx *ctx, const fem_stream *s) {
     }
 }
 
-// Runs levels 3..max_size through the cached (or newly captured) graph,
-// starting from the level-2 frequent set (device arrays + per-recording
-// offsets).  Returns FEM_OK and fills `out` when every level completed
-// without a flag; *used = false when the graph path did not apply (the
-// caller then continues on the host-driven path).
-int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
-                   const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, const std::vector<int32_t> &lo_vals,
-                   int max_size, int64_t F2, const uint16_t *f2_types, const int32_t *f2_lo, const int32_t *f2_hi,
-                   const uint32_t *f2_rec, const uint32_t *f2_counts, const std::vector<int64_t> &f2_off,
-                   TailResult *out, bool *used) {
+namespace {
+
+// Level-2 frequent set handed to a graph that starts at level 3.
+struct Level2In {
+    int64_t F2;
+    const uint16_t *types;
+    const int32_t *lo, *hi;
+    const uint32_t *rec, *counts;
+    const std::vector<int64_t> *off;
+};
+
+}  // namespace
+
+// Runs levels first..max_size through the cached (or newly captured) graph.
+static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
+                     const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr,
+                     const std::vector<int32_t> &lo_vals, int max_size, int first, bool prepass, int64_t cap_min,
+                     const Level2In *in2, TailResult *out, bool *used) {
     *used = false;
     const int n_recs = (int)recs.size();
-    if (max_size < 3 || F2 == 0) return FEM_OK;
     for (auto *s : recs)
         if (s->n_types > 8192 || s->n > INT32_MAX / 2) return FEM_OK;
-    // capacity: the first join cannot exceed sum over recordings of F2_r^2
-    int64_t bound = 0;
-    for (int r = 0; r < n_recs; ++r) {
-        const int64_t f = f2_off[r + 1] - f2_off[r];
-        bound += f * f;
-    }
+    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass);
     int64_t cap = 4096;
-    while (cap < 2 * bound && cap < (1 << 18)) cap <<= 1;
-    const std::string key = tail_key(recs, blo, bhi, thr, max_size, cap);
+    auto hint = ctx->graph_cap.find(key);
+    const int64_t want = std::max<int64_t>(cap_min, hint != ctx->graph_cap.end() ? hint->second : 0);
+    while (cap < want && cap < (1 << 22)) cap <<= 1;
+    if (cap < want) return FEM_OK;
     GraphTail *g = nullptr;
     auto it = ctx->graphs.find(key);
-    if (it != ctx->graphs.end()) {
+    if (it != ctx->graphs.end() && it->second->cap >= cap) {
         g = it->second;
     } else {
+        if (it != ctx->graphs.end()) {
+            delete it->second;
+            ctx->graphs.erase(it);
+        }
         if (ctx->graphs.size() >= 4) graph_cache_clear(ctx);
         std::unique_ptr<GraphTail> ng(new GraphTail());
         ng->ctx = ctx;
@@ -489,48 +786,66 @@ int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const st
         ng->recs = recs;
         ng->n_recs = n_recs;
         ng->max_size = max_size;
+        ng->first = first;
+        ng->prepass = prepass;
         ng->cap = cap;
-        const int st = build_tail(ng.get(), blo, bhi, thr, lo_vals);
+        const int st = build_graph(ng.get(), blo, bhi, thr, lo_vals);
         if (st == FEM_ERR_NOMEM || st == FEM_ERR_INVAL) return FEM_OK;  // not applicable: host path
         if (st != FEM_OK) return st;
         g = ng.release();
         ctx->graphs[key] = g;
     }
-    if (F2 > g->cap) return FEM_OK;
-    // level-2 frequent set into the graph's input buffers
     cudaStream_t st = ctx->stream;
-    FLevel &f2 = g->F[2];
-    FEM_CUDA_TRY(cudaMemcpyAsync(f2.types, f2_types, 2 * 2 * F2, cudaMemcpyDeviceToDevice, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(f2.lo, f2_lo, 4 * F2, cudaMemcpyDeviceToDevice, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(f2.hi, f2_hi, 4 * F2, cudaMemcpyDeviceToDevice, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(f2.rec, f2_rec, 4 * F2, cudaMemcpyDeviceToDevice, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(f2.counts, f2_counts, 4 * F2, cudaMemcpyDeviceToDevice, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(f2.foff, f2_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
-    std::vector<int32_t> c2(kCtr, 0);
-    c2[1] = (int32_t)F2;
-    FEM_CUDA_TRY(cudaMemcpyAsync(g->ctr + 2 * kCtr, c2.data(), 4 * kCtr, cudaMemcpyHostToDevice, st));
+    if (first == 3) {
+        if (!in2 || in2->F2 > g->cap) return FEM_OK;
+        FLevel &f2 = g->F[2];
+        const int64_t F2 = in2->F2;
+        FEM_CUDA_TRY(cudaMemcpyAsync(f2.types, in2->types, 2 * 2 * F2, cudaMemcpyDeviceToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(f2.lo, in2->lo, 4 * F2, cudaMemcpyDeviceToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(f2.hi, in2->hi, 4 * F2, cudaMemcpyDeviceToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(f2.rec, in2->rec, 4 * F2, cudaMemcpyDeviceToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(f2.counts, in2->counts, 4 * F2, cudaMemcpyDeviceToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(f2.foff, in2->off->data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+        std::vector<int32_t> c2(kCtr, 0);
+        c2[1] = (int32_t)F2;
+        FEM_CUDA_TRY(cudaMemcpyAsync(g->ctr + 2 * kCtr, c2.data(), 4 * kCtr, cudaMemcpyHostToDevice, st));
+    }
     cudaEventRecord(ctx->ev0, st);
     FEM_CUDA_TRY(cudaGraphLaunch(g->exec, st));
     cudaEventRecord(ctx->ev1, st);
     std::vector<int32_t> ctr((size_t)(max_size + 1) * kCtr);
     std::vector<int64_t> coff((size_t)(max_size + 1) * (n_recs + 1));
+    std::vector<int64_t> coff2(n_recs + 1, 0);
+    std::vector<unsigned long long> rel((size_t)max_size + 1, 0ull);
     FEM_CUDA_TRY(cudaMemcpyAsync(ctr.data(), g->ctr, 4 * ctr.size(), cudaMemcpyDeviceToHost, st));
     FEM_CUDA_TRY(cudaMemcpyAsync(coff.data(), g->coff, 8 * coff.size(), cudaMemcpyDeviceToHost, st));
-    std::vector<unsigned long long> rel((size_t)max_size + 1, 0ull);
+    if (first <= 2)
+        FEM_CUDA_TRY(cudaMemcpyAsync(coff2.data(), g->coff2, 8 * coff2.size(), cudaMemcpyDeviceToHost, st));
     FEM_CUDA_TRY(cudaMemcpyAsync(rel.data(), g->rel, 8 * rel.size(), cudaMemcpyDeviceToHost, st));
     FEM_TRY(sync_status(ctx));
-    for (int N = 3; N <= max_size; ++N) {
+    bool flagged = false;
+    int64_t need = 0;
+    for (int N = std::max(first, 2); N <= max_size; ++N) {
         const int32_t *c = &ctr[(size_t)N * kCtr];
-        if (c[2] != 0 || c[3] != 0) return FEM_OK;  // flagged: redo on the host path
+        if (c[2] != 0 || c[3] != 0) flagged = true;
+        if (c[2] & kFlagCap) need = std::max<int64_t>(need, (int64_t)c[5] + 1);
+        if (c[2] & kFlagFreq) need = std::max<int64_t>(need, 2 * g->cap);
+    }
+    if (flagged) {
+        // redo on the host path; a capacity overflow grows the next capture
+        if (need > 0) ctx->graph_cap[key] = std::max<int64_t>(need, 2 * g->cap);
+        return FEM_OK;
     }
     float gms = 0.f;
     cudaEventElapsedTime(&gms, ctx->ev0, ctx->ev1);
     out->graph_ms = gms;
+    out->kernel_nodes = g->kernel_nodes;
+    out->count_levels = max_size - std::max(first, 2) + 1;
     // count-kernel time of the levels from the graph's event nodes (the whole
     // graph's time if the driver cannot time them)
     float cms = 0.f;
     bool timed = true;
-    for (int N = 3; N <= max_size && timed; ++N) {
+    for (int N = std::max(first, 2); N <= max_size && timed; ++N) {
         float m = 0.f;
         if (cudaEventElapsedTime(&m, g->ev[2 * N], g->ev[2 * N + 1]) != cudaSuccess) timed = false;
         cms += m;
@@ -538,15 +853,18 @@ int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const st
     if (!timed) cudaGetLastError();
     out->count_ms = timed ? cms : gms;
     out->relevant = 0.0;
-    for (int N = 3; N <= max_size; ++N) out->relevant += (double)rel[N];
+    for (int N = std::max(first, 2); N <= max_size; ++N) out->relevant += (double)rel[N];
     // results
     out->levels.clear();
-    for (int N = 3; N <= max_size; ++N) {
+    for (int N = first; N <= max_size; ++N) {
         const int32_t *c = &ctr[(size_t)N * kCtr];
         TailLevel tl;
         tl.N = N;
-        tl.C = c[0];
-        tl.coff.assign(coff.begin() + (size_t)N * (n_recs + 1), coff.begin() + (size_t)(N + 1) * (n_recs + 1));
+        tl.C = N == 1 ? 0 : c[0];
+        if (N >= 2) {
+            tl.coff.assign(coff.begin() + (size_t)N * (n_recs + 1), coff.begin() + (size_t)(N + 1) * (n_recs + 1));
+            tl.goff = (N == 2 && first <= 2) ? coff2 : tl.coff;
+        }
         const int64_t Fn = c[1];
         tl.types.resize((size_t)Fn * N);
         tl.lo.resize((size_t)Fn * (N - 1));
@@ -556,17 +874,56 @@ int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const st
         if (Fn > 0) {
             const FLevel &f = g->F[N];
             FEM_CUDA_TRY(cudaMemcpyAsync(tl.types.data(), f.types, 2 * tl.types.size(), cudaMemcpyDeviceToHost, st));
-            FEM_CUDA_TRY(cudaMemcpyAsync(tl.lo.data(), f.lo, 4 * tl.lo.size(), cudaMemcpyDeviceToHost, st));
-            FEM_CUDA_TRY(cudaMemcpyAsync(tl.hi.data(), f.hi, 4 * tl.hi.size(), cudaMemcpyDeviceToHost, st));
+            if (N > 1) {
+                FEM_CUDA_TRY(cudaMemcpyAsync(tl.lo.data(), f.lo, 4 * tl.lo.size(), cudaMemcpyDeviceToHost, st));
+                FEM_CUDA_TRY(cudaMemcpyAsync(tl.hi.data(), f.hi, 4 * tl.hi.size(), cudaMemcpyDeviceToHost, st));
+            }
             FEM_CUDA_TRY(cudaMemcpyAsync(tl.rec.data(), f.rec, 4 * tl.rec.size(), cudaMemcpyDeviceToHost, st));
             FEM_CUDA_TRY(cudaMemcpyAsync(tl.counts.data(), f.counts, 4 * tl.counts.size(), cudaMemcpyDeviceToHost, st));
         }
         out->levels.push_back(std::move(tl));
-        if (c[0] == 0 || Fn == 0) break;
+        if ((N >= 2 && c[0] == 0) || Fn == 0) break;
     }
     FEM_CUDA_TRY(cudaStreamSynchronize(st));
     *used = true;
     return FEM_OK;
+}
+
+int run_graph_mining(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
+                     const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr,
+                     const std::vector<int32_t> &lo_vals, int max_size, bool prepass, TailResult *out, bool *used) {
+    *used = false;
+    if (max_size < 2 || blo.empty() || blo.size() > 8) return FEM_OK;
+    for (auto *s : recs)
+        if (s->n_types > 1024) prepass = false;
+    // without the pre-pass every level-2 pair is counted: capacity for all
+    int64_t cap_min = 0;
+    if (!prepass)
+        for (auto *s : recs) cap_min += (int64_t)s->n_types * (s->n_types - 1) * (int64_t)blo.size();
+    return run_graph(ctx, recs, blo, bhi, thr, lo_vals, max_size, 1, prepass, cap_min, nullptr, out, used);
+}
+
+// Levels 3..max_size from the level-2 frequent set (device arrays +
+// per-recording offsets).  Returns FEM_OK and fills `out` when every level
+// completed without a flag; *used = false when the graph path did not apply
+// (the caller then continues on the host-driven path).
+int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
+                   const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, const std::vector<int32_t> &lo_vals,
+                   int max_size, int64_t F2, const uint16_t *f2_types, const int32_t *f2_lo, const int32_t *f2_hi,
+                   const uint32_t *f2_rec, const uint32_t *f2_counts, const std::vector<int64_t> &f2_off,
+                   TailResult *out, bool *used) {
+    *used = false;
+    const int n_recs = (int)recs.size();
+    if (max_size < 3 || F2 == 0) return FEM_OK;
+    // capacity: the first join cannot exceed sum over recordings of F2_r^2
+    int64_t bound = 0;
+    for (int r = 0; r < n_recs; ++r) {
+        const int64_t f = f2_off[r + 1] - f2_off[r];
+        bound += f * f;
+    }
+    const Level2In in2{F2, f2_types, f2_lo, f2_hi, f2_rec, f2_counts, &f2_off};
+    return run_graph(ctx, recs, blo, bhi, thr, lo_vals, max_size, 3, false, std::min<int64_t>(2 * bound, 1 << 18),
+                     &in2, out, used);
 }
 
 }  // namespace fem

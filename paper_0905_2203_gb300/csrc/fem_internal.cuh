@@ -59,11 +59,12 @@ struct RecInfo {
     const int32_t *ttime;
 };
 
-// Results of the graph-captured tail (levels >= 3) of level-wise mining.
+// Results of the levels of level-wise mining run in a captured graph.
 struct TailLevel {
     int N = 0;
     int64_t C = 0;                    // candidates counted at this level
-    std::vector<int64_t> coff;        // per-recording candidate offsets
+    std::vector<int64_t> coff;        // per-recording offsets of the counted candidates
+    std::vector<int64_t> goff;        // per-recording offsets of the generated ones (level 2: before pruning)
     std::vector<uint16_t> types;      // frequent episodes, fixed stride N
     std::vector<int32_t> lo, hi;
     std::vector<uint32_t> rec, counts;
@@ -73,6 +74,8 @@ struct TailResult {
     float graph_ms = 0.f;             // device time of the graph launch
     float count_ms = 0.f;             // of which in the count kernels (+ stitch)
     double relevant = 0.0;            // relevant episode-events of the counted levels
+    int64_t kernel_nodes = 0;         // kernel launches of one run of the graph
+    int count_levels = 0;             // levels with a sparse counting launch
 };
 struct GraphTail;
 
@@ -101,7 +104,8 @@ struct fem_ctx {
     fem_stats last{};
     std::map<int, fem::DevBuf> scratch;  // slot -> buffer (grown on demand)
     std::map<std::string, fem::TuneVal> tune;  // autotuner cache
-    std::map<std::string, fem::GraphTail *> graphs;  // captured mining tails
+    std::map<std::string, fem::GraphTail *> graphs;  // captured mining graphs
+    std::map<std::string, int64_t> graph_cap;        // candidate capacity a graph key needed last time
     std::string tune_path;                     // JSON file backing the cache ("" = memory only)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -192,6 +196,13 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
 size_t sparse_smem_bytes(int nmax, int R);
 // Segment boundaries (P + 1 entries) of a stream cut into P segments at time changes.
 int launch_segments(cudaStream_t st, const int32_t *time, int64_t n, int P, int64_t *seg);
+// Levels 1..max_size in one captured graph (streams resident; no host step
+// between levels).  *used = false when it does not apply or a level raised a
+// flag (capacity, ring or entry-class overflow): the caller then mines on the
+// host-driven path.
+int run_graph_mining(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
+                     const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr,
+                     const std::vector<int32_t> &lo_vals, int max_size, bool prepass, TailResult *out, bool *used);
 int run_graph_tail(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
                    const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, const std::vector<int32_t> &lo_vals,
                    int max_size, int64_t F2, const uint16_t *f2_types, const int32_t *f2_lo, const int32_t *f2_hi,

@@ -703,6 +703,52 @@ int MineGroup::advance() {
     return finish_candidates();
 }
 
+// Copies the levels a captured graph produced into the result and the
+// statistics (level 2 counts the candidates the pre-pass dropped as pruned).
+static void fill_graph_levels(MineGroup &g, const TailResult &tr) {
+    const int n_recs = g.nrec();
+    for (const TailLevel &tl : tr.levels) {
+        const int N = tl.N;
+        if (N >= 2) {
+            if (tl.C == 0) break;
+            g.S.candidates_counted += tl.C;
+            for (int r = 0; r < n_recs; ++r) {
+                const double gr = (double)(tl.goff[r + 1] - tl.goff[r]);
+                const double cr = (double)(tl.coff[r + 1] - tl.coff[r]);
+                g.S.episode_events += gr * (double)g.recs[r]->n;
+                g.S.counted_episode_events += cr * (double)g.recs[r]->n;
+                g.S.candidates_pruned += (int64_t)(gr - cr);
+            }
+        }
+        g.S.levels = N;
+        std::vector<int64_t> off(n_recs + 1, 0);
+        for (uint32_t r : tl.rec) off[r + 1]++;
+        for (int r = 0; r < n_recs; ++r) off[r + 1] += off[r];
+        for (int r = 0; r < n_recs; ++r) {
+            fem_result::Level &out = g.res->lv[g.out_rec[r]][N];
+            out.offs.assign(1, 0);
+            out.types.clear();
+            out.lo.clear();
+            out.hi.clear();
+            out.counts.clear();
+            for (int64_t i = off[r]; i < off[r + 1]; ++i) {
+                out.types.insert(out.types.end(), tl.types.begin() + i * N, tl.types.begin() + (i + 1) * N);
+                if (N > 1) {
+                    out.lo.insert(out.lo.end(), tl.lo.begin() + i * (N - 1), tl.lo.begin() + (i + 1) * (N - 1));
+                    out.hi.insert(out.hi.end(), tl.hi.begin() + i * (N - 1), tl.hi.begin() + (i + 1) * (N - 1));
+                }
+                out.counts.push_back(tl.counts[i]);
+                out.offs.push_back((int64_t)out.types.size());
+            }
+        }
+    }
+    g.S.graph_tails += 1;
+    g.S.kernel_launches += tr.kernel_nodes;
+    g.S.sparse_launches += tr.count_levels;
+    g.S.count_kernel_ms += tr.count_ms;
+    g.S.relevant_events += tr.relevant;
+}
+
 // Levels 3..max_size through the captured graph (fem_graph.cu), starting
 // from the level-2 frequent set; when it does not apply or reports a flag the
 // group simply continues level by level.
@@ -712,43 +758,10 @@ int MineGroup::graph_tail() {
     FEM_TRY(run_graph_tail(ctx, recs, blo, bhi, thr, lo_vals, max_size, prev.n, prev.types, prev.lo, prev.hi, prev.rec,
                            prev.counts, prev.h_off, &tr, &used));
     if (!used) return FEM_OK;
-    // the level-3 candidates the host path had prepared are superseded
-    const int n_recs = nrec();
-    for (const TailLevel &tl : tr.levels) {
-        const int N = tl.N;
-        if (tl.C == 0) break;
-        S.levels = N;
-        S.candidates_counted += tl.C;
-        for (int r = 0; r < n_recs; ++r) {
-            const double cr = (double)(tl.coff[r + 1] - tl.coff[r]);
-            S.episode_events += cr * (double)recs[r]->n;
-            S.counted_episode_events += cr * (double)recs[r]->n;
-        }
-        std::vector<int64_t> off(n_recs + 1, 0);
-        for (uint32_t r : tl.rec) off[r + 1]++;
-        for (int r = 0; r < n_recs; ++r) off[r + 1] += off[r];
-        for (int r = 0; r < n_recs; ++r) {
-            fem_result::Level &out = res->lv[out_rec[r]][N];
-            out.offs.assign(1, 0);
-            out.types.clear();
-            out.lo.clear();
-            out.hi.clear();
-            out.counts.clear();
-            for (int64_t i = off[r]; i < off[r + 1]; ++i) {
-                out.types.insert(out.types.end(), tl.types.begin() + i * N, tl.types.begin() + (i + 1) * N);
-                out.lo.insert(out.lo.end(), tl.lo.begin() + i * (N - 1), tl.lo.begin() + (i + 1) * (N - 1));
-                out.hi.insert(out.hi.end(), tl.hi.begin() + i * (N - 1), tl.hi.begin() + (i + 1) * (N - 1));
-                out.counts.push_back(tl.counts[i]);
-                out.offs.push_back((int64_t)out.types.size());
-            }
-        }
-    }
-    S.graph_tails += 1;
-    S.count_kernel_ms += tr.count_ms;
-    S.relevant_events += tr.relevant;
-    // the episode-events of the level-3 candidates were added when they were
-    // prepared on the host; the graph recounted them, so remove that share
-    for (int r = 0; r < n_recs; ++r) S.episode_events -= (double)(c_off[r + 1] - c_off[r]) * (double)recs[r]->n;
+    // the level-3 candidates the host path had prepared are superseded: the
+    // graph accounts for them itself
+    for (int r = 0; r < nrec(); ++r) S.episode_events -= (double)(c_off[r + 1] - c_off[r]) * (double)recs[r]->n;
+    fill_graph_levels(*this, tr);
     done = true;
     level = 0;
     pcand.reset();
@@ -901,6 +914,28 @@ static int mine_impl(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
     g.bhi = bhi;
     g.thr = thr;
     g.max_size = max_size;
+    // The whole pass as one captured graph (sparse counting kernel, device-
+    // chosen segmentation) unless a tuning override asks for the host-driven
+    // path or an alphabet is small enough for the tiled kernel to be the
+    // better choice at level 2.
+    const fem_tuning &tu = ctx->tuning;
+    bool whole = tu.level_graph != -1 && tu.plain_path != 1 && tu.kernel == 0 && tu.segments == 0 &&
+                 tu.lanes_per_cta == 0 && tu.tile_events == 0 && max_size >= 2;
+    for (auto *s : recs)
+        if (s->n_types < 16) whole = false;
+    if (whole) {
+        std::vector<int32_t> lo_vals = blo;
+        std::sort(lo_vals.begin(), lo_vals.end());
+        lo_vals.erase(std::unique(lo_vals.begin(), lo_vals.end()), lo_vals.end());
+        TailResult tr;
+        bool used = false;
+        FEM_TRY(run_graph_mining(ctx, recs, blo, bhi, thr, lo_vals, max_size, tu.prepass != -1, &tr, &used));
+        if (used) {
+            fill_graph_levels(g, tr);
+            res->stats = g.S;
+            return FEM_OK;
+        }
+    }
     int st = g.begin();
     while (st == FEM_OK && !g.done) {
         st = count_group(g);

@@ -402,3 +402,58 @@ def test_level_graph_equals_host_path(fb, ctx, which):
         assert abs(s1["episode_events"] - sh["episode_events"]) < 1e-6 * sh["episode_events"]
     for x in streams:
         x.free()
+
+
+def test_graph_capacity_overflow_falls_back_then_grows(fb, ctx):
+    """More level-2 survivors than the graph's first capacity (4096): the
+    first call redoes the mining on the host path (same results), the next
+    call captures a graph with the capacity it needed and runs it."""
+    ty, tm = synth.tiny_random_stream(0xCA9, 200_000, 64, 2_000_000)
+    st = ctx.load_stream(ty, tm, 64)
+    bins = [(0, 50), (50, 100), (100, 150), (150, 200)]
+
+    def run():
+        res = ctx.mine_levelwise([st], bins, [100], 2)
+        out = [res.level(0, N) for N in (1, 2)]
+        s = res.stats()
+        res.free()
+        return out, s
+
+    a, sa = run()
+    b, sb = run()
+    ctx.set_tuning(level_graph=-1)
+    try:
+        h, sh = run()
+    finally:
+        ctx.reset_tuning()
+    assert len(h[1][1]) > 4096
+    assert a == h and b == h
+    assert sa["graph_tails"] == 0 and sb["graph_tails"] == 1
+    st.free()
+
+
+def test_graph_tail_after_host_level2(fb, ctx):
+    """With a kernel override the whole-pass graph does not apply: level 2 is
+    counted on the host-driven path and levels >= 3 run in the tail graph;
+    results equal the level-by-level path."""
+    s, cfg = synth.c2_mid(duration_s=80.0)
+    thr = int(0.0025 * s.n)
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+
+    def run(**tun):
+        ctx.set_tuning(**tun)
+        try:
+            res = ctx.mine_levelwise([st], cfg["bins"], [thr], cfg["max_size"])
+            out = [res.level(0, N) for N in range(1, cfg["max_size"] + 1)]
+            stt = res.stats()
+            res.free()
+        finally:
+            ctx.reset_tuning()
+        return out, stt
+
+    t, stt = run(kernel=2)
+    h, sth = run(kernel=2, level_graph=-1)
+    assert t == h
+    assert stt["graph_tails"] == 1 and sth["graph_tails"] == 0
+    assert stt["levels"] == sth["levels"] >= 3
+    st.free()
