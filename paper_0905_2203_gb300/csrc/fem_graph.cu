@@ -33,6 +33,7 @@ namespace {
 
 constexpr int kRingCap = 32;      // largest shared-memory ring in the graph path
 constexpr int kMaxPerRec = 4096;  // finest segmentation of a recording
+constexpr int64_t kFusedCap = 16384;  // largest level capacity for the single-block join / threshold
 
 // Counters per level: [0] candidates counted C, [1] frequent F, [2] flags,
 // [3] entry-class fallbacks (stitch), [4] candidates generated (level 2,
@@ -127,42 +128,96 @@ __global__ void k_g_gen2(const uint16_t *ft1, const int64_t *foff1, const int64_
 // Mining"): the non-overlapped occurrences of a -(lo,hi]-> b end at distinct
 // b-events, each with an a-event inside its window, so
 //     count(a, b, bin) <= UB = #{ b-events with an a-event in the window }.
-// One thread per event scans back over the widest window, marks each
-// (type, bin) once in a per-thread bitset and adds one to UB for it.
-__global__ void k_g_pair_ub(const RecInfo *ri, const int64_t *evpre, int n_recs, const uint32_t *nt,
+// A block takes a tile of kUbTile consecutive events of one recording and
+// stages the tile plus the events up to hi_max before it (at most kUbHalo) in
+// shared memory; one thread per event scans back over its window there (in
+// global memory beyond the staged halo), marks each (type, bin) once in its
+// bitset and adds one to UB for it.  The bins a time difference d falls in
+// come from a table of bin masks indexed by d (when hi_max < kUbLut), else
+// from a loop over the bins.  Word w of thread t's bitset sits at
+// bits[w * blockDim + t], so the lanes of a warp touch distinct banks.
+constexpr int kUbMaxBins = 8;
+constexpr int kUbLut = 65536;
+constexpr int kUbTile = 1024;
+constexpr int kUbHalo = 1024;
+
+__global__ void k_g_pair_ub(const RecInfo *ri, const int64_t *tpre, int n_recs, const uint32_t *nt,
                             const int64_t *ub_off, const int32_t *blo, const int32_t *bhi, int nb, int32_t hi_max,
-                            int words, uint32_t *ub) {
-    extern __shared__ uint32_t bits[];
-    uint32_t *my = bits + threadIdx.x * words;
-    const int64_t tot = evpre[n_recs];
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot; g += (int64_t)gridDim.x * blockDim.x) {
-        const int r = seg_of(evpre, n_recs, g);
-        const int64_t j = g - evpre[r];
+                            int words, const uint8_t *lut_g, uint32_t *ub) {
+    extern __shared__ uint32_t sm[];
+    const int bd = blockDim.x;
+    const int lut_words = lut_g ? (hi_max + 4) / 4 : 0;
+    uint8_t *lut = reinterpret_cast<uint8_t *>(sm);
+    int32_t *s_tm = reinterpret_cast<int32_t *>(sm + lut_words);
+    uint16_t *s_ty = reinterpret_cast<uint16_t *>(s_tm + kUbTile + kUbHalo);
+    uint32_t *my = sm + lut_words + (kUbTile + kUbHalo) + (kUbTile + kUbHalo) / 2 + threadIdx.x;
+    __shared__ int64_t s_h0;
+    if (lut_g) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(lut_g);
+        for (int w = threadIdx.x; w < lut_words; w += bd) sm[w] = src[w];
+    }
+    const int64_t tiles = tpre[n_recs];
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int r = seg_of(tpre, n_recs, tile);
+        const int64_t j0 = (tile - tpre[r]) * kUbTile;
+        const int64_t n = ri[r].n;
+        const int64_t j1 = min(n, j0 + kUbTile);
         const uint16_t *ty = ri[r].type;
         const int32_t *tm = ri[r].time;
         const uint32_t ntr = nt[r];
         const int wr = (int)((ntr * (uint32_t)nb + 31) / 32);
         uint32_t *u = ub + ub_off[r];
-        for (int w = 0; w < wr; ++w) my[w] = 0;
-        const int32_t t = tm[j];
-        const uint32_t b = ty[j];
-        const int64_t lim = (int64_t)t - hi_max;
-        for (int64_t i = j - 1; i >= 0 && (int64_t)tm[i] >= lim; --i) {
-            const int32_t d = t - tm[i];
-            if (d <= 0) continue;
-            const uint32_t a = ty[i];
-            if (a == b) continue;
-            for (int k = 0; k < nb; ++k) {
-                if (blo[k] < d && d <= bhi[k]) {
+        if (threadIdx.x == 0) {
+            // first event within hi_max of the tile's first event (capped)
+            const int64_t lim = (int64_t)tm[j0] - hi_max;
+            int64_t lo = max((int64_t)0, j0 - kUbHalo), hi = j0;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((int64_t)tm[mid] < lim) lo = mid + 1; else hi = mid;
+            }
+            s_h0 = lo;
+        }
+        __syncthreads();
+        const int64_t h0 = s_h0;
+        for (int64_t i = h0 + threadIdx.x; i < j1; i += bd) {
+            s_tm[i - h0] = tm[i];
+            s_ty[i - h0] = ty[i];
+        }
+        __syncthreads();
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += bd) {
+            for (int w = 0; w < wr; ++w) my[w * bd] = 0;
+            const int32_t t = s_tm[j - h0];
+            const uint32_t b = s_ty[j - h0];
+            const int64_t lim = (int64_t)t - hi_max;
+            for (int64_t i = j - 1; i >= 0; --i) {
+                const bool st = i >= h0;
+                const int32_t ti = st ? s_tm[i - h0] : tm[i];
+                if ((int64_t)ti < lim) break;
+                const int32_t d = t - ti;
+                if (d <= 0) continue;
+                const uint32_t a = st ? s_ty[i - h0] : ty[i];
+                if (a == b) continue;
+                uint32_t mask = 0;
+                if (lut_g) {
+                    mask = lut[d];
+                } else {
+                    for (int k = 0; k < nb; ++k)
+                        if (blo[k] < d && d <= bhi[k]) mask |= 1u << k;
+                }
+                while (mask) {
+                    const int k = __ffs(mask) - 1;
+                    mask &= mask - 1;
                     const uint32_t bit = a * (uint32_t)nb + (uint32_t)k;
                     const uint32_t m = 1u << (bit & 31);
-                    if (!(my[bit >> 5] & m)) {
-                        my[bit >> 5] |= m;
+                    uint32_t &wd = my[(bit >> 5) * bd];
+                    if (!(wd & m)) {
+                        wd |= m;
                         atomicAdd(&u[((size_t)a * ntr + b) * nb + k], 1u);
                     }
                 }
             }
         }
+        __syncthreads();  // the staged events are replaced by the next tile's
     }
 }
 
@@ -274,23 +329,50 @@ __global__ void k_g_join_write(const uint16_t *ft, const int32_t *fl, const int3
 }
 
 // ---- every level >= 2 --------------------------------------------------------
-// CSR offsets of the candidates and the identity slot order.
-__global__ void k_g_index(const int32_t *ctr, int N, int64_t cap, int64_t *offs, int32_t *iota) {
-    const int64_t C = ctr[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= cap; i += (int64_t)gridDim.x * blockDim.x) {
+// Exclusive scan of one value per thread over the block (a multiple of 32
+// threads, at most 1024); *total receives the block's sum.
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total) {
+    __shared__ int64_t s_w[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = lane < nw ? s_w[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= o) t += y;
+        }
+        s_w[lane] = t;
+    }
+    __syncthreads();
+    const int64_t before = (w > 0 ? s_w[w - 1] : 0) + x - v;
+    *total = s_w[nw - 1];
+    __syncthreads();  // s_w is reused by the next call
+    return before;
+}
+
+// CSR offsets of the candidates and the identity slot order (one block or a
+// grid: strided over the block's / grid's threads).
+__device__ __forceinline__ void level_index(int64_t C, int N, int64_t cap, int64_t *offs, int32_t *iota, int64_t t0,
+                                            int64_t stride) {
+    for (int64_t i = t0; i <= cap; i += stride) {
         if (i <= C) offs[i] = i * N;
         if (i < cap) iota[i] = (int32_t)i;
     }
 }
 
-// Per-level segmentation: the level's (candidate, segment) threads should
-// number about `target`, so a level with few candidates cuts its recordings
-// finely and one with many coarsely.  Segment boundaries are taken from the
-// recording's finest boundaries (pfine[r] segments, in segf) every s-th one.
-__global__ void k_g_recinfo(const uint32_t *crec, const int32_t *ctr, int n_recs, int64_t *coff, RecInfo *ri,
-                            int64_t *nthreads, const int64_t *segf, const int32_t *pfine, int32_t *sstep,
-                            int64_t *segl, int64_t target) {
-    const int64_t C = ctr[0];
+// Per-level segmentation (one block): the level's (candidate, segment)
+// threads should number about `target`, so a level with few candidates cuts
+// its recordings finely and one with many coarsely: recording r gets P_r
+// segments, every sstep[r]-th of its pfine[r] finest ones.  Also the
+// per-recording candidate offsets and the RecInfo fields that depend on them.
+__device__ void level_info(const uint32_t *crec, int64_t C, int n_recs, int64_t *coff, RecInfo *ri,
+                           int64_t *nthreads, const int32_t *pfine, int32_t *sstep, int64_t target) {
     for (int r = threadIdx.x; r <= n_recs; r += blockDim.x) {
         int64_t lo = 0, hi = C;  // first candidate of recording >= r
         while (lo < hi) {
@@ -319,20 +401,130 @@ __global__ void k_g_recinfo(const uint32_t *crec, const int32_t *ctr, int n_recs
         *nthreads = base;
     }
     __syncthreads();
-    for (int r = 0; r < n_recs; ++r) {
-        const int P = ri[r].P, st = sstep[r], pf = pfine[r];
-        const int64_t *f = segf + (size_t)r * (kMaxPerRec + 1);
-        int64_t *o = segl + (size_t)r * (kMaxPerRec + 1);
-        for (int p = threadIdx.x; p <= P; p += blockDim.x) o[p] = f[min(p * st, pf)];
+}
+
+__global__ void k_g_levelinfo(const uint32_t *crec, const int32_t *ctr, int N, int64_t cap, int64_t *offs,
+                              int32_t *iota, int n_recs, int64_t *coff, RecInfo *ri, int64_t *nthreads,
+                              const int32_t *pfine, int32_t *sstep, int64_t target) {
+    const int64_t C = ctr[0];
+    level_index(C, N, cap, offs, iota, threadIdx.x, blockDim.x);
+    level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target);
+}
+
+// Level N = M + 1 in one block: zero the level's counters, count each
+// frequent alpha's join partners, scan, write the candidates, then index and
+// segment the level (for levels whose capacity keeps one block fast).
+__global__ void __launch_bounds__(1024, 1)
+    k_g_join_fused(const uint16_t *ft, const int32_t *fl, const int32_t *fh, const uint32_t *frec,
+                   const int64_t *foff, const int32_t *ctr_prev, int M, int64_t cap, uint16_t *ct, int32_t *cl,
+                   int32_t *ch, uint32_t *crec, int32_t *ctr, unsigned long long *rel, int64_t *offs, int32_t *iota,
+                   int n_recs, int64_t *coff, RecInfo *ri, int64_t *nthreads, const int32_t *pfine, int32_t *sstep,
+                   int64_t target) {
+    const int N = M + 1;
+    const int64_t F = ctr_prev[1];
+    const int64_t per = (F + blockDim.x - 1) / blockDim.x;
+    const int64_t a0 = min(F, (int64_t)threadIdx.x * per), a1 = min(F, a0 + per);
+    int64_t cnt = 0;
+    for (int64_t a = a0; a < a1; ++a) {
+        const uint32_t r = frec[a];
+        for (int64_t b = foff[r]; b < foff[r + 1]; ++b)
+            if (g_joins(ft, fl, fh, M, a, b)) ++cnt;
+    }
+    int64_t total = 0;
+    int64_t o = block_excl_scan(cnt, &total);
+    for (int64_t a = a0; a < a1; ++a) {
+        const uint32_t r = frec[a];
+        for (int64_t b = foff[r]; b < foff[r + 1]; ++b) {
+            if (!g_joins(ft, fl, fh, M, a, b)) continue;
+            if (o < cap) {
+                for (int k = 0; k < M; ++k) ct[o * N + k] = ft[a * M + k];
+                ct[o * N + M] = ft[b * M + M - 1];
+                for (int k = 0; k < M - 1; ++k) {
+                    cl[o * (N - 1) + k] = fl[a * (M - 1) + k];
+                    ch[o * (N - 1) + k] = fh[a * (M - 1) + k];
+                }
+                cl[o * (N - 1) + M - 1] = fl[b * (M - 1) + M - 2];
+                ch[o * (N - 1) + M - 1] = fh[b * (M - 1) + M - 2];
+                crec[o] = r;
+            }
+            ++o;
+        }
+    }
+    const int64_t C = total < cap ? total : cap;
+    if (threadIdx.x == 0) {
+        ctr[0] = (int32_t)C;
+        ctr[1] = 0;
+        ctr[2] = total > cap ? kFlagCap : 0;
+        ctr[3] = 0;
+        ctr[4] = (int32_t)C;
+        ctr[5] = (int32_t)(total < INT32_MAX ? total : INT32_MAX);
+        *rel = 0ull;
+    }
+    level_index(C, N, cap, offs, iota, threadIdx.x, blockDim.x);
+    __syncthreads();  // crec complete
+    level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target);
+}
+
+// The level's threshold in one block: flags, scan, write of the frequent
+// episodes in candidate order, then the per-recording offsets.
+__global__ void __launch_bounds__(1024, 1)
+    k_g_thr_fused(const uint32_t *counts, const uint16_t *ct, const int32_t *cl, const int32_t *ch,
+                  const uint32_t *crec, const uint32_t *thr, int N, int64_t cap, uint16_t *ft, int32_t *fl,
+                  int32_t *fh, uint32_t *frec, uint32_t *fcnt, int32_t *ctr, int n_recs, int64_t *foff) {
+    const int64_t C = ctr[0];
+    const int64_t per = (C + blockDim.x - 1) / blockDim.x;
+    const int64_t i0 = min(C, (int64_t)threadIdx.x * per), i1 = min(C, i0 + per);
+    int64_t cnt = 0;
+    for (int64_t i = i0; i < i1; ++i)
+        if (counts[i] > thr[crec[i]]) ++cnt;
+    int64_t total = 0;
+    int64_t o = block_excl_scan(cnt, &total);
+    for (int64_t i = i0; i < i1; ++i) {
+        const uint32_t r = crec[i];
+        if (!(counts[i] > thr[r])) continue;
+        if (o < cap) {
+            for (int k = 0; k < N; ++k) ft[o * N + k] = ct[i * N + k];
+            for (int k = 0; k < N - 1; ++k) {
+                fl[o * (N - 1) + k] = cl[i * (N - 1) + k];
+                fh[o * (N - 1) + k] = ch[i * (N - 1) + k];
+            }
+            frec[o] = r;
+            fcnt[o] = counts[i];
+        }
+        ++o;
+    }
+    const int64_t F = total < cap ? total : cap;
+    if (threadIdx.x == 0) {
+        ctr[1] = (int32_t)F;
+        if (total > cap) atomicOr(&ctr[2], kFlagFreq);
+    }
+    __syncthreads();  // frec complete
+    for (int r = threadIdx.x; r <= n_recs; r += blockDim.x) {
+        int64_t lo = 0, hi = F;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int)frec[mid] < r) lo = mid + 1; else hi = mid;
+        }
+        foff[r] = lo;
     }
 }
 
 // Every node's ring must fit R_cap entries (window density + 1).  Also sums
 // the candidates' relevant events (sum over nodes of the node type's
 // frequency in the candidate's recording) into *rel.
+// It also writes the level's segment boundaries: every sstep[r]-th of the
+// recording's finest ones.
 __global__ void k_g_ringcheck(const uint16_t *ct, const int32_t *cl, const uint32_t *crec, const int32_t *ctr, int N,
                               const uint32_t *const *dens, const int32_t *lo_vals, int n_lo, int R_cap,
-                              const RecInfo *ri, int32_t *ctr_w, unsigned long long *rel) {
+                              const RecInfo *ri, int32_t *ctr_w, unsigned long long *rel, int n_recs,
+                              const int64_t *segf, const int32_t *pfine, const int32_t *sstep, int64_t *segl) {
+    const int64_t gt0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < n_recs; ++r) {
+        const int P = ri[r].P, st = sstep[r], pf = pfine[r];
+        const int64_t *f = segf + (size_t)r * (kMaxPerRec + 1);
+        int64_t *o = segl + (size_t)r * (kMaxPerRec + 1);
+        for (int64_t p = gt0; p <= P; p += gs) o[p] = f[min((int)p * st, pf)];
+    }
     const int64_t C = ctr[0];
     unsigned long long acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x) {
@@ -529,10 +721,23 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     const int64_t tot1 = ntpre[n_recs];
     const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
     if ((size_t)g->cap_threads * kRecWords * 4 > free_b / 4) return FEM_ERR_NOMEM;
-    // pre-pass launch shape (a per-thread bitset of n_types x bins bits)
+    // pre-pass launch shape: the bin-mask table (when hi_max < kUbLut), the
+    // staged events and a per-thread bitset of n_types x bins bits
     const int ub_words = (int)((nt_max * (uint32_t)std::max(nb, 1) + 31) / 32);
-    int ub_threads = std::max(32, std::min(256, (int)(48 * 1024 / (4 * ub_words)) / 32 * 32));
-    if ((size_t)ub_threads * ub_words * 4 > 48 * 1024) g->prepass = false;
+    const bool ub_lut = hi_max < kUbLut;
+    const size_t ub_lut_bytes = ub_lut ? (size_t)((hi_max + 4) / 4) * 4 : 0;
+    const size_t ub_stage = (size_t)(kUbTile + kUbHalo) * 4 + (size_t)(kUbTile + kUbHalo) / 2 * 4;
+    const int64_t ub_room = (int64_t)ctx->smem_optin - 1024 - (int64_t)ub_lut_bytes - (int64_t)ub_stage;
+    const int ub_threads =
+        ub_room > 0 ? (int)std::min<int64_t>(256, ub_room / (4 * (int64_t)ub_words) / 32 * 32) : 0;
+    const size_t ub_smem = ub_lut_bytes + ub_stage + (size_t)std::max(ub_threads, 0) * ub_words * 4;
+    if (ub_threads < 32 || nb > kUbMaxBins) g->prepass = false;
+    std::vector<int64_t> tpre(n_recs + 1, 0);
+    for (int r = 0; r < n_recs; ++r) tpre[r + 1] = tpre[r] + (g->recs[r]->n + kUbTile - 1) / kUbTile;
+    std::vector<uint8_t> lut_h(ub_lut ? (size_t)((hi_max + 4) / 4) * 4 : 0, 0);
+    for (int32_t d = 0; ub_lut && d <= hi_max; ++d)
+        for (int k = 0; k < nb; ++k)
+            if (blo[k] < d && d <= bhi[k]) lut_h[d] |= (uint8_t)(1u << k);
 
     RecInfo *d_ri;
     const uint32_t **d_dens;
@@ -580,7 +785,8 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_TRY(g->get(&f.foff, n_recs + 1));
     }
     // level-1 / level-2 inputs
-    int64_t *d_ntpre = nullptr, *d_evpre = nullptr, *d_uboff = nullptr;
+    int64_t *d_ntpre = nullptr, *d_evpre = nullptr, *d_uboff = nullptr, *d_tpre = nullptr;
+    uint8_t *d_lut = nullptr;
     uint32_t *d_nt = nullptr, *ub = nullptr;
     uint16_t *gt = nullptr;
     int32_t *glo = nullptr, *ghi = nullptr;
@@ -590,6 +796,8 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_TRY(g->get(&d_evpre, n_recs + 1));
         FEM_TRY(g->get(&d_uboff, n_recs + 1));
         FEM_TRY(g->get(&d_nt, n_recs));
+        FEM_TRY(g->get(&d_tpre, n_recs + 1));
+        if (ub_lut) FEM_TRY(g->get(&d_lut, lut_h.size()));
         FEM_TRY(g->get(&gt, (size_t)2 * std::max<int64_t>(cap2, 1)));
         FEM_TRY(g->get(&glo, std::max<int64_t>(cap2, 1)));
         FEM_TRY(g->get(&ghi, std::max<int64_t>(cap2, 1)));
@@ -599,6 +807,8 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_CUDA_TRY(cudaMemcpyAsync(d_evpre, evpre.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
         FEM_CUDA_TRY(cudaMemcpyAsync(d_uboff, ub_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
         FEM_CUDA_TRY(cudaMemcpyAsync(d_nt, nt_h.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_tpre, tpre.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+        if (ub_lut) FEM_CUDA_TRY(cudaMemcpyAsync(d_lut, lut_h.data(), lut_h.size(), cudaMemcpyHostToDevice, st));
     }
     FEM_CUDA_TRY(cudaMemcpyAsync(d_ri, ri_h.data(), sizeof(RecInfo) * n_recs, cudaMemcpyHostToDevice, st));
     FEM_CUDA_TRY(cudaMemcpyAsync(d_dens, dens_h.data(), sizeof(void *) * dens_h.size(), cudaMemcpyHostToDevice, st));
@@ -616,20 +826,32 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     const unsigned gb = (unsigned)std::min<int64_t>((cap + 256) / 256, 4 * ctx->n_sm);
     const unsigned gb2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap2 + 256) / 256, 8 * ctx->n_sm));
     const unsigned gb1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot1 + 256) / 256, 4 * ctx->n_sm));
-    const unsigned gbe = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>((evpre[n_recs] + ub_threads - 1) / ub_threads, 8 * ctx->n_sm));
+    const unsigned gbe = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tpre[n_recs], 8 * ctx->n_sm));
+    if (g->prepass && ub_smem > 48 * 1024) {
+        if (cudaFuncSetAttribute((const void *)k_g_pair_ub, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ub_smem) != cudaSuccess) {
+            cudaGetLastError();
+            g->prepass = false;
+        }
+    }
     cudaGraph_t graph = nullptr;
     FEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int cst = FEM_OK;
     auto ok = [&](cudaError_t e) {
         if (cst == FEM_OK && e != cudaSuccess) cst = FEM_ERR_CUDA;
     };
+    // levels whose candidate capacity keeps one block fast use the fused
+    // single-block join and threshold kernels
+    const bool fused = cap <= kFusedCap;
     for (int N = first; N <= L && cst == FEM_OK; ++N) {
         int32_t *cn = g->ctr + (size_t)N * kCtr;
         int64_t *coffN = g->coff + (size_t)N * (n_recs + 1);
         FLevel &nf = g->F[N];
-        ok(cudaMemsetAsync(cn, 0, sizeof(int32_t) * kCtr, st));
-        ok(cudaMemsetAsync(g->rel + N, 0, sizeof(unsigned long long), st));
+        const bool fuse_join = fused && N >= 3;
+        if (!fuse_join) {
+            ok(cudaMemsetAsync(cn, 0, sizeof(int32_t) * kCtr, st));
+            ok(cudaMemsetAsync(g->rel + N, 0, sizeof(unsigned long long), st));
+        }
         if (N == 1) {
             k_g_l1_flags<<<gb1, 256, 0, st>>>(d_ri, g->d_thr, d_ntpre, n_recs, tot1, pos);
             if (cst == FEM_OK) cst = scan_exclusive(st, pos, tot1 + 1, scan_tmp, nullptr, nullptr);
@@ -647,8 +869,8 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                                           grec);
             if (g->prepass) {
                 ok(cudaMemsetAsync(ub, 0, sizeof(uint32_t) * std::max<int64_t>(ub_off[n_recs], 1), st));
-                k_g_pair_ub<<<gbe, ub_threads, (size_t)ub_threads * ub_words * 4, st>>>(
-                    d_ri, d_evpre, n_recs, d_nt, d_uboff, d_blo, d_bhi, nb, hi_max, ub_words, ub);
+                k_g_pair_ub<<<gbe, ub_threads, ub_smem, st>>>(d_ri, d_tpre, n_recs, d_nt, d_uboff, d_blo, d_bhi, nb,
+                                                              hi_max, ub_words, d_lut, ub);
             }
             const uint32_t *ubp = g->prepass ? ub : nullptr;
             k_g_prune_flags<<<gb2, 256, 0, st>>>(gt, glo, ghi, grec, cn, cap2, ubp, d_uboff, d_nt, d_blo, d_bhi, nb,
@@ -656,20 +878,27 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap2 + 1, scan_tmp, nullptr, nullptr);
             k_g_prune_write<<<gb2, 256, 0, st>>>(pos, gt, glo, ghi, grec, cap2, ubp, d_uboff, d_nt, d_blo, d_bhi, nb,
                                                  g->d_thr, cap, ct, cl, ch, crec, cn);
+            k_g_levelinfo<<<1, 256, 0, st>>>(crec, cn, N, cap, offs, iota, n_recs, coffN, d_ri, nthreads, g->pfine,
+                                             g->sstep, g->target);
         } else {
             const int M = N - 1;
             const FLevel &pf = g->F[M];
             int32_t *cp = g->ctr + (size_t)M * kCtr;  // previous level's counters
-            k_g_join_count<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos);
-            if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
-            k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl, ch,
-                                               crec, cn);
+            if (fuse_join) {
+                k_g_join_fused<<<1, 1024, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, ct, cl, ch,
+                                                   crec, cn, g->rel + N, offs, iota, n_recs, coffN, d_ri, nthreads,
+                                                   g->pfine, g->sstep, g->target);
+            } else {
+                k_g_join_count<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos);
+                if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
+                k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl,
+                                                   ch, crec, cn);
+                k_g_levelinfo<<<1, 256, 0, st>>>(crec, cn, N, cap, offs, iota, n_recs, coffN, d_ri, nthreads,
+                                                 g->pfine, g->sstep, g->target);
+            }
         }
-        k_g_index<<<gb, 256, 0, st>>>(cn, N, cap, offs, iota);
-        k_g_recinfo<<<1, 256, 0, st>>>(crec, cn, n_recs, coffN, d_ri, nthreads, g->segf, g->pfine, g->sstep, g->segl,
-                                       g->target);
         k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), g->ring_cap, d_ri,
-                                          cn, g->rel + N);
+                                          cn, g->rel + N, n_recs, g->segf, g->pfine, g->sstep, g->segl);
         // external event nodes: their timestamps time the count kernels of
         // this level on every launch of the graph
         ok(cudaEventRecordWithFlags(g->ev[2 * N], st, cudaEventRecordExternal));
@@ -678,11 +907,16 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                                    iota, crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov,
                                    (int)lo_vals.size());
         ok(cudaEventRecordWithFlags(g->ev[2 * N + 1], st, cudaEventRecordExternal));
-        k_g_thr_flags<<<gb, 256, 0, st>>>(counts, crec, g->d_thr, cn, cap, pos);
-        if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
-        k_g_thr_write<<<gb, 256, 0, st>>>(pos, counts, ct, cl, ch, crec, g->d_thr, N, cap, nf.types, nf.lo, nf.hi,
-                                          nf.rec, nf.counts, cn);
-        k_g_foff<<<1, 256, 0, st>>>(nf.rec, cn, n_recs, nf.foff);
+        if (fused) {
+            k_g_thr_fused<<<1, 1024, 0, st>>>(counts, ct, cl, ch, crec, g->d_thr, N, cap, nf.types, nf.lo, nf.hi,
+                                              nf.rec, nf.counts, cn, n_recs, nf.foff);
+        } else {
+            k_g_thr_flags<<<gb, 256, 0, st>>>(counts, crec, g->d_thr, cn, cap, pos);
+            if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
+            k_g_thr_write<<<gb, 256, 0, st>>>(pos, counts, ct, cl, ch, crec, g->d_thr, N, cap, nf.types, nf.lo,
+                                              nf.hi, nf.rec, nf.counts, cn);
+            k_g_foff<<<1, 256, 0, st>>>(nf.rec, cn, n_recs, nf.foff);
+        }
         ok(cudaGetLastError());
     }
     const cudaError_t ce = cudaStreamEndCapture(st, &graph);

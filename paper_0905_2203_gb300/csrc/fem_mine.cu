@@ -150,15 +150,17 @@ __global__ void k_perm2_write(const int32_t *pos, const int64_t *f_off, const in
 //                                            bin's window }.
 // One pass over the stream: every event j looks back over the widest bin
 // window and marks, per bin, which types occur (a per-thread bitset in shared
-// memory dedupes repeated types), then adds one to UB(a, type_j, bin) for
-// every marked (a, bin).  The table is per recording: ub[rec][a][b][bin].
+// memory dedupes repeated types; word w of thread t at bits[w * blockDim + t]
+// so a warp's lanes touch distinct banks), then adds one to UB(a, type_j,
+// bin) for every marked (a, bin).  The table is per recording: ub[a][b][bin].
 __global__ void k_pair_ub(const uint16_t *__restrict__ ty, const int32_t *__restrict__ tm, int64_t n,
                           uint32_t n_types, const int32_t *__restrict__ blo, const int32_t *__restrict__ bhi, int nb,
                           int32_t hi_max, int words, uint32_t *__restrict__ ub) {
     extern __shared__ uint32_t bits[];
-    uint32_t *my = bits + threadIdx.x * words;
+    uint32_t *my = bits + threadIdx.x;
+    const int bd = blockDim.x;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        for (int w = 0; w < words; ++w) my[w] = 0;
+        for (int w = 0; w < words; ++w) my[w * bd] = 0;
         const int32_t t = tm[j];
         const uint32_t b = ty[j];
         const int64_t lim = (int64_t)t - hi_max;
@@ -171,8 +173,9 @@ __global__ void k_pair_ub(const uint16_t *__restrict__ ty, const int32_t *__rest
                 if (blo[k] < d && d <= bhi[k]) {
                     const uint32_t bit = a * (uint32_t)nb + (uint32_t)k;
                     const uint32_t m = 1u << (bit & 31);
-                    if (!(my[bit >> 5] & m)) {
-                        my[bit >> 5] |= m;
+                    uint32_t &wd = my[(bit >> 5) * bd];
+                    if (!(wd & m)) {
+                        wd |= m;
                         atomicAdd(&ub[((size_t)a * n_types + b) * nb + k], 1u);
                     }
                 }
