@@ -1522,19 +1522,31 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
                     if (j < N && E[j] == E[k]) m |= 1u << j;
                 nodes[k] = m;
                 const int64_t b0 = ri.toff[E[k]], b1 = ri.toff[E[k] + 1];
-                int64_t lo_i = b0, hi_i = b1;
-                while (lo_i < hi_i) {
-                    const int64_t mid = (lo_i + hi_i) >> 1;
-                    if ((int64_t)ri.ttime[mid] < haloT) lo_i = mid + 1; else hi_i = mid;
-                }
-                int64_t e_i = b1;
-                if (seg_e < ri.n) {
-                    int64_t l2 = lo_i, h2 = b1;
-                    while (l2 < h2) {
-                        const int64_t mid = (l2 + h2) >> 1;
-                        if (ri.ttime[mid] < Tend) l2 = mid + 1; else h2 = mid;
+                int64_t lo_i, e_i;
+                if (ri.tseg) {
+                    // list positions of the segment's boundaries from the
+                    // table, then back over the halo's few events
+                    const int32_t *tq = ri.tseg + (size_t)E[k] * ri.tstride;
+                    const int qmax = ri.tstride - 1;
+                    lo_i = b0 + tq[min(p * ri.sstep, qmax)];
+                    e_i = b0 + tq[min((p + 1) * ri.sstep, qmax)];
+                    while (lo_i > b0 && (int64_t)ri.ttime[lo_i - 1] >= haloT) --lo_i;
+                } else {
+                    lo_i = b0;
+                    int64_t hi_i = b1;
+                    while (lo_i < hi_i) {
+                        const int64_t mid = (lo_i + hi_i) >> 1;
+                        if ((int64_t)ri.ttime[mid] < haloT) lo_i = mid + 1; else hi_i = mid;
                     }
-                    e_i = l2;
+                    e_i = b1;
+                    if (seg_e < ri.n) {
+                        int64_t l2 = lo_i, h2 = b1;
+                        while (l2 < h2) {
+                            const int64_t mid = (l2 + h2) >> 1;
+                            if (ri.ttime[mid] < Tend) l2 = mid + 1; else h2 = mid;
+                        }
+                        e_i = l2;
+                    }
                 }
                 cur[k] = (int32_t)lo_i;
                 end[k] = (int32_t)e_i;

@@ -52,6 +52,29 @@ __device__ __forceinline__ int seg_of(const int64_t *pre, int n, int64_t i) {
     return lo;
 }
 
+// For every type a of one recording and finest segment boundary q (pf + 1
+// of them; the last is the recording's end): the index, relative to the
+// start of a's event list, of a's first event at or after the boundary.
+__global__ void k_g_tseg(const int64_t *toff, const int32_t *ttime, const int32_t *time, int64_t n,
+                         const int64_t *segf, int pf, uint32_t n_types, int32_t *tseg) {
+    const int64_t m = (int64_t)n_types * (pf + 1);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < m; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = idx / (pf + 1), q = idx % (pf + 1);
+        const int64_t b0 = toff[a], b1 = toff[a + 1];
+        int64_t v = b1 - b0;
+        if (q < pf && segf[q] < n) {
+            const int32_t T = time[segf[q]];
+            int64_t lo = b0, hi = b1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (ttime[mid] < T) lo = mid + 1; else hi = mid;
+            }
+            v = lo - b0;
+        }
+        tseg[idx] = (int32_t)v;
+    }
+}
+
 // ---- level 1 ---------------------------------------------------------------
 // Frequent types of every recording, in type order: flags over the
 // concatenated type ranges (ntpre = prefix of n_types), then write.
@@ -393,6 +416,7 @@ __device__ void level_info(const uint32_t *crec, int64_t C, int n_recs, int64_t 
             const int st = (pf + (int)want - 1) / (int)want;
             const int P = (pf + st - 1) / st;
             sstep[r] = st;
+            ri[r].sstep = st;
             ri[r].P = P;
             ri[r].slot_first = (int)coff[r];
             ri[r].recbase = base;
@@ -677,8 +701,15 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         const int P = (int)std::max(1.0, std::min<double>(kMaxPerRec, (double)s->n / min_seg));
         pfine_h[r] = P;
         FEM_TRY(launch_segments(st, s->d_time, s->n, P, segs + (size_t)r * (kMaxPerRec + 1)));
+        // list positions of the finest boundaries, per type
+        int32_t *tseg = nullptr;
+        FEM_TRY(g->get(&tseg, (size_t)s->n_types * (P + 1)));
+        const int64_t tm = (int64_t)s->n_types * (P + 1);
+        k_g_tseg<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((tm + 255) / 256, 4 * ctx->n_sm)), 256, 0, st>>>(
+            s->d_toff, s->d_ttime, s->d_time, s->n, segs + (size_t)r * (kMaxPerRec + 1), P, s->n_types, tseg);
+        FEM_CUDA_TRY(cudaGetLastError());
         ri_h[r] = RecInfo{s->d_type, s->d_time, s->n, g->segl + (size_t)r * (kMaxPerRec + 1), 1, 0, 0,
-                          s->d_freq, s->d_toff, s->d_ttime};
+                          s->d_freq, s->d_toff, s->d_ttime, tseg, P + 1, 1};
     }
     FEM_CUDA_TRY(cudaMemcpyAsync(g->pfine, pfine_h.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
     g->segf = segs;

@@ -57,6 +57,13 @@ struct RecInfo {
     const uint32_t *freq;
     const int64_t *toff;  // per-type event lists (sparse kernel only)
     const int32_t *ttime;
+    // Optional (null elsewhere): for every type a and finest segment boundary
+    // q, the index in a's list of its first event at or after the boundary,
+    // tseg[a * tstride + q]; segment p of this launch starts at finest
+    // boundary p * sstep (capped at tstride - 1, the end of the recording).
+    const int32_t *tseg;
+    int tstride;
+    int sstep;
 };
 
 // Results of the levels of level-wise mining run in a captured graph.
