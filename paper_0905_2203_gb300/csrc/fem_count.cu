@@ -753,13 +753,13 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
     }
 }
 
-// One block per episode, for episodes with more than min_P segments: 256
+// One block per episode, for episodes with more than min_P segments: 512
 // lanes compose their runs, each warp composes its lanes' maps, and the
-// eight warp maps (shared memory) are applied in order.
-constexpr int kStitchBlock = 256;
+// sixteen warp maps (shared memory) are applied in order.
+constexpr int kStitchBlock = 512;
 constexpr int kStitchSplit = 256;  // episodes with more segments take a block
 
-__global__ void __launch_bounds__(kStitchBlock)
+__global__ void __launch_bounds__(kStitchBlock, 1)
     k_stitch_block(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
                    const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
                    int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
