@@ -84,27 +84,72 @@ static bool tune_parse(const std::string &text, std::map<std::string, TuneVal> *
     return true;
 }
 
+// Device allocations go through a per-context cache of freed blocks: a
+// request takes the smallest cached block of at least its size (and at most
+// 1.25x + 64 KB of it), else cudaMalloc; a free parks the block in the cache
+// while the cache stays below a quarter of the budget (at most 8 GB).  A
+// failed cudaMalloc releases the cache and retries once.  `used` counts the
+// blocks in use against the context's budget.
+static size_t pool_limit(const fem_ctx *ctx) { return std::min<size_t>(ctx->budget / 4, (size_t)8 << 30); }
+
+void pool_release(fem_ctx *ctx) {
+    std::lock_guard<std::mutex> g(ctx->pool_mu);
+    for (auto &kv : ctx->cached) cudaFree(kv.second);
+    ctx->cached.clear();
+    ctx->cached_bytes = 0;
+}
+
 int dev_alloc(fem_ctx *ctx, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~size_t(255);
     if (ctx->used.load() + bytes > ctx->budget) return FEM_ERR_NOMEM;
+    {
+        std::lock_guard<std::mutex> g(ctx->pool_mu);
+        auto it = ctx->cached.lower_bound(bytes);
+        if (it != ctx->cached.end() && it->first <= bytes + bytes / 4 + (64 << 10)) {
+            *p = it->second;
+            const size_t sz = it->first;
+            ctx->cached_bytes -= sz;
+            ctx->cached.erase(it);
+            ctx->live[*p] = sz;
+            ctx->used += sz;
+            return FEM_OK;
+        }
+    }
     cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        pool_release(ctx);
+        e = cudaMalloc(p, bytes);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return e == cudaErrorMemoryAllocation ? FEM_ERR_NOMEM : FEM_ERR_CUDA;
     }
+    std::lock_guard<std::mutex> g(ctx->pool_mu);
+    ctx->live[*p] = bytes;
     ctx->used += bytes;
     return FEM_OK;
 }
 
 void dev_free(fem_ctx *ctx, void *p, size_t bytes) {
     if (!p) return;
-    if (bytes == 0) bytes = 16;
-    bytes = (bytes + 255) & ~size_t(255);
-    cudaFree(p);
-    ctx->used -= bytes;
+    std::lock_guard<std::mutex> g(ctx->pool_mu);
+    auto it = ctx->live.find(p);
+    size_t sz = (bytes == 0 ? 16 : (bytes + 255) & ~size_t(255));
+    if (it != ctx->live.end()) {
+        sz = it->second;
+        ctx->live.erase(it);
+    }
+    ctx->used -= sz;
+    if (ctx->cached_bytes + sz <= pool_limit(ctx)) {
+        ctx->cached.emplace(sz, p);
+        ctx->cached_bytes += sz;
+    } else {
+        cudaFree(p);
+    }
 }
 
 int scratch(fem_ctx *ctx, int slot, size_t bytes, void **p) {
@@ -244,6 +289,98 @@ __global__ void k_density_resolve(uint32_t *dens, const uint32_t *freq, uint32_t
         if (dens[a] == kDensUnknown) dens[a] = freq[a];
 }
 
+// Window densities for up to kDensLo lower bounds at once, from the per-type
+// lists: event i of type a sees the type-a events in [t_i - lo, t_i] by
+// scanning back over a's list only; dens[j][a] = the largest such number
+// (kDensUnknown after `cap` steps).
+constexpr int kDensLo = 8;
+
+__global__ void k_density_lists(const int64_t *__restrict__ toff, const int32_t *__restrict__ ttime,
+                                uint32_t n_types, int64_t n, const int32_t *__restrict__ los, int n_lo, int cap,
+                                uint32_t *const *dens) {
+    int32_t lo_v[kDensLo];
+#pragma unroll
+    for (int k = 0; k < kDensLo; ++k) lo_v[k] = k < n_lo ? los[k] : 0;
+    int32_t lo_max = 0;
+#pragma unroll
+    for (int k = 0; k < kDensLo; ++k) lo_max = max(lo_max, lo_v[k]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = (int)n_types;  // type a: toff[a] <= i < toff[a + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (toff[mid] <= i) lo = mid; else hi = mid;
+        }
+        const int a = lo;
+        const int64_t b0 = toff[a];
+        const int64_t t = ttime[i];
+        uint32_t c[kDensLo];
+#pragma unroll
+        for (int k = 0; k < kDensLo; ++k) c[k] = 1;
+        int64_t j = i - 1;
+        int steps = 0;
+        for (; j >= b0 && (int64_t)ttime[j] >= t - lo_max && steps < cap; --j, ++steps) {
+#pragma unroll
+            for (int k = 0; k < kDensLo; ++k)
+                if ((int64_t)ttime[j] >= t - lo_v[k]) c[k] += 1;
+        }
+        const bool more = j >= b0;
+#pragma unroll
+        for (int k = 0; k < kDensLo; ++k) {
+            if (k >= n_lo) break;
+            const bool unknown = more && (int64_t)ttime[j] >= t - lo_v[k];
+            atomicMax(&dens[k][a], unknown ? kDensUnknown : c[k]);
+        }
+    }
+}
+
+int stream_densities(fem_ctx *ctx, fem_stream *s, const std::vector<int32_t> &los) {
+    std::vector<int32_t> miss;
+    for (int32_t l : los)
+        if (!s->dens.count(l) && std::find(miss.begin(), miss.end(), l) == miss.end()) miss.push_back(l);
+    if (miss.empty() || s->n == 0) return FEM_OK;
+    if (stream_bytype(ctx, s) != FEM_OK) return FEM_OK;  // stream_density computes them one by one
+    for (size_t g0 = 0; g0 < miss.size(); g0 += kDensLo) {
+        const int m = (int)std::min<size_t>(kDensLo, miss.size() - g0);
+        std::vector<uint32_t *> outs(m, nullptr);
+        for (int k = 0; k < m; ++k) {
+            void *p = nullptr;
+            const int st = dev_alloc(ctx, &p, sizeof(uint32_t) * s->n_types);
+            if (st != FEM_OK) {
+                for (int q = 0; q < k; ++q) dev_free(ctx, outs[q], sizeof(uint32_t) * s->n_types);
+                return st;
+            }
+            outs[k] = static_cast<uint32_t *>(p);
+            FEM_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(uint32_t) * s->n_types, ctx->stream));
+        }
+        struct {
+            int32_t lo[kDensLo];
+            uint32_t *d[kDensLo];
+        } hb{};
+        for (int k = 0; k < m; ++k) {
+            hb.lo[k] = miss[g0 + k];
+            hb.d[k] = outs[k];
+        }
+        void *pb = nullptr;
+        FEM_TRY(scratch(ctx, kSlotDensArgs, sizeof(hb), &pb));
+        FEM_CUDA_TRY(cudaMemcpyAsync(pb, &hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream));
+        const auto *db = static_cast<const char *>(pb);
+        k_density_lists<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((s->n + 255) / 256, 8 * ctx->n_sm)), 256,
+                          0, ctx->stream>>>(s->d_toff, s->d_ttime, s->n_types, s->n,
+                                            reinterpret_cast<const int32_t *>(db),
+                                            m, 4096, reinterpret_cast<uint32_t *const *>(db + sizeof(hb.lo)));
+        for (int k = 0; k < m; ++k)
+            k_density_resolve<<<(s->n_types + 255) / 256, 256, 0, ctx->stream>>>(outs[k], s->d_freq, s->n_types);
+        FEM_CUDA_TRY(cudaGetLastError());
+        // the argument block is reused by the next group: wait for this one
+        if (g0 + kDensLo < miss.size()) FEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        for (int k = 0; k < m; ++k) {
+            s->dens[miss[g0 + k]] = outs[k];
+            s->bytes += sizeof(uint32_t) * s->n_types;
+        }
+    }
+    return FEM_OK;
+}
+
 int stream_density(fem_ctx *ctx, fem_stream *s, int32_t lo, uint32_t **d_dens) {
     auto it = s->dens.find(lo);
     if (it != s->dens.end()) {
@@ -340,6 +477,9 @@ extern "C" void fem_ctx_destroy(fem_ctx *ctx) {
     for (auto &kv : ctx->scratch) dev_free(ctx, kv.second.p, kv.second.cap);
     ctx->scratch.clear();
     dev_free(ctx, ctx->d_status, sizeof(int) * 4);
+    pool_release(ctx);
+    for (auto &kv : ctx->live) cudaFree(kv.first);
+    ctx->live.clear();
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);

@@ -1942,6 +1942,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     std::vector<uint32_t> nt_h(n_recs);
     for (int r = 0; r < n_recs; ++r) {
         nt_h[r] = cc.recs[r]->n_types;
+        FEM_TRY(stream_densities(ctx, cc.recs[r], lov));
         for (size_t j = 0; j < lov.size(); ++j) {
             uint32_t *d = nullptr;
             FEM_TRY(stream_density(ctx, cc.recs[r], lov[j], &d));

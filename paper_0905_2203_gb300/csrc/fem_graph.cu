@@ -688,6 +688,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     for (int r = 0; r < n_recs; ++r) {
         fem_stream *s = g->recs[r];
         FEM_TRY(stream_bytype(ctx, s));
+        FEM_TRY(stream_densities(ctx, s, lo_vals));
         for (size_t j = 0; j < lo_vals.size(); ++j) {
             uint32_t *d = nullptr;
             FEM_TRY(stream_density(ctx, s, lo_vals[j], &d));

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <map>
+#include <unordered_map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -114,6 +115,14 @@ struct fem_ctx {
     std::map<std::string, fem::GraphTail *> graphs;  // captured mining graphs
     std::map<std::string, int64_t> graph_cap;        // candidate capacity a graph key needed last time
     std::string tune_path;                     // JSON file backing the cache ("" = memory only)
+    // Allocation cache: freed device blocks kept for reuse (all of a
+    // context's work is ordered on its stream, so a block freed after its
+    // last use there can serve the next allocation).  `live` maps a block
+    // in use to its size; `cached` holds free blocks by size.
+    std::mutex pool_mu;
+    std::unordered_map<void *, size_t> live;
+    std::multimap<size_t, void *> cached;
+    size_t cached_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -164,12 +173,18 @@ int stream_segments(fem_ctx *ctx, fem_stream *s, int P, const int64_t **seg);
 int stream_bytype(fem_ctx *ctx, fem_stream *s);
 // Density table for one lo (computed on first use, cached in the stream).
 int stream_density(fem_ctx *ctx, fem_stream *s, int32_t lo, uint32_t **d_dens);
+// Densities for several lower bounds in one pass over the per-type lists
+// (cached like stream_density; falls back to it when the lists cannot be
+// built).
+int stream_densities(fem_ctx *ctx, fem_stream *s, const std::vector<int32_t> &los);
+// Returns every cached free block to the driver.
+void pool_release(fem_ctx *ctx);
 
 // Scratch slot ids.
 enum Slot : int {
     kSlotCandOffs = 1, kSlotCandTypes, kSlotCandLo, kSlotCandHi, kSlotCandRec,
     kSlotPrep, kSlotPerm, kSlotBucket, kSlotRecords, kSlotSeg, kSlotCounts,
-    kSlotFallback, kSlotRings, kSlotDensTab, kSlotScanTmp, kSlotMisc, kSlotRecTab,
+    kSlotFallback, kSlotRings, kSlotDensTab, kSlotScanTmp, kSlotMisc, kSlotRecTab, kSlotDensArgs,
     kSlotMine0 = 64,
 };
 
