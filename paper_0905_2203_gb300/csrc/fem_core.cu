@@ -292,8 +292,11 @@ __global__ void k_density_resolve(uint32_t *dens, const uint32_t *freq, uint32_t
 // Window densities for up to kDensLo lower bounds at once, from the per-type
 // lists: event i of type a sees the type-a events in [t_i - lo, t_i] by
 // scanning back over a's list only; dens[j][a] = the largest such number
-// (kDensUnknown after `cap` steps).
+// (kDensUnknown after `cap` steps).  Each thread walks a run of kDensRun
+// consecutive list positions (mostly one type) and writes its running
+// maxima only when the type changes, so a type's counter sees few atomics.
 constexpr int kDensLo = 8;
+constexpr int kDensRun = 16;
 
 __global__ void k_density_lists(const int64_t *__restrict__ toff, const int32_t *__restrict__ ttime,
                                 uint32_t n_types, int64_t n, const int32_t *__restrict__ los, int n_lo, int cap,
@@ -304,32 +307,50 @@ __global__ void k_density_lists(const int64_t *__restrict__ toff, const int32_t 
     int32_t lo_max = 0;
 #pragma unroll
     for (int k = 0; k < kDensLo; ++k) lo_max = max(lo_max, lo_v[k]);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = (int)n_types;  // type a: toff[a] <= i < toff[a + 1]
+    const int64_t runs = (n + kDensRun - 1) / kDensRun;
+    for (int64_t run = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; run < runs;
+         run += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = run * kDensRun, i1 = min(n, i0 + kDensRun);
+        int lo = 0, hi = (int)n_types;  // type of position i0: toff[a] <= i0 < toff[a + 1]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (toff[mid] <= i) lo = mid; else hi = mid;
+            if (toff[mid] <= i0) lo = mid; else hi = mid;
         }
-        const int a = lo;
-        const int64_t b0 = toff[a];
-        const int64_t t = ttime[i];
-        uint32_t c[kDensLo];
+        int a = lo;
+        int64_t b0 = toff[a], b1 = toff[a + 1];
+        uint32_t best[kDensLo];
 #pragma unroll
-        for (int k = 0; k < kDensLo; ++k) c[k] = 1;
-        int64_t j = i - 1;
-        int steps = 0;
-        for (; j >= b0 && (int64_t)ttime[j] >= t - lo_max && steps < cap; --j, ++steps) {
+        for (int k = 0; k < kDensLo; ++k) best[k] = 0;
+        for (int64_t i = i0; i < i1; ++i) {
+            while (i >= b1) {  // next type: write this one's maxima
 #pragma unroll
-            for (int k = 0; k < kDensLo; ++k)
-                if ((int64_t)ttime[j] >= t - lo_v[k]) c[k] += 1;
+                for (int k = 0; k < kDensLo; ++k)
+                    if (k < n_lo && best[k]) atomicMax(&dens[k][a], best[k]), best[k] = 0;
+                ++a;
+                b0 = b1;
+                b1 = toff[a + 1];
+            }
+            const int64_t t = ttime[i];
+            uint32_t c[kDensLo];
+#pragma unroll
+            for (int k = 0; k < kDensLo; ++k) c[k] = 1;
+            int64_t j = i - 1;
+            int steps = 0;
+            for (; j >= b0 && (int64_t)ttime[j] >= t - lo_max && steps < cap; --j, ++steps) {
+#pragma unroll
+                for (int k = 0; k < kDensLo; ++k)
+                    if ((int64_t)ttime[j] >= t - lo_v[k]) c[k] += 1;
+            }
+            const bool more = j >= b0;
+#pragma unroll
+            for (int k = 0; k < kDensLo; ++k) {
+                const bool unknown = more && (int64_t)ttime[j] >= t - lo_v[k];
+                best[k] = max(best[k], unknown ? kDensUnknown : c[k]);
+            }
         }
-        const bool more = j >= b0;
 #pragma unroll
-        for (int k = 0; k < kDensLo; ++k) {
-            if (k >= n_lo) break;
-            const bool unknown = more && (int64_t)ttime[j] >= t - lo_v[k];
-            atomicMax(&dens[k][a], unknown ? kDensUnknown : c[k]);
-        }
+        for (int k = 0; k < kDensLo; ++k)
+            if (k < n_lo && best[k]) atomicMax(&dens[k][a], best[k]);
     }
 }
 
@@ -364,7 +385,8 @@ int stream_densities(fem_ctx *ctx, fem_stream *s, const std::vector<int32_t> &lo
         FEM_TRY(scratch(ctx, kSlotDensArgs, sizeof(hb), &pb));
         FEM_CUDA_TRY(cudaMemcpyAsync(pb, &hb, sizeof(hb), cudaMemcpyHostToDevice, ctx->stream));
         const auto *db = static_cast<const char *>(pb);
-        k_density_lists<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((s->n + 255) / 256, 8 * ctx->n_sm)), 256,
+        const int64_t runs = (s->n + kDensRun - 1) / kDensRun;
+        k_density_lists<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((runs + 255) / 256, 8 * ctx->n_sm)), 256,
                           0, ctx->stream>>>(s->d_toff, s->d_ttime, s->n_types, s->n,
                                             reinterpret_cast<const int32_t *>(db),
                                             m, 4096, reinterpret_cast<uint32_t *const *>(db + sizeof(hb.lo)));
