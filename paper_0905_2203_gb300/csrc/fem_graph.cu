@@ -435,44 +435,58 @@ __global__ void k_g_levelinfo(const uint32_t *crec, const int32_t *ctr, int N, i
     level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target);
 }
 
-// Level N = M + 1 in one block: zero the level's counters, count each
-// frequent alpha's join partners, scan, write the candidates, then index and
-// segment the level (for levels whose capacity keeps one block fast).
+// Level N = M + 1 in one block: zero the level's counters, check every
+// (alpha, beta) pair of frequent (N-1)-episodes of the same recording for the
+// join (pairs numbered alpha-major, each thread a contiguous run of them),
+// scan, write the candidates in that order, then index and segment the level
+// (for levels whose capacity keeps one block fast; at most kFusedRecs
+// recordings).
+constexpr int kFusedRecs = 1024;
+
 __global__ void __launch_bounds__(1024, 1)
     k_g_join_fused(const uint16_t *ft, const int32_t *fl, const int32_t *fh, const uint32_t *frec,
                    const int64_t *foff, const int32_t *ctr_prev, int M, int64_t cap, uint16_t *ct, int32_t *cl,
                    int32_t *ch, uint32_t *crec, int32_t *ctr, unsigned long long *rel, int64_t *offs, int32_t *iota,
                    int n_recs, int64_t *coff, RecInfo *ri, int64_t *nthreads, const int32_t *pfine, int32_t *sstep,
                    int64_t target) {
+    __shared__ int64_t s_pp[kFusedRecs + 1];  // pair offsets per recording
     const int N = M + 1;
-    const int64_t F = ctr_prev[1];
-    const int64_t per = (F + blockDim.x - 1) / blockDim.x;
-    const int64_t a0 = min(F, (int64_t)threadIdx.x * per), a1 = min(F, a0 + per);
+    {
+        const int64_t Fr = threadIdx.x < n_recs ? foff[threadIdx.x + 1] - foff[threadIdx.x] : 0;
+        int64_t tot = 0;
+        const int64_t before = block_excl_scan(Fr * Fr, &tot);
+        if (threadIdx.x < n_recs) s_pp[threadIdx.x] = before;
+        if (threadIdx.x == 0) s_pp[n_recs] = tot;
+        __syncthreads();
+    }
+    const int64_t npairs = s_pp[n_recs];
+    const int64_t per = (npairs + blockDim.x - 1) / blockDim.x;
+    const int64_t p0 = min(npairs, (int64_t)threadIdx.x * per), p1 = min(npairs, p0 + per);
     int64_t cnt = 0;
-    for (int64_t a = a0; a < a1; ++a) {
-        const uint32_t r = frec[a];
-        for (int64_t b = foff[r]; b < foff[r + 1]; ++b)
-            if (g_joins(ft, fl, fh, M, a, b)) ++cnt;
+    for (int64_t q = p0; q < p1; ++q) {
+        const int r = seg_of(s_pp, n_recs, q);
+        const int64_t Fr = foff[r + 1] - foff[r], loc = q - s_pp[r];
+        if (g_joins(ft, fl, fh, M, foff[r] + loc / Fr, foff[r] + loc % Fr)) ++cnt;
     }
     int64_t total = 0;
     int64_t o = block_excl_scan(cnt, &total);
-    for (int64_t a = a0; a < a1; ++a) {
-        const uint32_t r = frec[a];
-        for (int64_t b = foff[r]; b < foff[r + 1]; ++b) {
-            if (!g_joins(ft, fl, fh, M, a, b)) continue;
-            if (o < cap) {
-                for (int k = 0; k < M; ++k) ct[o * N + k] = ft[a * M + k];
-                ct[o * N + M] = ft[b * M + M - 1];
-                for (int k = 0; k < M - 1; ++k) {
-                    cl[o * (N - 1) + k] = fl[a * (M - 1) + k];
-                    ch[o * (N - 1) + k] = fh[a * (M - 1) + k];
-                }
-                cl[o * (N - 1) + M - 1] = fl[b * (M - 1) + M - 2];
-                ch[o * (N - 1) + M - 1] = fh[b * (M - 1) + M - 2];
-                crec[o] = r;
+    for (int64_t q = p0; q < p1; ++q) {
+        const int r = seg_of(s_pp, n_recs, q);
+        const int64_t Fr = foff[r + 1] - foff[r], loc = q - s_pp[r];
+        const int64_t a = foff[r] + loc / Fr, b = foff[r] + loc % Fr;
+        if (!g_joins(ft, fl, fh, M, a, b)) continue;
+        if (o < cap) {
+            for (int k = 0; k < M; ++k) ct[o * N + k] = ft[a * M + k];
+            ct[o * N + M] = ft[b * M + M - 1];
+            for (int k = 0; k < M - 1; ++k) {
+                cl[o * (N - 1) + k] = fl[a * (M - 1) + k];
+                ch[o * (N - 1) + k] = fh[a * (M - 1) + k];
             }
-            ++o;
+            cl[o * (N - 1) + M - 1] = fl[b * (M - 1) + M - 2];
+            ch[o * (N - 1) + M - 1] = fh[b * (M - 1) + M - 2];
+            crec[o] = (uint32_t)r;
         }
+        ++o;
     }
     const int64_t C = total < cap ? total : cap;
     if (threadIdx.x == 0) {
@@ -874,7 +888,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     };
     // levels whose candidate capacity keeps one block fast use the fused
     // single-block join and threshold kernels
-    const bool fused = cap <= kFusedCap;
+    const bool fused = cap <= kFusedCap && n_recs <= kFusedRecs;
     for (int N = first; N <= L && cst == FEM_OK; ++N) {
         int32_t *cn = g->ctr + (size_t)N * kCtr;
         int64_t *coffN = g->coff + (size_t)N * (n_recs + 1);
