@@ -98,7 +98,10 @@ typedef struct {
                              shared-memory broadcast kernel, 2 = the sparse
                              per-type-list kernel where it applies, 3 = the
                              sparse kernel with per-node branching instead of
-                             its node-uniform variant (comparison) */
+                             its node-uniform variant (comparison), 4 = node-
+                             by-node local tracking over the per-type lists
+                             (section "Parallel Local Tracking": parallel
+                             over events, for few long episodes) */
     int level_graph;      /* mining: 0 = run the levels as one captured CUDA
                              graph where it applies (all levels when no
                              other override is set and every alphabet has at

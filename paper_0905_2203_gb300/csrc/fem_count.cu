@@ -1718,26 +1718,6 @@ __global__ void k_toff(const int32_t *__restrict__ keyoff, int n_types, int64_t 
 }
 
 // Temporary device allocations freed together (after the stream drains).
-struct TmpDev {
-    fem_ctx *ctx;
-    std::vector<std::pair<void *, size_t>> held;
-    explicit TmpDev(fem_ctx *c) : ctx(c) {}
-    ~TmpDev() {
-        if (held.empty()) return;
-        cudaStreamSynchronize(ctx->stream);
-        for (auto &h : held) dev_free(ctx, h.first, h.second);
-    }
-    template <typename T>
-    int get(T **p, size_t n) {
-        void *q = nullptr;
-        const size_t b = std::max<size_t>(n, 1) * sizeof(T);
-        FEM_TRY(dev_alloc(ctx, &q, b));
-        held.push_back({q, b});
-        *p = static_cast<T *>(q);
-        return FEM_OK;
-    }
-};
-
 int stream_bytype(fem_ctx *ctx, fem_stream *s) {
     if (s->d_ttime) return FEM_OK;
     if (s->n_types > 8192 || s->n > INT32_MAX / 2) return FEM_ERR_INVAL;
@@ -2503,6 +2483,19 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
 }
 
 static int run_count(CountCall &cc, const int32_t *subset, int64_t n_sub, int force_segments) {
+    // node-by-node local tracking (fem_plt.cu) when asked for
+    if (cc.mode != 1 && force_segments == 0 && cc.ctx->tuning.kernel == 4) {
+        std::vector<int32_t> work(n_sub);
+        if (subset) {
+            FEM_CUDA_TRY(cudaMemcpyAsync(work.data(), subset, 4 * n_sub, cudaMemcpyDeviceToHost, cc.ctx->stream));
+            FEM_CUDA_TRY(cudaStreamSynchronize(cc.ctx->stream));
+        } else {
+            for (int64_t i = 0; i < n_sub; ++i) work[i] = (int32_t)i;
+        }
+        FEM_TRY(count_plt(cc.ctx, cc.recs, cc.offs, cc.types, cc.lo, cc.hi, cc.cand_rec, work, cc.mode == 2,
+                          cc.counts, &cc.stats, &cc.count_ms));
+        return sync_status(cc.ctx);
+    }
     return count_core(cc, subset, n_sub, force_segments);
 }
 

@@ -180,6 +180,33 @@ int stream_densities(fem_ctx *ctx, fem_stream *s, const std::vector<int32_t> &lo
 // Returns every cached free block to the driver.
 void pool_release(fem_ctx *ctx);
 
+// Device buffers released together at scope exit (after the stream drains).
+struct TmpDev {
+    fem_ctx *ctx;
+    std::vector<std::pair<void *, size_t>> held;
+    explicit TmpDev(fem_ctx *c) : ctx(c) {}
+    ~TmpDev() {
+        if (held.empty()) return;
+        cudaStreamSynchronize(ctx->stream);
+        for (auto &h : held) dev_free(ctx, h.first, h.second);
+    }
+    template <typename T>
+    int get(T **p, size_t n) {
+        void *q = nullptr;
+        const size_t b = std::max<size_t>(n, 1) * sizeof(T);
+        FEM_TRY(dev_alloc(ctx, &q, b));
+        held.push_back({q, b});
+        *p = static_cast<T *>(q);
+        return FEM_OK;
+    }
+};
+
+// Counting by node-by-node local tracking (fem_plt.cu): the candidates
+// `work` of the device CSR arrays; relaxed = every lower bound taken as 0.
+int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t *d_offs, const uint16_t *d_types,
+              const int32_t *d_lo, const int32_t *d_hi, const uint32_t *d_rec, const std::vector<int32_t> &work,
+              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms);
+
 // Scratch slot ids.
 enum Slot : int {
     kSlotCandOffs = 1, kSlotCandTypes, kSlotCandLo, kSlotCandHi, kSlotCandRec,

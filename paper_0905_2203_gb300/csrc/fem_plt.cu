@@ -1,0 +1,325 @@
+// fem_plt.cu -- counting by node-by-node local tracking, for few episodes.
+//
+// Section "Parallel Local Tracking" (Algorithm 2) finds the occurrences of an
+// episode node by node, in parallel over the events of each node's type, and
+// "Problem decomposition" then removes overlaps with the greedy of
+// Algorithm 1.  Here the tracking keeps, per event of node k's type, only the
+// latest start of any partial occurrence of nodes 1..k ending at that event
+// (the greedy needs no other start), so one step per node does:
+//   for every event j of type E_{k+1} (one thread each):
+//     i* = last event of E_k with t_i < t_j - lo_k   (binary search in E_k's list)
+//     v  = newest E_k event at or before i* that ends a partial occurrence
+//          (an inclusive max-scan of valid positions over E_k's list)
+//     L_{k+1}(j) = L_k(v) when t_v >= t_j - hi_k, else none;
+// the latest start is non-decreasing along a node's valid events, so v
+// carries the largest start in the window.  After the last node, Algorithm 1
+// walks the end events in time order and keeps an end when its latest start
+// is after the previous kept end.  Work per episode is its node types' events
+// (times a logarithm), spread over all events, so a single long episode on a
+// long stream still fills the GPU -- the regime the section addresses.
+#include <algorithm>
+#include <vector>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+namespace {
+
+// One episode in one step: its node-k list (A) and node-(k+1) list (B).
+struct PltItem {
+    int64_t a_start, b_start;  // first index of the lists in the recording's per-type times
+    int32_t fa, fb;            // list lengths
+    int64_t prev_base;         // first position of A's values in the previous step's arrays
+    int64_t base;              // first position of B's values in this step's arrays
+    const int32_t *ttime;      // the recording's per-type times
+    int32_t lo, hi;
+};
+
+__device__ __forceinline__ int item_of(const PltItem *items, int n_items, int64_t g) {
+    int lo = 0, hi = n_items;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (items[mid].base <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Step k -> k+1 for every (episode, event of E_{k+1}) pair; first = k is
+// node 1 (every E_1 event starts a partial occurrence at its own time).
+__global__ void k_plt_step(const PltItem *__restrict__ items, int n_items, int64_t total, int first,
+                           const int32_t *__restrict__ Lprev, const int32_t *__restrict__ Vprev,
+                           int32_t *__restrict__ Lnext, int32_t *__restrict__ flag) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const PltItem it = items[item_of(items, n_items, g)];
+        const int64_t j = g - it.base;
+        const int32_t *ta = it.ttime + it.a_start;
+        const int64_t tj = it.ttime[it.b_start + j];
+        // i* = last A event with t < tj - lo
+        int64_t lo = 0, hi = it.fa;
+        const int64_t lim = tj - it.lo;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)ta[mid] < lim) lo = mid + 1; else hi = mid;
+        }
+        const int64_t istar = lo - 1;
+        int32_t L = INT32_MIN;
+        if (istar >= 0) {
+            int64_t v;
+            int32_t Lv;
+            if (first) {
+                v = istar;
+                Lv = ta[istar];
+            } else {
+                const int64_t gv = Vprev[it.prev_base + istar];  // global position or -1
+                v = gv >= it.prev_base ? gv - it.prev_base : -1;
+                Lv = v >= 0 ? Lprev[gv] : INT32_MIN;
+            }
+            if (v >= 0 && (int64_t)ta[v] >= tj - it.hi) L = Lv;
+        }
+        Lnext[g] = L;
+        flag[g] = L != INT32_MIN ? (int32_t)g : -1;
+    }
+}
+
+// Inclusive max-scan of int32 (three passes: per-block scan, scan of the
+// block maxima, add-back).
+constexpr int kMsBlock = 1024;
+
+__global__ void k_maxscan_blocks(int32_t *d, int64_t m, int32_t *bmax) {
+    __shared__ int32_t s_w[32];
+    const int64_t i = blockIdx.x * (int64_t)kMsBlock + threadIdx.x;
+    int32_t x = i < m ? d[i] : -1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x = max(x, y);
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int32_t t = s_w[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= o) t = max(t, y);
+        }
+        s_w[lane] = t;
+    }
+    __syncthreads();
+    if (w > 0) x = max(x, s_w[w - 1]);
+    if (i < m) d[i] = x;
+    if (threadIdx.x == kMsBlock - 1) bmax[blockIdx.x] = x;
+}
+
+__global__ void k_maxscan_top(int32_t *bmax, int64_t nb) {
+    // one block: sequential carry over chunks of kMsBlock block maxima
+    __shared__ int32_t s_w[32];
+    __shared__ int32_t s_carry;
+    if (threadIdx.x == 0) s_carry = -1;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < nb; c0 += kMsBlock) {
+        const int64_t i = c0 + threadIdx.x;
+        int32_t x = i < nb ? bmax[i] : -1;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x = max(x, y);
+        }
+        if (lane == 31) s_w[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int32_t t = s_w[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+                if (lane >= o) t = max(t, y);
+            }
+            s_w[lane] = t;
+        }
+        __syncthreads();
+        if (w > 0) x = max(x, s_w[w - 1]);
+        x = max(x, s_carry);
+        if (i < nb) bmax[i] = x;
+        __syncthreads();
+        if (threadIdx.x == kMsBlock - 1) s_carry = x;
+        __syncthreads();
+    }
+}
+
+__global__ void k_maxscan_add(int32_t *d, int64_t m, const int32_t *bmax) {
+    const int64_t i = blockIdx.x * (int64_t)kMsBlock + threadIdx.x;
+    if (blockIdx.x > 0 && i < m) d[i] = max(d[i], bmax[blockIdx.x - 1]);
+}
+
+// Algorithm 1 per episode over its last node's events in time order: keep
+// an end when its latest start is after the previous kept end.
+__global__ void k_plt_greedy(const PltItem *__restrict__ items, int n_items, const int32_t *__restrict__ L,
+                             const int32_t *__restrict__ cand, uint32_t *__restrict__ counts) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_items) return;
+    const PltItem it = items[e];
+    const int32_t *tb = it.ttime + it.b_start;
+    int64_t prev = INT64_MIN;
+    uint32_t c = 0;
+    for (int64_t j = 0; j < it.fb; ++j) {
+        const int32_t l = L[it.base + j];
+        if (l != INT32_MIN && (int64_t)l > prev) {
+            ++c;
+            prev = tb[j];
+        }
+    }
+    counts[cand[e]] = c;
+}
+
+}  // namespace
+
+static int maxscan(cudaStream_t st, int32_t *d, int64_t m, int32_t *tmp) {
+    if (m <= 0) return FEM_OK;
+    const int64_t nb = (m + kMsBlock - 1) / kMsBlock;
+    k_maxscan_blocks<<<(unsigned)nb, kMsBlock, 0, st>>>(d, m, tmp);
+    if (nb > 1) {
+        k_maxscan_top<<<1, kMsBlock, 0, st>>>(tmp, nb);
+        k_maxscan_add<<<(unsigned)nb, kMsBlock, 0, st>>>(d, m, tmp);
+    }
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+// Counts the candidates `work` (indices into the CSR arrays on the device)
+// by local tracking.  relaxed: every lower bound taken as 0.
+int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t *d_offs, const uint16_t *d_types,
+              const int32_t *d_lo, const int32_t *d_hi, const uint32_t *d_rec, const std::vector<int32_t> &work,
+              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms) {
+    cudaStream_t st = ctx->stream;
+    const int64_t C = (int64_t)work.size();
+    if (C == 0) return FEM_OK;
+    // candidates to the host (few of them by construction)
+    int32_t wmin = work[0], wmax = work[0];
+    for (int32_t w : work) wmin = std::min(wmin, w), wmax = std::max(wmax, w);
+    const int64_t span = (int64_t)wmax - wmin + 1;
+    std::vector<int64_t> offs(span + 1);
+    FEM_CUDA_TRY(cudaMemcpyAsync(offs.data(), d_offs + wmin, 8 * (span + 1), cudaMemcpyDeviceToHost, st));
+    std::vector<uint32_t> crec(span, 0);
+    if (d_rec) FEM_CUDA_TRY(cudaMemcpyAsync(crec.data(), d_rec + wmin, 4 * span, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    const int64_t n0 = offs[0], n1 = offs[span];
+    std::vector<uint16_t> types(n1 - n0);
+    const int64_t e0 = n0 - wmin, e1 = n1 - (wmax + 1);
+    std::vector<int32_t> lo(std::max<int64_t>(e1 - e0, 1)), hi(std::max<int64_t>(e1 - e0, 1));
+    FEM_CUDA_TRY(cudaMemcpyAsync(types.data(), d_types + n0, 2 * (n1 - n0), cudaMemcpyDeviceToHost, st));
+    if (e1 > e0) {
+        FEM_CUDA_TRY(cudaMemcpyAsync(lo.data(), d_lo + e0, 4 * (e1 - e0), cudaMemcpyDeviceToHost, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(hi.data(), d_hi + e0, 4 * (e1 - e0), cudaMemcpyDeviceToHost, st));
+    }
+    // per-type list offsets of every recording
+    std::vector<std::vector<int64_t>> toff(recs.size());
+    for (size_t r = 0; r < recs.size(); ++r) {
+        FEM_TRY(stream_bytype(ctx, recs[r]));
+        toff[r].resize(recs[r]->n_types + 1);
+        FEM_CUDA_TRY(cudaMemcpyAsync(toff[r].data(), recs[r]->d_toff, 8 * toff[r].size(), cudaMemcpyDeviceToHost,
+                                     st));
+    }
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    // 1-node episodes: the frequency; others grouped by size
+    std::vector<std::vector<int32_t>> by_n(FEM_MAX_NODES + 1);
+    std::vector<uint32_t> n1_counts;
+    std::vector<int32_t> n1_cand;
+    double relevant = 0, counted = 0;
+    for (int32_t w : work) {
+        const int64_t o = offs[w - wmin], N = offs[w - wmin + 1] - o;
+        const uint32_t r = crec[w - wmin];
+        counted += (double)recs[r]->n;
+        const std::vector<int64_t> &tf = toff[r];
+        for (int64_t k = 0; k < N; ++k) {
+            const uint16_t a = types[o - n0 + k];
+            relevant += (double)(tf[a + 1] - tf[a]);
+        }
+        if (N == 1) {
+            const uint16_t a = types[o - n0];
+            n1_cand.push_back(w);
+            n1_counts.push_back((uint32_t)(tf[a + 1] - tf[a]));
+        } else {
+            by_n[N].push_back(w);
+        }
+    }
+    if (!n1_cand.empty()) {
+        // the count of a 1-node episode is the type's frequency (distinct times)
+        for (size_t i = 0; i < n1_cand.size(); ++i)
+            FEM_CUDA_TRY(cudaMemcpyAsync(d_counts + n1_cand[i], &n1_counts[i], 4, cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    float ms_total = 0.f;
+    for (int N = 2; N <= FEM_MAX_NODES; ++N) {
+        const std::vector<int32_t> &grp = by_n[N];
+        if (grp.empty()) continue;
+        const int G = (int)grp.size();
+        // per step k: items and array sizes
+        std::vector<std::vector<PltItem>> steps(N - 1, std::vector<PltItem>(G));
+        std::vector<int64_t> tot(N - 1, 0);
+        for (int k = 0; k + 1 < N; ++k) {
+            int64_t base = 0;
+            for (int e = 0; e < G; ++e) {
+                const int32_t w = grp[e];
+                const int64_t o = offs[w - wmin];
+                const int64_t eo = o - w;
+                const uint32_t r = crec[w - wmin];
+                const std::vector<int64_t> &tf = toff[r];
+                const uint16_t A = types[o - n0 + k], B = types[o - n0 + k + 1];
+                PltItem &it = steps[k][e];
+                it.a_start = tf[A];
+                it.fa = (int32_t)(tf[A + 1] - tf[A]);
+                it.b_start = tf[B];
+                it.fb = (int32_t)(tf[B + 1] - tf[B]);
+                it.prev_base = k > 0 ? steps[k - 1][e].base : 0;
+                it.base = base;
+                it.ttime = recs[r]->d_ttime;
+                it.lo = relaxed ? 0 : lo[eo - e0 + k];
+                it.hi = hi[eo - e0 + k];
+                base += it.fb;
+            }
+            tot[k] = base;
+        }
+        int64_t tmax = 1;
+        for (int64_t t : tot) tmax = std::max(tmax, t);
+        TmpDev tmp(ctx);
+        PltItem *d_items;
+        int32_t *La, *Lb, *Va, *Vb, *bm, *d_cand;
+        FEM_TRY(tmp.get(&d_items, (size_t)G * (N - 1)));
+        FEM_TRY(tmp.get(&La, tmax));
+        FEM_TRY(tmp.get(&Lb, tmax));
+        FEM_TRY(tmp.get(&Va, tmax));
+        FEM_TRY(tmp.get(&Vb, tmax));
+        FEM_TRY(tmp.get(&bm, tmax / kMsBlock + 2));
+        FEM_TRY(tmp.get(&d_cand, G));
+        for (int k = 0; k + 1 < N; ++k)
+            FEM_CUDA_TRY(cudaMemcpyAsync(d_items + (size_t)k * G, steps[k].data(), sizeof(PltItem) * G,
+                                         cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(d_cand, grp.data(), 4 * G, cudaMemcpyHostToDevice, st));
+        cudaEventRecord(ctx->ev0, st);
+        for (int k = 0; k + 1 < N; ++k) {
+            const int64_t T = tot[k];
+            if (T > 0) {
+                const unsigned gsz = (unsigned)std::max<int64_t>(1, std::min<int64_t>((T + 255) / 256, 8 * ctx->n_sm));
+                k_plt_step<<<gsz, 256, 0, st>>>(d_items + (size_t)k * G, G, T, k == 0 ? 1 : 0, La, Va, Lb, Vb);
+                FEM_TRY(maxscan(st, Vb, T, bm));
+            }
+            std::swap(La, Lb);
+            std::swap(Va, Vb);
+        }
+        // La holds the last node's latest starts
+        k_plt_greedy<<<(G + 127) / 128, 128, 0, st>>>(d_items + (size_t)(N - 2) * G, G, La, d_cand, d_counts);
+        cudaEventRecord(ctx->ev1, st);
+        FEM_CUDA_TRY(cudaGetLastError());
+        FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        ms_total += ms;
+        stats->kernel_launches += 1 + (N - 1) * 4;
+    }
+    stats->candidates_counted += C;
+    stats->counted_episode_events += counted;
+    stats->relevant_events += relevant;
+    *kernel_ms += ms_total;
+    return FEM_OK;
+}
+
+}  // namespace fem

@@ -98,13 +98,14 @@ def test_golden_cases_on_gpu(fb, ctx):
         st.free()
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 4])
 @pytest.mark.parametrize("segments,lanes,tile", [(0, 0, 0), (1, 32, 256), (7, 64, 512), (64, 256, 1024),
                                                   (300, 96, 4096)])
 def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
     """Many random episodes (sizes 1-6, lower bounds 0..6) over random streams
     with frequent equal times, under several segment / CTA / tile settings,
-    with the tiled (1) and the sparse (2) counting kernel."""
+    with the tiled (1) and the sparse (2) counting kernel and with local
+    tracking (4; segment settings do not apply to it)."""
     r = synth.Rng(99, segments + 7)
     ctx.set_tuning(lanes_per_cta=lanes, segments=segments, tile_events=tile, kernel=kernel)
     try:
@@ -130,7 +131,7 @@ def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
         ctx.reset_tuning()
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 4])
 @pytest.mark.parametrize("segments", [0, 33, 1000, 4099])
 def test_few_episodes_many_segments(fb, ctx, segments, kernel):
     """Few episodes over the 1M-event mid stream cut into up to ~4k segments:
@@ -180,7 +181,7 @@ def test_upper_bound_is_relaxed_count(fb, ctx):
     st.free()
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4])
 def test_bursty_stream_mixed_sizes(fb, ctx, kernel):
     """Network bursts (dense windows) with sizes 2-8 and the 4-bin set."""
     s = synth.bursty_60(0xFE0003, 150_000)
@@ -456,4 +457,35 @@ def test_graph_tail_after_host_level2(fb, ctx):
     assert t == h
     assert stt["graph_tails"] == 1 and sth["graph_tails"] == 0
     assert stt["levels"] == sth["levels"] >= 3
+    st.free()
+
+
+def test_local_tracking_relaxed_bound_and_mining(fb, ctx):
+    """Local tracking (kernel 4): the relaxed upper bound equals the oracle's
+    count with every lower bound 0, and level-wise mining with it equals the
+    oracle miner; edge cases (empty stream, 1-node and 16-node episodes)."""
+    s, cfg = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    offs, ct, lo, hi = synth.random_candidates(19, 400, s.n_types, 1, 6, [(2, 5), (3, 9)], s.chains, 0.3)
+    ctx.set_tuning(kernel=4)
+    try:
+        ub = ctx.upper_bound(st, fb.Cands(offs, ct, lo, hi)).astype(np.int64)
+        assert np.array_equal(ub, oracle_counts(s.types, s.times, offs, ct, np.zeros_like(lo), hi))
+        res = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
+        want = oracle.mine_levelwise(s.types, s.times, s.n_types, cfg["bins"], cfg["threshold"], cfg["max_size"])
+        for N in range(1, cfg["max_size"] + 1):
+            eps, counts = res.level(0, N)
+            assert list(zip(eps, counts)) == want[N], N
+        res.free()
+        E = np.array([3, 3, 7, 3] * 4, np.uint16)
+        got = ctx.count_episodes(st, fb.Cands(np.array([0, 16], np.int64), E, np.zeros(15, np.int32),
+                                              np.full(15, 40, np.int32)))
+        assert int(got[0]) == oracle.count_fsm(s.types, s.times, E, np.zeros(15, np.int32), np.full(15, 40, np.int32))
+        st0 = ctx.load_stream(np.zeros(0, np.uint16), np.zeros(0, np.int32), 3)
+        got = ctx.count_episodes(st0, fb.Cands(np.array([0, 2, 3]), np.array([0, 1, 2], np.uint16),
+                                               np.array([0], np.int32), np.array([4], np.int32)))
+        assert got.tolist() == [0, 0]
+        st0.free()
+    finally:
+        ctx.reset_tuning()
     st.free()
