@@ -94,7 +94,9 @@ typedef struct {
                              CTA, tile size, segment count, kernel) the first
                              time a workload signature is seen and keep the
                              fastest in the context's tuning cache */
-    int kernel;           /* 0 = choose per launch, 1 = always the tiled
+    int kernel;           /* 0 = choose per launch (local tracking for at
+                             most 256 episodes over a recording of at least
+                             2^20 events), 1 = always the tiled
                              shared-memory broadcast kernel, 2 = the sparse
                              per-type-list kernel where it applies, 3 = the
                              sparse kernel with per-node branching instead of

@@ -2482,9 +2482,26 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     return FEM_OK;
 }
 
+constexpr int64_t kPltMaxCands = 256;        // automatic local tracking: at most this many episodes
+constexpr int64_t kPltMinEvents = 1 << 20;   // ... over a recording of at least this many events
+
 static int run_count(CountCall &cc, const int32_t *subset, int64_t n_sub, int force_segments) {
-    // node-by-node local tracking (fem_plt.cu) when asked for
-    if (cc.mode != 1 && force_segments == 0 && cc.ctx->tuning.kernel == 4) {
+    // node-by-node local tracking (fem_plt.cu): when asked for, or for few
+    // episodes over long recordings (its steps are parallel over the events
+    // of the episodes' node types; the per-episode kernels need many
+    // episodes, or many segments with their halos and records, to fill the
+    // GPU)
+    bool plt = cc.ctx->tuning.kernel == 4;
+    if (cc.ctx->tuning.kernel == 0 && n_sub <= kPltMaxCands) {
+        int64_t nmax = 0;
+        bool lists = true;
+        for (auto *r : cc.recs) {
+            nmax = std::max(nmax, r->n);
+            lists = lists && r->n_types <= 8192 && r->n <= INT32_MAX / 2;
+        }
+        plt = lists && nmax >= kPltMinEvents;
+    }
+    if (cc.mode != 1 && force_segments == 0 && plt) {
         std::vector<int32_t> work(n_sub);
         if (subset) {
             FEM_CUDA_TRY(cudaMemcpyAsync(work.data(), subset, 4 * n_sub, cudaMemcpyDeviceToHost, cc.ctx->stream));

@@ -150,24 +150,65 @@ __global__ void k_maxscan_add(int32_t *d, int64_t m, const int32_t *bmax) {
     if (blockIdx.x > 0 && i < m) d[i] = max(d[i], bmax[blockIdx.x - 1]);
 }
 
-// Algorithm 1 per episode over its last node's events in time order: keep
-// an end when its latest start is after the previous kept end.
-__global__ void k_plt_greedy(const PltItem *__restrict__ items, int n_items, const int32_t *__restrict__ L,
-                             const int32_t *__restrict__ cand, uint32_t *__restrict__ counts) {
+// Algorithm 1 over an episode's end events (its last node's list, in time
+// order): keep an end when its latest start is after the previous kept end.
+// The latest starts are non-decreasing along the valid ends, so with PM(j) =
+// the latest start of the newest valid end at or before j (from the max-scan
+// of valid positions), the end kept after end j is the first j' with
+// PM(j') > t_j (a binary search), and the first end kept is the first valid
+// one.  The count is the length of the chain from there, by pointer jumping.
+__device__ __forceinline__ int32_t plt_pm(const int32_t *L, const int32_t *V, int64_t base, int64_t j) {
+    const int32_t v = V[base + j];
+    return v >= base ? L[v] : INT32_MIN;
+}
+
+// nxt[g] = global position of the end kept after g (or -1); cnt[g] = 1 for
+// valid ends.
+__global__ void k_plt_next(const PltItem *__restrict__ items, int n_items, int64_t total,
+                           const int32_t *__restrict__ L, const int32_t *__restrict__ V, int32_t *__restrict__ nxt,
+                           int32_t *__restrict__ cnt) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const PltItem it = items[item_of(items, n_items, g)];
+        const int64_t j = g - it.base;
+        int32_t nx = -1, c = 0;
+        if (L[g] != INT32_MIN) {
+            c = 1;
+            const int64_t tj = it.ttime[it.b_start + j];
+            int64_t lo = j + 1, hi = it.fb;  // first j' > j with PM(j') > t_j
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((int64_t)plt_pm(L, V, it.base, mid) > tj) hi = mid; else lo = mid + 1;
+            }
+            if (lo < it.fb) nx = (int32_t)(it.base + lo);
+        }
+        nxt[g] = nx;
+        cnt[g] = c;
+    }
+}
+
+// One pointer-jumping round: cnt'[g] = cnt[g] + cnt[nxt[g]], nxt'[g] = nxt[nxt[g]].
+__global__ void k_plt_jump(int64_t total, const int32_t *__restrict__ nxt, const int32_t *__restrict__ cnt,
+                           int32_t *__restrict__ nxt2, int32_t *__restrict__ cnt2) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t n = nxt[g];
+        cnt2[g] = cnt[g] + (n >= 0 ? cnt[n] : 0);
+        nxt2[g] = n >= 0 ? nxt[n] : -1;
+    }
+}
+
+// count = chain length from the first valid end (first j with PM(j) > -inf).
+__global__ void k_plt_count(const PltItem *__restrict__ items, int n_items, const int32_t *__restrict__ L,
+                            const int32_t *__restrict__ V, const int32_t *__restrict__ cnt,
+                            const int32_t *__restrict__ cand, uint32_t *__restrict__ counts) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_items) return;
     const PltItem it = items[e];
-    const int32_t *tb = it.ttime + it.b_start;
-    int64_t prev = INT64_MIN;
-    uint32_t c = 0;
-    for (int64_t j = 0; j < it.fb; ++j) {
-        const int32_t l = L[it.base + j];
-        if (l != INT32_MIN && (int64_t)l > prev) {
-            ++c;
-            prev = tb[j];
-        }
+    int64_t lo = 0, hi = it.fb;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (plt_pm(L, V, it.base, mid) != INT32_MIN) hi = mid; else lo = mid + 1;
     }
-    counts[cand[e]] = c;
+    counts[cand[e]] = lo < it.fb ? (uint32_t)cnt[it.base + lo] : 0u;
 }
 
 }  // namespace
@@ -282,12 +323,16 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
         for (int64_t t : tot) tmax = std::max(tmax, t);
         TmpDev tmp(ctx);
         PltItem *d_items;
-        int32_t *La, *Lb, *Va, *Vb, *bm, *d_cand;
+        int32_t *La, *Lb, *Va, *Vb, *bm, *d_cand, *n1, *n2, *c1, *c2;
         FEM_TRY(tmp.get(&d_items, (size_t)G * (N - 1)));
         FEM_TRY(tmp.get(&La, tmax));
         FEM_TRY(tmp.get(&Lb, tmax));
         FEM_TRY(tmp.get(&Va, tmax));
         FEM_TRY(tmp.get(&Vb, tmax));
+        FEM_TRY(tmp.get(&n1, tmax));
+        FEM_TRY(tmp.get(&n2, tmax));
+        FEM_TRY(tmp.get(&c1, tmax));
+        FEM_TRY(tmp.get(&c2, tmax));
         FEM_TRY(tmp.get(&bm, tmax / kMsBlock + 2));
         FEM_TRY(tmp.get(&d_cand, G));
         for (int k = 0; k + 1 < N; ++k)
@@ -305,15 +350,30 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
             std::swap(La, Lb);
             std::swap(Va, Vb);
         }
-        // La holds the last node's latest starts
-        k_plt_greedy<<<(G + 127) / 128, 128, 0, st>>>(d_items + (size_t)(N - 2) * G, G, La, d_cand, d_counts);
+        // La / Va: the last node's latest starts and newest valid positions
+        const PltItem *last = d_items + (size_t)(N - 2) * G;
+        const int64_t T = tot[N - 2];
+        int64_t fmax = 1;
+        for (const PltItem &it : steps[N - 2]) fmax = std::max<int64_t>(fmax, it.fb);
+        int rounds = 0;
+        while ((int64_t(1) << rounds) < fmax) ++rounds;
+        if (T > 0) {
+            const unsigned gsz = (unsigned)std::max<int64_t>(1, std::min<int64_t>((T + 255) / 256, 8 * ctx->n_sm));
+            k_plt_next<<<gsz, 256, 0, st>>>(last, G, T, La, Va, n1, c1);
+            for (int q = 0; q < rounds; ++q) {
+                k_plt_jump<<<gsz, 256, 0, st>>>(T, n1, c1, n2, c2);
+                std::swap(n1, n2);
+                std::swap(c1, c2);
+            }
+        }
+        k_plt_count<<<(G + 127) / 128, 128, 0, st>>>(last, G, La, Va, c1, d_cand, d_counts);
         cudaEventRecord(ctx->ev1, st);
         FEM_CUDA_TRY(cudaGetLastError());
         FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
         ms_total += ms;
-        stats->kernel_launches += 1 + (N - 1) * 4;
+        stats->kernel_launches += (N - 1) * 4 + 2 + rounds;
     }
     stats->candidates_counted += C;
     stats->counted_episode_events += counted;

@@ -131,12 +131,14 @@ def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
         ctx.reset_tuning()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4])
 @pytest.mark.parametrize("segments", [0, 33, 1000, 4099])
 def test_few_episodes_many_segments(fb, ctx, segments, kernel):
     """Few episodes over the 1M-event mid stream cut into up to ~4k segments:
     each episode's count is stitched from thousands of segment records
-    (several per lane of the stitch warp, with a ragged last run)."""
+    (several per lane of the stitch warp, with a ragged last run); with the
+    automatic choice (0) and no segment override these few episodes over a
+    long recording go to local tracking."""
     s, cfg = synth.c2_mid()
     st = ctx.load_stream(s.types, s.times, s.n_types)
     offs, ct, lo, hi = synth.random_candidates(0xFE0102, 48, s.n_types, 2, 6, cfg["bins"], s.chains, 0.5)
