@@ -251,7 +251,7 @@ def _lat_summary(lat_s, ee, span_s):
 
 
 def serving_leg(n_jobs: int = 12, n_cap: int = 500_000, stress_n: int = 0, load: float = 0.7,
-                seed: int = 0xFE0005):
+                seed: int = 0xFE0005, plain: bool = True):
     """Serving on a bounded sample of the job list (the first `n_jobs` jobs
     with at most `n_cap` events, plus the stress job when stress_n > 0).
     Arrivals are Poisson (seeded) at `load` x the served path's measured
@@ -335,7 +335,10 @@ def serving_leg(n_jobs: int = 12, n_cap: int = 500_000, stress_n: int = 0, load:
         return lat, ee, arrays, end - arrive[0], svc
 
     lat_o, ee_o, arr_o, span_o, svc_o = fifo(False)
-    lat_p, ee_p, arr_p, span_p, svc_p = fifo(True)
+    if plain:
+        lat_p, ee_p, arr_p, span_p, svc_p = fifo(True)
+    else:
+        arr_p = arr_o
     parity = all(_same_levels(a, b) and _same_levels(a, c) for a, b, c in zip(arr_srv, arr_o, arr_p))
     return {
         "workload": f"serving sample: {K} jobs of the job list (n <= {n_cap}"
@@ -344,7 +347,8 @@ def serving_leg(n_jobs: int = 12, n_cap: int = 500_000, stress_n: int = 0, load:
         "arrivals": f"Poisson, {lam:.2f} jobs/s = {load} x served capacity ({capacity:.2f} jobs/s)",
         "served": _lat_summary(lat_srv, ee_srv, t_b - t_a),
         "ours_fifo": dict(_lat_summary(lat_o, ee_o, span_o), service_ms_mean=1e3 * float(np.mean(svc_o))),
-        "plain_fifo": dict(_lat_summary(lat_p, ee_p, span_p), service_ms_mean=1e3 * float(np.mean(svc_p))),
+        "plain_fifo": (dict(_lat_summary(lat_p, ee_p, span_p), service_ms_mean=1e3 * float(np.mean(svc_p)))
+                       if plain else "not run (--c5-no-plain)"),
         "parity_across_arms": bool(parity),
         "note": "p99 over the sample's jobs (interpolated); FIFO arms queued on the same arrivals",
     }
@@ -623,6 +627,7 @@ def main():
     ap.add_argument("--c5-jobs", type=int, default=40, help="jobs of the serving sample (--workload c5)")
     ap.add_argument("--c5-cap", type=int, default=4_000_000, help="largest job of the serving sample (--workload c5)")
     ap.add_argument("--c5-stress", type=int, default=0, help="add the stress job with this many events (--workload c5)")
+    ap.add_argument("--c5-no-plain", action="store_true", help="skip the plain-path arm (--workload c5)")
     ap.add_argument("--quick", action="store_true",
                     help="time the tiled path only (no plain-path, e2e or CPU legs); for profiling")
     ap.add_argument("--case", default=None,
@@ -643,8 +648,8 @@ def main():
         return
     if args.workload == "c5":
         if rank == 0:
-            print(json.dumps({"workload": "c5", "serving": serving_leg(args.c5_jobs, args.c5_cap, args.c5_stress)}),
-                  flush=True)
+            print(json.dumps({"workload": "c5", "serving": serving_leg(args.c5_jobs, args.c5_cap, args.c5_stress,
+                                                                       plain=not args.c5_no_plain)}), flush=True)
         return
     if world > 1:
         import torch
