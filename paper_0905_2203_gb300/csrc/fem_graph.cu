@@ -632,6 +632,52 @@ struct FLevel {
     int64_t *foff = nullptr;
 };
 
+// Layout of the results the graph's last node writes to mapped host memory:
+// the status word, the counters, the per-recording offsets, the relevant-
+// event sums, then per level its frequent set (capacity-sized regions).
+struct PackLayout {
+    int64_t o_ctr, o_coff, o_coff2, o_rel;  // byte offsets
+    int64_t o_lvl[FEM_MAX_NODES + 1];       // per level: types, then lo, hi, rec, counts
+    int64_t fcap[FEM_MAX_NODES + 1];        // per level capacity
+};
+
+__device__ __forceinline__ void pack_copy(char *dst, const char *src, int64_t bytes, int64_t t0, int64_t stride) {
+    // 4-byte words (every region is a multiple of 4 bytes and 8-byte aligned)
+    const int64_t w = bytes / 4;
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (int64_t i = t0; i < w; i += stride) d[i] = s[i];
+}
+
+__global__ void k_g_pack(const int *status, const int32_t *ctr, const int64_t *coff, const int64_t *coff2,
+                         const unsigned long long *rel, const FLevel *F, PackLayout lay, int first, int L,
+                         int n_recs, char *out) {
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    if (t0 == 0) *reinterpret_cast<int *>(out) = *status;
+    pack_copy(out + lay.o_ctr, reinterpret_cast<const char *>(ctr), 4 * (int64_t)(L + 1) * kCtr, t0, gs);
+    pack_copy(out + lay.o_coff, reinterpret_cast<const char *>(coff), 8 * (int64_t)(L + 1) * (n_recs + 1), t0, gs);
+    pack_copy(out + lay.o_coff2, reinterpret_cast<const char *>(coff2), 8 * (int64_t)(n_recs + 1), t0, gs);
+    pack_copy(out + lay.o_rel, reinterpret_cast<const char *>(rel), 8 * (int64_t)(L + 1), t0, gs);
+    for (int N = first; N <= L; ++N) {
+        const int64_t Fn = ctr[N * kCtr + 1], fc = lay.fcap[N];
+        const FLevel f = F[N];
+        char *o = out + lay.o_lvl[N];
+        const int64_t tb = ((2 * fc * N) + 7) / 8 * 8, eb = 4 * fc * (N - 1);
+        // types: 2-byte entries, copied as bytes pairs
+        {
+            const uint16_t *s = f.types;
+            uint16_t *d = reinterpret_cast<uint16_t *>(o);
+            for (int64_t i = t0; i < Fn * N; i += gs) d[i] = s[i];
+        }
+        if (N > 1) {
+            pack_copy(o + tb, reinterpret_cast<const char *>(f.lo), 4 * Fn * (N - 1), t0, gs);
+            pack_copy(o + tb + eb, reinterpret_cast<const char *>(f.hi), 4 * Fn * (N - 1), t0, gs);
+        }
+        pack_copy(o + tb + 2 * eb, reinterpret_cast<const char *>(f.rec), 4 * Fn, t0, gs);
+        pack_copy(o + tb + 2 * eb + 4 * fc, reinterpret_cast<const char *>(f.counts), 4 * Fn, t0, gs);
+    }
+}
+
 }  // namespace
 
 struct GraphTail {
@@ -654,6 +700,9 @@ struct GraphTail {
     unsigned long long *rel = nullptr;     // relevant events counted, per level
     std::vector<cudaEvent_t> ev;           // around each level's count kernels
     int64_t kernel_nodes = 0;              // kernel launches per run of the graph
+    char *h_out = nullptr;                 // mapped host buffer the last node writes the results to
+    size_t out_bytes = 0;
+    PackLayout lay{};
     cudaGraphExec_t exec = nullptr;
 
     template <typename T>
@@ -670,6 +719,7 @@ struct GraphTail {
         cudaStreamSynchronize(ctx->stream);
         for (auto e : ev) cudaEventDestroy(e);
         for (auto &h : held) dev_free(ctx, h.first, h.second);
+        if (h_out) cudaFreeHost(h_out);
     }
 };
 
@@ -866,6 +916,37 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     FEM_CUDA_TRY(cudaMemcpyAsync(g->d_thr, thr.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
     int32_t *scan_tmp;
     FEM_TRY(g->get(&scan_tmp, (scan_m + 2) / 1024 + 2));
+    // results in mapped host memory (written by the graph's last node)
+    {
+        PackLayout &lay = g->lay;
+        int64_t o = 8;
+        auto take = [&](int64_t bytes) {
+            const int64_t at = o;
+            o += (bytes + 7) / 8 * 8;
+            return at;
+        };
+        lay.o_ctr = take(4 * (int64_t)(L + 1) * kCtr);
+        lay.o_coff = take(8 * (int64_t)(L + 1) * (n_recs + 1));
+        lay.o_coff2 = take(8 * (int64_t)(n_recs + 1));
+        lay.o_rel = take(8 * (int64_t)(L + 1));
+        for (int N = first; N <= L; ++N) {
+            const int64_t fc = N == 1 ? std::max<int64_t>(tot1, 1) : cap;
+            lay.fcap[N] = fc;
+            const int64_t tb = ((2 * fc * N) + 7) / 8 * 8, eb = 4 * fc * (N - 1);
+            lay.o_lvl[N] = take(tb + 2 * eb + 8 * fc);
+        }
+        g->out_bytes = (size_t)o;
+        if (cudaHostAlloc(reinterpret_cast<void **>(&g->h_out), g->out_bytes, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            g->h_out = nullptr;
+            return FEM_ERR_NOMEM;
+        }
+    }
+    char *d_out = nullptr;
+    FEM_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_out), g->h_out, 0));
+    FLevel *d_F = nullptr;
+    FEM_TRY(g->get(&d_F, (size_t)L + 1));
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_F, g->F.data(), sizeof(FLevel) * (L + 1), cudaMemcpyHostToDevice, st));
     FEM_CUDA_TRY(cudaStreamSynchronize(st));
 
     // ---- capture levels first..L
@@ -963,6 +1044,11 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                                               nf.hi, nf.rec, nf.counts, cn);
             k_g_foff<<<1, 256, 0, st>>>(nf.rec, cn, n_recs, nf.foff);
         }
+        ok(cudaGetLastError());
+    }
+    if (cst == FEM_OK) {
+        k_g_pack<<<(unsigned)(2 * ctx->n_sm), 256, 0, st>>>(ctx->d_status, g->ctr, g->coff, g->coff2, g->rel, d_F,
+                                                           g->lay, first, L, n_recs, d_out);
         ok(cudaGetLastError());
     }
     const cudaError_t ce = cudaStreamEndCapture(st, &graph);
@@ -1093,16 +1179,19 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
     cudaEventRecord(ctx->ev0, st);
     FEM_CUDA_TRY(cudaGraphLaunch(g->exec, st));
     cudaEventRecord(ctx->ev1, st);
-    std::vector<int32_t> ctr((size_t)(max_size + 1) * kCtr);
-    std::vector<int64_t> coff((size_t)(max_size + 1) * (n_recs + 1));
-    std::vector<int64_t> coff2(n_recs + 1, 0);
-    std::vector<unsigned long long> rel((size_t)max_size + 1, 0ull);
-    FEM_CUDA_TRY(cudaMemcpyAsync(ctr.data(), g->ctr, 4 * ctr.size(), cudaMemcpyDeviceToHost, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(coff.data(), g->coff, 8 * coff.size(), cudaMemcpyDeviceToHost, st));
-    if (first <= 2)
-        FEM_CUDA_TRY(cudaMemcpyAsync(coff2.data(), g->coff2, 8 * coff2.size(), cudaMemcpyDeviceToHost, st));
-    FEM_CUDA_TRY(cudaMemcpyAsync(rel.data(), g->rel, 8 * rel.size(), cudaMemcpyDeviceToHost, st));
-    FEM_TRY(sync_status(ctx));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    const char *ho = g->h_out;
+    const int status = *reinterpret_cast<const int *>(ho);
+    if (status) {
+        FEM_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+        FEM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (status & kStatusTimeout) return FEM_ERR_TIMEOUT;
+        return FEM_ERR_INVAL;
+    }
+    const int32_t *ctr = reinterpret_cast<const int32_t *>(ho + g->lay.o_ctr);
+    const int64_t *coff = reinterpret_cast<const int64_t *>(ho + g->lay.o_coff);
+    const int64_t *coff2 = reinterpret_cast<const int64_t *>(ho + g->lay.o_coff2);
+    const unsigned long long *rel = reinterpret_cast<const unsigned long long *>(ho + g->lay.o_rel);
     bool flagged = false;
     int64_t need = 0;
     for (int N = std::max(first, 2); N <= max_size; ++N) {
@@ -1142,29 +1231,25 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
         tl.N = N;
         tl.C = N == 1 ? 0 : c[0];
         if (N >= 2) {
-            tl.coff.assign(coff.begin() + (size_t)N * (n_recs + 1), coff.begin() + (size_t)(N + 1) * (n_recs + 1));
-            tl.goff = (N == 2 && first <= 2) ? coff2 : tl.coff;
+            tl.coff.assign(coff + (size_t)N * (n_recs + 1), coff + (size_t)(N + 1) * (n_recs + 1));
+            tl.goff = (N == 2 && first <= 2) ? std::vector<int64_t>(coff2, coff2 + n_recs + 1) : tl.coff;
         }
-        const int64_t Fn = c[1];
-        tl.types.resize((size_t)Fn * N);
-        tl.lo.resize((size_t)Fn * (N - 1));
-        tl.hi.resize((size_t)Fn * (N - 1));
-        tl.rec.resize(Fn);
-        tl.counts.resize(Fn);
-        if (Fn > 0) {
-            const FLevel &f = g->F[N];
-            FEM_CUDA_TRY(cudaMemcpyAsync(tl.types.data(), f.types, 2 * tl.types.size(), cudaMemcpyDeviceToHost, st));
-            if (N > 1) {
-                FEM_CUDA_TRY(cudaMemcpyAsync(tl.lo.data(), f.lo, 4 * tl.lo.size(), cudaMemcpyDeviceToHost, st));
-                FEM_CUDA_TRY(cudaMemcpyAsync(tl.hi.data(), f.hi, 4 * tl.hi.size(), cudaMemcpyDeviceToHost, st));
-            }
-            FEM_CUDA_TRY(cudaMemcpyAsync(tl.rec.data(), f.rec, 4 * tl.rec.size(), cudaMemcpyDeviceToHost, st));
-            FEM_CUDA_TRY(cudaMemcpyAsync(tl.counts.data(), f.counts, 4 * tl.counts.size(), cudaMemcpyDeviceToHost, st));
-        }
+        const int64_t Fn = c[1], fc = g->lay.fcap[N];
+        const char *o = ho + g->lay.o_lvl[N];
+        const int64_t tb = ((2 * fc * N) + 7) / 8 * 8, eb = 4 * fc * (N - 1);
+        const uint16_t *ty = reinterpret_cast<const uint16_t *>(o);
+        const int32_t *lo = reinterpret_cast<const int32_t *>(o + tb);
+        const int32_t *hi = reinterpret_cast<const int32_t *>(o + tb + eb);
+        const uint32_t *rc = reinterpret_cast<const uint32_t *>(o + tb + 2 * eb);
+        const uint32_t *ct = reinterpret_cast<const uint32_t *>(o + tb + 2 * eb + 4 * fc);
+        tl.types.assign(ty, ty + Fn * N);
+        tl.lo.assign(lo, lo + Fn * (N - 1));
+        tl.hi.assign(hi, hi + Fn * (N - 1));
+        tl.rec.assign(rc, rc + Fn);
+        tl.counts.assign(ct, ct + Fn);
         out->levels.push_back(std::move(tl));
         if ((N >= 2 && c[0] == 0) || Fn == 0) break;
     }
-    FEM_CUDA_TRY(cudaStreamSynchronize(st));
     *used = true;
     return FEM_OK;
 }
