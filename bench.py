@@ -542,8 +542,8 @@ def run_ours(args, rank, world, local_rank):
         res = ctx.mine_levelwise([st2], bins, [thr], max_size)
         out_bytes = 0
         for N in range(1, max_size + 1):
-            eps, counts = res.level(0, N)
-            out_bytes += len(counts) * (4 + 2 * N + 8 * max(N - 1, 0) + 8)
+            offs_n, types_n, lo_n, hi_n, counts_n = res.level_arrays(0, N)
+            out_bytes += offs_n.nbytes + types_n.nbytes + lo_n.nbytes + hi_n.nbytes + counts_n.nbytes
         e2e_ee += res.stats()["episode_events"]
         res.free()
         st2.free()

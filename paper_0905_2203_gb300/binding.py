@@ -280,6 +280,30 @@ class Result:
     def __init__(self, h, n_recs: int, max_size: int):
         self.h, self.n_recs, self.max_size = h, n_recs, max_size
 
+    def level_arrays(self, rec: int, level: int):
+        """One recording's frequent episodes of one level as numpy arrays in
+        the CSR layout of fem_result_level: (offs[n+1], types, lo, hi,
+        counts[n]) -- copies of the result's arrays, no per-episode objects."""
+        n = I64()
+        po, pt, pl, ph, pc = VP(), VP(), VP(), VP(), VP()
+        check(fem_result_level(self.h, rec, level, ctypes.byref(n), ctypes.byref(po),
+                               ctypes.byref(pt), ctypes.byref(pl), ctypes.byref(ph),
+                               ctypes.byref(pc)), "fem_result_level")
+        n = int(n.value)
+        if n == 0:
+            z = np.zeros(0, np.int32)
+            return np.zeros(1, np.int64), np.zeros(0, np.uint16), z, z.copy(), np.zeros(0, np.uint32)
+        offs = np.ctypeslib.as_array(ctypes.cast(po, ctypes.POINTER(I64)), (n + 1,)).copy()
+        nn = int(offs[-1])
+        types = np.ctypeslib.as_array(ctypes.cast(pt, ctypes.POINTER(ctypes.c_uint16)), (nn,)).copy()
+        ne = nn - n
+        lo = (np.ctypeslib.as_array(ctypes.cast(pl, ctypes.POINTER(I32)), (ne,)).copy()
+              if ne else np.zeros(0, np.int32))
+        hi = (np.ctypeslib.as_array(ctypes.cast(ph, ctypes.POINTER(I32)), (ne,)).copy()
+              if ne else np.zeros(0, np.int32))
+        counts = np.ctypeslib.as_array(ctypes.cast(pc, ctypes.POINTER(U32)), (n,)).copy()
+        return offs, types, lo, hi, counts
+
     def level(self, rec: int, level: int):
         """(list of (types, lo, hi) tuples, counts list) for one recording and level."""
         n = I64()

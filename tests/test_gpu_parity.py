@@ -491,3 +491,21 @@ def test_local_tracking_relaxed_bound_and_mining(fb, ctx):
     finally:
         ctx.reset_tuning()
     st.free()
+
+
+def test_result_level_arrays_match_tuples(fb, ctx):
+    """Result.level_arrays (numpy CSR) carries the same episodes and counts
+    as Result.level (tuples)."""
+    s, cfg = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    res = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
+    for N in range(1, cfg["max_size"] + 1):
+        eps, counts = res.level(0, N)
+        offs, types, lo, hi, cnt = res.level_arrays(0, N)
+        assert len(offs) == len(eps) + 1 and cnt.tolist() == counts
+        for c, (E, l, h) in enumerate(eps):
+            o, p = int(offs[c]), int(offs[c + 1])
+            assert tuple(types[o:p].tolist()) == E
+            assert tuple(lo[o - c:p - c - 1].tolist()) == l and tuple(hi[o - c:p - c - 1].tolist()) == h
+    res.free()
+    st.free()
