@@ -103,7 +103,13 @@ typedef struct {
                              its node-uniform variant (comparison), 4 = node-
                              by-node local tracking over the per-type lists
                              (section "Parallel Local Tracking": parallel
-                             over events, for few long episodes) */
+                             over events, for few long episodes), 5 / 6 =
+                             local tracking that materialises every partial
+                             occurrence, compacting each step's list with
+                             atomics (5) or count, scan and write (6); an
+                             episode whose list would pass 2^25 entries is
+                             counted as with 4 and adds to
+                             fallback_recounts */
     int level_graph;      /* mining: 0 = run the levels as one captured CUDA
                              graph where it applies (all levels when no
                              other override is set and every alphabet has at

@@ -2491,7 +2491,8 @@ static int run_count(CountCall &cc, const int32_t *subset, int64_t n_sub, int fo
     // of the episodes' node types; the per-episode kernels need many
     // episodes, or many segments with their halos and records, to fill the
     // GPU)
-    bool plt = cc.ctx->tuning.kernel == 4;
+    const int kern = cc.ctx->tuning.kernel;
+    bool plt = kern >= 4;
     if (cc.ctx->tuning.kernel == 0 && n_sub <= kPltMaxCands) {
         int64_t nmax = 0;
         bool lists = true;
@@ -2510,7 +2511,7 @@ static int run_count(CountCall &cc, const int32_t *subset, int64_t n_sub, int fo
             for (int64_t i = 0; i < n_sub; ++i) work[i] = (int32_t)i;
         }
         FEM_TRY(count_plt(cc.ctx, cc.recs, cc.offs, cc.types, cc.lo, cc.hi, cc.cand_rec, work, cc.mode == 2,
-                          cc.counts, &cc.stats, &cc.count_ms));
+                          cc.counts, &cc.stats, &cc.count_ms, kern >= 5 ? kern - 4 : 0));
         return sync_status(cc.ctx);
     }
     return count_core(cc, subset, n_sub, force_segments);

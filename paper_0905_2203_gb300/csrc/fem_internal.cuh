@@ -202,10 +202,12 @@ struct TmpDev {
 };
 
 // Counting by node-by-node local tracking (fem_plt.cu): the candidates
-// `work` of the device CSR arrays; relaxed = every lower bound taken as 0.
+// `work` of the device CSR arrays; relaxed = every lower bound taken as 0;
+// variant 0 = latest start per event, 1 / 2 = occurrence lists compacted with
+// atomics / count-scan-write.
 int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t *d_offs, const uint16_t *d_types,
               const int32_t *d_lo, const int32_t *d_hi, const uint32_t *d_rec, const std::vector<int32_t> &work,
-              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms);
+              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms, int variant);
 
 // Scratch slot ids.
 enum Slot : int {

@@ -85,6 +85,9 @@ __global__ void k_plt_step(const PltItem *__restrict__ items, int n_items, int64
 // Inclusive max-scan of int32 (three passes: per-block scan, scan of the
 // block maxima, add-back).
 constexpr int kMsBlock = 1024;
+// Entries an occurrence list may hold (episodes beyond it are counted by the
+// latest-start steps).
+constexpr int64_t kOccCap = int64_t(1) << 25;
 
 __global__ void k_maxscan_blocks(int32_t *d, int64_t m, int32_t *bmax) {
     __shared__ int32_t s_w[32];
@@ -211,6 +214,118 @@ __global__ void k_plt_count(const PltItem *__restrict__ items, int n_items, cons
     counts[cand[e]] = lo < it.fb ? (uint32_t)cnt[it.base + lo] : 0u;
 }
 
+// ---- the section's own form: every partial occurrence, node by node ------
+// An occurrence list holds (start time, position in the current node's type
+// list).  A step finds, for each partial occurrence ending at time t, the
+// next node's events in (t + lo, t + hi] (two binary searches) and emits one
+// entry per event; the output is compacted either with atomics (a block
+// reserves its range with one global atomic after its threads reserved
+// theirs in shared memory, "Lock-based compaction") or with count, scan,
+// write ("Lock-free compaction").  After the last node the latest start per
+// end event feeds the same overlap removal as above.
+
+__device__ __forceinline__ void occ_range(const int32_t *tb, int64_t fb, int64_t t, int32_t lo, int32_t hi,
+                                          int64_t &j0, int64_t &j1) {
+    int64_t a = 0, b = fb;
+    while (a < b) {  // first event with time > t + lo
+        const int64_t mid = (a + b) >> 1;
+        if ((int64_t)tb[mid] <= t + lo) a = mid + 1; else b = mid;
+    }
+    j0 = a;
+    b = fb;
+    while (a < b) {  // first event with time > t + hi
+        const int64_t mid = (a + b) >> 1;
+        if ((int64_t)tb[mid] <= t + hi) a = mid + 1; else b = mid;
+    }
+    j1 = a;
+}
+
+__global__ void k_occ_init(const int32_t *__restrict__ ta, int64_t fa, int32_t *__restrict__ s, int32_t *__restrict__ p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < fa; i += (int64_t)gridDim.x * blockDim.x) {
+        s[i] = ta[i];
+        p[i] = (int32_t)i;
+    }
+}
+
+// Lock-free compaction, count pass: matches per partial occurrence, and
+// their exact 64-bit total (the int32 scan runs only when it fits).
+__global__ void k_occ_count(const int32_t *__restrict__ p, int64_t m, const int32_t *__restrict__ ta,
+                            const int32_t *__restrict__ tb, int64_t fb, int32_t lo, int32_t hi,
+                            int32_t *__restrict__ cnt, unsigned long long *total) {
+    for (int64_t o0 = blockIdx.x * (int64_t)blockDim.x; o0 <= m; o0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = o0 + threadIdx.x;
+        int64_t c = 0;
+        if (o < m) {
+            int64_t j0, j1;
+            occ_range(tb, fb, ta[p[o]], lo, hi, j0, j1);
+            c = j1 - j0;
+        }
+        if (o <= m) cnt[o] = (int32_t)min(c, (int64_t)INT32_MAX);
+        unsigned long long w = (unsigned long long)c;
+        for (int q = 16; q > 0; q >>= 1) w += __shfl_down_sync(0xFFFFFFFFu, w, q);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, w);
+    }
+}
+
+__global__ void k_fill_i32(int32_t *d, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = v;
+}
+
+// Lock-free compaction, write pass at the scanned offsets.
+__global__ void k_occ_write_scan(const int32_t *__restrict__ s, const int32_t *__restrict__ p, int64_t m,
+                                 const int32_t *__restrict__ off, const int32_t *__restrict__ ta,
+                                 const int32_t *__restrict__ tb, int64_t fb, int32_t lo, int32_t hi, int64_t cap,
+                                 int32_t *__restrict__ s2, int32_t *__restrict__ p2) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < m; o += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j0, j1;
+        occ_range(tb, fb, ta[p[o]], lo, hi, j0, j1);
+        int64_t w = off[o];
+        for (int64_t j = j0; j < j1 && w < cap; ++j, ++w) {
+            s2[w] = s[o];
+            p2[w] = (int32_t)j;
+        }
+    }
+}
+
+// Lock-based compaction: threads reserve in shared memory, the block once
+// globally; *total counts every match (capacity overflow when > cap).
+__global__ void k_occ_write_atomic(const int32_t *__restrict__ s, const int32_t *__restrict__ p, int64_t m,
+                                   const int32_t *__restrict__ ta, const int32_t *__restrict__ tb, int64_t fb,
+                                   int32_t lo, int32_t hi, int64_t cap, int32_t *__restrict__ s2,
+                                   int32_t *__restrict__ p2, unsigned long long *total) {
+    __shared__ unsigned long long s_cnt, s_base;
+    for (int64_t o0 = blockIdx.x * (int64_t)blockDim.x; o0 < m; o0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = o0 + threadIdx.x;
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        int64_t j0 = 0, j1 = 0;
+        if (o < m) occ_range(tb, fb, ta[p[o]], lo, hi, j0, j1);
+        const unsigned long long mine = atomicAdd(&s_cnt, (unsigned long long)(j1 - j0));
+        __syncthreads();
+        if (threadIdx.x == 0) s_base = atomicAdd(total, (unsigned long long)s_cnt);
+        __syncthreads();
+        int64_t w = (int64_t)(s_base + mine);
+        for (int64_t j = j0; j < j1 && w < cap; ++j, ++w) {
+            s2[w] = s[o];
+            p2[w] = (int32_t)j;
+        }
+        __syncthreads();
+    }
+}
+
+// Latest start per end event (positions in the last node's list).
+__global__ void k_occ_final(const int32_t *__restrict__ s, const int32_t *__restrict__ p, int64_t m,
+                            int32_t *__restrict__ L) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < m; o += (int64_t)gridDim.x * blockDim.x)
+        atomicMax(&L[p[o]], s[o]);
+}
+
+__global__ void k_occ_flags(const int32_t *__restrict__ L, int64_t fb, int32_t *__restrict__ V) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < fb; j += (int64_t)gridDim.x * blockDim.x)
+        V[j] = L[j] != INT32_MIN ? (int32_t)j : -1;
+}
+
 }  // namespace
 
 static int maxscan(cudaStream_t st, int32_t *d, int64_t m, int32_t *tmp) {
@@ -225,11 +340,91 @@ static int maxscan(cudaStream_t st, int32_t *d, int64_t m, int32_t *tmp) {
     return FEM_OK;
 }
 
+// One episode by occurrence lists (variant 1: atomic compaction, 2: count,
+// scan, write).  *ok = false when a step's occurrences exceed `cap` (the
+// caller then counts the episode with the latest-start steps).
+static int count_occ_one(fem_ctx *ctx, const std::vector<PltItem> &its, int variant, int64_t cap, int32_t *s,
+                         int32_t *p, int32_t *s2, int32_t *p2, int32_t *cnt, int32_t *scan_tmp,
+                         unsigned long long *d_tot, int32_t *L, int32_t *V, int32_t *bm, int32_t *n1, int32_t *n2,
+                         int32_t *c1, int32_t *c2, PltItem *d_item, const int32_t *d_cand, uint32_t *d_counts,
+                         bool *ok, int64_t *launches) {
+    cudaStream_t st = ctx->stream;
+    *ok = true;
+    const int N = (int)its.size() + 1;
+    const unsigned g8 = (unsigned)(8 * ctx->n_sm);
+    auto grid = [&](int64_t m) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, g8)); };
+    int64_t m = its[0].fa;
+    const int32_t *ta0 = its[0].ttime + its[0].a_start;
+    if (m > cap) {
+        *ok = false;
+        return FEM_OK;
+    }
+    k_occ_init<<<grid(m), 256, 0, st>>>(ta0, m, s, p);
+    ++*launches;
+    for (int k = 0; k + 1 < N && m > 0; ++k) {
+        const PltItem &it = its[k];
+        const int32_t *ta = it.ttime + it.a_start, *tb = it.ttime + it.b_start;
+        unsigned long long tot = 0;
+        FEM_CUDA_TRY(cudaMemsetAsync(d_tot, 0, 8, st));
+        if (variant == 2) {
+            k_occ_count<<<grid(m + 1), 256, 0, st>>>(p, m, ta, tb, it.fb, it.lo, it.hi, cnt, d_tot);
+            FEM_CUDA_TRY(cudaMemcpyAsync(&tot, d_tot, 8, cudaMemcpyDeviceToHost, st));
+            FEM_CUDA_TRY(cudaStreamSynchronize(st));
+            if ((int64_t)tot > cap) {
+                *ok = false;
+                return FEM_OK;
+            }
+            FEM_TRY(scan_exclusive(st, cnt, m + 1, scan_tmp, nullptr, launches));
+            k_occ_write_scan<<<grid(m), 256, 0, st>>>(s, p, m, cnt, ta, tb, it.fb, it.lo, it.hi, cap, s2, p2);
+            *launches += 2;
+        } else {
+            k_occ_write_atomic<<<grid(m), 256, 0, st>>>(s, p, m, ta, tb, it.fb, it.lo, it.hi, cap, s2, p2, d_tot);
+            FEM_CUDA_TRY(cudaMemcpyAsync(&tot, d_tot, 8, cudaMemcpyDeviceToHost, st));
+            FEM_CUDA_TRY(cudaStreamSynchronize(st));
+            if ((int64_t)tot > cap) {
+                *ok = false;
+                return FEM_OK;
+            }
+            ++*launches;
+        }
+        std::swap(s, s2);
+        std::swap(p, p2);
+        m = (int64_t)tot;
+    }
+    // latest start per end event, then the overlap removal of the other path
+    const PltItem &last = its.back();
+    const int64_t fb = last.fb;
+    PltItem li = last;
+    li.base = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_item, &li, sizeof(PltItem), cudaMemcpyHostToDevice, st));
+    if (fb > 0) {
+        k_fill_i32<<<grid(fb), 256, 0, st>>>(L, fb, INT32_MIN);
+        if (m > 0) k_occ_final<<<grid(m), 256, 0, st>>>(s, p, m, L);
+        k_occ_flags<<<grid(fb), 256, 0, st>>>(L, fb, V);
+        FEM_TRY(maxscan(st, V, fb, bm));
+        int rounds = 0;
+        while ((int64_t(1) << rounds) < fb) ++rounds;
+        k_plt_next<<<grid(fb), 256, 0, st>>>(d_item, 1, fb, L, V, n1, c1);
+        for (int q = 0; q < rounds; ++q) {
+            k_plt_jump<<<grid(fb), 256, 0, st>>>(fb, n1, c1, n2, c2);
+            std::swap(n1, n2);
+            std::swap(c1, c2);
+        }
+        *launches += 6 + rounds;
+    }
+    k_plt_count<<<1, 32, 0, st>>>(d_item, 1, L, V, c1, d_cand, d_counts);
+    ++*launches;
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
 // Counts the candidates `work` (indices into the CSR arrays on the device)
-// by local tracking.  relaxed: every lower bound taken as 0.
+// by local tracking.  relaxed: every lower bound taken as 0.  variant 0:
+// latest start per event; 1 / 2: occurrence lists with atomic / count-scan-
+// write compaction.
 int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t *d_offs, const uint16_t *d_types,
               const int32_t *d_lo, const int32_t *d_hi, const uint32_t *d_rec, const std::vector<int32_t> &work,
-              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms) {
+              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms, int variant) {
     cudaStream_t st = ctx->stream;
     const int64_t C = (int64_t)work.size();
     if (C == 0) return FEM_OK;
@@ -290,35 +485,90 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
     }
     float ms_total = 0.f;
     for (int N = 2; N <= FEM_MAX_NODES; ++N) {
-        const std::vector<int32_t> &grp = by_n[N];
+        std::vector<int32_t> grp = by_n[N];
         if (grp.empty()) continue;
-        const int G = (int)grp.size();
-        // per step k: items and array sizes
-        std::vector<std::vector<PltItem>> steps(N - 1, std::vector<PltItem>(G));
-        std::vector<int64_t> tot(N - 1, 0);
-        for (int k = 0; k + 1 < N; ++k) {
-            int64_t base = 0;
-            for (int e = 0; e < G; ++e) {
-                const int32_t w = grp[e];
-                const int64_t o = offs[w - wmin];
-                const int64_t eo = o - w;
-                const uint32_t r = crec[w - wmin];
-                const std::vector<int64_t> &tf = toff[r];
-                const uint16_t A = types[o - n0 + k], B = types[o - n0 + k + 1];
-                PltItem &it = steps[k][e];
-                it.a_start = tf[A];
-                it.fa = (int32_t)(tf[A + 1] - tf[A]);
-                it.b_start = tf[B];
-                it.fb = (int32_t)(tf[B + 1] - tf[B]);
-                it.prev_base = k > 0 ? steps[k - 1][e].base : 0;
-                it.base = base;
-                it.ttime = recs[r]->d_ttime;
-                it.lo = relaxed ? 0 : lo[eo - e0 + k];
-                it.hi = hi[eo - e0 + k];
-                base += it.fb;
+        // per step k: items and array sizes for the episodes in grp
+        std::vector<std::vector<PltItem>> steps;
+        std::vector<int64_t> tot;
+        auto build_steps = [&]() {
+            const int G = (int)grp.size();
+            steps.assign(N - 1, std::vector<PltItem>(G));
+            tot.assign(N - 1, 0);
+            for (int k = 0; k + 1 < N; ++k) {
+                int64_t base = 0;
+                for (int e = 0; e < G; ++e) {
+                    const int32_t w = grp[e];
+                    const int64_t o = offs[w - wmin];
+                    const int64_t eo = o - w;
+                    const uint32_t r = crec[w - wmin];
+                    const std::vector<int64_t> &tf = toff[r];
+                    const uint16_t A = types[o - n0 + k], B = types[o - n0 + k + 1];
+                    PltItem &it = steps[k][e];
+                    it.a_start = tf[A];
+                    it.fa = (int32_t)(tf[A + 1] - tf[A]);
+                    it.b_start = tf[B];
+                    it.fb = (int32_t)(tf[B + 1] - tf[B]);
+                    it.prev_base = k > 0 ? steps[k - 1][e].base : 0;
+                    it.base = base;
+                    it.ttime = recs[r]->d_ttime;
+                    it.lo = relaxed ? 0 : lo[eo - e0 + k];
+                    it.hi = hi[eo - e0 + k];
+                    base += it.fb;
+                }
+                tot[k] = base;
             }
-            tot[k] = base;
+        };
+        build_steps();
+        if (variant != 0) {
+            // occurrence lists, one episode at a time
+            const int G = (int)grp.size();
+            TmpDev to(ctx);
+            int64_t fmax = 1;
+            for (int k = 0; k + 1 < N; ++k)
+                for (const PltItem &it : steps[k]) fmax = std::max<int64_t>(fmax, std::max(it.fa, it.fb));
+            const int64_t cap = kOccCap;
+            int32_t *s_, *p_, *s2, *p2, *cnt, *stmp, *L, *V, *bm1, *n1o, *n2o, *c1o, *c2o, *dc;
+            unsigned long long *dtot;
+            PltItem *ditem;
+            FEM_TRY(to.get(&s_, cap));
+            FEM_TRY(to.get(&p_, cap));
+            FEM_TRY(to.get(&s2, cap));
+            FEM_TRY(to.get(&p2, cap));
+            FEM_TRY(to.get(&cnt, cap + 1));
+            FEM_TRY(to.get(&stmp, (cap + 1) / 1024 + 2));
+            FEM_TRY(to.get(&L, fmax));
+            FEM_TRY(to.get(&V, fmax));
+            FEM_TRY(to.get(&bm1, fmax / kMsBlock + 2));
+            FEM_TRY(to.get(&n1o, fmax));
+            FEM_TRY(to.get(&n2o, fmax));
+            FEM_TRY(to.get(&c1o, fmax));
+            FEM_TRY(to.get(&c2o, fmax));
+            FEM_TRY(to.get(&dtot, 1));
+            FEM_TRY(to.get(&ditem, 1));
+            FEM_TRY(to.get(&dc, G));
+            FEM_CUDA_TRY(cudaMemcpyAsync(dc, grp.data(), 4 * G, cudaMemcpyHostToDevice, st));
+            std::vector<int32_t> rest;  // episodes whose occurrence lists overflowed
+            cudaEventRecord(ctx->ev0, st);
+            for (int e = 0; e < G; ++e) {
+                std::vector<PltItem> its(N - 1);
+                for (int k = 0; k + 1 < N; ++k) its[k] = steps[k][e];
+                bool ok = true;
+                FEM_TRY(count_occ_one(ctx, its, variant, cap, s_, p_, s2, p2, cnt, stmp, dtot, L, V, bm1, n1o, n2o,
+                                      c1o, c2o, ditem, dc + e, d_counts, &ok, &stats->kernel_launches));
+                if (!ok) rest.push_back(grp[e]);
+            }
+            cudaEventRecord(ctx->ev1, st);
+            FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            ms_total += ms;
+            if (rest.empty()) continue;
+            // the latest-start steps below count the rest
+            stats->fallback_recounts += (int64_t)rest.size();
+            grp.swap(rest);
+            build_steps();
         }
+        const int G = (int)grp.size();
         int64_t tmax = 1;
         for (int64_t t : tot) tmax = std::max(tmax, t);
         TmpDev tmp(ctx);

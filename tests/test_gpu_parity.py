@@ -98,14 +98,15 @@ def test_golden_cases_on_gpu(fb, ctx):
         st.free()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 4, 5, 6])
 @pytest.mark.parametrize("segments,lanes,tile", [(0, 0, 0), (1, 32, 256), (7, 64, 512), (64, 256, 1024),
                                                   (300, 96, 4096)])
 def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
     """Many random episodes (sizes 1-6, lower bounds 0..6) over random streams
     with frequent equal times, under several segment / CTA / tile settings,
     with the tiled (1) and the sparse (2) counting kernel and with local
-    tracking (4; segment settings do not apply to it)."""
+    tracking (4: latest starts; 5 / 6: occurrence lists compacted by atomics
+    / count-scan-write; segment settings do not apply to local tracking)."""
     r = synth.Rng(99, segments + 7)
     ctx.set_tuning(lanes_per_cta=lanes, segments=segments, tile_events=tile, kernel=kernel)
     try:
@@ -131,7 +132,7 @@ def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
         ctx.reset_tuning()
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5, 6])
 @pytest.mark.parametrize("segments", [0, 33, 1000, 4099])
 def test_few_episodes_many_segments(fb, ctx, segments, kernel):
     """Few episodes over the 1M-event mid stream cut into up to ~4k segments:
@@ -183,7 +184,7 @@ def test_upper_bound_is_relaxed_count(fb, ctx):
     st.free()
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5, 6])
 def test_bursty_stream_mixed_sizes(fb, ctx, kernel):
     """Network bursts (dense windows) with sizes 2-8 and the 4-bin set."""
     s = synth.bursty_60(0xFE0003, 150_000)
@@ -490,6 +491,34 @@ def test_local_tracking_relaxed_bound_and_mining(fb, ctx):
         st0.free()
     finally:
         ctx.reset_tuning()
+    st.free()
+
+
+@pytest.mark.parametrize("kernel", [5, 6])
+def test_occurrence_lists_overflow_falls_back(fb, ctx, kernel):
+    """Occurrence-list local tracking: an episode whose partial occurrences
+    outgrow the list capacity (one type, 100 successors per event in the
+    window: 2e5 x 100^k entries) is recounted with latest starts; a small
+    episode next to it stays on the lists; both equal the oracle."""
+    n = 200_000
+    ty = np.zeros(n, np.uint16)
+    ty[1::7] = 1
+    tm = np.arange(n, dtype=np.int32)
+    st = ctx.load_stream(ty, tm, 2)
+    offs = np.array([0, 4, 6], np.int64)
+    ct = np.array([0, 0, 0, 0, 0, 1], np.uint16)
+    lo = np.array([0, 0, 0, 2], np.int32)
+    hi = np.array([100, 100, 100, 9], np.int32)
+    want = oracle_counts(ty, tm, offs, ct, lo, hi)
+    ctx.set_tuning(kernel=kernel)
+    try:
+        got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+        stats = ctx.last_stats()
+    finally:
+        ctx.reset_tuning()
+    assert np.array_equal(got, want), (got, want)
+    assert stats["fallback_recounts"] == 1
+    assert want.min() > 0
     st.free()
 
 
