@@ -244,6 +244,40 @@ int fem_count_episodes_noalloc(const uint16_t *types, const int32_t *times, int6
                                const uint16_t *ep_types, const int32_t *lo, const int32_t *hi, int64_t n_cand,
                                uint32_t *counts, void *cuda_stream);
 
+/* ---- counting over a growing stream -------------------------------------- */
+
+/* Exact counts kept while a recording grows by appends (section "Future
+ * Work" names counting over arriving data; here the counts stay exact).
+ * After any sequence of appends, fem_session_counts returns what
+ * fem_count_episodes would return on the concatenation of every appended
+ * chunk.  The session keeps, per episode, its count and the time of the
+ * last occurrence kept by the greedy of Algorithm 1, plus the tail of the
+ * stream that later occurrences can reach back into: the events at or after
+ * t_last - S, S = the largest sum of upper bounds (hi) over the episodes.
+ * Each append counts the tail followed by the new events by node-by-node
+ * local tracking and keeps only occurrences that end at a new event.
+ *   fem_session_create: candidates as in fem_cands (host or device, copied;
+ *     FEM_ERR_INVAL on a malformed candidate or a type >= n_types); n_types in
+ *     [1, 8192] is the alphabet of every chunk.
+ *   fem_session_append: types[n] / times[n] (host, or device when
+ *     ptr_is_device) under fem_load_stream's rules, checked together with the
+ *     retained tail: the first new event may not precede the last appended
+ *     one (FEM_ERR_UNSORTED) nor repeat a (type, time) pair of it
+ *     (FEM_ERR_DUP); on those errors, and on FEM_ERR_INVAL / FEM_ERR_RANGE, the
+ *     session is unchanged.  n = 0 is a no-op.  A FEM_ERR_NOMEM or
+ *     FEM_ERR_CUDA during counting leaves the counts undefined: destroy the
+ *     session.  The retained tail plus the chunk must stay below 2^30 events.
+ *   fem_session_counts: uint32 counts[n_cand] (host or device) in input order.
+ *   fem_session_info: events appended so far and events in the retained tail.
+ * Calls on one session are serialised by its context. */
+typedef struct fem_session fem_session;
+int fem_session_create(fem_ctx *ctx, const fem_cands *c, uint32_t n_types, fem_session **out);
+int fem_session_append(fem_session *s, const uint16_t *types, const int32_t *times, int64_t n,
+                       int ptr_is_device);
+int fem_session_counts(fem_session *s, uint32_t *counts, int out_is_device);
+int fem_session_info(const fem_session *s, int64_t *events_seen, int64_t *tail_events);
+void fem_session_destroy(fem_session *s);
+
 /* ---- level-wise mining --------------------------------------------------- */
 
 /* Level-wise frequent-episode discovery (section "Temporal Data Mining"):

@@ -101,6 +101,11 @@ _SIGS = {
                                 ctypes.POINTER(U64)]),
     "fem_server_wait": (I32, [VP, U64, I32, ctypes.POINTER(VP), ctypes.POINTER(fem_job_info)]),
     "fem_server_destroy": (None, [VP]),
+    "fem_session_create": (I32, [VP, ctypes.POINTER(fem_cands), U32, ctypes.POINTER(VP)]),
+    "fem_session_append": (I32, [VP, VP, VP, I64, I32]),
+    "fem_session_counts": (I32, [VP, VP, I32]),
+    "fem_session_info": (I32, [VP, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+    "fem_session_destroy": (None, [VP]),
     "fem_strerror": (ctypes.c_char_p, [I32]),
     "fem_version": (ctypes.c_char_p, []),
 }
@@ -247,6 +252,9 @@ class Context:
               "fem_count_batch")
         return keep
 
+    def session(self, cands: Cands, n_types: int) -> "Session":
+        return Session(self, cands, n_types)
+
     def mine_levelwise(self, streams, bins, thresholds, max_size: int) -> "Result":
         arr = (VP * len(streams))(*[s.h for s in streams])
         blo = np.ascontiguousarray([b[0] for b in bins], np.int32)
@@ -257,6 +265,42 @@ class Context:
                                  len(bins), VP(thr.ctypes.data), int(max_size), ctypes.byref(h)),
               "fem_mine_levelwise")
         return Result(h, len(streams), int(max_size))
+
+
+class Session:
+    """Exact counts of a fixed candidate set over a stream that grows by
+    appends (fem_session_*): counts() equals count_episodes on the
+    concatenation of every appended chunk."""
+
+    def __init__(self, ctx: Context, cands: Cands, n_types: int):
+        self.ctx, self.n = ctx, cands.n
+        self.h = VP()
+        check(fem_session_create(ctx.h, ctypes.byref(cands.c), int(n_types), ctypes.byref(self.h)),
+              "fem_session_create")
+
+    def append(self, types, times):
+        tp, d0, k0 = _ptr(types, np.uint16)
+        mp, d1, k1 = _ptr(times, np.int32)
+        if d0 != d1:
+            raise ValueError("types and times must both be host or both be device")
+        check(fem_session_append(self.h, tp, mp, int(len(types)), d0), "fem_session_append")
+
+    def counts(self, out=None):
+        if out is None:
+            out = np.zeros(max(self.n, 1), np.uint32)[: self.n]
+        op, od, keep = _ptr(out, np.uint32)
+        check(fem_session_counts(self.h, op, od), "fem_session_counts")
+        return keep
+
+    def info(self):
+        seen, tail = I64(), I64()
+        check(fem_session_info(self.h, ctypes.byref(seen), ctypes.byref(tail)), "fem_session_info")
+        return int(seen.value), int(tail.value)
+
+    def close(self):
+        if self.h:
+            fem_session_destroy(self.h)
+            self.h = None
 
 
 class Stream:

@@ -232,7 +232,8 @@ __global__ void k_validate(const uint16_t *__restrict__ ty, const int32_t *__res
 }
 
 // Level 1 (a 1-node episode's count is its frequency): per-type histogram,
-// privatised in shared memory when the alphabet fits.
+// privatised in shared memory when the alphabet fits.  It runs before the
+// host has read the validation result, so out-of-range types are skipped.
 __global__ void k_histogram(const uint16_t *__restrict__ ty, int64_t n, uint32_t n_types,
                             uint32_t *__restrict__ freq) {
     extern __shared__ uint32_t h[];
@@ -243,6 +244,7 @@ __global__ void k_histogram(const uint16_t *__restrict__ ty, int64_t n, uint32_t
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint16_t a = ty[i];
+        if (a >= n_types) continue;
         if (priv)
             atomicAdd(&h[a], 1u);
         else

@@ -201,13 +201,24 @@ struct TmpDev {
     }
 };
 
+// Counting continued over appended events: the recording is a retained
+// tail of earlier events followed by the new ones; tail_cnt[a] = events of
+// type a in the tail (their ends were counted before); d_prev[c] = time of
+// candidate c's last kept end (INT32_MIN: none), updated.  Counts are added.
+struct PltSession {
+    const std::vector<int64_t> *tail_cnt;
+    int32_t *d_prev;
+};
+
 // Counting by node-by-node local tracking (fem_plt.cu): the candidates
 // `work` of the device CSR arrays; relaxed = every lower bound taken as 0;
 // variant 0 = latest start per event, 1 / 2 = occurrence lists compacted with
-// atomics / count-scan-write.
+// atomics / count-scan-write; sess (variant 0, one recording): continue the
+// counts over appended events.
 int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t *d_offs, const uint16_t *d_types,
               const int32_t *d_lo, const int32_t *d_hi, const uint32_t *d_rec, const std::vector<int32_t> &work,
-              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms, int variant);
+              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms, int variant,
+              const PltSession *sess = nullptr);
 
 // Scratch slot ids.
 enum Slot : int {

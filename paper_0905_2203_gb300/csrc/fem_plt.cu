@@ -34,6 +34,7 @@ struct PltItem {
     int64_t base;              // first position of B's values in this step's arrays
     const int32_t *ttime;      // the recording's per-type times
     int32_t lo, hi;
+    int32_t j0;                // last step: first B position whose end may be counted
 };
 
 __device__ __forceinline__ int item_of(const PltItem *items, int n_items, int64_t g) {
@@ -169,7 +170,7 @@ __device__ __forceinline__ int32_t plt_pm(const int32_t *L, const int32_t *V, in
 // valid ends.
 __global__ void k_plt_next(const PltItem *__restrict__ items, int n_items, int64_t total,
                            const int32_t *__restrict__ L, const int32_t *__restrict__ V, int32_t *__restrict__ nxt,
-                           int32_t *__restrict__ cnt) {
+                           int32_t *__restrict__ cnt, int32_t *__restrict__ lst) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const PltItem it = items[item_of(items, n_items, g)];
         const int64_t j = g - it.base;
@@ -186,32 +187,56 @@ __global__ void k_plt_next(const PltItem *__restrict__ items, int n_items, int64
         }
         nxt[g] = nx;
         cnt[g] = c;
+        if (lst) lst[g] = (int32_t)g;
     }
 }
 
-// One pointer-jumping round: cnt'[g] = cnt[g] + cnt[nxt[g]], nxt'[g] = nxt[nxt[g]].
+// One pointer-jumping round: cnt'[g] = cnt[g] + cnt[nxt[g]], nxt'[g] =
+// nxt[nxt[g]], and (optionally) the chain's last end lst'[g] = lst[nxt[g]].
 __global__ void k_plt_jump(int64_t total, const int32_t *__restrict__ nxt, const int32_t *__restrict__ cnt,
-                           int32_t *__restrict__ nxt2, int32_t *__restrict__ cnt2) {
+                           int32_t *__restrict__ nxt2, int32_t *__restrict__ cnt2, const int32_t *__restrict__ lst,
+                           int32_t *__restrict__ lst2) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int32_t n = nxt[g];
         cnt2[g] = cnt[g] + (n >= 0 ? cnt[n] : 0);
         nxt2[g] = n >= 0 ? nxt[n] : -1;
+        if (lst) lst2[g] = n >= 0 ? lst[n] : lst[g];
     }
 }
 
-// count = chain length from the first valid end (first j with PM(j) > -inf).
+// count = chain length from the first kept end: the first j >= j0 with
+// PM(j) > prev, prev = the previous kept end (-inf without `prev`).  With
+// `prev` (appended events) the count is added and prev becomes the time of
+// the chain's last end; earlier ends (j < j0) have latest starts <= prev, so
+// PM over them never passes prev.
 __global__ void k_plt_count(const PltItem *__restrict__ items, int n_items, const int32_t *__restrict__ L,
                             const int32_t *__restrict__ V, const int32_t *__restrict__ cnt,
-                            const int32_t *__restrict__ cand, uint32_t *__restrict__ counts) {
+                            const int32_t *__restrict__ cand, uint32_t *__restrict__ counts,
+                            int32_t *__restrict__ prev, const int32_t *__restrict__ lst) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_items) return;
     const PltItem it = items[e];
-    int64_t lo = 0, hi = it.fb;
+    const int32_t pv = prev ? prev[cand[e]] : INT32_MIN;
+    int64_t lo = it.j0, hi = it.fb;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (plt_pm(L, V, it.base, mid) != INT32_MIN) hi = mid; else lo = mid + 1;
+        if (plt_pm(L, V, it.base, mid) > pv) hi = mid; else lo = mid + 1;
     }
-    counts[cand[e]] = lo < it.fb ? (uint32_t)cnt[it.base + lo] : 0u;
+    const bool hit = lo < it.fb && plt_pm(L, V, it.base, lo) > pv;
+    if (!prev) {
+        counts[cand[e]] = hit ? (uint32_t)cnt[it.base + lo] : 0u;
+    } else if (hit) {
+        counts[cand[e]] += (uint32_t)cnt[it.base + lo];
+        prev[cand[e]] = it.ttime[it.b_start + (lst[it.base + lo] - it.base)];
+    }
+}
+
+// 1-node episodes: the count is the type's number of (new) events.
+__global__ void k_n1_counts(const int32_t *__restrict__ cand, const uint32_t *__restrict__ val, int n,
+                            uint32_t *__restrict__ counts, int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    counts[cand[i]] = (accumulate ? counts[cand[i]] : 0u) + val[i];
 }
 
 // ---- the section's own form: every partial occurrence, node by node ------
@@ -404,15 +429,15 @@ static int count_occ_one(fem_ctx *ctx, const std::vector<PltItem> &its, int vari
         FEM_TRY(maxscan(st, V, fb, bm));
         int rounds = 0;
         while ((int64_t(1) << rounds) < fb) ++rounds;
-        k_plt_next<<<grid(fb), 256, 0, st>>>(d_item, 1, fb, L, V, n1, c1);
+        k_plt_next<<<grid(fb), 256, 0, st>>>(d_item, 1, fb, L, V, n1, c1, nullptr);
         for (int q = 0; q < rounds; ++q) {
-            k_plt_jump<<<grid(fb), 256, 0, st>>>(fb, n1, c1, n2, c2);
+            k_plt_jump<<<grid(fb), 256, 0, st>>>(fb, n1, c1, n2, c2, nullptr, nullptr);
             std::swap(n1, n2);
             std::swap(c1, c2);
         }
         *launches += 6 + rounds;
     }
-    k_plt_count<<<1, 32, 0, st>>>(d_item, 1, L, V, c1, d_cand, d_counts);
+    k_plt_count<<<1, 32, 0, st>>>(d_item, 1, L, V, c1, d_cand, d_counts, nullptr, nullptr);
     ++*launches;
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
@@ -424,7 +449,9 @@ static int count_occ_one(fem_ctx *ctx, const std::vector<PltItem> &its, int vari
 // write compaction.
 int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t *d_offs, const uint16_t *d_types,
               const int32_t *d_lo, const int32_t *d_hi, const uint32_t *d_rec, const std::vector<int32_t> &work,
-              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms, int variant) {
+              bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms, int variant,
+              const PltSession *sess) {
+    if (sess && (variant != 0 || relaxed || recs.size() != 1)) return FEM_ERR_INVAL;
     cudaStream_t st = ctx->stream;
     const int64_t C = (int64_t)work.size();
     if (C == 0) return FEM_OK;
@@ -461,6 +488,18 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
     std::vector<int32_t> n1_cand;
     double relevant = 0, counted = 0;
     for (int32_t w : work) {
+        // the checks the per-episode kernels make on the device
+        const int64_t o = offs[w - wmin], N = offs[w - wmin + 1] - o;
+        const uint32_t r = crec[w - wmin];
+        if (N < 1 || N > FEM_MAX_NODES || r >= recs.size()) return FEM_ERR_INVAL;
+        for (int64_t k = 0; k < N; ++k)
+            if (types[o - n0 + k] >= recs[r]->n_types) return FEM_ERR_INVAL;
+        for (int64_t k = 0; k + 1 < N; ++k) {
+            const int64_t eo = o - w - e0 + k;
+            if (lo[eo] < 0 || lo[eo] >= hi[eo]) return FEM_ERR_INVAL;
+        }
+    }
+    for (int32_t w : work) {
         const int64_t o = offs[w - wmin], N = offs[w - wmin + 1] - o;
         const uint32_t r = crec[w - wmin];
         counted += (double)recs[r]->n;
@@ -471,17 +510,27 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
         }
         if (N == 1) {
             const uint16_t a = types[o - n0];
+            const int64_t old = sess ? (*sess->tail_cnt)[a] : 0;
             n1_cand.push_back(w);
-            n1_counts.push_back((uint32_t)(tf[a + 1] - tf[a]));
+            n1_counts.push_back((uint32_t)(tf[a + 1] - tf[a] - old));
         } else {
             by_n[N].push_back(w);
         }
     }
     if (!n1_cand.empty()) {
-        // the count of a 1-node episode is the type's frequency (distinct times)
-        for (size_t i = 0; i < n1_cand.size(); ++i)
-            FEM_CUDA_TRY(cudaMemcpyAsync(d_counts + n1_cand[i], &n1_counts[i], 4, cudaMemcpyHostToDevice, st));
-        FEM_CUDA_TRY(cudaStreamSynchronize(st));
+        // the count of a 1-node episode is the type's frequency (distinct
+        // times); appended events add their own
+        TmpDev t1(ctx);
+        int32_t *dc;
+        uint32_t *dv;
+        const int n1n = (int)n1_cand.size();
+        FEM_TRY(t1.get(&dc, n1n));
+        FEM_TRY(t1.get(&dv, n1n));
+        FEM_CUDA_TRY(cudaMemcpyAsync(dc, n1_cand.data(), 4 * n1n, cudaMemcpyHostToDevice, st));
+        FEM_CUDA_TRY(cudaMemcpyAsync(dv, n1_counts.data(), 4 * n1n, cudaMemcpyHostToDevice, st));
+        k_n1_counts<<<(n1n + 255) / 256, 256, 0, st>>>(dc, dv, n1n, d_counts, sess ? 1 : 0);
+        FEM_CUDA_TRY(cudaGetLastError());
+        stats->kernel_launches += 1;
     }
     float ms_total = 0.f;
     for (int N = 2; N <= FEM_MAX_NODES; ++N) {
@@ -513,6 +562,7 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
                     it.ttime = recs[r]->d_ttime;
                     it.lo = relaxed ? 0 : lo[eo - e0 + k];
                     it.hi = hi[eo - e0 + k];
+                    it.j0 = sess && k + 2 == N ? (int32_t)(*sess->tail_cnt)[B] : 0;
                     base += it.fb;
                 }
                 tot[k] = base;
@@ -607,16 +657,24 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
         for (const PltItem &it : steps[N - 2]) fmax = std::max<int64_t>(fmax, it.fb);
         int rounds = 0;
         while ((int64_t(1) << rounds) < fmax) ++rounds;
+        // appended events: also the last end of every chain
+        int32_t *l1 = nullptr, *l2 = nullptr;
+        if (sess) {
+            FEM_TRY(tmp.get(&l1, tmax));
+            FEM_TRY(tmp.get(&l2, tmax));
+        }
         if (T > 0) {
             const unsigned gsz = (unsigned)std::max<int64_t>(1, std::min<int64_t>((T + 255) / 256, 8 * ctx->n_sm));
-            k_plt_next<<<gsz, 256, 0, st>>>(last, G, T, La, Va, n1, c1);
+            k_plt_next<<<gsz, 256, 0, st>>>(last, G, T, La, Va, n1, c1, l1);
             for (int q = 0; q < rounds; ++q) {
-                k_plt_jump<<<gsz, 256, 0, st>>>(T, n1, c1, n2, c2);
+                k_plt_jump<<<gsz, 256, 0, st>>>(T, n1, c1, n2, c2, l1, l2);
                 std::swap(n1, n2);
                 std::swap(c1, c2);
+                std::swap(l1, l2);
             }
         }
-        k_plt_count<<<(G + 127) / 128, 128, 0, st>>>(last, G, La, Va, c1, d_cand, d_counts);
+        k_plt_count<<<(G + 127) / 128, 128, 0, st>>>(last, G, La, Va, c1, d_cand, d_counts,
+                                                     sess ? sess->d_prev : nullptr, l1);
         cudaEventRecord(ctx->ev1, st);
         FEM_CUDA_TRY(cudaGetLastError());
         FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));

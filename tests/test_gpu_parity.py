@@ -64,6 +64,10 @@ def test_stream_validation_errors(fb, ctx):
     with pytest.raises(fb.FemError) as e:
         ctx.load_stream(np.array([0, 2], np.uint16), np.array([0, 1], np.int32), 2)
     assert e.value.status == fb.FEM_ERR_INVAL
+    for nt in (32, 128, 12288, 12289):  # a type just past the alphabet, every histogram layout
+        with pytest.raises(fb.FemError) as e:
+            ctx.load_stream(np.array([0, nt, 1], np.uint16), np.array([0, 1, 2], np.int32), nt)
+        assert e.value.status == fb.FEM_ERR_INVAL
     with pytest.raises(fb.FemError) as e:
         ctx.load_stream(np.array([0, 1], np.uint16), np.array([-3, 1], np.int32), 2)
     assert e.value.status == fb.FEM_ERR_RANGE
@@ -537,4 +541,134 @@ def test_result_level_arrays_match_tuples(fb, ctx):
             assert tuple(types[o:p].tolist()) == E
             assert tuple(lo[o - c:p - c - 1].tolist()) == l and tuple(hi[o - c:p - c - 1].tolist()) == h
     res.free()
+    st.free()
+
+
+def _chunks(r, n, n_chunks):
+    """Random cut points (some chunks empty, cuts between equal times too)."""
+    cuts = np.sort(r.integers(0, n, n_chunks - 1))
+    return np.concatenate([[0], cuts, [n]]).astype(np.int64)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_session_appends_equal_prefix_counts(fb, ctx, seed):
+    """Counting over a growing stream: after every append the session's
+    counts equal the oracle's counts over the prefix appended so far, for
+    episodes of 1-6 nodes with lower bounds 0..6 over random streams with
+    frequent equal times (cuts fall between equal times, some chunks are
+    empty)."""
+    r = synth.Rng(0x5E55, seed)
+    n_types = 5
+    n = 4000
+    ty, tm = synth.tiny_random_stream(2000 + seed, n, n_types, 3 * n)
+    nc = 400
+    sizes = r.integers(1, 6, nc)
+    offs = np.zeros(nc + 1, np.int64)
+    offs[1:] = np.cumsum(sizes)
+    ct = r.integers(0, n_types - 1, int(offs[-1])).astype(np.uint16)
+    ne = int(offs[-1]) - nc
+    lo = r.integers(0, 6, ne).astype(np.int32)
+    hi = (lo + r.integers(1, 30, ne)).astype(np.int32)
+    sess = ctx.session(fb.Cands(offs, ct, lo, hi), n_types)
+    try:
+        cuts = _chunks(r, len(ty), 12)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            sess.append(ty[a:b], tm[a:b])
+            got = sess.counts().astype(np.int64)
+            want = oracle_counts(ty[:b], tm[:b], offs, ct, lo, hi)
+            bad = np.nonzero(got != want)[0]
+            assert bad.size == 0, (int(b), bad[:5], got[bad[:5]], want[bad[:5]])
+        seen, tail = sess.info()
+        assert seen == len(ty) and 0 < tail < len(ty)
+    finally:
+        sess.close()
+
+
+def test_session_errors_leave_counts_unchanged(fb, ctx):
+    """An append that goes back in time or repeats a (type, time) pair across
+    the join is refused and changes nothing; counting then continues exactly.
+    A gap longer than every episode's span shrinks the retained tail to the
+    events at the last time."""
+    s, cfg = synth.c1_tiny()
+    offs, ct, lo, hi = synth.random_candidates(21, 300, s.n_types, 1, 5, [(0, 5), (3, 9)], s.chains, 0.3)
+    sess = ctx.session(fb.Cands(offs, ct, lo, hi), s.n_types)
+    try:
+        h = len(s.types) // 2
+        sess.append(s.types[:h], s.times[:h])
+        before = sess.counts().copy()
+        last_t = int(s.times[h - 1])
+        with pytest.raises(fb.FemError) as e:
+            sess.append(np.array([0], np.uint16), np.array([last_t - 1], np.int32))
+        assert e.value.status == fb.FEM_ERR_UNSORTED
+        with pytest.raises(fb.FemError) as e:
+            sess.append(np.array([s.types[h - 1]], np.uint16), np.array([last_t], np.int32))
+        assert e.value.status == fb.FEM_ERR_DUP
+        with pytest.raises(fb.FemError) as e:
+            sess.append(np.array([s.n_types], np.uint16), np.array([last_t + 1], np.int32))
+        assert e.value.status == fb.FEM_ERR_INVAL
+        assert np.array_equal(sess.counts(), before)
+        sess.append(s.types[h:], s.times[h:])
+        assert np.array_equal(sess.counts().astype(np.int64),
+                              oracle_counts(s.types, s.times, offs, ct, lo, hi))
+        # a long gap: only the events at the last time stay in the tail
+        t_end = int(s.times[-1])
+        gap_ty = np.array([1, 2], np.uint16)
+        gap_tm = np.array([t_end + 10**6, t_end + 10**6], np.int32)
+        sess.append(gap_ty, gap_tm)
+        assert sess.info()[1] == 2
+        all_ty = np.concatenate([s.types, gap_ty])
+        all_tm = np.concatenate([s.times, gap_tm])
+        assert np.array_equal(sess.counts().astype(np.int64), oracle_counts(all_ty, all_tm, offs, ct, lo, hi))
+    finally:
+        sess.close()
+    with pytest.raises(fb.FemError) as e:
+        ctx.session(fb.Cands(np.array([0, 2]), np.array([0, 1], np.uint16), np.array([5], np.int32),
+                             np.array([5], np.int32)), 4)
+    assert e.value.status == fb.FEM_ERR_INVAL
+
+
+def test_session_long_stream_device_chunks(fb, ctx):
+    """The 1M-event mid stream appended in ten chunks of device tensors, 48
+    episodes of 2-6 nodes: counts after the 3rd and the last chunk equal the
+    oracle's."""
+    import torch
+    s, cfg = synth.c2_mid()
+    offs, ct, lo, hi = synth.random_candidates(0xFE0102, 48, s.n_types, 2, 6, cfg["bins"], s.chains, 0.5)
+    sess = ctx.session(fb.Cands(offs, ct, lo, hi), s.n_types)
+    try:
+        dty = torch.from_numpy(s.types.astype(np.int16)).cuda()
+        dtm = torch.from_numpy(s.times).cuda()
+        cuts = np.linspace(0, len(s.types), 11).astype(np.int64)
+        for i, (a, b) in enumerate(zip(cuts[:-1], cuts[1:])):
+            sess.append(dty[a:b], dtm[a:b])
+            if i in (2, 9):
+                want = oracle_counts(s.types[:b], s.times[:b], offs, ct, lo, hi)
+                assert np.array_equal(sess.counts().astype(np.int64), want), i
+                assert want.max() > 0
+        out = torch.zeros(48, dtype=torch.int32, device="cuda")
+        sess.counts(out)
+        assert np.array_equal(out.cpu().numpy().astype(np.int64),
+                              oracle_counts(s.types, s.times, offs, ct, lo, hi))
+    finally:
+        sess.close()
+
+
+@pytest.mark.parametrize("kernel", [4, 5, 6])
+def test_local_tracking_rejects_malformed_candidates(fb, ctx, kernel):
+    """Local tracking checks candidates like the per-episode kernels do."""
+    s, _ = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    bad = [
+        (np.array([0, 2]), np.array([0, 1]), np.array([5]), np.array([5])),
+        (np.array([0, 2]), np.array([0, 1]), np.array([-1]), np.array([5])),
+        (np.array([0, 2]), np.array([0, 40]), np.array([0]), np.array([5])),
+    ]
+    ctx.set_tuning(kernel=kernel)
+    try:
+        for offs, ct, lo, hi in bad:
+            with pytest.raises(fb.FemError) as e:
+                ctx.count_episodes(st, fb.Cands(offs, ct, lo, hi))
+            assert e.value.status == fb.FEM_ERR_INVAL
+    finally:
+        ctx.reset_tuning()
     st.free()
