@@ -18,6 +18,9 @@ Contents
                      Data Mining": level 1 = event frequencies, level N
                      candidates joined from frequent (N-1)-episodes, counted
                      with O1, kept when count > threshold.
+  coarse_bound       (submodule, plain Python) the coarse-tick upper bound
+                     on the count, written from its definition; pinned in
+                     tests/test_oracle_coarse_bound.py.
 
 Parity status: O1, O2 and O3 are pinned against each other, against closed
 forms and against invariants (tests/test_oracle_pins.py) and the pins are
