@@ -216,6 +216,27 @@ int fem_count_episodes_plain(fem_ctx *ctx, const fem_stream *s, const fem_cands 
 int fem_upper_bound(fem_ctx *ctx, const fem_stream *s, const fem_cands *c, uint32_t *ub,
                     int out_is_device);
 
+/* Coarse-tick upper bound: ub[c] >= count(c), cheaper than the count on
+ * long streams (a pre-pass for pruning, section "Temporal Data Mining").
+ * Time is cut into ticks of w units, tick(t) = floor(t / w); an edge (lo, hi]
+ * joins ticks whose difference is in [floor((lo + 1) / w),
+ * floor((hi + w - 1) / w)].  With M_1 = the ticks holding an E_1 event and
+ * M_{k+1} = the ticks holding an E_{k+1} event reachable from M_k, ub[c] is
+ * the number of E_N events whose tick is in M_N: every event that ends an
+ * occurrence is counted, and non-overlapped occurrences end at distinct
+ * events.  With w = 1 it is exactly the number of events that end at least
+ * one occurrence; a 1-node episode gets its frequency.
+ *   tick          0 = choose: the smallest w with hi <= 31 w for every edge,
+ *                 doubled while the stream's tables (2 bits per tick and
+ *                 type, kept with the stream) would pass 256 MiB; else the
+ *                 w to use, which must satisfy hi <= 31 w (FEM_ERR_INVAL).
+ *   ub            uint32[n_cand], host or device (out_is_device).
+ *   tick_used     optional: receives w.
+ * Errors: FEM_ERR_INVAL on a malformed candidate or an alphabet above 8192
+ * types, FEM_ERR_NOMEM, FEM_ERR_CUDA. */
+int fem_upper_bound_coarse(fem_ctx *ctx, const fem_stream *s, const fem_cands *c, int32_t tick, uint32_t *ub,
+                           int out_is_device, int32_t *tick_used);
+
 /* Counting without any memory allocation.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory
  * when they ask for a count -- code running inside an allocator or a memory

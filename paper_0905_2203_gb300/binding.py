@@ -89,6 +89,7 @@ _SIGS = {
     "fem_count_batch": (I32, [VP, VP, I32, ctypes.POINTER(fem_cands), VP, VP, I32]),
     "fem_count_episodes_plain": (I32, [VP, VP, ctypes.POINTER(fem_cands), VP, I32]),
     "fem_upper_bound": (I32, [VP, VP, ctypes.POINTER(fem_cands), VP, I32]),
+    "fem_upper_bound_coarse": (I32, [VP, VP, ctypes.POINTER(fem_cands), I32, VP, I32, ctypes.POINTER(I32)]),
     "fem_count_episodes_noalloc": (I32, [VP, VP, I64, VP, VP, VP, VP, I64, VP, VP]),
     "fem_mine_levelwise": (I32, [VP, VP, I32, VP, VP, I32, VP, I32, ctypes.POINTER(VP)]),
     "fem_result_level": (I32, [VP, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(VP),
@@ -239,6 +240,16 @@ class Context:
 
     def upper_bound(self, stream, cands: Cands, out=None):
         return self._count(fem_upper_bound, stream, cands, out, "fem_upper_bound")
+
+    def upper_bound_coarse(self, stream, cands: Cands, tick: int = 0, out=None):
+        """Coarse-tick upper bound (fem_upper_bound_coarse): (ub, tick used)."""
+        if out is None:
+            out = np.zeros(max(cands.n, 1), np.uint32)[: cands.n]
+        op, od, keep = _ptr(out, np.uint32)
+        w = I32()
+        check(fem_upper_bound_coarse(self.h, stream.h, ctypes.byref(cands.c), int(tick), op, od, ctypes.byref(w)),
+              "fem_upper_bound_coarse")
+        return keep, int(w.value)
 
     def count_batch(self, streams, cands: Cands, rec_id, out=None):
         arr = (VP * len(streams))(*[s.h for s in streams])

@@ -651,6 +651,7 @@ void fem::stream_free_unlocked(fem_stream *s) {
     dev_free(ctx, s->d_freq, sizeof(uint32_t) * s->n_types);
     for (auto &kv : s->dens) dev_free(ctx, kv.second, sizeof(uint32_t) * s->n_types);
     for (auto &kv : s->segs) dev_free(ctx, kv.second, sizeof(int64_t) * (kv.first + 1));
+    coarse_free(ctx, s);
     if (s->d_toff) dev_free(ctx, s->d_toff, sizeof(int64_t) * (s->n_types + 1));
     if (s->d_ttime) dev_free(ctx, s->d_ttime, sizeof(int32_t) * std::max<int64_t>(s->n, 1));
     delete s;

@@ -126,6 +126,17 @@ struct fem_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
+// Coarse-tick tables of a stream for one tick width w (fem_bound.cu):
+// bits[a * W + i] = ticks 32i..32i+31 (counted from tau0 = t_first / w)
+// holding a type-a event; cum[a * (W + 1) + i] = index, in type a's time
+// list, of its first event in word i or later.  W is a multiple of 32.
+struct fem_coarse_tab {
+    uint32_t *bits = nullptr;
+    uint32_t *cum = nullptr;
+    int64_t W = 0, tau0 = 0;
+    size_t bytes = 0;
+};
+
 struct fem_stream {
     fem_ctx *ctx = nullptr;
     int64_t n = 0;
@@ -137,8 +148,9 @@ struct fem_stream {
     int32_t t_first = 0, t_last = 0;  // first and last event time (n > 0)
     int64_t *d_toff = nullptr;    // per-type event lists (built on first use): offsets [n_types + 1]
     int32_t *d_ttime = nullptr;   // times grouped by type, ascending within a type [n]
-    std::map<int32_t, uint32_t *> dens;
-    std::map<int, int64_t *> segs;    // P -> segment boundaries (P + 1), cached  // lo -> per-type max events in a closed window of length lo
+    std::map<int32_t, uint32_t *> dens;  // lo -> per-type max events in a closed window of length lo
+    std::map<int, int64_t *> segs;       // P -> segment boundaries (P + 1), cached
+    std::map<int32_t, fem_coarse_tab> coarse;  // tick width -> coarse-tick tables
 };
 
 namespace fem {
@@ -179,6 +191,17 @@ int stream_density(fem_ctx *ctx, fem_stream *s, int32_t lo, uint32_t **d_dens);
 int stream_densities(fem_ctx *ctx, fem_stream *s, const std::vector<int32_t> &los);
 // Returns every cached free block to the driver.
 void pool_release(fem_ctx *ctx);
+// Coarse-tick upper bound (fem_bound.cu) of device-resident candidates over
+// one stream with tick width w (every edge's hi <= 31 w); ub is uint32 on
+// the device.
+int coarse_bound_dev(fem_ctx *ctx, fem_stream *s, int64_t n_cand, const int64_t *d_offs, const uint16_t *d_types,
+                     const int32_t *d_lo, const int32_t *d_hi, int max_nodes, int32_t w, uint32_t *d_ub,
+                     int64_t *launches);
+// The tick width a bound uses for edges with upper bounds up to hi_max: the
+// smallest w with hi_max <= 31 w, doubled while the stream's tables would
+// pass `budget` bytes.
+int32_t coarse_tick(const fem_stream *s, int64_t hi_max, size_t budget);
+void coarse_free(fem_ctx *ctx, fem_stream *s);
 
 // Device buffers released together at scope exit (after the stream drains).
 struct TmpDev {

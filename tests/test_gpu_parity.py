@@ -672,3 +672,84 @@ def test_local_tracking_rejects_malformed_candidates(fb, ctx, kernel):
     finally:
         ctx.reset_tuning()
     st.free()
+
+
+def _coarse_case(seed, n_cand, n=8000, n_types=5, t_max=40_000, hi_span=25):
+    r = synth.Rng(0xC0A6, seed)
+    ty, tm = synth.tiny_random_stream(3000 + seed, n, n_types, t_max)
+    sizes = r.integers(1, 6, n_cand)
+    offs = np.zeros(n_cand + 1, np.int64)
+    offs[1:] = np.cumsum(sizes)
+    ct = r.integers(0, n_types - 1, int(offs[-1])).astype(np.uint16)
+    ne = int(offs[-1]) - n_cand
+    lo = r.integers(0, 6, ne).astype(np.int32)
+    hi = (lo + r.integers(1, hi_span, ne)).astype(np.int32)
+    return ty, tm, offs, ct, lo, hi
+
+
+def _sub(offs, ct, lo, hi, idx):
+    """Candidates idx of a CSR set, as a new CSR set."""
+    o2, c2, l2, h2 = [0], [], [], []
+    for c in idx:
+        a, b = int(offs[c]), int(offs[c + 1])
+        c2 += list(ct[a:b])
+        l2 += list(lo[a - c:b - c - 1])
+        h2 += list(hi[a - c:b - c - 1])
+        o2.append(len(c2))
+    return (np.array(o2, np.int64), np.array(c2, np.uint16), np.array(l2, np.int32), np.array(h2, np.int32))
+
+
+@pytest.mark.parametrize("tick", [1, 3, 0])
+@pytest.mark.parametrize("n_cand", [300, 12000])
+def test_coarse_bound_matches_oracle(fb, ctx, tick, n_cand):
+    """Coarse-tick bound: element by element equal to the oracle's definition
+    (on a sample when the set is large) and never below the oracle's count;
+    40k ticks = 40 warp chunks, so a few candidates run as many stream slices
+    (one chunk of warm-up each) and many candidates as whole-stream warps."""
+    from oracle import coarse_bound as cb
+    ty, tm, offs, ct, lo, hi = _coarse_case(tick + n_cand, n_cand)
+    st = ctx.load_stream(ty, tm, 5)
+    ub, w = ctx.upper_bound_coarse(st, fb.Cands(offs, ct, lo, hi), tick)
+    assert w == (tick if tick else cb.default_tick(int(hi.max())))
+    ub = ub.astype(np.int64)
+    assert np.all(ub >= oracle_counts(ty, tm, offs, ct, lo, hi))
+    sample = np.arange(n_cand) if n_cand <= 300 else synth.Rng(5, n_cand).integers(0, n_cand - 1, 300)
+    want = cb.coarse_ub_many(ty, tm, *_sub(offs, ct, lo, hi, sample), w)
+    bad = np.nonzero(ub[sample] != want)[0]
+    assert bad.size == 0, (bad[:5], ub[sample][bad[:5]], want[bad[:5]])
+    st.free()
+
+
+def test_coarse_bound_edges_and_full_size(fb, ctx):
+    """Edge cases (empty stream, 1-node episodes = frequency, a tick too small
+    for an edge) and a 200k-event recording of the many-recordings workload
+    with 3- and 4-node candidates of the 4-bin set: never below the oracle's
+    count, and equal to the oracle's definition on a sample."""
+    from oracle import coarse_bound as cb
+    st0 = ctx.load_stream(np.zeros(0, np.uint16), np.zeros(0, np.int32), 3)
+    ub, _ = ctx.upper_bound_coarse(st0, fb.Cands(np.array([0, 2, 3]), np.array([0, 1, 2], np.uint16),
+                                                 np.array([0], np.int32), np.array([4], np.int32)))
+    assert ub.tolist() == [0, 0]
+    st0.free()
+    s, _ = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    c1 = fb.Cands(np.arange(s.n_types + 1, dtype=np.int64), np.arange(s.n_types, dtype=np.uint16),
+                  np.zeros(0, np.int32), np.zeros(0, np.int32))
+    ub, _ = ctx.upper_bound_coarse(st, c1)
+    assert np.array_equal(ub, st.freq())
+    with pytest.raises(fb.FemError) as e:
+        ctx.upper_bound_coarse(st, fb.Cands(np.array([0, 2]), np.array([0, 1], np.uint16),
+                                            np.array([0], np.int32), np.array([64], np.int32)), 2)
+    assert e.value.status == fb.FEM_ERR_INVAL
+    st.free()
+    s, cfg = synth.c4_recordings(n_rec=2)[1]  # 190,695 events
+    offs, ct, lo, hi = synth.random_candidates(0xC0A7, 3000, s.n_types, 3, 4, cfg["bins"], s.chains, 0.1)
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    ub, w = ctx.upper_bound_coarse(st, fb.Cands(offs, ct, lo, hi))
+    ub = ub.astype(np.int64)
+    exact = oracle_counts(s.types, s.times, offs, ct, lo, hi)
+    assert np.all(ub >= exact)
+    sample = synth.Rng(6, 1).integers(0, 2999, 12)
+    want = cb.coarse_ub_many(s.types, s.times, *_sub(offs, ct, lo, hi, sample), w)
+    assert np.array_equal(ub[sample], want)
+    st.free()
