@@ -203,6 +203,22 @@ __global__ void k_prune2_flags(const int32_t *order, int64_t C, const uint16_t *
     if (!keep) counts[c] = 0;
 }
 
+// Levels >= 3: candidates whose coarse-tick bound is at most the threshold
+// get count 0 (they can never pass) and leave the counting order.
+__global__ void k_prune_ub_flags(int64_t C, const uint32_t *ub, const uint32_t *crec, const uint32_t *thr,
+                                 int32_t *flags, uint32_t *counts) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const bool keep = ub[c] > thr[crec[c]];
+    flags[c] = keep ? 1 : 0;
+    if (!keep) counts[c] = 0;
+}
+
+__global__ void k_prune_ub_write(const int32_t *pos, const int32_t *flags_copy, int64_t C, int32_t *kept) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < C && flags_copy[c]) kept[pos[c]] = (int32_t)c;
+}
+
 __global__ void k_prune2_write(const int32_t *pos, const int32_t *flags_copy, const int32_t *order, int64_t C,
                                int32_t *kept) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -386,6 +402,10 @@ int copy_level_to_host(fem_ctx *ctx, const DevLevel &L, fem_result *res, const s
 // candidates; after the candidates have been counted (by anyone: a counting
 // call of its own, or a launch shared with other groups), advance() applies
 // the threshold and prepares the next level's candidates.
+// Levels >= 3 of at least this many candidates get the coarse-tick bound
+// before the exact count (automatic pre-pass setting).
+constexpr int64_t kCoarseMinCands = 4096;
+
 struct MineGroup {
     fem_ctx *ctx = nullptr;
     std::vector<fem_stream *> recs;
@@ -417,6 +437,7 @@ struct MineGroup {
   private:
     int gen_level2();
     int gen_join();
+    int coarse_prune();
     int finish_candidates();
 };
 
@@ -641,6 +662,56 @@ int MineGroup::gen_join() {
     FEM_CUDA_TRY(cudaMemcpyAsync(c_off.data(), d_coff_rec, 8 * (n_recs + 1), cudaMemcpyDeviceToHost, st));
     FEM_CUDA_TRY(cudaStreamSynchronize(st));
     S.kernel_launches += 2;
+    return coarse_prune();
+}
+
+// Coarse-tick bound of the level's candidates (fem_bound.cu), one launch per
+// recording; candidates at or below their threshold are dropped before the
+// exact count.  Automatic for levels of at least kCoarseMinCands candidates
+// (below that the count itself is short), always with prepass = 1, never
+// with prepass = -1 or 2.
+int MineGroup::coarse_prune() {
+    const int n_recs = nrec();
+    const int N = level;
+    const int64_t C = cand.n;
+    const int pp = ctx->tuning.prepass;
+    if (C == 0 || N < 3 || pp == -1 || pp == 2 || (pp != 1 && C < kCoarseMinCands)) return FEM_OK;
+    cudaStream_t st = ctx->stream;
+    const int B = 256;
+    int32_t hi_max = 1;
+    for (int32_t h : bhi) hi_max = std::max(hi_max, h);
+    Pool tmp(ctx);
+    uint32_t *d_ub;
+    int32_t *d_pf, *d_pf2, *d_ptmp, *d_ptot, *d_kept;
+    FEM_TRY(tmp.get(&d_ub, C));
+    for (int r = 0; r < n_recs; ++r) {
+        const int64_t c0 = c_off[r], n = c_off[r + 1] - c0;
+        if (n == 0) continue;
+        if (recs[r]->n_types > 8192 || recs[r]->n > INT32_MAX / 2) {
+            FEM_CUDA_TRY(cudaMemsetAsync(d_ub + c0, 0xFF, 4 * n, st));  // no bound: keep all
+            continue;
+        }
+        const int32_t w = coarse_tick(recs[r], hi_max, 0);
+        // dense layout: the first n + 1 entries of d_coffs are 0, N, ..., nN
+        FEM_TRY(coarse_bound_dev(ctx, recs[r], n, d_coffs, cand.types + c0 * N, cand.lo + c0 * (N - 1),
+                                 cand.hi + c0 * (N - 1), N, w, d_ub + c0, &S.kernel_launches));
+    }
+    FEM_TRY(tmp.get(&d_pf, C + 1));
+    FEM_TRY(tmp.get(&d_pf2, C + 1));
+    FEM_TRY(tmp.get(&d_ptmp, C / 1024 + 2));
+    FEM_TRY(tmp.get(&d_ptot, 2));
+    FEM_TRY(pcand->get(&d_kept, C));
+    k_prune_ub_flags<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(C, d_ub, cand.rec, d_thr, d_pf, cand.counts);
+    FEM_CUDA_TRY(cudaMemcpyAsync(d_pf2, d_pf, 4 * C, cudaMemcpyDeviceToDevice, st));
+    FEM_TRY(scan_exclusive(st, d_pf, C, d_ptmp, d_ptot, &S.kernel_launches));
+    k_prune_ub_write<<<(unsigned)((C + B - 1) / B), B, 0, st>>>(d_pf, d_pf2, C, d_kept);
+    S.kernel_launches += 2;
+    int32_t kept = 0;
+    FEM_CUDA_TRY(cudaMemcpyAsync(&kept, d_ptot, 4, cudaMemcpyDeviceToHost, st));
+    FEM_CUDA_TRY(cudaStreamSynchronize(st));
+    S.candidates_pruned += C - kept;
+    n_order = kept;
+    d_order = d_kept;
     return FEM_OK;
 }
 

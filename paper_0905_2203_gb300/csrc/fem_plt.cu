@@ -18,6 +18,8 @@
 // (times a logarithm), spread over all events, so a single long episode on a
 // long stream still fills the GPU -- the regime the section addresses.
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "fem_internal.cuh"
@@ -89,6 +91,8 @@ constexpr int kMsBlock = 1024;
 // Entries an occurrence list may hold (episodes beyond it are counted by the
 // latest-start steps).
 constexpr int64_t kOccCap = int64_t(1) << 25;
+// Largest total length of one step's arrays in a latest-start launch.
+constexpr int64_t kPltMaxTotal = int64_t(1) << 28;
 
 __global__ void k_maxscan_blocks(int32_t *d, int64_t m, int32_t *bmax) {
     __shared__ int32_t s_w[32];
@@ -204,18 +208,20 @@ __global__ void k_plt_jump(int64_t total, const int32_t *__restrict__ nxt, const
     }
 }
 
+// Episode e's last-step item is items[idx[e]] (items[e] without idx).
 // count = chain length from the first kept end: the first j >= j0 with
 // PM(j) > prev, prev = the previous kept end (-inf without `prev`).  With
 // `prev` (appended events) the count is added and prev becomes the time of
 // the chain's last end; earlier ends (j < j0) have latest starts <= prev, so
 // PM over them never passes prev.
-__global__ void k_plt_count(const PltItem *__restrict__ items, int n_items, const int32_t *__restrict__ L,
-                            const int32_t *__restrict__ V, const int32_t *__restrict__ cnt,
-                            const int32_t *__restrict__ cand, uint32_t *__restrict__ counts,
-                            int32_t *__restrict__ prev, const int32_t *__restrict__ lst) {
+__global__ void k_plt_count(const PltItem *__restrict__ items, int n_eps, const int32_t *__restrict__ idx,
+                            const int32_t *__restrict__ L, const int32_t *__restrict__ V,
+                            const int32_t *__restrict__ cnt, const int32_t *__restrict__ cand,
+                            uint32_t *__restrict__ counts, int32_t *__restrict__ prev,
+                            const int32_t *__restrict__ lst) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_items) return;
-    const PltItem it = items[e];
+    if (e >= n_eps) return;
+    const PltItem it = items[idx ? idx[e] : e];
     const int32_t pv = prev ? prev[cand[e]] : INT32_MIN;
     int64_t lo = it.j0, hi = it.fb;
     while (lo < hi) {
@@ -437,7 +443,7 @@ static int count_occ_one(fem_ctx *ctx, const std::vector<PltItem> &its, int vari
         }
         *launches += 6 + rounds;
     }
-    k_plt_count<<<1, 32, 0, st>>>(d_item, 1, L, V, c1, d_cand, d_counts, nullptr, nullptr);
+    k_plt_count<<<1, 32, 0, st>>>(d_item, 1, nullptr, L, V, c1, d_cand, d_counts, nullptr, nullptr);
     ++*launches;
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
@@ -618,70 +624,121 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
             grp.swap(rest);
             build_steps();
         }
-        const int G = (int)grp.size();
-        int64_t tmax = 1;
-        for (int64_t t : tot) tmax = std::max(tmax, t);
-        TmpDev tmp(ctx);
-        PltItem *d_items;
-        int32_t *La, *Lb, *Va, *Vb, *bm, *d_cand, *n1, *n2, *c1, *c2;
-        FEM_TRY(tmp.get(&d_items, (size_t)G * (N - 1)));
-        FEM_TRY(tmp.get(&La, tmax));
-        FEM_TRY(tmp.get(&Lb, tmax));
-        FEM_TRY(tmp.get(&Va, tmax));
-        FEM_TRY(tmp.get(&Vb, tmax));
-        FEM_TRY(tmp.get(&n1, tmax));
-        FEM_TRY(tmp.get(&n2, tmax));
-        FEM_TRY(tmp.get(&c1, tmax));
-        FEM_TRY(tmp.get(&c2, tmax));
-        FEM_TRY(tmp.get(&bm, tmax / kMsBlock + 2));
-        FEM_TRY(tmp.get(&d_cand, G));
-        for (int k = 0; k + 1 < N; ++k)
-            FEM_CUDA_TRY(cudaMemcpyAsync(d_items + (size_t)k * G, steps[k].data(), sizeof(PltItem) * G,
-                                         cudaMemcpyHostToDevice, st));
-        FEM_CUDA_TRY(cudaMemcpyAsync(d_cand, grp.data(), 4 * G, cudaMemcpyHostToDevice, st));
-        cudaEventRecord(ctx->ev0, st);
-        for (int k = 0; k + 1 < N; ++k) {
-            const int64_t T = tot[k];
+        // Batches of episodes whose per-step array totals stay within
+        // kPltMaxTotal (positions in the step arrays are int32); a batch holds
+        // at least one episode (a type list has fewer than 2^30 events).
+        for (int b0 = 0, b1 = 0; b0 < (int)grp.size(); b0 = b1) {
+            std::vector<int64_t> acc(N - 1, 0);
+            for (b1 = b0; b1 < (int)grp.size(); ++b1) {
+                bool fits = true;
+                for (int k = 0; k + 1 < N; ++k) fits = fits && acc[k] + steps[k][b1].fb <= kPltMaxTotal;
+                if (!fits && b1 > b0) break;
+                for (int k = 0; k + 1 < N; ++k) acc[k] += steps[k][b1].fb;
+            }
+            const int G = b1 - b0;
+            // Prefix sharing: episodes of one recording whose first k + 2 nodes
+            // and k + 1 edges agree share the step-k item and its arrays (a trie
+            // over the episode set, one level per node; level-N candidates joined
+            // from one frequent (N-1)-episode share all but their last step).
+            std::vector<std::vector<PltItem>> uit(N - 1);
+            std::vector<int64_t> utot(N - 1, 0);
+            std::vector<int32_t> leaf(G);
+            {
+                std::map<std::pair<uint32_t, uint16_t>, int32_t> root;
+                std::map<std::tuple<int32_t, int32_t, int32_t, int64_t>, int32_t> child;
+                for (int e = 0; e < G; ++e) {
+                    const int32_t w = grp[b0 + e];
+                    const auto key = std::make_pair(crec[w - wmin], types[offs[w - wmin] - n0]);
+                    leaf[e] = root.emplace(key, (int32_t)root.size()).first->second;
+                }
+                for (int k = 0; k + 1 < N; ++k) {
+                    child.clear();
+                    for (int e = 0; e < G; ++e) {
+                        const PltItem &it = steps[k][b0 + e];
+                        const auto key = std::make_tuple(leaf[e], it.lo, it.hi, it.b_start);
+                        const auto ins = child.emplace(key, (int32_t)uit[k].size());
+                        if (ins.second) {
+                            PltItem u = it;
+                            u.prev_base = k > 0 ? uit[k - 1][leaf[e]].base : 0;
+                            u.base = utot[k];
+                            utot[k] += u.fb;
+                            uit[k].push_back(u);
+                        }
+                        leaf[e] = ins.first->second;
+                    }
+                }
+            }
+            int64_t tmax = 1, n_items = 0;
+            for (int64_t t : utot) tmax = std::max(tmax, t);
+            std::vector<int64_t> ioff(N, 0);
+            for (int k = 0; k + 1 < N; ++k) ioff[k + 1] = ioff[k] + (int64_t)uit[k].size();
+            n_items = ioff[N - 1];
+            TmpDev tmp(ctx);
+            PltItem *d_items;
+            int32_t *La, *Lb, *Va, *Vb, *bm, *d_cand, *d_leaf, *n1, *n2, *c1, *c2;
+            FEM_TRY(tmp.get(&d_items, (size_t)n_items));
+            FEM_TRY(tmp.get(&La, tmax));
+            FEM_TRY(tmp.get(&Lb, tmax));
+            FEM_TRY(tmp.get(&Va, tmax));
+            FEM_TRY(tmp.get(&Vb, tmax));
+            FEM_TRY(tmp.get(&n1, tmax));
+            FEM_TRY(tmp.get(&n2, tmax));
+            FEM_TRY(tmp.get(&c1, tmax));
+            FEM_TRY(tmp.get(&c2, tmax));
+            FEM_TRY(tmp.get(&bm, tmax / kMsBlock + 2));
+            FEM_TRY(tmp.get(&d_cand, G));
+            FEM_TRY(tmp.get(&d_leaf, G));
+            for (int k = 0; k + 1 < N; ++k)
+                FEM_CUDA_TRY(cudaMemcpyAsync(d_items + ioff[k], uit[k].data(), sizeof(PltItem) * uit[k].size(),
+                                             cudaMemcpyHostToDevice, st));
+            FEM_CUDA_TRY(cudaMemcpyAsync(d_cand, grp.data() + b0, 4 * G, cudaMemcpyHostToDevice, st));
+            FEM_CUDA_TRY(cudaMemcpyAsync(d_leaf, leaf.data(), 4 * G, cudaMemcpyHostToDevice, st));
+            cudaEventRecord(ctx->ev0, st);
+            for (int k = 0; k + 1 < N; ++k) {
+                const int64_t T = utot[k];
+                if (T > 0) {
+                    const unsigned gsz = (unsigned)std::max<int64_t>(1, std::min<int64_t>((T + 255) / 256, 8 * ctx->n_sm));
+                    k_plt_step<<<gsz, 256, 0, st>>>(d_items + ioff[k], (int)uit[k].size(), T, k == 0 ? 1 : 0, La, Va, Lb,
+                                                    Vb);
+                    FEM_TRY(maxscan(st, Vb, T, bm));
+                }
+                std::swap(La, Lb);
+                std::swap(Va, Vb);
+            }
+            // La / Va: the last node's latest starts and newest valid positions
+            const PltItem *last = d_items + ioff[N - 2];
+            const int n_last = (int)uit[N - 2].size();
+            const int64_t T = utot[N - 2];
+            int64_t fmax = 1;
+            for (const PltItem &it : uit[N - 2]) fmax = std::max<int64_t>(fmax, it.fb);
+            int rounds = 0;
+            while ((int64_t(1) << rounds) < fmax) ++rounds;
+            // appended events: also the last end of every chain
+            int32_t *l1 = nullptr, *l2 = nullptr;
+            if (sess) {
+                FEM_TRY(tmp.get(&l1, tmax));
+                FEM_TRY(tmp.get(&l2, tmax));
+            }
             if (T > 0) {
                 const unsigned gsz = (unsigned)std::max<int64_t>(1, std::min<int64_t>((T + 255) / 256, 8 * ctx->n_sm));
-                k_plt_step<<<gsz, 256, 0, st>>>(d_items + (size_t)k * G, G, T, k == 0 ? 1 : 0, La, Va, Lb, Vb);
-                FEM_TRY(maxscan(st, Vb, T, bm));
+                k_plt_next<<<gsz, 256, 0, st>>>(last, n_last, T, La, Va, n1, c1, l1);
+                for (int q = 0; q < rounds; ++q) {
+                    k_plt_jump<<<gsz, 256, 0, st>>>(T, n1, c1, n2, c2, l1, l2);
+                    std::swap(n1, n2);
+                    std::swap(c1, c2);
+                    std::swap(l1, l2);
+                }
             }
-            std::swap(La, Lb);
-            std::swap(Va, Vb);
+            k_plt_count<<<(G + 127) / 128, 128, 0, st>>>(last, G, d_leaf, La, Va, c1, d_cand, d_counts,
+                                                         sess ? sess->d_prev : nullptr, l1);
+            cudaEventRecord(ctx->ev1, st);
+            FEM_CUDA_TRY(cudaGetLastError());
+            FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            ms_total += ms;
+            stats->kernel_launches += (N - 1) * 4 + 2 + rounds;
         }
-        // La / Va: the last node's latest starts and newest valid positions
-        const PltItem *last = d_items + (size_t)(N - 2) * G;
-        const int64_t T = tot[N - 2];
-        int64_t fmax = 1;
-        for (const PltItem &it : steps[N - 2]) fmax = std::max<int64_t>(fmax, it.fb);
-        int rounds = 0;
-        while ((int64_t(1) << rounds) < fmax) ++rounds;
-        // appended events: also the last end of every chain
-        int32_t *l1 = nullptr, *l2 = nullptr;
-        if (sess) {
-            FEM_TRY(tmp.get(&l1, tmax));
-            FEM_TRY(tmp.get(&l2, tmax));
-        }
-        if (T > 0) {
-            const unsigned gsz = (unsigned)std::max<int64_t>(1, std::min<int64_t>((T + 255) / 256, 8 * ctx->n_sm));
-            k_plt_next<<<gsz, 256, 0, st>>>(last, G, T, La, Va, n1, c1, l1);
-            for (int q = 0; q < rounds; ++q) {
-                k_plt_jump<<<gsz, 256, 0, st>>>(T, n1, c1, n2, c2, l1, l2);
-                std::swap(n1, n2);
-                std::swap(c1, c2);
-                std::swap(l1, l2);
-            }
-        }
-        k_plt_count<<<(G + 127) / 128, 128, 0, st>>>(last, G, La, Va, c1, d_cand, d_counts,
-                                                     sess ? sess->d_prev : nullptr, l1);
-        cudaEventRecord(ctx->ev1, st);
-        FEM_CUDA_TRY(cudaGetLastError());
-        FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-        ms_total += ms;
-        stats->kernel_launches += (N - 1) * 4 + 2 + rounds;
     }
     stats->candidates_counted += C;
     stats->counted_episode_events += counted;

@@ -374,6 +374,90 @@ def test_prepass_prunes_but_never_changes_results(fb, ctx):
     st.free()
 
 
+@pytest.mark.parametrize("relaxed", [False, True])
+def test_local_tracking_shared_prefixes(fb, ctx, relaxed):
+    """Local tracking shares the steps of episodes with a common prefix (a
+    trie over the candidate set): joined level-3 and level-4 candidates (each
+    frequent pair prefixes many of them), with repeated candidates mixed in,
+    equal the oracle's counts (and, relaxed, its counts with lower bounds 0)."""
+    s, cfg = synth.c1_tiny()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    ftypes = list(range(12))
+    pairs = oracle.generate_candidates([], 2, ftypes, [(0, 5), (2, 8)])
+    l3 = oracle.generate_candidates(pairs[:60], 3, ftypes, [])
+    l4 = oracle.generate_candidates(l3[:200], 4, ftypes, [])
+    eps = l3[:150] + l4[:100] + l3[:20]
+    offs, ct, lo, hi = oracle.to_csr(eps)
+    ctx.set_tuning(kernel=4)
+    try:
+        if relaxed:
+            got = ctx.upper_bound(st, fb.Cands(offs, ct, lo, hi)).astype(np.int64)
+            want = oracle_counts(s.types, s.times, offs, ct, np.zeros_like(lo), hi)
+        else:
+            got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+            want = oracle_counts(s.types, s.times, offs, ct, lo, hi)
+    finally:
+        ctx.reset_tuning()
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:5]
+    assert want.max() > 0
+    st.free()
+
+
+def test_local_tracking_batches_long_step_arrays(fb, ctx):
+    """300 two-node episodes over a 2M-event stream (1M events of the end
+    type): the step arrays of one launch would hold 3e8 positions, so local
+    tracking splits the episodes into batches of at most 2^28 positions;
+    counts equal the oracle's."""
+    r = synth.Rng(0xBA7C, 1)
+    n = 2_000_000
+    tm = np.cumsum(r.integers(1, 4, n)).astype(np.int32)
+    ty = (np.arange(n) % 2).astype(np.uint16)
+    st = ctx.load_stream(ty, tm, 2)
+    nc = 300
+    offs = np.arange(0, 2 * nc + 1, 2, dtype=np.int64)
+    ct = np.tile(np.array([0, 1], np.uint16), nc)
+    lo = (np.arange(nc) % 7).astype(np.int32)
+    hi = (lo + 1 + np.arange(nc) // 7).astype(np.int32)
+    ctx.set_tuning(kernel=4)
+    try:
+        got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+    finally:
+        ctx.reset_tuning()
+    want = oracle_counts(ty, tm, offs, ct, lo, hi)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:5]
+    assert want.min() > 0
+    st.free()
+
+
+def test_coarse_prepass_in_level_wise_mining(fb, ctx):
+    """Host-driven mining of two recordings of the many-recordings workload
+    with the coarse-tick bound forced on every level >= 3 (prepass = 1):
+    equal to the oracle miner, with level >= 3 candidates pruned beyond the
+    level-2 pair bound's (prepass = 2 keeps only that one)."""
+    recs = synth.c4_recordings(n_rec=2)
+    streams = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
+    thr = [c["threshold"] for _, c in recs]
+    bins = recs[0][1]["bins"]
+    stats = {}
+    try:
+        for pp in (1, 2):
+            ctx.set_tuning(prepass=pp, level_graph=-1)
+            res = ctx.mine_levelwise(streams, bins, thr, 4)
+            stats[pp] = res.stats()
+            for r, (s, c) in enumerate(recs):
+                want = oracle.mine_levelwise(s.types, s.times, s.n_types, bins, c["threshold"], 4)
+                for N in range(1, 5):
+                    eps, counts = res.level(r, N)
+                    assert list(zip(eps, counts)) == want[N], (pp, r, N)
+            res.free()
+    finally:
+        ctx.reset_tuning()
+        for st in streams:
+            st.free()
+    assert stats[1]["candidates_pruned"] > stats[2]["candidates_pruned"]
+    assert stats[1]["counted_episode_events"] < stats[2]["counted_episode_events"]
+
+
 @pytest.mark.parametrize("which", ["c2", "multi"])
 def test_level_graph_equals_host_path(fb, ctx, which):
     """Levels >= 3 run as one captured CUDA graph; results equal the
