@@ -87,12 +87,10 @@ typedef struct {
     int segments;         /* stream segments per recording (>= 1) */
     int tile_events;      /* events per shared-memory stage (multiple of 256) */
     int prepass;          /* upper-bound pre-passes of level-wise mining:
-                             0 = automatic (the level-2 pair bound; on the
-                             host-driven levels, the coarse-tick bound of
-                             fem_upper_bound_coarse for levels >= 3 of at
-                             least 4096 candidates), 1 = both on every
-                             level they apply to, 2 = the level-2 pair
-                             bound only, -1 = none */
+                             0 = the level-2 pair bound, 1 = also the
+                             coarse-tick bound of fem_upper_bound_coarse on
+                             every level >= 3 (candidates at or below the
+                             threshold skip the exact count), -1 = none */
     int plain_path;       /* 1 = count with the one-thread-per-episode plain
                              path (comparison baseline) instead of the tiled
                              kernels */

@@ -69,49 +69,37 @@ struct CoarseArgs {
     uint32_t *ub;
 };
 
-// One warp per (episode, slice of the stream).
+// One warp walks chunks [c0, c1) of the stream for one episode (types[N],
+// lo / hi[N - 1]) and returns this lane's share of the bound; the chunk
+// before c0 (if any) only warms up the carried words.
 template <int NMAX>
-__global__ void __launch_bounds__(256, NMAX <= 4 ? 4 : (NMAX <= 8 ? 2 : 1)) k_coarse_ub(CoarseArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (wid >= a.n_cand * a.n_slices) return;  // whole warps
-    const int64_t c = wid / a.n_slices;
-    const int sl = (int)(wid % a.n_slices);
-    const int64_t o = a.offs[c];
-    const int N = (int)(a.offs[c + 1] - o);
-    const int64_t eo = o - c;
-    if (N == 1) {
-        if (sl == 0 && lane == 0) {
-            const int e = a.types[o];
-            a.ub[c] = (uint32_t)(a.toff[e + 1] - a.toff[e]);
-        }
-        return;
-    }
+__device__ __forceinline__ uint32_t coarse_walk(const uint16_t *__restrict__ types, const int32_t *__restrict__ lo,
+                                                const int32_t *__restrict__ hi, int N,
+                                                const uint32_t *__restrict__ bits, const uint32_t *__restrict__ cum,
+                                                const int64_t *__restrict__ toff, const int32_t *__restrict__ ttime,
+                                                int64_t W, int64_t tau0, int32_t w, int64_t c0, int64_t c1, int lane) {
     int E[NMAX], dlo[NMAX], lr[NMAX];
     uint32_t carry[NMAX];
-    int last = 0;
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) {
-        E[k] = k < N ? (int)a.types[o + k] : 0;
+        E[k] = k < N ? (int)types[k] : 0;
         dlo[k] = 0;
         lr[k] = 1;
         if (k < N - 1) {
-            const int32_t l = a.lo[eo + k], h = a.hi[eo + k];
-            dlo[k] = (l + 1) / a.w;
-            lr[k] = (int)(((int64_t)h + a.w - 1) / a.w) - dlo[k] + 1;
+            const int32_t l = lo[k], h = hi[k];
+            dlo[k] = (l + 1) / w;
+            lr[k] = (int)(((int64_t)h + w - 1) / w) - dlo[k] + 1;
         }
         carry[k] = 0;
     }
-    last = a.types[o + N - 1];  // (not E[N - 1]: a dynamic index would put E in local memory)
-    const int64_t c0 = (int64_t)sl * a.slice_chunks;
-    const int64_t c1 = min(c0 + (int64_t)a.slice_chunks, a.n_chunks);
-    const uint32_t *bl = a.bits + (int64_t)last * a.W;
-    const uint32_t *cl = a.cum + (int64_t)last * (a.W + 1);
-    const int32_t *tl = a.ttime + a.toff[last];
+    const int last = types[N - 1];  // (not E[N - 1]: a dynamic index would put E in local memory)
+    const uint32_t *bl = bits + (int64_t)last * W;
+    const uint32_t *cl = cum + (int64_t)last * (W + 1);
+    const int32_t *tl = ttime + toff[last];
     uint32_t acc = 0;
     for (int64_t ch = c0 > 0 ? c0 - 1 : 0; ch < c1; ++ch) {
         const int64_t i = ch * 32 + lane;
-        uint32_t m = a.bits[(int64_t)E[0] * a.W + i];
+        uint32_t m = bits[(int64_t)E[0] * W + i];
 #pragma unroll
         for (int k = 0; k < NMAX - 1; ++k) {
             if (k < N - 1) {
@@ -132,7 +120,7 @@ __global__ void __launch_bounds__(256, NMAX <= 4 ? 4 : (NMAX <= 8 ? 2 : 1)) k_co
                         }
                     const uint64_t Y = Z | (Z << (lr[k] - s));
                     const uint32_t D = (uint32_t)((Y << dlo[k]) >> 32);
-                    m = D ? (a.bits[(int64_t)E[k + 1] * a.W + i] & D) : 0u;
+                    m = D ? (bits[(int64_t)E[k + 1] * W + i] & D) : 0u;
                 } else {
                     m = 0u;
                 }
@@ -145,16 +133,83 @@ __global__ void __launch_bounds__(256, NMAX <= 4 ? 4 : (NMAX <= 8 ? 2 : 1)) k_co
                     acc += (uint32_t)__popc(m);  // one event per set tick
                 } else {
                     for (uint32_t q = q0; q < q1; ++q) {
-                        const int64_t u = (int64_t)tl[q] / a.w - a.tau0;
+                        const int64_t u = (int64_t)tl[q] / w - tau0;
                         acc += (m >> (u & 31)) & 1u;
                     }
                 }
             }
         }
     }
+    return acc;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
 #pragma unroll
-    for (int q = 16; q > 0; q >>= 1) acc += __shfl_down_sync(kFull, acc, q);
+    for (int q = 16; q > 0; q >>= 1) v += __shfl_down_sync(kFull, v, q);
+    return v;
+}
+
+// One warp per (episode, slice of the stream).
+template <int NMAX>
+__global__ void __launch_bounds__(256, NMAX <= 4 ? 4 : (NMAX <= 8 ? 2 : 1)) k_coarse_ub(CoarseArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= a.n_cand * a.n_slices) return;  // whole warps
+    const int64_t c = wid / a.n_slices;
+    const int sl = (int)(wid % a.n_slices);
+    const int64_t o = a.offs[c];
+    const int N = (int)(a.offs[c + 1] - o);
+    const int64_t eo = o - c;
+    if (N == 1) {
+        if (sl == 0 && lane == 0) {
+            const int e = a.types[o];
+            a.ub[c] = (uint32_t)(a.toff[e + 1] - a.toff[e]);
+        }
+        return;
+    }
+    const int64_t c0 = (int64_t)sl * a.slice_chunks;
+    const int64_t c1 = min(c0 + (int64_t)a.slice_chunks, a.n_chunks);
+    const uint32_t acc = warp_sum(coarse_walk<NMAX>(a.types + o, a.lo + eo, a.hi + eo, N, a.bits, a.cum, a.toff,
+                                                    a.ttime, a.W, a.tau0, a.w, c0, c1, lane));
     if (lane == 0 && acc) atomicAdd(&a.ub[c], acc);
+}
+
+// Inside the captured mining graph: level-N candidates in fixed stride
+// (ct[c * N + k], cl / ch[c * (N - 1) + k]) of several recordings, their
+// live count in *d_n; each recording's stream cut into n_slices slices.
+// Below min_cands candidates the level is not bounded.
+template <int NMAX>
+__global__ void __launch_bounds__(256, NMAX <= 4 ? 3 : (NMAX <= 8 ? 2 : 1))
+    k_coarse_graph(const uint16_t *__restrict__ ct, const int32_t *__restrict__ cl, const int32_t *__restrict__ ch,
+                   const uint32_t *__restrict__ crec, const int32_t *__restrict__ d_n, int64_t cap, int N,
+                   const CoarseDesc *__restrict__ desc, int n_slices, int64_t min_cands, uint32_t *__restrict__ ub) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = min((int64_t)*d_n, cap);
+    if (n < min_cands) return;
+    const int64_t items = n * n_slices;
+    for (int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wid < items;
+         wid += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t c = wid / n_slices;
+        const int sl = (int)(wid % n_slices);
+        const CoarseDesc d = desc[crec[c]];
+        const int64_t c0 = (int64_t)sl * d.slice_chunks;
+        const int64_t c1 = min(c0 + (int64_t)d.slice_chunks, d.n_chunks);
+        if (c0 >= c1) continue;  // warp-uniform
+        const uint32_t acc =
+            warp_sum(coarse_walk<NMAX>(ct + c * N, cl + c * (N - 1), ch + c * (N - 1), N, d.bits, d.cum, d.toff,
+                                       d.ttime, d.W, d.tau0, d.w, c0, c1, lane));
+        if (lane == 0 && acc) atomicAdd(&ub[c], acc);
+    }
+}
+
+// skip[c] = 1 when candidate c's bound cannot pass its recording's threshold.
+__global__ void k_coarse_skip(const uint32_t *__restrict__ ub, const uint32_t *__restrict__ crec,
+                              const uint32_t *__restrict__ thr, const int32_t *__restrict__ d_n, int64_t cap,
+                              int64_t min_cands, uint8_t *__restrict__ skip) {
+    const int64_t n = min((int64_t)*d_n, cap);
+    const bool on = n >= min_cands;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+        skip[c] = on && ub[c] <= thr[crec[c]] ? 1 : 0;
 }
 
 int64_t coarse_words(const fem_stream *s, int32_t w) {
@@ -264,6 +319,41 @@ int coarse_bound_dev(fem_ctx *ctx, fem_stream *s, int64_t n_cand, const int64_t 
         k_coarse_ub<16><<<blocks, 256, 0, st>>>(a);
     FEM_CUDA_TRY(cudaGetLastError());
     if (launches) *launches += 1;
+    return FEM_OK;
+}
+
+int coarse_desc(fem_ctx *ctx, fem_stream *s, int32_t w, int n_slices, CoarseDesc *out) {
+    const fem_coarse_tab *t = nullptr;
+    FEM_TRY(stream_coarse(ctx, s, w, &t));
+    CoarseDesc d{};
+    d.bits = t->bits;
+    d.cum = t->cum;
+    d.toff = s->d_toff;
+    d.ttime = s->d_ttime;
+    d.W = t->W;
+    d.tau0 = t->tau0;
+    d.n_chunks = t->W / 32;
+    d.w = w;
+    d.slice_chunks = (int32_t)((d.n_chunks + n_slices - 1) / n_slices);
+    *out = d;
+    return FEM_OK;
+}
+
+int coarse_graph_level(cudaStream_t st, int n_sm, int N, const uint16_t *ct, const int32_t *cl, const int32_t *ch,
+                       const uint32_t *crec, const int32_t *d_n, int64_t cap, const CoarseDesc *d_desc, int n_slices,
+                       const uint32_t *thr, int64_t min_cands, uint32_t *ub, uint8_t *skip) {
+    if (N < 2 || N > FEM_MAX_NODES || cap <= 0) return FEM_ERR_INVAL;
+    FEM_CUDA_TRY(cudaMemsetAsync(ub, 0, sizeof(uint32_t) * cap, st));
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap * n_slices + 7) / 8, 16 * n_sm));
+    if (N <= 4)
+        k_coarse_graph<4><<<blocks, 256, 0, st>>>(ct, cl, ch, crec, d_n, cap, N, d_desc, n_slices, min_cands, ub);
+    else if (N <= 8)
+        k_coarse_graph<8><<<blocks, 256, 0, st>>>(ct, cl, ch, crec, d_n, cap, N, d_desc, n_slices, min_cands, ub);
+    else
+        k_coarse_graph<16><<<blocks, 256, 0, st>>>(ct, cl, ch, crec, d_n, cap, N, d_desc, n_slices, min_cands, ub);
+    const unsigned sb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + 255) / 256, 8 * n_sm));
+    k_coarse_skip<<<sb, 256, 0, st>>>(ub, crec, thr, d_n, cap, min_cands, skip);
+    FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
 

@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
     k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
              const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
              int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
-             const int32_t *d_n_slots = nullptr, int max_P = INT32_MAX) {
+             const int32_t *d_n_slots = nullptr, int max_P = INT32_MAX, const uint8_t *skip = nullptr) {
     const int lane = threadIdx.x & 31;
     const int n_live = d_n_slots ? *d_n_slots : n_slots;
     for (int wi = blockIdx.x * kStitchWarps + (threadIdx.x >> 5); wi < n_live; wi += gridDim.x * kStitchWarps) {
@@ -727,6 +727,10 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
         const RecInfo ri = rinfo[r_id];
         const int P = ri.P;
         if (P > max_P) continue;
+        if (skip && skip[cand]) {  // pruned by a bound: count 0
+            if (lane == 0) counts[cand] = 0;
+            continue;
+        }
         const int4 *base = reinterpret_cast<const int4 *>(
             rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * P) * kRecWords);
         const int per = (P + 31) >> 5;
@@ -763,7 +767,7 @@ __global__ void __launch_bounds__(kStitchBlock, 1)
     k_stitch_block(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
                    const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
                    int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
-                   const int32_t *d_n_slots, int min_P) {
+                   const int32_t *d_n_slots, int min_P, const uint8_t *skip = nullptr) {
     constexpr int W = kStitchBlock / 32;
     __shared__ int32_t s_thr[W][kChunkClasses], s_last[W][kChunkClasses];
     __shared__ uint32_t s_cnt[W][kChunkClasses];
@@ -777,6 +781,10 @@ __global__ void __launch_bounds__(kStitchBlock, 1)
         const RecInfo ri = rinfo[r_id];
         const int P = ri.P;
         if (P <= min_P) continue;  // block-uniform
+        if (skip && skip[cand]) {  // pruned by a bound: count 0 (block-uniform)
+            if (tid == 0) counts[cand] = 0;
+            continue;
+        }
         const int4 *base = reinterpret_cast<const int4 *>(
             rec + (ri.recbase + (int64_t)(slot - ri.slot_first) * P) * kRecWords);
         const int per = (P + kStitchBlock - 1) / kStitchBlock;
@@ -1236,6 +1244,7 @@ struct SparseArgs {
     const int32_t *lo_vals;
     int n_lo;
     int slab;
+    const uint8_t *skip;  // if set, candidates c with skip[c] != 0 are not counted
 };
 
 // RR > 0: register rings.  RR == 0: shared-memory rings in 64-thread blocks,
@@ -1440,6 +1449,7 @@ __global__ void __launch_bounds__(64) k_count_sparse_u(SparseArgs a) {
         const int slot = ri.slot_first + (int)(local / ri.P);
         const int p = (int)(local % ri.P);
         const int cand = a.slot2cand[slot];
+        if (a.skip && a.skip[cand]) continue;  // the stitch writes its count (0)
         const int64_t o = a.offs[cand];
         const int N = (int)(a.offs[cand + 1] - o);
         const int64_t eo = o - cand;
@@ -1788,7 +1798,7 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
                      int64_t cap_threads, const int64_t *offs, const uint16_t *ctypes, const int32_t *clo,
                      const int32_t *chi, const int32_t *slot2cand, const uint32_t *cand_rec, int32_t *rec,
                      const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count,
-                     const uint32_t *const *dens, const int32_t *lo_vals, int n_lo) {
+                     const uint32_t *const *dens, const int32_t *lo_vals, int n_lo, const uint8_t *skip) {
     const int nclass = nmax == 2 ? 0 : nmax == 4 ? 1 : nmax == 8 ? 2 : 3;
     SparseUFn f = sparse_u_fn(nclass);
     if (!f) return FEM_ERR_CUDA;
@@ -1810,6 +1820,7 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
     sa.lo_vals = lo_vals;
     sa.n_lo = n_lo;
     sa.slab = (nodes - 1) * R;  // every node's ring fits R entries (checked by the caller)
+    sa.skip = skip;
     const size_t sm = sparse_u_smem(nmax, sa.slab);
     if (sm > 48 * 1024 &&
         cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
@@ -1828,9 +1839,10 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
     const int64_t gsb = std::min<int64_t>(cap_slots, (int64_t)std::max(1, nsm) * 4);
     if (cap_slots > 0) {
         k_stitch<<<(unsigned)gst, kStitchWarps * 32, 0, st>>>(rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots,
-                                                            counts, fb_list, fb_count, d_n_slots, kStitchSplit);
+                                                            counts, fb_list, fb_count, d_n_slots, kStitchSplit, skip);
         k_stitch_block<<<(unsigned)gsb, kStitchBlock, 0, st>>>(rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots,
-                                                               counts, fb_list, fb_count, d_n_slots, kStitchSplit);
+                                                               counts, fb_list, fb_count, d_n_slots, kStitchSplit,
+                                                               skip);
     }
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;

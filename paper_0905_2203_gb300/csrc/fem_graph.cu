@@ -686,6 +686,14 @@ struct GraphTail {
     std::vector<fem_stream *> recs;
     int n_recs = 0, max_size = 0, first = 3;
     bool prepass = false;
+    // coarse-tick bound of levels >= 3 (prepass = 1); a level below
+    // coarse_min candidates is not bounded
+    int coarse = 0;
+    int64_t coarse_min = 0;
+    int coarse_slices = 8;
+    CoarseDesc *d_cdesc = nullptr;
+    uint32_t *cub = nullptr;
+    uint8_t *skip = nullptr;
     int64_t cap = 0, cap2 = 0, cap_threads = 0;
     std::vector<std::pair<void *, size_t>> held;
     std::vector<FLevel> F;                 // F[N] for N = 1..max_size
@@ -947,6 +955,18 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     FLevel *d_F = nullptr;
     FEM_TRY(g->get(&d_F, (size_t)L + 1));
     FEM_CUDA_TRY(cudaMemcpyAsync(d_F, g->F.data(), sizeof(FLevel) * (L + 1), cudaMemcpyHostToDevice, st));
+    // coarse-tick tables of every recording (built once per stream and tick)
+    if (g->coarse && L >= 3) {
+        std::vector<CoarseDesc> cd(n_recs);
+        for (int r = 0; r < n_recs; ++r)
+            FEM_TRY(coarse_desc(ctx, g->recs[r], coarse_tick(g->recs[r], hi_max, 0), g->coarse_slices, &cd[r]));
+        FEM_TRY(g->get(&g->d_cdesc, (size_t)n_recs));
+        FEM_TRY(g->get(&g->cub, (size_t)cap));
+        FEM_TRY(g->get(&g->skip, (size_t)cap));
+        FEM_CUDA_TRY(cudaMemcpyAsync(g->d_cdesc, cd.data(), sizeof(CoarseDesc) * n_recs, cudaMemcpyHostToDevice, st));
+    } else {
+        g->coarse = 0;
+    }
     FEM_CUDA_TRY(cudaStreamSynchronize(st));
 
     // ---- capture levels first..L
@@ -1024,6 +1044,10 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                                                  g->pfine, g->sstep, g->target);
             }
         }
+        const bool bounded = g->coarse && N >= 3;
+        if (bounded && cst == FEM_OK)
+            cst = coarse_graph_level(st, ctx->n_sm, N, ct, cl, ch, crec, cn, cap, g->d_cdesc, g->coarse_slices,
+                                     g->d_thr, g->coarse_min, g->cub, g->skip);
         k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), g->ring_cap, d_ri,
                                           cn, g->rel + N, n_recs, g->segf, g->pfine, g->sstep, g->segl);
         // external event nodes: their timestamps time the count kernels of
@@ -1032,7 +1056,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         if (cst == FEM_OK)
             cst = launch_count_dev(st, nmax, N, g->ring_cap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch,
                                    iota, crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov,
-                                   (int)lo_vals.size());
+                                   (int)lo_vals.size(), bounded ? g->skip : nullptr);
         ok(cudaEventRecordWithFlags(g->ev[2 * N + 1], st, cudaEventRecordExternal));
         if (fused) {
             k_g_thr_fused<<<1, 1024, 0, st>>>(counts, ct, cl, ch, crec, g->d_thr, N, cap, nf.types, nf.lo, nf.hi,
@@ -1080,12 +1104,12 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
 
 static std::string graph_key(const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
                              const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, int max_size,
-                             int first, bool prepass) {
+                             int first, bool prepass, int coarse) {
     std::ostringstream k;
     for (auto *s : recs) k << (const void *)s << ':' << s->n << ';';
     for (size_t i = 0; i < blo.size(); ++i) k << blo[i] << ',' << bhi[i] << ';';
     for (auto t : thr) k << t << ';';
-    k << max_size << '/' << first << '/' << (prepass ? 1 : 0);
+    k << max_size << '/' << first << '/' << (prepass ? 1 : 0) << '/' << coarse;
     return k.str();
 }
 
@@ -1130,7 +1154,9 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
     const int n_recs = (int)recs.size();
     for (auto *s : recs)
         if (s->n_types > 8192 || s->n > INT32_MAX / 2) return FEM_OK;
-    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass);
+    // coarse-tick bound of levels >= 3: only with prepass = 1
+    const int coarse = ctx->tuning.prepass == 1 ? 1 : 0;
+    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass, coarse);
     int64_t cap = 4096;
     auto hint = ctx->graph_cap.find(key);
     const int64_t want = std::max<int64_t>(cap_min, hint != ctx->graph_cap.end() ? hint->second : 0);
@@ -1154,6 +1180,8 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
         ng->max_size = max_size;
         ng->first = first;
         ng->prepass = prepass;
+        ng->coarse = coarse;
+        ng->coarse_min = 0;
         ng->cap = cap;
         const int st = build_graph(ng.get(), blo, bhi, thr, lo_vals);
         if (st == FEM_ERR_NOMEM || st == FEM_ERR_INVAL) return FEM_OK;  // not applicable: host path

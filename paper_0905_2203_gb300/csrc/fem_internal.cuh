@@ -202,6 +202,22 @@ int coarse_bound_dev(fem_ctx *ctx, fem_stream *s, int64_t n_cand, const int64_t 
 // pass `budget` bytes.
 int32_t coarse_tick(const fem_stream *s, int64_t hi_max, size_t budget);
 void coarse_free(fem_ctx *ctx, fem_stream *s);
+// One recording's coarse-tick tables as the mining graph's bound kernel reads
+// them (the stream cut into n_slices slices).
+struct CoarseDesc {
+    const uint32_t *bits, *cum;
+    const int64_t *toff;
+    const int32_t *ttime;
+    int64_t W, tau0, n_chunks;
+    int32_t w, slice_chunks;
+};
+int coarse_desc(fem_ctx *ctx, fem_stream *s, int32_t w, int n_slices, CoarseDesc *out);
+// Captured-graph level step: bound the *d_n live level-N candidates (fixed
+// stride, recordings crec) and set skip[c] when the bound is at most the
+// recording's threshold (no candidate is skipped below min_cands).
+int coarse_graph_level(cudaStream_t st, int n_sm, int N, const uint16_t *ct, const int32_t *cl, const int32_t *ch,
+                       const uint32_t *crec, const int32_t *d_n, int64_t cap, const CoarseDesc *d_desc, int n_slices,
+                       const uint32_t *thr, int64_t min_cands, uint32_t *ub, uint8_t *skip);
 
 // Device buffers released together at scope exit (after the stream drains).
 struct TmpDev {
@@ -277,7 +293,8 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
                      int64_t cap_threads, const int64_t *offs, const uint16_t *ctypes, const int32_t *clo,
                      const int32_t *chi, const int32_t *slot2cand, const uint32_t *cand_rec, int32_t *rec,
                      const int32_t *d_n_slots, int64_t cap_slots, uint32_t *counts, int32_t *fb_list, int *fb_count,
-                     const uint32_t *const *dens, const int32_t *lo_vals, int n_lo);
+                     const uint32_t *const *dens, const int32_t *lo_vals, int n_lo,
+                     const uint8_t *skip = nullptr);
 size_t sparse_smem_bytes(int nmax, int R);
 // Segment boundaries (P + 1 entries) of a stream cut into P segments at time changes.
 int launch_segments(cudaStream_t st, const int32_t *time, int64_t n, int P, int64_t *seg);

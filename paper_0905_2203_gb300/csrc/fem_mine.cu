@@ -402,10 +402,6 @@ int copy_level_to_host(fem_ctx *ctx, const DevLevel &L, fem_result *res, const s
 // candidates; after the candidates have been counted (by anyone: a counting
 // call of its own, or a launch shared with other groups), advance() applies
 // the threshold and prepares the next level's candidates.
-// Levels >= 3 of at least this many candidates get the coarse-tick bound
-// before the exact count (automatic pre-pass setting).
-constexpr int64_t kCoarseMinCands = 4096;
-
 struct MineGroup {
     fem_ctx *ctx = nullptr;
     std::vector<fem_stream *> recs;
@@ -667,15 +663,16 @@ int MineGroup::gen_join() {
 
 // Coarse-tick bound of the level's candidates (fem_bound.cu), one launch per
 // recording; candidates at or below their threshold are dropped before the
-// exact count.  Automatic for levels of at least kCoarseMinCands candidates
-// (below that the count itself is short), always with prepass = 1, never
-// with prepass = -1 or 2.
+// exact count.  Only with prepass = 1: on the many-recordings workload the
+// bound costs about half of the count it replaces, and the candidates it
+// keeps (frequent types) are the expensive ones, so it does not pay by
+// default.
 int MineGroup::coarse_prune() {
     const int n_recs = nrec();
     const int N = level;
     const int64_t C = cand.n;
     const int pp = ctx->tuning.prepass;
-    if (C == 0 || N < 3 || pp == -1 || pp == 2 || (pp != 1 && C < kCoarseMinCands)) return FEM_OK;
+    if (C == 0 || N < 3 || pp != 1) return FEM_OK;
     cudaStream_t st = ctx->stream;
     const int B = 256;
     int32_t hi_max = 1;

@@ -431,16 +431,16 @@ def test_local_tracking_batches_long_step_arrays(fb, ctx):
 
 def test_coarse_prepass_in_level_wise_mining(fb, ctx):
     """Host-driven mining of two recordings of the many-recordings workload
-    with the coarse-tick bound forced on every level >= 3 (prepass = 1):
-    equal to the oracle miner, with level >= 3 candidates pruned beyond the
-    level-2 pair bound's (prepass = 2 keeps only that one)."""
+    with the coarse-tick bound on every level >= 3 (prepass = 1): equal to
+    the oracle miner, with level >= 3 candidates pruned beyond the level-2
+    pair bound's (prepass = 0 keeps only that one)."""
     recs = synth.c4_recordings(n_rec=2)
     streams = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
     thr = [c["threshold"] for _, c in recs]
     bins = recs[0][1]["bins"]
     stats = {}
     try:
-        for pp in (1, 2):
+        for pp in (1, 0):
             ctx.set_tuning(prepass=pp, level_graph=-1)
             res = ctx.mine_levelwise(streams, bins, thr, 4)
             stats[pp] = res.stats()
@@ -454,8 +454,36 @@ def test_coarse_prepass_in_level_wise_mining(fb, ctx):
         ctx.reset_tuning()
         for st in streams:
             st.free()
-    assert stats[1]["candidates_pruned"] > stats[2]["candidates_pruned"]
-    assert stats[1]["counted_episode_events"] < stats[2]["counted_episode_events"]
+    assert stats[1]["candidates_pruned"] > stats[0]["candidates_pruned"]
+    assert stats[1]["counted_episode_events"] < stats[0]["counted_episode_events"]
+
+
+@pytest.mark.parametrize("pp", [1, 0])
+def test_coarse_bound_inside_mining_graph(fb, ctx, pp):
+    """The whole-pass mining graph with the coarse-tick bound on levels >= 3
+    (prepass = 1; 0 = without it): pruned candidates skip the count kernels
+    and get count 0; the frequent sets of four recordings mined in one call
+    equal the oracle miner's and the graph path is the one that ran."""
+    recs = synth.c4_recordings(n_rec=4)
+    streams = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
+    thr = [c["threshold"] for _, c in recs]
+    bins = recs[0][1]["bins"]
+    wants = [oracle.mine_levelwise(s.types, s.times, s.n_types, bins, c["threshold"], 5) for s, c in recs]
+    try:
+        ctx.set_tuning(prepass=pp)
+        for rep in range(2):  # the first call may grow the graph's capacity; the second reuses it
+            res = ctx.mine_levelwise(streams, bins, thr, 5)
+            st = res.stats()
+            assert rep == 0 or st["graph_tails"] >= 1
+            for r in range(len(recs)):
+                for N in range(1, 6):
+                    eps, counts = res.level(r, N)
+                    assert list(zip(eps, counts)) == wants[r][N], (pp, rep, r, N)
+            res.free()
+    finally:
+        ctx.reset_tuning()
+        for st_ in streams:
+            st_.free()
 
 
 @pytest.mark.parametrize("which", ["c2", "multi"])
