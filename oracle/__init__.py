@@ -187,8 +187,8 @@ def count_many(types, times, offs, ctypes_, lo, hi, threads: int = 0, method: st
 # generated from frequent (N-1)-episodes, counted in one pass, and kept when
 # their count is greater than the threshold).
 #
-# An episode is a tuple (types, lo, hi) of python tuples.  Readings (listed in
-# the design doc): candidates use distinct types; level 2 pairs every ordered pair
+# An episode is a tuple (types, lo, hi) of python tuples.  Readings of what
+# the paper leaves open: candidates use distinct types; level 2 pairs every ordered pair
 # of distinct frequent types with every interval bin; level N >= 3 joins
 # alpha and beta of size N-1 when alpha minus its first node equals beta minus
 # its last node (types and intervals), giving alpha followed by beta's last

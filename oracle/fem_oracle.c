@@ -15,7 +15,7 @@
  *     node, with t_low^k < t_{k+1} - t_k <= t_high^k on every edge k.
  *   - Frequency = size of the largest set of non-overlapped occurrences.
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   R1  Two occurrences are non-overlapped when one ends strictly before the
  *       other starts (Algorithm 1's test "prev_e < s_i", strict in time).
  *   R2  Algorithm 1 starts with prev_e = 0; we start with prev_e = -infinity so
