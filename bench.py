@@ -167,7 +167,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": desc + f" (n={s.n})", "levels": "2 (sample)", "l2": "stream 6.4 MB fits L2"},
+        "config": {"workload": desc + f" (n={s.n})", "levels": "2 (sample)",
+                   "l2": f"stream {6 * s.n / 1e6:.1f} MB fits L2"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
