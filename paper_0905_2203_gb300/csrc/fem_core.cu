@@ -679,7 +679,7 @@ extern "C" const char *fem_strerror(int status) {
         case FEM_ERR_INVAL: return "invalid argument";
         case FEM_ERR_UNSORTED: return "stream times are not non-decreasing";
         case FEM_ERR_DUP: return "stream repeats a (type, time) event";
-        case FEM_ERR_RANGE: return "time out of range (negative)";
+        case FEM_ERR_RANGE: return "time out of range (negative or INT32_MAX)";
         case FEM_ERR_NOMEM: return "device memory budget exceeded";
         case FEM_ERR_TIMEOUT: return "device-side wait timed out";
         case FEM_ERR_CUDA: return "CUDA runtime error";
