@@ -166,8 +166,8 @@ extern "C" int fem_session_append(fem_session *s, const uint16_t *types, const i
     if (!s || n < 0 || (n > 0 && (!types || !times))) return FEM_ERR_INVAL;
     if (n == 0) return FEM_OK;
     fem_ctx *ctx = s->ctx;
-    if (s->n_tail + n > INT32_MAX / 2) return FEM_ERR_INVAL;
     std::lock_guard<std::mutex> g(ctx->mu);
+    if (s->n_tail + n > INT32_MAX / 2) return FEM_ERR_INVAL;
     cudaSetDevice(ctx->device);
     const double t0 = now_s();
     cudaStream_t st = ctx->stream;
