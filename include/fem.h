@@ -98,9 +98,10 @@ typedef struct {
                              CTA, tile size, segment count, kernel) the first
                              time a workload signature is seen and keep the
                              fastest in the context's tuning cache */
-    int kernel;           /* 0 = choose per launch (local tracking for at
-                             most 256 episodes over a recording of at least
-                             2^20 events), 1 = always the tiled
+    int kernel;           /* 0 = choose per launch (grid-wide local
+                             tracking (4) for at most 256 episodes over a
+                             recording of at least 2^20 events, otherwise
+                             warp-per-item local tracking (7)), 1 = always the tiled
                              shared-memory broadcast kernel, 2 = the sparse
                              per-type-list kernel where it applies, 3 = the
                              sparse kernel with per-node branching instead of
@@ -113,13 +114,24 @@ typedef struct {
                              atomics (5) or count, scan and write (6); an
                              episode whose list would pass 2^25 entries is
                              counted as with 4 and adds to
-                             fallback_recounts */
+                             fallback_recounts; 7 = local tracking with one
+                             warp per (episode, segment) work item taken
+                             from an atomic queue by one persistent launch
+                             for every multi-node episode of the call */
     int level_graph;      /* mining: 0 = run the levels as one captured CUDA
                              graph where it applies (all levels when no
                              other override is set and every alphabet has at
                              least 16 types; otherwise levels >= 3 after a
                              host-driven level 2), -1 = level by level from
                              the host */
+    int wait_polls;       /* 0 = default: a wait of the tiled kernel's shared-
+                             memory pipeline gives up after 2^30 polls or 4 s;
+                             n > 0 = after n non-blocking polls (a short limit
+                             for tests of the timeout path).  A wait that gives
+                             up makes the call return FEM_ERR_TIMEOUT; the
+                             kernel first waits (with the default limit) for
+                             its copies in flight, so the context stays
+                             usable */
 } fem_tuning;
 
 /* Per-call statistics filled by the counting / mining calls. */
@@ -134,9 +146,10 @@ typedef struct {
     int64_t candidates_pruned;  /* dropped by the upper-bound pre-pass */
     int64_t fallback_recounts;  /* episodes recounted unsegmented */
     int64_t kernel_launches;    /* library kernels launched by the call */
-    int64_t sparse_launches;    /* counting launches that used the sparse
-                                   per-type-list kernel (the rest used the
-                                   tiled broadcast kernel) */
+    int64_t sparse_launches;    /* counting launches over the per-type
+                                   lists (sparse or warp-per-item local
+                                   tracking kernel; the rest used the tiled
+                                   broadcast kernel) */
     double count_kernel_ms;     /* device time of the exact-count kernels */
     double total_ms;            /* wall time of the call */
     int levels;                 /* mining: deepest level reached */
@@ -257,11 +270,12 @@ int fem_upper_bound_coarse(fem_ctx *ctx, const fem_stream *s, const fem_cands *c
  *   first call before any stream capture.  All calls on a device share the
  *   array, so calls that overlap on the GPU (different host threads or
  *   streams) race and must be serialised by the caller.
- *   Limits: n_cand * 30 <= 4,194,296 (about 139,800 episodes); each episode's
- *   per-node ring holds min(32, 4,194,296 / (n_cand * (largest size - 1)))
- *   timestamps.  FEM_ERR_NOMEM if n_cand is too large or if a burst in the
+ *   Limits: n_cand * (largest size - 1) * 2 <= 4,194,296 (for example
+ *   139,800 episodes of up to 16 nodes, or 2,097,148 of 2 nodes); each
+ *   episode's per-node ring holds min(32, 4,194,296 / (n_cand * (largest
+ *   size - 1))) timestamps.  FEM_ERR_NOMEM if n_cand is too large or if a burst in the
  *   stream needs a longer ring than that (use fem_count_episodes then);
- *   FEM_ERR_INVAL on a malformed candidate.  It performs no stream
+ *   FEM_ERR_INVAL on a malformed candidate or when offs[0] != 0.  It performs no stream
  *   validation: the stream must already satisfy fem_load_stream's rules.
  * The counts are those of fem_count_episodes (one thread per episode, the
  * serial state machine, rings in the static array). */

@@ -50,7 +50,8 @@ class fem_cands(ctypes.Structure):
 
 class fem_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_cta", I32), ("segments", I32), ("tile_events", I32), ("prepass", I32),
-                ("plain_path", I32), ("autotune", I32), ("kernel", I32), ("level_graph", I32)]
+                ("plain_path", I32), ("autotune", I32), ("kernel", I32), ("level_graph", I32),
+                ("wait_polls", I32)]
 
 
 class fem_stats(ctypes.Structure):
@@ -194,8 +195,9 @@ class Context:
             pass
 
     def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0, plain_path=0, autotune=0,
-                   kernel=0, level_graph=0):
-        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path, autotune, kernel, level_graph)
+                   kernel=0, level_graph=0, wait_polls=0):
+        t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path, autotune, kernel, level_graph,
+                       wait_polls)
         check(fem_ctx_set_tuning(self.h, ctypes.byref(t)), "fem_ctx_set_tuning")
 
     def reset_tuning(self):
@@ -446,16 +448,27 @@ class Server:
 def count_episodes_noalloc(types, times, offs, ep_types, lo, hi, out, cuda_stream=None):
     """Counts with no memory allocation (fem_count_episodes_noalloc): every
     argument is a CUDA torch tensor owned by the caller; `out` (uint32 or
-    int32, n_cand) receives the counts.  For callers that cannot allocate
-    device memory at call time; see include/fem.h for the scratch limits and
-    the rule that overlapping calls on one device must be serialised."""
+    int32, n_cand) receives the counts.  Every tensor must sit on the current
+    CUDA device; the work runs on `cuda_stream`, by default torch's current
+    stream.  For callers that cannot allocate device memory at call time; see
+    include/fem.h for the scratch limits and the rule that overlapping calls
+    on one device must be serialised."""
+    import torch
     ptrs = []
+    cur = torch.cuda.current_device()
     for x, dt in ((types, np.uint16), (times, np.int32), (offs, np.int64), (ep_types, np.uint16),
                   (lo, np.int32), (hi, np.int32), (out, np.uint32)):
         p, dev, _ = _ptr(x, dt)
         if not dev:
             raise ValueError("fem_count_episodes_noalloc takes device tensors only")
+        if x.device.index != cur:
+            raise ValueError(f"fem_count_episodes_noalloc: tensor on {x.device}, current device is cuda:{cur}")
         ptrs.append(p)
+    # default: torch's current stream, so the inputs written there are ordered
+    # before the kernels (torch's streams do not synchronise with the legacy
+    # default stream)
+    if cuda_stream is None:
+        cuda_stream = torch.cuda.current_stream(out.device).cuda_stream
     st = VP(int(cuda_stream)) if cuda_stream else None
     check(fem_count_episodes_noalloc(ptrs[0], ptrs[1], int(len(types)), ptrs[2], ptrs[3], ptrs[4], ptrs[5],
                                      int(len(offs) - 1), ptrs[6], st), "fem_count_episodes_noalloc")

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "fem_internal.cuh"
+#include "fem_machine.cuh"
 
 namespace fem {
 
@@ -67,231 +68,9 @@ struct TiledArgs {
     int T;
     int relaxed;
     int small_alpha;      // every type < 128: the warp filter lives in registers
+    uint32_t wait_polls;  // 0: default wait limits; n: pipeline waits give up after n tests
     int32_t *rec;         // records, kRecWords each
     int *status;
-};
-
-// ---------------------------------------------------------------------------
-// Per-node rings of (time, latest start) entries, newest first.  Node 0's
-// latest start is its own time, so it stores times only.
-//
-// Register rings: R entries per node held as a shift register (every index a
-// compile-time constant after unrolling).
-template <int NMAX, int R>
-struct Rings {
-    int32_t t[NMAX - 1][R];
-    int32_t L[NMAX > 2 ? NMAX - 2 : 1][R];
-
-    __device__ __forceinline__ void init(int32_t *, int32_t *, int, int) {
-#pragma unroll
-        for (int k = 0; k < NMAX - 1; ++k)
-#pragma unroll
-            for (int r = 0; r < R; ++r) t[k][r] = INT32_MIN;
-#pragma unroll
-        for (int k = 0; k < (NMAX > 2 ? NMAX - 2 : 1); ++k)
-#pragma unroll
-            for (int r = 0; r < R; ++r) L[k][r] = 0;
-    }
-
-    // Dropping the oldest entry is safe if it is empty, expired for every
-    // query at time >= tt, or if the next-older entry is already past its
-    // lower bound (so the oldest can never again be the newest eligible one).
-    __device__ __forceinline__ void push(int k, int32_t tt, int32_t LL, int32_t lo, int32_t hi, int &flags) {
-        const int32_t o1 = t[k][R - 1], o2 = t[k][R - 2];
-        if (o1 != INT32_MIN && o1 >= tt - hi && o2 >= tt - lo) flags |= kMetaRingOverflow;
-#pragma unroll
-        for (int r = R - 1; r > 0; --r) {
-            t[k][r] = t[k][r - 1];
-            if (k > 0) L[k > 0 ? k - 1 : 0][r] = L[k > 0 ? k - 1 : 0][r - 1];
-        }
-        t[k][0] = tt;
-        if (k > 0) L[k > 0 ? k - 1 : 0][0] = LL;
-    }
-
-    // Newest entry already past its lower bound at time tt; valid when within
-    // the upper bound.  Returns its latest start through LL.
-    __device__ __forceinline__ bool query(int k, int32_t tt, int32_t lo, int32_t hi, int32_t &LL) const {
-        const int32_t elig = tt - lo;
-        int32_t tp = INT32_MIN, lp = 0;
-        bool found = false;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const bool c = !found && (t[k][r] < elig);
-            if (c) {
-                tp = t[k][r];
-                lp = (k == 0) ? t[k][r] : L[k > 0 ? k - 1 : 0][r];
-            }
-            found = found || c;
-        }
-        LL = lp;
-        return found && tp >= tt - hi;
-    }
-};
-
-// Shared-memory rings (R chosen at launch): entry r of node k of this lane at
-// base[(k * R + r) * K]; a per-node head index in registers.
-template <int NMAX>
-struct Rings<NMAX, 0> {
-    int32_t *rt;
-    int32_t *rl;
-    int K;
-    int cap[NMAX - 1];       // entries of node k's ring
-    int off[NMAX - 1];       // first entry of node k's ring in this lane's slab
-    int head[NMAX - 1];
-
-    // Uniform rings: R entries per node.
-    __device__ __forceinline__ void init(int32_t *rt_, int32_t *rl_, int R_, int K_) {
-        rt = rt_;
-        rl = rl_;
-        K = K_;
-#pragma unroll
-        for (int k = 0; k < NMAX - 1; ++k) {
-            head[k] = 0;
-            cap[k] = R_;
-            off[k] = k * R_;
-        }
-        for (int e = 0; e < (NMAX - 1) * R_; ++e) rt[e * K] = INT32_MIN;
-    }
-
-    // Rings sized per node (cap[] already set, at least 2 each); their sum
-    // must fit the lane's slab.
-    __device__ __forceinline__ void init_var(int32_t *rt_, int32_t *rl_, int K_) {
-        rt = rt_;
-        rl = rl_;
-        K = K_;
-        int o = 0;
-#pragma unroll
-        for (int k = 0; k < NMAX - 1; ++k) {
-            head[k] = 0;
-            off[k] = o;
-            o += cap[k];
-        }
-        for (int e = 0; e < o; ++e) rt[e * K] = INT32_MIN;
-    }
-
-    __device__ __forceinline__ void push(int k, int32_t tt, int32_t LL, int32_t lo, int32_t hi, int &flags) {
-        const int h = head[k];
-        const int R = cap[k];
-        int32_t *bt = rt + off[k] * K;
-        int32_t *bl = rl + off[k] * K;
-        const int h2 = (h + 1 == R) ? 0 : h + 1;
-        const int32_t o1 = bt[h * K];
-        const int32_t o2 = bt[h2 * K];
-        if (o1 != INT32_MIN && o1 >= tt - hi && o2 >= tt - lo) flags |= kMetaRingOverflow;
-        bt[h * K] = tt;
-        bl[h * K] = LL;
-        head[k] = h2;
-    }
-
-    __device__ __forceinline__ bool query(int k, int32_t tt, int32_t lo, int32_t hi, int32_t &LL) const {
-        const int R = cap[k];
-        const int32_t *bt = rt + off[k] * K;
-        const int32_t *bl = rl + off[k] * K;
-        const int32_t elig = tt - lo;
-        int idx = head[k];
-        for (int i = 0; i < R; ++i) {
-            idx = (idx == 0) ? R - 1 : idx - 1;
-            const int32_t tp = bt[idx * K];
-            if (tp < elig) {
-                LL = bl[idx * K];
-                return tp >= tt - hi;
-            }
-        }
-        return false;
-    }
-};
-
-// Per-lane machine: the episode, its rings, and Algorithm 1 per entry class.
-template <int NMAX, int RR>
-struct Machine {
-    int N;
-    uint32_t E[NMAX];        // 0xFFFFFFFF beyond N (and for idle lanes)
-    int32_t lo[NMAX - 1];
-    int32_t hi[NMAX - 1];
-    Rings<NMAX, RR> rings;
-    int32_t cthr[kClasses];
-    int32_t cprev[kClasses];
-    uint32_t ccnt[kClasses];
-    int ncls;
-    uint32_t live;           // classes not merged into class 0 (bit 0 = class 0)
-    int32_t M;
-    int open;
-    int flags;
-
-    // Algorithm 1 step for an end event at time t whose latest start is Lq,
-    // for every entry class of this (episode, segment) machine; a new class
-    // is opened while no occurrence has started inside the segment yet.
-    // A class whose last selection equals class 0's has the same future: it
-    // is merged (its count kept as an offset from class 0's), so the steady
-    // state is a single comparison.
-    __device__ __forceinline__ void greedy_end(int32_t t, int32_t Lq, int32_t Tp) {
-        if (!open && live == 1u) {
-            if (Lq > cprev[0]) {
-                ccnt[0] += 1;
-                cprev[0] = t;
-            }
-            return;
-        }
-#pragma unroll
-        for (int j = 0; j < kClasses; ++j)
-            if (((live >> j) & 1u) && Lq > cprev[j]) {
-                ccnt[j] += 1;
-                cprev[j] = t;
-            }
-        if (open && Lq > M) {
-            if (ncls < kClasses) {
-#pragma unroll
-                for (int j = 0; j < kClasses; ++j)
-                    if (j == ncls) {
-                        cthr[j] = Lq;
-                        ccnt[j] = 1;
-                        cprev[j] = t;
-                    }
-                live |= 1u << ncls;
-                ncls += 1;
-            } else {
-                flags |= kMetaClassOverflow;
-            }
-            M = Lq;
-            if (Lq >= Tp) open = 0;
-        }
-#pragma unroll
-        for (int j = 1; j < kClasses; ++j)
-            if (((live >> j) & 1u) && cprev[j] == cprev[0]) {
-                ccnt[j] -= ccnt[0];  // offset from class 0 from here on
-                live &= ~(1u << j);
-            }
-    }
-
-    // Final per-class (count, last selection): merged classes follow class 0.
-    __device__ __forceinline__ void finish() {
-#pragma unroll
-        for (int j = 1; j < kClasses; ++j)
-            if (j < ncls && !((live >> j) & 1u)) {
-                ccnt[j] += ccnt[0];
-                cprev[j] = cprev[0];
-            }
-    }
-
-    // One event offered to this lane's episode.  Nodes are visited last to
-    // first; an entry pushed at time et never serves a query at the same time
-    // (0 <= lo), so the order only mirrors the serial algorithm.
-    __device__ __forceinline__ void step(uint32_t ety, int32_t et, bool in_seg, int32_t Tp) {
-#pragma unroll
-        for (int k = NMAX - 1; k >= 1; --k) {
-            if (E[k] == ety) {
-                int32_t Lq;
-                if (rings.query(k - 1, et, lo[k - 1], hi[k - 1], Lq)) {
-                    if (k == N - 1) {
-                        if (in_seg) greedy_end(et, Lq, Tp);
-                    } else {
-                        rings.push(k, et, Lq, lo[k], hi[k], flags);
-                    }
-                }
-            }
-        }
-        if (E[0] == ety) rings.push(0, et, et, lo[0], hi[0], flags);
-    }
 };
 
 __device__ __forceinline__ int64_t lower_bound_time(const int32_t *tm, int64_t lo, int64_t hi, int64_t v) {
@@ -435,7 +214,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ?
             for (int64_t k = 0; k < ntiles; ++k) {
                 const int s = (int)(k % kStages);
                 if (k >= kStages) {
-                    if (!dev::mbar_wait(&empty[s], (uint32_t)(((k / kStages) - 1) & 1), kMaxPoll, kMaxNs)) {
+                    if (!dev::mbar_wait_n(&empty[s], (uint32_t)(((k / kStages) - 1) & 1), a.wait_polls, kMaxPoll,
+                                          kMaxNs)) {
                         atomicOr(a.status, kStatusTimeout);
                         s_abort = 1;
                         break;
@@ -461,7 +241,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32 + 32, ((NMAX == 2 && RR <= 4) ?
         const bool small = a.small_alpha != 0;
         for (int64_t k = 0; k < ntiles; ++k) {
             const int s = (int)(k % kStages);
-            if (!dev::mbar_wait(&full[s], (uint32_t)((k / kStages) & 1), kMaxPoll, kMaxNs)) {
+            if (!dev::mbar_wait_n(&full[s], (uint32_t)((k / kStages) & 1), a.wait_polls, kMaxPoll, kMaxNs)) {
                 atomicOr(a.status, kStatusTimeout);
                 s_abort = 1;
                 break;
@@ -942,6 +722,7 @@ struct PrepArgs {
     int n_recs;
     int mode;                  // 0 exact, 1 plain, 2 relaxed (upper bound)
     int force_plain_ring;
+    int track;                 // every multi-node episode in bucket 0 (local-tracking kernel)
     int32_t *key;              // out: bucket * n_recs + rec
     int32_t *ring;             // out: R per candidate
     int *bucket_maxR;          // out: per bucket max R
@@ -1012,6 +793,8 @@ __global__ void k_prep(PrepArgs a) {
         bucket = kBucketPlain;
     } else if (N == 1) {
         bucket = kBucketN1;
+    } else if (a.track) {
+        bucket = 0;  // one launch for every size and ring: the kernel keeps no rings
     } else if (R > kMaxRingTiled || a.force_plain_ring) {
         bucket = kBucketPlain;
     } else {
@@ -1770,7 +1553,12 @@ int stream_bytype(fem_ctx *ctx, fem_stream *s) {
         FEM_CUDA_TRY(cudaMemsetAsync(toff, 0, sizeof(int64_t) * (s->n_types + 1), cs));
     }
     FEM_CUDA_TRY(cudaGetLastError());
+    // longest per-type list (sizes the per-warp buffers of local tracking)
+    std::vector<int64_t> toff_h(s->n_types + 1, 0);
+    FEM_CUDA_TRY(cudaMemcpyAsync(toff_h.data(), toff, sizeof(int64_t) * (s->n_types + 1), cudaMemcpyDeviceToHost, cs));
     FEM_CUDA_TRY(cudaStreamSynchronize(cs));
+    s->max_list = 0;
+    for (uint32_t a = 0; a < s->n_types; ++a) s->max_list = std::max(s->max_list, toff_h[a + 1] - toff_h[a]);
     s->d_toff = toff;
     s->d_ttime = ttime;
     s->bytes += sizeof(int64_t) * (s->n_types + 1) + sizeof(int32_t) * n;
@@ -1925,6 +1713,22 @@ static int run_count(CountCall &cc, const int32_t *subset, int64_t n_sub, int fo
 static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int force_segments) {
     fem_ctx *ctx = cc.ctx;
     const int n_recs = (int)cc.recs.size();
+    // Local tracking, one warp per (episode, segment), one launch for every
+    // multi-node episode: the default (kernel 0) and kernel 7; the last
+    // fallback round and the explicit kernel choices 1-3 keep the
+    // per-episode state machines.
+    bool track = (ctx->tuning.kernel == 0 || ctx->tuning.kernel == 7) && !cc.force_tiled && cc.mode != 1;
+    for (auto *r : cc.recs)
+        if (r->n_types > 8192 || r->n > INT32_MAX / 2) track = false;
+    if (track)
+        for (auto *r : cc.recs) {
+            const int sb = stream_bytype(ctx, r);
+            if (sb == FEM_ERR_NOMEM) {
+                track = false;
+                break;
+            }
+            if (sb != FEM_OK) return sb;
+        }
     const int n_keys = kBuckets * n_recs;
     // --- density tables and per-recording tables
     std::vector<int32_t> lov = cc.lo_vals;
@@ -1951,7 +1755,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     const size_t o_lo = carve(lov.size() * 4), o_nt = carve(n_recs * 4),
                  o_dp = carve(dens_h.size() * sizeof(void *)), o_ri = carve(n_recs * sizeof(RecInfo)),
                  o_bm = carve(4 * kBuckets * 4), o_rel = carve(8), o_fb = carve(8),
-                 o_units = carve(2 * kBuckets * 8);
+                 o_units = carve(2 * kBuckets * 8), o_q = carve(8);
     void *misc = nullptr;
     FEM_TRY(scratch(ctx, kSlotMisc, off, &misc));
     char *mb = static_cast<char *>(misc);
@@ -2004,6 +1808,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     pa.n_recs = n_recs;
     pa.mode = cc.mode;
     pa.force_plain_ring = 0;
+    pa.track = track ? 1 : 0;
     pa.key = d_key;
     pa.ring = d_ring;
     pa.bucket_maxR = reinterpret_cast<int *>(mb + o_bm);
@@ -2044,6 +1849,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     struct Plan {
         int bucket;
         bool sparse;
+        bool track = false;   // local-tracking kernel (bucket 0 in track mode)
         int K, R, nclass, T;
         int slab;         // largest sum of per-node ring sizes in the bucket
         std::vector<RecInfo> ri;
@@ -2061,6 +1867,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         Plan pl;
         pl.bucket = b;
         pl.sparse = sparse;
+        pl.track = sparse && track && b == 0;
         pl.nclass = b / kBucketRing;
         pl.R = std::max(bmax[b], 2);
         pl.slab = std::max(bmax[3 * kBuckets + b], 2);
@@ -2076,7 +1883,8 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         double seg_len;
         if (sparse) {
             // enough (episode, segment) threads to fill the GPU ~4 times
-            const double desired = 4.0 * ctx->n_sm * 2048.0;
+            // (local tracking: about four work items per resident warp)
+            const double desired = pl.track ? 4.0 * track_blocks(ctx->n_sm) * kTrackWarps : 4.0 * ctx->n_sm * 2048.0;
             double work = 0;
             for (int r = 0; r < n_recs; ++r) {
                 const int c = key_off[b * n_recs + r + 1] - key_off[b * n_recs + r];
@@ -2170,6 +1978,40 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         FEM_CUDA_TRY(cudaMemcpyAsync(d_ri, pl.ri.data(), pl.ri.size() * sizeof(RecInfo), cudaMemcpyHostToDevice,
                                      ctx->stream));
         *d_ri_out = d_ri;
+        if (pl.track) {
+            // per-warp entry lists: 4 x (longest per-type list) words each;
+            // fewer resident warps when that would pass a quarter of the
+            // free budget
+            int64_t cap = 1;
+            for (int r = 0; r < n_recs; ++r) cap = std::max(cap, cc.recs[r]->max_list);
+            int blocks = track_blocks(ctx->n_sm);
+            const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+            while (blocks > ctx->n_sm && track_buf_bytes(blocks, cap) > free_b / 4) blocks -= ctx->n_sm;
+            const int64_t n_items = limit > 0 ? std::min(limit, pl.records) : pl.records;
+            blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (n_items + kTrackWarps - 1) / kTrackWarps));
+            void *pb = nullptr;
+            FEM_TRY(scratch(ctx, kSlotTrack, track_buf_bytes(blocks, cap) + 256, &pb));
+            TrackArgs ta{};
+            ta.rinfo = d_ri;
+            ta.n_recs = n_recs;
+            ta.rec_first = pl.ri.empty() ? 0 : pl.ri[0].recbase;
+            ta.n_items = n_items;
+            ta.d_n_items = nullptr;
+            ta.offs = cc.offs;
+            ta.ctypes = cc.types;
+            ta.clo = cc.lo;
+            ta.chi = cc.hi;
+            ta.slot2cand = d_perm;
+            ta.relaxed = cc.mode == 2;
+            ta.skip = nullptr;
+            ta.queue = reinterpret_cast<unsigned long long *>(mb + o_q);
+            ta.buf = reinterpret_cast<int32_t *>(static_cast<char *>(pb) + 256);
+            ta.cap = cap;
+            ta.rec = rec_base;
+            FEM_TRY(launch_track(ctx->stream, blocks, ta));
+            cc.stats.kernel_launches += 2;  // queue reset + kernel
+            return FEM_OK;
+        }
         if (pl.sparse) {
             SparseArgs sa{};
             sa.rinfo = d_ri;
@@ -2234,6 +2076,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         ta.T = pl.T;
         ta.relaxed = cc.mode == 2;
         ta.small_alpha = small_alpha ? 1 : 0;
+        ta.wait_polls = (uint32_t)ctx->tuning.wait_polls;
         ta.rec = rec_base;
         ta.status = ctx->d_status;
         const int64_t n_items = limit > 0 ? std::min<int64_t>(limit, pl.items.size()) : (int64_t)pl.items.size();
@@ -2271,6 +2114,13 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         }
         if (b == kBucketPlain) {
             plain_buckets.push_back(b);
+            continue;
+        }
+        if (track && b == 0) {
+            // local tracking: one plan, every multi-node episode, no tuning
+            Plan pl = make_plan(b, true, 32, T_def, 1.0, records_needed);
+            records_needed += pl.records;
+            plans.push_back(std::move(pl));
             continue;
         }
         const int nclass = b / kBucketRing;

@@ -67,6 +67,31 @@ struct RecInfo {
     int sstep;
 };
 
+// Node-by-node local tracking with one warp per (episode, segment) work item
+// (fem_track.cu).  Items are numbered like the records of the other counting
+// kernels (recording-major, then episode slot, then segment) and taken from
+// an atomic counter by a persistent grid.
+constexpr int kTrackWarps = 8;           // warps per block
+constexpr int kTrackMaxBlocksPerSm = 4;  // resident blocks per SM the grid asks for
+struct TrackArgs {
+    const RecInfo *rinfo;
+    int n_recs;
+    int64_t rec_first;           // first record index of this launch
+    int64_t n_items;             // items (records) of this launch ...
+    const int64_t *d_n_items;    // ... or, if set, read from device memory
+    const int64_t *offs;
+    const uint16_t *ctypes;
+    const int32_t *clo;
+    const int32_t *chi;
+    const int32_t *slot2cand;
+    int relaxed;                 // every lower bound taken as 0 (upper bound)
+    const uint8_t *skip;         // if set, candidates c with skip[c] != 0 are not counted
+    unsigned long long *queue;   // work counter (zeroed by launch_track)
+    int32_t *buf;                // per warp 4 * cap words (entry lists, ping-pong)
+    int64_t cap;                 // at least the longest per-type list of every recording
+    int32_t *rec;                // records, kRecWords each
+};
+
 // Results of the levels of level-wise mining run in a captured graph.
 struct TailLevel {
     int N = 0;
@@ -148,6 +173,7 @@ struct fem_stream {
     int32_t t_first = 0, t_last = 0;  // first and last event time (n > 0)
     int64_t *d_toff = nullptr;    // per-type event lists (built on first use): offsets [n_types + 1]
     int32_t *d_ttime = nullptr;   // times grouped by type, ascending within a type [n]
+    int64_t max_list = 0;         // longest per-type list (set with the lists)
     std::map<int32_t, uint32_t *> dens;  // lo -> per-type max events in a closed window of length lo
     std::map<int, int64_t *> segs;       // P -> segment boundaries (P + 1), cached
     std::map<int32_t, fem_coarse_tab> coarse;  // tick width -> coarse-tick tables
@@ -259,11 +285,18 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
               bool relaxed, uint32_t *d_counts, fem_stats *stats, float *kernel_ms, int variant,
               const PltSession *sess = nullptr);
 
+// Persistent grid of the local-tracking kernel on this device (blocks), the
+// bytes of its per-warp buffers, and its launch (queue reset + kernel).
+int track_blocks(int n_sm);
+size_t track_buf_bytes(int blocks, int64_t cap);
+int launch_track(cudaStream_t st, int blocks, const TrackArgs &a);
+
 // Scratch slot ids.
 enum Slot : int {
     kSlotCandOffs = 1, kSlotCandTypes, kSlotCandLo, kSlotCandHi, kSlotCandRec,
     kSlotPrep, kSlotPerm, kSlotBucket, kSlotRecords, kSlotSeg, kSlotCounts,
     kSlotFallback, kSlotRings, kSlotDensTab, kSlotScanTmp, kSlotMisc, kSlotRecTab, kSlotDensArgs,
+    kSlotTrack,
     kSlotMine0 = 64,
 };
 
@@ -364,6 +397,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -381,6 +427,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 255u) == 255u && globaltimer_ns() - t0 > max_ns) return false;
     }
+    return false;
+}
+
+// A wait with a caller-chosen limit: polls > 0 gives up after that many
+// non-blocking tests; polls == 0 is mbar_wait with the given defaults.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t *bar, uint32_t parity, uint32_t polls, uint32_t max_iter,
+                                            uint64_t max_ns) {
+    if (polls == 0) return mbar_wait(bar, parity, max_iter, max_ns);
+    for (uint32_t i = 0; i < polls; ++i)
+        if (mbar_test_wait(bar, parity)) return true;
     return false;
 }
 

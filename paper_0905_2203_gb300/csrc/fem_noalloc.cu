@@ -47,12 +47,16 @@ int noalloc_setup(int dev, int32_t **out) {
     return FEM_OK;
 }
 
-// Header: [0] error bits (1 invalid candidate, 2 ring capacity exceeded),
+// Header: [0] error bits (1 invalid candidate or offs[0] != 0, 2 ring
+// capacity exceeded),
 // [1] largest episode size.
 __global__ void k_noalloc_check(const int64_t *__restrict__ offs, const uint16_t *__restrict__ ctypes,
                                 const int32_t *__restrict__ clo, const int32_t *__restrict__ chi, int64_t n_cand,
                                 int32_t *hdr) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // The CSR must start at 0: the kernels index types and bounds from
+    // offs[c], so a slice of a larger candidate set would read past them.
+    if (c == 0 && offs[0] != 0) atomicOr(&hdr[0], 1);
     if (c >= n_cand) return;
     const int64_t o = offs[c];
     const int64_t N = offs[c + 1] - o;
@@ -152,8 +156,9 @@ extern "C" int fem_count_episodes_noalloc(const uint16_t *types, const int32_t *
     if (n < 0 || n_cand < 0) return FEM_ERR_INVAL;
     if (n_cand == 0) return FEM_OK;
     if (!offs || !ep_types || !lo || !hi || !counts || (n > 0 && (!types || !times))) return FEM_ERR_INVAL;
-    // At least two ring entries for each of up to 15 edges per episode.
-    if ((size_t)n_cand * (FEM_MAX_NODES - 1) * 2 > kNoallocWords - kNoallocHeader) return FEM_ERR_NOMEM;
+    // At least two ring entries per edge: checked against the largest
+    // episode below; every episode has at least one edge or none.
+    if ((size_t)n_cand * 2 > kNoallocWords - kNoallocHeader) return FEM_ERR_NOMEM;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return FEM_ERR_CUDA;
     int32_t *scratch = nullptr;

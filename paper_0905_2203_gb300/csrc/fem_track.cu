@@ -1,0 +1,248 @@
+// fem_track.cu -- exact counting by node-by-node local tracking, one warp per
+// (episode, segment) work item, in one persistent launch fed by an atomic
+// work queue.
+//
+// The count is the size of the largest set of non-overlapped occurrences,
+// found by Algorithm 1 ("Problem decomposition") over end events, each with
+// the LATEST start of an occurrence ending there:
+//     L_1(j) = t_j,   L_k(j) = max { L_{k-1}(i) : lo < t_j - t_i <= hi }.
+// Over the events of node k-1 that have a valid L (the node's entries), L is
+// non-decreasing in time, so L_k(j) is the L of the newest entry older than
+// t_j - lo, provided that entry is not older than t_j - hi.  Section
+// "Parallel Local Tracking" tracks an episode node by node over the per-type
+// event lists; here one warp does that for one work item:
+//   * node k's events (its type's list, inside the segment and its halo) are
+//     taken 32 at a time, one per lane, in time order;
+//   * each lane finds its predecessor among node k-1's entries with a window
+//     walk: the warp loads 32 consecutive entries, every lane ranks its own
+//     query in them by a 5-step binary search over the lanes' registers, and
+//     the window moves on until every lane has its rank; queries of a node
+//     come in time order, so the window only moves forward;
+//   * the lanes that found a valid predecessor append (t, L) to the node's
+//     entry list in the warp's buffer (ballot + prefix count);
+//   * at the last node the valid ends inside the segment are handed, in time
+//     order, to Algorithm 1 for every entry class of the segment (the same
+//     machine and record as the other counting kernels, so k_stitch composes
+//     the segments; section "MapConcat").
+// Every lane of the warp does the same work on the same list, so lanes stay
+// converged, list reads are coalesced and no per-node ring is needed: the
+// entry lists live in a per-warp global buffer of 4 x (longest list) words.
+//
+// The launch is persistent: each warp takes the next item index from a
+// counter until the items run out, so items of very different lengths (long
+// and short recordings, short and long episodes) balance across the GPU.
+#include <algorithm>
+
+#include "fem_internal.cuh"
+#include "fem_machine.cuh"
+
+namespace fem {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// First i in [lo, hi) with v[i] >= q (hi if none), computed by the whole warp
+// (every lane returns it): a 32-way search whose probes are one strided load.
+__device__ __forceinline__ int64_t warp_lower_bound(const int32_t *__restrict__ v, int64_t lo, int64_t hi, int64_t q,
+                                                    int lane) {
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t pos = lo + step * (lane + 1) - 1;
+        const bool below = pos < hi && (int64_t)v[pos] < q;
+        const int c = __popc(__ballot_sync(kFull, below));
+        if (c == 32) return hi;
+        // probe c is the first at or above q (or past hi): the answer lies
+        // after probe c-1 and at or before probe c
+        const int64_t pc = lo + step * (c + 1) - 1;
+        lo = lo + step * c;
+        hi = pc + 1 < hi ? pc + 1 : hi;
+    }
+    const int64_t pos = lo + lane;
+    const bool below = pos < hi && (int64_t)v[pos] < q;
+    return lo + __popc(__ballot_sync(kFull, below));
+}
+
+// Number of the 32 values held one per lane (ascending with the lane) that
+// are below q, for this lane's own q.
+__device__ __forceinline__ int window_rank(int32_t vt, int64_t q) {
+    int c = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const int32_t v = __shfl_sync(kFull, vt, c + s - 1);
+        if ((int64_t)v < q) c += s;
+    }
+    const int32_t v31 = __shfl_sync(kFull, vt, 31);
+    if (c == 31 && (int64_t)v31 < q) c = 32;
+    return c;
+}
+
+__global__ void __launch_bounds__(kTrackWarps * 32, 4) k_count_track(TrackArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int32_t *const bT0 = a.buf + gw * 4 * a.cap;
+    int32_t *const bL0 = bT0 + a.cap;
+    int32_t *const bT1 = bT0 + 2 * a.cap;
+    int32_t *const bL1 = bT0 + 3 * a.cap;
+    const int64_t n_items = a.d_n_items ? *a.d_n_items : a.n_items;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(a.queue, 1ull);
+        it = __shfl_sync(kFull, it, 0);
+        if ((int64_t)it >= n_items) break;
+        const int64_t tr = a.rec_first + (int64_t)it;
+        int lo_r = 0, hi_r = a.n_recs;  // last recording whose records start at or before tr
+        while (hi_r - lo_r > 1) {
+            const int mid = (lo_r + hi_r) >> 1;
+            if (a.rinfo[mid].recbase <= tr) lo_r = mid; else hi_r = mid;
+        }
+        const RecInfo &ri = a.rinfo[lo_r];
+        const int P = ri.P;
+        const int64_t local = tr - ri.recbase;
+        const int slot = ri.slot_first + (int)(local / P);
+        const int p = (int)(local % P);
+        const int cand = a.slot2cand[slot];
+        if (a.skip && a.skip[cand]) continue;  // the stitch writes its count (0)
+        const int64_t o = a.offs[cand];
+        const int N = (int)(a.offs[cand + 1] - o);
+        const int64_t eo = o - cand;
+
+        Machine<2, 0> st;  // Algorithm 1 per entry class (its rings are unused); the same in every lane
+        st.N = N;
+        st.ncls = 0;
+        st.live = 0;
+        st.M = INT32_MIN;
+        st.open = 1;
+        st.flags = 0;
+#pragma unroll
+        for (int j = 0; j < kClasses; ++j) {
+            st.cthr[j] = 0;
+            st.cprev[j] = 0;
+            st.ccnt[j] = 0;
+        }
+        int64_t sumhi = 0;
+        for (int k = 0; k < N - 1; ++k) sumhi += a.chi[eo + k];
+        const int64_t seg_b = ri.seg[p], seg_e = ri.seg[p + 1];
+        if (seg_b < seg_e && N >= 2) {
+            const int32_t Tp = ri.time[seg_b];
+            const int64_t haloT = (p == 0) ? INT64_MIN : (int64_t)Tp - sumhi;
+            const int64_t Tend = (seg_e < ri.n) ? (int64_t)ri.time[seg_e] : INT64_MAX;
+            const int64_t *toff = ri.toff;
+            const int32_t *ttime = ri.ttime;
+            // list range of type E inside [haloT, Tend)
+            auto range = [&](uint32_t E, int64_t &b, int64_t &e) {
+                const int64_t b0 = toff[E], b1 = toff[E + 1];
+                if (ri.tseg) {
+                    const int32_t *tq = ri.tseg + (size_t)E * ri.tstride;
+                    const int qmax = ri.tstride - 1;
+                    const int64_t s0 = b0 + tq[min(p * ri.sstep, qmax)];
+                    e = b0 + tq[min((p + 1) * ri.sstep, qmax)];
+                    b = (p == 0) ? s0 : warp_lower_bound(ttime, b0, s0, haloT, lane);
+                } else {
+                    b = (p == 0) ? b0 : warp_lower_bound(ttime, b0, b1, haloT, lane);
+                    e = (seg_e < ri.n) ? warp_lower_bound(ttime, b, b1, Tend, lane) : b1;
+                }
+            };
+            int64_t pb = 0, pe = 0;
+            range(a.ctypes[o], pb, pe);
+            // node k-1's entries: times pT[0..m), latest starts pL (node 0: its times)
+            const int32_t *pT = ttime + pb;
+            const int32_t *pL = nullptr;
+            int64_t m = pe - pb;
+            for (int k = 1; k < N && m > 0; ++k) {
+                const uint32_t E = a.ctypes[o + k];
+                const int32_t lo_e = a.relaxed ? 0 : a.clo[eo + k - 1];
+                const int32_t hi_e = a.chi[eo + k - 1];
+                int64_t cb = 0, ce = 0;
+                range(E, cb, ce);
+                const bool last = (k == N - 1);
+                int32_t *oT = (k & 1) ? bT1 : bT0;
+                int32_t *oL = (k & 1) ? bL1 : bL0;
+                int64_t w = 0;   // window start: every remaining query ranks at or after it
+                int64_t wc = 0;  // entries written for node k
+                for (int64_t base = cb; base < ce; base += 32) {
+                    const int64_t j = base + lane;
+                    const bool in = j < ce;
+                    const int32_t t = in ? ttime[j] : INT32_MAX;
+                    const int64_t q = in ? (int64_t)t - lo_e : INT64_MAX;
+                    const int64_t q0 = (int64_t)__shfl_sync(kFull, t, 0) - lo_e;
+                    int64_t idx = 0;
+                    bool done = !in;
+                    for (;;) {
+                        const int64_t wi = w + lane;
+                        const int32_t vt = wi < m ? pT[wi] : INT32_MAX;
+                        const int32_t top = __shfl_sync(kFull, vt, 31);
+                        if ((int64_t)top < q0 && w + 32 < m) {  // the whole window precedes every query
+                            w += 32;
+                            continue;
+                        }
+                        const int c = window_rank(vt, q);
+                        if (!done && c < 32) {
+                            idx = w + c;
+                            done = true;
+                        }
+                        if (__all_sync(kFull, done)) break;
+                        w += 32;
+                    }
+                    bool ok = false;
+                    int32_t Lv = 0;
+                    if (in && idx > 0) {
+                        const int32_t tp = pT[idx - 1];
+                        if ((int64_t)tp >= (int64_t)t - hi_e) {
+                            ok = true;
+                            Lv = pL ? pL[idx - 1] : tp;
+                        }
+                    }
+                    if (!last) {
+                        const unsigned bm = __ballot_sync(kFull, ok);
+                        if (ok) {
+                            const int r = __popc(bm & ((1u << lane) - 1u));
+                            oT[wc + r] = t;
+                            oL[wc + r] = Lv;
+                        }
+                        wc += __popc(bm);
+                    } else {
+                        unsigned bm = __ballot_sync(kFull, ok && t >= Tp);
+                        while (bm) {
+                            const int b = __ffs(bm) - 1;
+                            bm &= bm - 1;
+                            st.greedy_end(__shfl_sync(kFull, t, b), __shfl_sync(kFull, Lv, b), Tp);
+                        }
+                    }
+                    // the next 32 queries rank at or after this chunk's last one
+                    w = __shfl_sync(kFull, idx, 31);
+                }
+                // node k's entries become the predecessors of node k+1
+                __syncwarp();
+                pT = oT;
+                pL = oL;
+                m = wc;
+            }
+        }
+        st.finish();
+        if (lane == 0) write_record(a.rec + tr * kRecWords, st);
+    }
+}
+
+}  // namespace
+
+int track_blocks(int n_sm) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_track, kTrackWarps * 32, 0);
+    cudaGetLastError();
+    return std::max(1, n_sm) * std::max(1, std::min(per_sm, kTrackMaxBlocksPerSm));
+}
+
+size_t track_buf_bytes(int blocks, int64_t cap) {
+    return (size_t)blocks * kTrackWarps * 4 * (size_t)std::max<int64_t>(cap, 1) * sizeof(int32_t);
+}
+
+int launch_track(cudaStream_t st, int blocks, const TrackArgs &a) {
+    if (blocks < 1) return FEM_OK;
+    if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st) != cudaSuccess) return FEM_ERR_CUDA;
+    k_count_track<<<(unsigned)blocks, kTrackWarps * 32, 0, st>>>(a);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+}  // namespace fem

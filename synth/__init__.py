@@ -135,6 +135,18 @@ def _in_windows(ts: np.ndarray, starts: np.ndarray, ends: np.ndarray) -> np.ndar
     return res
 
 
+def _sorted_unique(key: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (np.unique's result, by a plain sort and a
+    neighbour comparison, which stays fast on tens of millions of keys)."""
+    key = np.sort(key)
+    if key.size:
+        keep = np.empty(key.size, bool)
+        keep[0] = True
+        np.not_equal(key[1:], key[:-1], out=keep[1:])
+        key = key[keep]
+    return key
+
+
 def _finish(types_list, times_list, tick_s: float, n_types: int, chains, meta) -> Stream:
     ty = np.concatenate(types_list).astype(np.int64) if types_list else np.zeros(0, np.int64)
     ts = np.concatenate(times_list) if times_list else np.zeros(0)
@@ -144,7 +156,7 @@ def _finish(types_list, times_list, tick_s: float, n_types: int, chains, meta) -
     if ticks.size and ticks.max() >= 2**31 - 1:
         raise ValueError("stream span overflows int32 ticks")
     key = ticks * 65536 + ty
-    key = np.unique(key)  # sorts by (time, type) and drops (type, tick) duplicates
+    key = _sorted_unique(key)  # sorts by (time, type) and drops (type, tick) duplicates
     times = (key // 65536).astype(np.int32)
     types = (key % 65536).astype(np.uint16)
     return Stream(types, times, n_types, tick_s, chains, meta)
@@ -393,7 +405,7 @@ def tiny_random_stream(rng_seed: int, n: int, n_types: int, t_max: int, sid: int
     r = Rng(rng_seed, 100 + sid)
     ty = r.integers(0, n_types - 1, n)
     tm = r.integers(0, t_max, n)
-    key = np.unique(tm * 65536 + ty)
+    key = _sorted_unique(tm * 65536 + ty)
     tm = key // 65536
     ty = key % 65536
     # random order among equal times (Definition 1 allows any order of ties)

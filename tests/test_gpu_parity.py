@@ -102,15 +102,16 @@ def test_golden_cases_on_gpu(fb, ctx):
         st.free()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [1, 2, 4, 5, 6, 7])
 @pytest.mark.parametrize("segments,lanes,tile", [(0, 0, 0), (1, 32, 256), (7, 64, 512), (64, 256, 1024),
                                                   (300, 96, 4096)])
 def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
     """Many random episodes (sizes 1-6, lower bounds 0..6) over random streams
     with frequent equal times, under several segment / CTA / tile settings,
-    with the tiled (1) and the sparse (2) counting kernel and with local
-    tracking (4: latest starts; 5 / 6: occurrence lists compacted by atomics
-    / count-scan-write; segment settings do not apply to local tracking)."""
+    with the tiled (1) and the sparse (2) counting kernel, with grid-wide
+    local tracking (4: latest starts; 5 / 6: occurrence lists compacted by
+    atomics / count-scan-write; segment settings do not apply to them) and
+    with warp-per-item local tracking (7; segments apply)."""
     r = synth.Rng(99, segments + 7)
     ctx.set_tuning(lanes_per_cta=lanes, segments=segments, tile_events=tile, kernel=kernel)
     try:
@@ -136,7 +137,7 @@ def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
         ctx.reset_tuning()
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5, 6, 7])
 @pytest.mark.parametrize("segments", [0, 33, 1000, 4099])
 def test_few_episodes_many_segments(fb, ctx, segments, kernel):
     """Few episodes over the 1M-event mid stream cut into up to ~4k segments:
@@ -188,7 +189,7 @@ def test_upper_bound_is_relaxed_count(fb, ctx):
     st.free()
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5, 6])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5, 6, 7])
 def test_bursty_stream_mixed_sizes(fb, ctx, kernel):
     """Network bursts (dense windows) with sizes 2-8 and the 4-bin set."""
     s = synth.bursty_60(0xFE0003, 150_000)
