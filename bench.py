@@ -1,15 +1,24 @@
 """Benchmark: level-wise frequent-episode mining on GB300.
 
 One step = one full level-wise mining pass (levels 1..6: candidate
-generation, exact counting, threshold) over the mid-size spike-train workload
-(128 neurons, log-normal 2-20 Hz, 1 us ticks, ~1.07M events, six embedded
-chains, bins {(0,5],(5,10],(10,15],(15,20]} ms, threshold 0.25% of n).
+generation, upper-bound pre-pass, exact counting, threshold) over the
+many-recordings workload: 256 synthetic 60-channel spike-train recordings of
+log-uniform lengths 1e4..5e6 events (about 2.2e8 events in all, 10 us ticks,
+three embedded chains each, bins {(0,5],(5,10],(10,15],(15,20]} ms, threshold
+max(20, 0.25% of n) per recording), every recording mined in the same call.
 
-Metric: episode-events counted per second = sum over every counted
-(candidate, recording) of the recording's event count, divided by the step
-time.  `value` times the step with the stream already resident in HBM;
-`e2e` times the same step through the C ABI from host buffers (stream upload,
-mining, result download inside the timed region).
+Metric: episode-events counted per second = sum over every exactly counted
+(candidate, recording) pair of the recording's event count, divided by the
+step time.  Candidates that the level-2 pre-pass proves infrequent are not
+counted and are reported apart (`pruned`).  `value` times the step with the
+streams already resident in HBM; `e2e` times the same step through the C ABI
+from pinned host buffers (stream upload, mining, result download inside the
+timed region).
+
+Beside the headline: the plain per-level GPU path on a sample of recordings
+(and the library on the same sample), the mid-size single recording mining
+pass, the 200k-candidate batched counting call, the serving workload (Poisson
+job arrivals, 200 jobs plus one 1e8-event stress job), and the CPU oracle.
 
 Multi-GPU: the path does not shard (replicas only); with N ranks each rank
 mines its own replica and value = all ranks' episode-events / max rank time.
@@ -20,6 +29,7 @@ cores) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -36,6 +46,10 @@ import synth  # noqa: E402
 
 METRIC = "episode-events counted/s (level-wise mining pass, exact)"
 UNIT = "episode-events/s"
+C4_DESC = ("batched multi-recording mining: 256 synthetic 60-channel recordings, lengths log-uniform "
+           "1e4-5e6 events, 10 us ticks, levels 1-6, threshold max(20, 0.25% n)")
+TRACK_SRC = os.path.join(ROOT, "paper_0905_2203_gb300", "csrc", "fem_track.cu")
+COUNTERS = os.path.join(ROOT, "profiles", "track_counters.json")
 
 
 def _peaks():
@@ -43,6 +57,23 @@ def _peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 class ClockSampler:
@@ -118,97 +149,192 @@ def aggregate_over_ranks(local_ms: float, local_units: float, world: int, device
     return t_max, float(sm[1].item()) / (t_max / 1e3)
 
 
-def workload(name: str):
-    if name == "c2":
-        s, cfg = synth.c2_mid()
-        return s, cfg, "plain level-wise mining, mid: 128 neurons, lognormal 2-20 Hz, 1 us ticks"
-    if name == "c1":
-        s, cfg = synth.c1_tiny()
-        return s, cfg, "plain level-wise mining, tiny: 32 neurons, 5 Hz, 30 s, 1 ms ticks"
-    raise SystemExit(f"unknown workload {name}")
+def track_counters():
+    """ncu counters of the local-tracking count kernel (DRAM bytes and issue
+    activity of one launch, from the committed profile summary), or None once
+    the kernel source has changed since they were taken."""
+    try:
+        d = json.load(open(COUNTERS))
+        sha = hashlib.sha256(open(TRACK_SRC, "rb").read()).hexdigest()[:16]
+        return d if d.get("kernel_sha16") == sha else None
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# Workload pieces
+
+def c4_workload(n_rec: int = 256):
+    """The first n_rec of the 256 recordings (all by default)."""
+    return synth.c4_recordings(which=range(n_rec))
+
+
+def plain_sample(recs, max_events: int = 3_000_000):
+    """Indices of the recordings the plain per-level path is timed on: every
+    16th recording in length order (a spread of lengths), kept while their
+    events add up to at most max_events."""
+    order = np.argsort([s.n for s, _ in recs])
+    pick, tot = [], 0
+    for i in order[::16]:
+        if tot + recs[i][0].n > max_events:
+            break
+        pick.append(int(i))
+        tot += recs[i][0].n
+    return sorted(pick)
+
+
+def sample_recordings(seed: int, k: int = 4):
+    """k of the 256 recordings in a seeded order (drawn alone)."""
+    return synth.c4_recordings(which=_sample_idx(seed, k))
+
+
+def _sample_idx(seed: int, k: int = 4):
+    return [int(i) for i in np.argsort(synth.Rng(seed, 3).uniform(256))[:k]]
+
+
+def oracle_sample(recs, seconds: float, threads: int, seed: int = 0):
+    """A bounded oracle sample of the many-recordings workload: level-2
+    candidates (ordered pairs of frequent types x bins) of the given
+    recordings, counted with the serial state machine; grown until it is
+    about `seconds` of work on `threads` threads.  Returns (one-call
+    function, description, episode-events per call)."""
+    import oracle
+    rng = synth.Rng(seed, 5)
+    jobs = []
+    for s, cfg in recs:
+        freq = np.bincount(s.types.astype(np.int64), minlength=s.n_types)
+        ftypes = [a for a in range(s.n_types) if freq[a] > cfg["threshold"]]
+        cands = oracle.generate_candidates([], 2, ftypes, cfg["bins"])
+        pick = np.argsort(rng.uniform(len(cands)))
+        jobs.append((s, cands, pick))
+
+    def make(m):
+        parts = []
+        for s, cands, pick in jobs:
+            k = min(len(cands), m)
+            parts.append((s, oracle.to_csr([cands[j] for j in pick[:k]]), k))
+        return parts
+
+    def run(parts):
+        used = 0
+        for s, (offs, ct, lo, hi), _ in parts:
+            _, used = oracle.count_many(s.types, s.times, offs, ct, lo, hi, threads=threads)
+        return used
+
+    m = 4 * threads
+    parts = make(m)
+    t0 = time.perf_counter()
+    run(parts)
+    dt = time.perf_counter() - t0
+    m = int(max(m, m * seconds / max(dt, 1e-3)))
+    parts = make(m)
+    ee = float(sum(k * s.n for s, _, k in parts))
+    desc = (f"level-2 candidates (ordered pairs of frequent types x 4 bins) of {len(parts)} recordings of the "
+            f"256 ({', '.join(str(s.n) for s, _, _ in parts)} events), up to {m} random candidates each, "
+            f"{int(sum(k for _, _, k in parts))} candidates per call")
+    return (lambda: run(parts)), desc, ee
 
 
 # ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
-    """CPU oracle on a bounded sample: level-2 candidates of the workload
-    counted with the serial state machine on all host cores."""
+    """The CPU oracle on a bounded sample of the headline workload (level-2
+    candidates of a few of the 256 recordings, about 5 s per step on all host
+    cores), on the same metric and unit as the GPU arm."""
     if rank != 0:
         return
-    import oracle
-    s, cfg, desc = workload(args.workload)
-    freq = np.bincount(s.types.astype(np.int64), minlength=s.n_types)
-    ftypes = [a for a in range(s.n_types) if freq[a] > cfg["threshold"]]
-    cands = oracle.generate_candidates([], 2, ftypes, cfg["bins"])
-    rng = synth.Rng(0xBE, 1)
+    recs = sample_recordings(0xBE)
     threads = len(os.sched_getaffinity(0))
-    # calibrate the sample size to ~1.5 s of CPU work per step
-    pick = np.argsort(rng.uniform(len(cands)))
-    m = min(len(cands), 64 * threads)
-    offs, ct, lo, hi = oracle.to_csr([cands[i] for i in pick[:m]])
-    t0 = time.perf_counter()
-    oracle.count_many(s.types, s.times, offs, ct, lo, hi, threads=threads)
-    dt = time.perf_counter() - t0
-    m2 = int(min(len(cands), max(m, m * 1.5 / max(dt, 1e-3))))
-    offs, ct, lo, hi = oracle.to_csr([cands[i] for i in pick[:m2]])
-    for _ in range(args.warmup if args.warmup < 2 else 1):
-        oracle.count_many(s.types, s.times, offs[: min(len(offs), 33)], ct, lo, hi, threads=threads)
-    times = []
+    call, desc, ee = oracle_sample(recs, args.ref_seconds, threads)
+    for _ in range(min(args.warmup, 1)):
+        call()
+    times, used = [], threads
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _, used = oracle.count_many(s.types, s.times, offs, ct, lo, hi, threads=threads)
+        used = call()
         times.append(time.perf_counter() - t0)
     total = sum(times)
-    ee = float(m2) * s.n * args.steps
-    v = ee / total
-    sample = (f"{m2} of {len(cands)} level-2 candidates (random) over the full {s.n}-event stream "
-              f"per step; serial state-machine counter, one candidate per task")
+    v = ee * args.steps / total
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": desc + f" (n={s.n})", "levels": "2 (sample)",
-                   "l2": f"stream {6 * s.n / 1e6:.1f} MB fits L2"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
+        "config": {"workload": C4_DESC, "sample": "oracle on a bounded sample per step"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_leg(s, cfg):
-    """Bounded oracle timing (~10-20 s of CPU work) for the cpu_baseline key."""
+def cpu_baseline_leg(recs):
+    """The oracle as it stands on the machine's host cores: a bounded sample of the
+    headline workload on all cores and on one core, plus one whole mining pass
+    of the mid-size recording (oracle.mine_levelwise)."""
     import oracle
-    freq = np.bincount(s.types.astype(np.int64), minlength=s.n_types)
-    ftypes = [a for a in range(s.n_types) if freq[a] > cfg["threshold"]]
-    cands = oracle.generate_candidates([], 2, ftypes, cfg["bins"])
-    rng = synth.Rng(0xBE, 2)
-    pick = np.argsort(rng.uniform(len(cands)))
     threads = len(os.sched_getaffinity(0))
-    m = min(len(cands), 32 * threads)
-    offs, ct, lo, hi = oracle.to_csr([cands[i] for i in pick[:m]])
+    call, desc, ee = oracle_sample([recs[i] for i in _sample_idx(0xBF)], 10.0, threads)
     t0 = time.perf_counter()
-    oracle.count_many(s.types, s.times, offs, ct, lo, hi, threads=threads)
+    used = call()
     dt = time.perf_counter() - t0
-    m2 = int(min(len(cands), max(m, m * 10.0 / max(dt, 1e-3))))
-    offs, ct, lo, hi = oracle.to_csr([cands[i] for i in pick[:m2]])
-    t0 = time.perf_counter()
-    _, used = oracle.count_many(s.types, s.times, offs, ct, lo, hi, threads=threads)
-    dt = time.perf_counter() - t0
-    return {"value": m2 * s.n / dt, "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"{m2} of {len(cands)} level-2 candidates over the full {s.n}-event stream, "
-                      f"serial state-machine counter on {used} threads, {dt:.1f} s"}
+    call1, desc1, ee1 = oracle_sample([recs[i] for i in _sample_idx(0xC0)], 4.0, 1)
+    t1 = time.perf_counter()
+    call1()
+    dt1 = time.perf_counter() - t1
+    s, cfg = synth.c2_mid()
+    t2 = time.perf_counter()
+    oracle.mine_levelwise(s.types, s.times, s.n_types, cfg["bins"], cfg["threshold"], cfg["max_size"],
+                          threads=threads)
+    dt2 = time.perf_counter() - t2
+    return {"value": ee / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": desc + f", {dt:.1f} s", "cpu_model": cpu_model(),
+            "single_core": {"value": ee1 / dt1, "unit": UNIT, "cores": 1, "sample": desc1 + f", {dt1:.1f} s"},
+            "c2_mining_pass_s": dt2,
+            "c2_mining_pass": f"oracle.mine_levelwise of the mid-size recording (n={s.n}, levels 1-6) on "
+                              f"{threads} threads"}
 
 
-def c3_leg(ctx, tstream, flush, steps: int = 2):
+def c2_leg(ctx, tstream, flush, steps: int):
+    """Mid-size single recording (128 neurons, ~1.07M events, 1 us ticks):
+    one mining pass (levels 1-6, one captured graph) per step."""
+    import torch
+    s, cfg = synth.c2_mid()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    stt = []
+    for _ in range(3):
+        r = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
+        r.free()
+    ms = 0.0
+    for k in range(steps):
+        flush.fill_(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(tstream)
+        r = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
+        b.record(tstream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        stt.append(r.stats())
+        r.free()
+    st.free()
+    ee = sum(x["counted_episode_events"] for x in stt)
+    return {"workload": f"plain level-wise mining, mid: 128 neurons, lognormal 2-20 Hz, 1 us ticks (n={s.n}, "
+                        f"levels 1-6, threshold {cfg['threshold']})",
+            "value": ee / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "pruned_per_step": float(np.mean([x["candidates_pruned"] for x in stt])),
+            "counted_per_step": float(np.mean([x["candidates_counted"] for x in stt])),
+            "graph": bool(stt[-1]["graph_tails"])}
+
+
+def c3_leg(ctx, tstream, flush, steps: int = 3):
     """Batched counting: one 4M-event bursty 60-type stream and 200k
     candidates (sizes 2-8, 4-bin intervals), one count_episodes call per
-    step, stream resident; episode-events/s over all 200k x 4M pairs."""
+    step, stream resident; every candidate is counted over the whole
+    stream, so episode-events = 200k x 4M per call."""
     import torch
     from paper_0905_2203_gb300 import binding as fb
     s, (offs, ct, lo, hi) = synth.c3_batched()
     st = ctx.load_stream(s.types, s.times, s.n_types)
     cands = fb.Cands(offs, ct, lo, hi)
-    ctx.set_tuning()  # default kernel choice, no autotuning trials here
     ctx.count_episodes(st, cands)  # warm-up: builds per-type lists and densities
     ms, rel, kms, sp = 0.0, 0.0, 0.0, 0
     for k in range(steps):
@@ -224,12 +350,11 @@ def c3_leg(ctx, tstream, flush, steps: int = 2):
         kms += S["count_kernel_ms"]
         sp += S["sparse_launches"]
     st.free()
-    ctx.set_tuning(autotune=1)
     n_c = len(offs) - 1
     return {"workload": f"one bursty 60-type stream, n={s.n}, {n_c} candidates sizes 2-8, 4 bins",
             "value": n_c * s.n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "relevant_events_per_s": rel / (kms / 1e3) if kms else None,
-            "sparse_launches_per_step": sp / steps}
+            "count_launches_per_step": sp / steps}
 
 
 def _level_arrays(res, n_recs: int, max_size: int):
@@ -251,48 +376,48 @@ def _lat_summary(lat_s, ee, span_s):
             "episode_events_per_s": float(ee / span_s) if span_s > 0 else None}
 
 
-def serving_leg(n_jobs: int = 12, n_cap: int = 500_000, stress_n: int = 0, load: float = 0.7,
-                seed: int = 0xFE0005, plain: bool = True):
-    """Serving on a bounded sample of the job list (the first `n_jobs` jobs
-    with at most `n_cap` events, plus the stress job when stress_n > 0).
-    Arrivals are Poisson (seeded) at `load` x the served path's measured
-    capacity.  Three arms on the same arrival times:
+def serving_leg(n_jobs: int = 200, stress_n: int = 100_000_000, load: float = 0.7, seed: int = 0xFE0005,
+                plain_jobs: int = 12, plain_cap: int = 500_000):
+    """Serving: the job list (n log-uniform in [5e4, 2e7], 60-256 types, max
+    size 4-8, threshold 0.1-1% of n) plus the stress job.  Arrivals are
+    Poisson (seeded) at `load` x the served path's measured capacity.  Arms,
+    on the same arrival times:
       served      -- the serving loop (admission by device memory, streams and
                      candidates resident, ready levels of all admitted jobs
                      counted together), live; latency = result ready - submit;
-      ours_fifo   -- the library's mine_levelwise, one job at a time;
-      plain_fifo  -- the plain per-level GPU path, one job at a time.
-    The FIFO arms' per-job service times (stream upload, mining, result read)
-    are measured on the GPU and queued first-in first-out on the arrival
-    times.  Every job's frequent episodes and counts must agree across arms."""
+      ours_fifo   -- the library's mine_levelwise, one job at a time, each
+                     job's measured service time queued first-in first-out;
+      plain_fifo  -- the plain per-level GPU path, the same way, on the first
+                     `plain_jobs` jobs of at most `plain_cap` events (the plain
+                     path needs hours for the whole list), against ours_fifo
+                     on the same jobs.
+    Every job's frequent episodes and counts must agree across arms."""
     import torch
     from paper_0905_2203_gb300 import binding as fb
-    jobs = [j for j in synth.serving_jobs(seed, stress_n=stress_n)]
-    stress = [j for j in jobs if j["n"] == stress_n] if stress_n else []
-    pick = [j for j in jobs if j["n"] <= n_cap][:n_jobs] + stress
-    data = [synth.make_job_stream(j) for j in pick]
-    K = len(pick)
+    jobs = [j for j in synth.serving_jobs(seed, n_jobs=n_jobs, stress_n=stress_n)]
+    data = [synth.make_job_stream(j) for j in jobs]
+    K = len(jobs)
     srv = fb.Server(0, 0, 16)
 
     def submit(i):
         s, cfg = data[i]
         return srv.submit(s.types, s.times, s.n_types, cfg["bins"], cfg["threshold"], cfg["max_size"])
 
-    def collect(ids):
+    def collect(ids, idx):
         lat, ee, arrays, sub, fin = [], 0.0, [], [], []
-        for i, jid in enumerate(ids):
+        for i, jid in zip(idx, ids):
             res, info = srv.wait(jid)
             lat.append(info["finish_s"] - info["submit_s"])
             sub.append(info["submit_s"])
             fin.append(info["finish_s"])
-            ee += res.stats()["episode_events"]
+            ee += res.stats()["counted_episode_events"]
             arrays.append(_level_arrays(res, 1, data[i][1]["max_size"]))
             res.free()
         return lat, ee, arrays, min(sub), max(fin)
 
     # warm-up (kernel loading, first allocations), then capacity: all at once
-    collect([submit(0)])
-    _, ee_all, _, t_a, t_b = collect([submit(i) for i in range(K)])
+    collect([submit(0)], [0])
+    _, ee_all, _, t_a, t_b = collect([submit(i) for i in range(K)], list(range(K)))
     capacity = K / max(t_b - t_a, 1e-9)
     lam = load * capacity
     u = synth.Rng(seed, 11).uniform(K)
@@ -304,147 +429,107 @@ def serving_leg(n_jobs: int = 12, n_cap: int = 500_000, stress_n: int = 0, load:
         if d > 0:
             time.sleep(d)
         ids.append(submit(i))
-    lat_srv, ee_srv, arr_srv, t_a, t_b = collect(ids)
+    lat_srv, ee_srv, arr_srv, t_a, t_b = collect(ids, list(range(K)))
     srv.close()
 
-    def fifo(plain: bool):
+    def service(plain: bool, idx):
         ctx = fb.Context(0)
         if plain:
             ctx.set_tuning(plain_path=1)
-        svc, arrays, ee = [], [], 0.0
-        for i in range(-1, K):  # i = -1: warm-up on the first job
-            s, cfg = data[max(i, 0)]
+        svc, arrays, ee = [], [], []
+        for i in [idx[0]] + list(idx):  # the first one twice: warm-up
+            s, cfg = data[i]
             torch.cuda.synchronize()
             t = time.perf_counter()
             st = ctx.load_stream(s.types, s.times, s.n_types)
             res = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
             a = _level_arrays(res, 1, cfg["max_size"])
-            e = res.stats()["episode_events"]
+            e = res.stats()["counted_episode_events"]
             res.free()
             st.free()
-            dt = time.perf_counter() - t
-            if i >= 0:
-                svc.append(dt)
-                arrays.append(a)
-                ee += e
+            svc.append(time.perf_counter() - t)
+            arrays.append(a)
+            ee.append(e)
         ctx.close()
-        end, lat = 0.0, []
-        for i in range(K):
-            start = max(arrive[i], end)
-            end = start + svc[i]
-            lat.append(end - arrive[i])
-        return lat, ee, arrays, end - arrive[0], svc
+        return svc[1:], arrays[1:], ee[1:]
 
-    lat_o, ee_o, arr_o, span_o, svc_o = fifo(False)
-    if plain:
-        lat_p, ee_p, arr_p, span_p, svc_p = fifo(True)
-    else:
-        arr_p = arr_o
-    parity = all(_same_levels(a, b) and _same_levels(a, c) for a, b, c in zip(arr_srv, arr_o, arr_p))
+    def fifo(svc, arr):
+        end, lat = 0.0, []
+        for a, sv in zip(arr, svc):
+            start = max(a, end)
+            end = start + sv
+            lat.append(end - a)
+        return lat, end - arr[0]
+
+    svc_o, arr_o, ee_o = service(False, list(range(K)))
+    lat_o, span_o = fifo(svc_o, arrive)
+    small = [i for i in range(K) if jobs[i]["n"] <= plain_cap][:plain_jobs]
+    svc_p, arr_p, ee_p = service(True, small)
+    sub_arrive = np.cumsum(-np.log1p(-synth.Rng(seed, 12).uniform(len(small))) / lam)
+    lat_p, span_p = fifo(svc_p, sub_arrive)
+    svc_os = [svc_o[i] for i in small]
+    lat_os, span_os = fifo(svc_os, sub_arrive)
+    parity = all(_same_levels(a, b) for a, b in zip(arr_srv, arr_o))
+    parity = parity and all(_same_levels(arr_o[i], b) for i, b in zip(small, arr_p))
+    n_ev = int(sum(d[0].n for d in data))
     return {
-        "workload": f"serving sample: {K} jobs of the job list (n <= {n_cap}"
-                    + (f", plus the {stress_n}-event stress job" if stress else "") + "), "
-                    f"{int(sum(d[0].n for d in data))} events, 60-256 types, max size 4-8, 10 us ticks",
+        "workload": f"serving: {K - (1 if stress_n else 0)} jobs of the job list"
+                    + (f" plus the {stress_n}-event stress job" if stress_n else "")
+                    + f", {n_ev} events, 60-256 types, max size 4-8, 10 us ticks",
         "arrivals": f"Poisson, {lam:.2f} jobs/s = {load} x served capacity ({capacity:.2f} jobs/s)",
         "served": _lat_summary(lat_srv, ee_srv, t_b - t_a),
-        "ours_fifo": dict(_lat_summary(lat_o, ee_o, span_o), service_ms_mean=1e3 * float(np.mean(svc_o))),
-        "plain_fifo": (dict(_lat_summary(lat_p, ee_p, span_p), service_ms_mean=1e3 * float(np.mean(svc_p)))
-                       if plain else "not run (--c5-no-plain)"),
+        "ours_fifo": dict(_lat_summary(lat_o, sum(ee_o), span_o), service_ms_mean=1e3 * float(np.mean(svc_o))),
+        "plain_sample": {
+            "jobs": f"the first {len(small)} jobs of at most {plain_cap} events, own Poisson arrivals at the "
+                    f"same rate",
+            "plain_fifo": dict(_lat_summary(lat_p, sum(ee_p), span_p), service_ms_mean=1e3 * float(np.mean(svc_p))),
+            "ours_fifo": dict(_lat_summary(lat_os, sum(ee_o[i] for i in small), span_os),
+                              service_ms_mean=1e3 * float(np.mean(svc_os))),
+        },
+        "stress_job_ms": {"served": 1e3 * lat_srv[-1], "ours_service": 1e3 * svc_o[-1]} if stress_n else None,
         "parity_across_arms": bool(parity),
-        "note": "p99 over the sample's jobs (interpolated); FIFO arms queued on the same arrivals",
+        "note": "p99 over the jobs (interpolated); FIFO arms queued on the same arrivals",
     }
-
-
-def run_c4(args):
-    """Multi-recording batched mining on a bounded sample of the 256-recording
-    set (the first `--c4-recs` recordings): levels 1-6 of all of them in one
-    mine_levelwise call per step, against one call per recording and against
-    the plain per-level path; results must agree recording by recording."""
-    import torch
-    from paper_0905_2203_gb300 import binding as fb
-    recs = synth.c4_recordings()[: args.c4_recs]
-    ctx = fb.Context(0)
-    sts = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
-    bins = recs[0][1]["bins"]
-    thr = [c["threshold"] for _, c in recs]
-    max_size = recs[0][1]["max_size"]
-
-    def batched():
-        res = ctx.mine_levelwise(sts, bins, thr, max_size)
-        a = _level_arrays(res, len(sts), max_size)
-        ee = res.stats()["episode_events"]
-        res.free()
-        return a, ee
-
-    def per_rec():
-        out, ee = [], 0.0
-        for st, t in zip(sts, thr):
-            res = ctx.mine_levelwise([st], bins, [t], max_size)
-            out += _level_arrays(res, 1, max_size)
-            ee += res.stats()["episode_events"]
-            res.free()
-        return out, ee
-
-    def timed(fn, steps):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(steps):
-            a, ee = fn()
-        torch.cuda.synchronize()
-        return a, ee, (time.perf_counter() - t) / steps
-
-    a_b, ee_b, t_b = timed(batched, args.steps)
-    a_r, ee_r, t_r = timed(per_rec, max(1, args.steps // 2))
-    ctx.set_tuning(plain_path=1)
-    a_p, ee_p, t_p = timed(per_rec, 1)
-    n_tot = sum(s.n for s, _ in recs)
-    line = {"metric": METRIC, "value": ee_b / t_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_b, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"batched multi-recording mining: first {len(recs)} of the 256 60-channel "
-                                   f"recordings ({n_tot} events), levels 1-{max_size}, one call per step",
-                       "timing": "host wall clock around synchronised steps"},
-            "per_recording_calls": {"value": ee_r / t_r, "ms_per_step": 1e3 * t_r},
-            "plain_gpu": {"value": ee_p / t_p, "ms_per_step": 1e3 * t_p},
-            "parity_batched_vs_per_recording": _same_levels(a_b, a_r),
-            "parity_batched_vs_plain": _same_levels(a_b, a_p)}
-    for st in sts:
-        st.free()
-    ctx.close()
-    print(json.dumps(line), flush=True)
 
 
 def run_case(name: str):
     """Small fixed invocations used for ncu captures (no timing line):
-    c2_level2_tiled -- one C2 mining pass with the pre-pass off and the tiled
-                       kernel forced (level 2 counts all 55k candidates);
-    c3_mid_sparse   -- one count of 20k episodes (sizes 2-8) over a 1M-event
-                       bursty stream with the sparse kernel forced;
-    c2_mining       -- one default C2 mining pass."""
+    c4_mining      -- one mining call of the first 32 recordings of the
+                      many-recordings set (after one warm-up call);
+    c3_mid         -- one count of 20k episodes (sizes 2-8) over a 1M-event
+                      bursty stream (after one warm-up call);
+    c2_mining      -- one default C2 mining pass (after one warm-up call)."""
     import torch
     from paper_0905_2203_gb300 import binding as fb
     ctx = fb.Context(0)
-    if name in ("c2_level2_tiled", "c2_mining"):
+    sts = []
+    if name == "c4_mining":
+        recs = c4_workload(32)
+        sts = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
+        for _ in range(2):
+            res = ctx.mine_levelwise(sts, recs[0][1]["bins"], [c["threshold"] for _, c in recs], 6)
+            stats = res.stats()
+            res.free()
+    elif name == "c2_mining":
         s, cfg = synth.c2_mid()
-        st = ctx.load_stream(s.types, s.times, s.n_types)
-        if name == "c2_level2_tiled":
-            ctx.set_tuning(prepass=-1, kernel=1)
-        res = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], cfg["max_size"])
-        print(json.dumps({"case": name, "stats": res.stats()}))
-        res.free()
-    elif name == "c3_mid_sparse":
+        sts = [ctx.load_stream(s.types, s.times, s.n_types)]
+        for _ in range(2):
+            res = ctx.mine_levelwise(sts, cfg["bins"], [cfg["threshold"]], cfg["max_size"])
+            stats = res.stats()
+            res.free()
+    elif name == "c3_mid":
         s = synth.bursty_60(0xFE0003, 1_000_000)
         offs, ct, lo, hi = synth.random_candidates(0xFE0003, 20000, 60, 2, 8, synth.BINS_4, s.chains, 0.05)
-        st = ctx.load_stream(s.types, s.times, s.n_types)
-        ctx.set_tuning(kernel=2)
-        ctx.count_episodes(st, fb.Cands(offs, ct, lo, hi))
-        print(json.dumps({"case": name, "stats": ctx.last_stats()}))
+        sts = [ctx.load_stream(s.types, s.times, s.n_types)]
+        for _ in range(2):
+            ctx.count_episodes(sts[0], fb.Cands(offs, ct, lo, hi))
+        stats = ctx.last_stats()
     else:
         raise SystemExit(f"unknown case {name}")
+    print(json.dumps({"case": name, "stats": stats}))
     torch.cuda.synchronize()
-    st.free()
+    for st in sts:
+        st.free()
     ctx.close()
 
 
@@ -455,18 +540,19 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
-    s, cfg, desc = workload(args.workload)
+    recs = c4_workload(args.c4_recs)
+    bins = recs[0][1]["bins"]
+    thr = [c["threshold"] for _, c in recs]
+    max_size = recs[0][1]["max_size"]
+    n_tot = int(sum(s.n for s, _ in recs))
     tstream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(tstream)
     ctx = fb.Context(local_rank, 0, tstream.cuda_stream)
-    st = ctx.load_stream(s.types, s.times, s.n_types)
-    # autotuner on: its timing trials run during the warm-up steps
-    ctx.set_tuning(autotune=1)
-    bins, thr, max_size = cfg["bins"], cfg["threshold"], cfg["max_size"]
+    sts = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
 
     def step():
-        res = ctx.mine_levelwise([st], bins, [thr], max_size)
+        res = ctx.mine_levelwise(sts, bins, thr, max_size)
         stt = res.stats()
         res.free()
         return stt
@@ -484,7 +570,7 @@ def run_ours(args, rank, world, local_rank):
     stats = []
     with ClockSampler(local_rank) as clk:
         for k in range(args.steps):
-            flush.fill_(k)  # evict the stream from L2 between timed steps (untimed)
+            flush.fill_(k)  # evict from L2 between timed steps (untimed)
             ev[k][0].record(tstream)
             stats.append(step())
             ev[k][1].record(tstream)
@@ -492,147 +578,167 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    ee = sum(x["episode_events"] for x in stats)
     ee_counted = sum(x["counted_episode_events"] for x in stats)
-    pruned = float(np.mean([x["candidates_pruned"] for x in stats]))
+    ee_all = sum(x["episode_events"] for x in stats)
     rel = sum(x["relevant_events"] for x in stats)
     cnt_ms = sum(x["count_kernel_ms"] for x in stats)
     launches = sum(x["kernel_launches"] for x in stats)
-    t_max, value = aggregate_over_ranks(ms, ee, world, dev)
+    t_max, value = aggregate_over_ranks(ms, ee_counted, world, dev)
 
     if args.quick:
         if rank == 0:
-            print(json.dumps({"quick": True, "value": ee * world / (t_max / 1e3), "ms_per_step": t_max / args.steps,
-                              "count_kernel_ms_per_step": cnt_ms / args.steps, "gpu_launches": int(launches)}))
-        st.free()
+            print(json.dumps({"quick": True, "value": value, "ms_per_step": t_max / args.steps,
+                              "count_kernel_ms_per_step": cnt_ms / args.steps, "gpu_launches": int(launches),
+                              "graph": bool(stats[-1]["graph_tails"])}))
         ctx.close()
         return
 
-    sparse_launches = sum(x["sparse_launches"] for x in stats)
-    graph_tails = sum(x["graph_tails"] for x in stats)
-
-    # --- plain per-level GPU path (comparison): same step, one thread per episode
-    ctx.set_tuning(plain_path=1)
-    step()
-    torch.cuda.synchronize()
-    pe = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    pst = []
-    p_steps = max(1, min(args.steps, 3))
-    flush.fill_(7)
-    pe[0].record(tstream)
-    for _ in range(p_steps):
-        pst.append(step())
-    pe[1].record(tstream)
-    torch.cuda.synchronize()
-    p_ms = pe[0].elapsed_time(pe[1])
-    ctx.set_tuning(autotune=1)
-    plain_value = sum(x["episode_events"] for x in pst) / (p_ms / 1e3)
-
-    # --- end to end through the C ABI from host buffers
-    types_pin = torch.from_numpy(s.types.view(np.int16)).pin_memory()
-    times_pin = torch.from_numpy(s.times).pin_memory()
-    e2e_ms = 0.0
-    e2e_ee = 0.0
-    d2h = 0
-    for k in range(max(1, min(args.steps, 5))):
+    # --- end to end through the C ABI from pinned host buffers
+    pins = [(torch.from_numpy(s.types.view(np.int16)).pin_memory(), torch.from_numpy(s.times).pin_memory())
+            for s, _ in recs]
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_ms, e2e_ee, d2h = 0.0, 0.0, 0
+    for k in range(e2e_steps + 1):  # the first run warms the new streams' tables and graph
         flush.fill_(k)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(tstream)
-        st2 = ctx.load_stream(types_pin.numpy().view(np.uint16), times_pin.numpy(), s.n_types)
-        res = ctx.mine_levelwise([st2], bins, [thr], max_size)
+        sts2 = [ctx.load_stream(tp.numpy().view(np.uint16), mp.numpy(), s.n_types)
+                for (tp, mp), (s, _) in zip(pins, recs)]
+        res = ctx.mine_levelwise(sts2, bins, thr, max_size)
         out_bytes = 0
-        for N in range(1, max_size + 1):
-            offs_n, types_n, lo_n, hi_n, counts_n = res.level_arrays(0, N)
-            out_bytes += offs_n.nbytes + types_n.nbytes + lo_n.nbytes + hi_n.nbytes + counts_n.nbytes
-        e2e_ee += res.stats()["episode_events"]
+        for r in range(len(sts2)):
+            for N in range(1, max_size + 1):
+                arrs = res.level_arrays(r, N)
+                out_bytes += sum(x.nbytes for x in arrs)
+        ee_k = res.stats()["counted_episode_events"]
         res.free()
-        st2.free()
+        for st2 in sts2:
+            st2.free()
         b.record(tstream)
         torch.cuda.synchronize()
-        e2e_ms += a.elapsed_time(b)
-        d2h = out_bytes
-    e2e_steps = max(1, min(args.steps, 5))
+        if k > 0:
+            e2e_ms += a.elapsed_time(b)
+            e2e_ee += ee_k
+            d2h = out_bytes
+    del pins
     e2e_value = e2e_ee * world / (e2e_ms / 1e3)
 
-    c3 = None if args.no_c3 else c3_leg(ctx, tstream, flush)
-    serving = None if args.no_serving else serving_leg()
+    # --- plain per-level GPU path (comparison) on a sample of recordings, and
+    # the library on the same sample
+    pick = plain_sample(recs)
+    sub = [sts[i] for i in pick]
+    sub_thr = [thr[i] for i in pick]
+
+    def sub_step(plain: bool):
+        ctx.set_tuning(plain_path=1 if plain else 0)
+        try:
+            res = ctx.mine_levelwise(sub, bins, sub_thr, max_size)
+            a = _level_arrays(res, len(sub), max_size)
+            e = res.stats()["counted_episode_events"]
+            res.free()
+        finally:
+            ctx.reset_tuning()
+        return a, e
+
+    sub_step(False)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    a_o, e_o = sub_step(False)
+    torch.cuda.synchronize()
+    t_o = time.perf_counter() - t
+    sub_step(True)  # warm-up of the plain path's tables
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    a_p, e_p = sub_step(True)
+    torch.cuda.synchronize()
+    t_p = time.perf_counter() - t
+    plain = {"recordings": f"{len(pick)} of the 256 (every 16th in length order, "
+                           f"{int(sum(recs[i][0].n for i in pick))} events)",
+             "value": e_p / t_p, "unit": UNIT, "ms_per_step": 1e3 * t_p,
+             "ours_same_sample": {"value": e_o / t_o, "ms_per_step": 1e3 * t_o},
+             "speedup": (e_o / t_o) / (e_p / t_p) if e_p else None,
+             "parity": _same_levels(a_o, a_p), "timing": "host wall clock around a synchronised call"}
+
+    c2 = None if args.no_legs else c2_leg(ctx, tstream, flush, max(3, min(args.steps, 20)))
+    c3 = None if args.no_legs else c3_leg(ctx, tstream, flush)
+    for st in sts:
+        st.free()
+    serving = None if (args.no_legs or args.no_serving) else serving_leg()
     if rank != 0:
+        ctx.close()
         return
     peaks = _peaks()
     clocks = clk.summary()
-    # roofline of the dominant kernel (the tiled exact-count kernel): its
-    # algorithmic work is one state update per relevant (episode, event) pair
+    # roofline of the dominant kernel (the local-tracking count kernel): its
+    # algorithmic work is one update per relevant (episode, event) pair
     # (events whose type is one of the episode's node types); peak = one
-    # lane-instruction per lane per cycle: SMs x 4 schedulers x 32 lanes x clock.
+    # lane-instruction per lane per cycle: SMs x 4 schedulers x 32 lanes x clock
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_alu = props.multi_processor_count * 128 * sm_max * 1e6
     achieved = rel / (cnt_ms / 1e3) if cnt_ms > 0 else 0.0
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # algorithmic bytes of the count kernels per step: the stream read once per
-    # level pass (6 B/event) + candidate CSR (~22 B/candidate) + counts (4 B)
-    levels = np.mean([x["levels"] for x in stats])
-    cand = np.mean([x["candidates_counted"] + x["candidates_pruned"] for x in stats])
-    alg_bytes = (levels - 1) * 6 * s.n + cand * 26
+    counters = track_counters()
+    pruned = float(np.mean([x["candidates_pruned"] for x in stats]))
+    counted = float(np.mean([x["candidates_counted"] for x in stats]))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": desc + f" (n={s.n}, levels 1-{max_size}, threshold {thr})",
+        "config": {"workload": C4_DESC + f" ({len(recs)} recordings, n={n_tot})",
                    "parallelism": f"replicas x{world}",
-                   "l2": "256 MB buffer written between timed steps (stream 6.4 MB < L2)",
-                   "candidates_per_step": float(cand), "levels": float(levels),
-                   "numerator": "every generated candidate x n (resolved by the exact count or, at level 2, "
-                                "by the upper-bound pre-pass)",
-                   "pruned_by_prepass_per_step": pruned},
-        "counted_exact": {"value": ee_counted * world / (t_max / 1e3), "unit": UNIT,
-                          "note": "episode-events resolved by the exact counting kernels only"},
+                   "l2": f"inputs ({6 * n_tot / 1e9:.2f} GB of streams) larger than L2; a 256 MB buffer is also "
+                         f"written between timed steps",
+                   "candidates_counted_per_step": counted, "levels": float(np.mean([x["levels"] for x in stats])),
+                   "numerator": "episode-events of exactly counted (candidate, recording) pairs"},
+        "pruned": {"value": (ee_all - ee_counted) * world / (t_max / 1e3), "unit": "episode-events/s pruned",
+                   "candidates_per_step": pruned,
+                   "note": "level-2 candidates resolved by the upper-bound pre-pass (never counted)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu,
                      "unit": "relevant episode-events/s", "frac": achieved / peak_alu,
-                     "traffic": None,
-                     "note": "peak = SMs x 128 lanes x sm_max_mhz (one lane-op per relevant episode-event)"},
-        "hbm": {"achieved_gbs": alg_bytes / (cnt_ms / 1e3 / args.steps) / 1e9 if cnt_ms else None,
-                "peak_gbs": hbm_peak,
-                "frac": (alg_bytes / (cnt_ms / 1e3 / args.steps) / 1e9) / hbm_peak if cnt_ms else None},
+                     "traffic": counters.get("dram_bytes_per_launch") if counters else None,
+                     "issue_active": counters.get("issue_active_pct") if counters else None,
+                     "note": "peak = SMs x 128 lanes x sm_max_mhz (one lane-op per relevant episode-event); "
+                             "achieved over the count kernels' device time (CUDA events inside the graph); "
+                             "traffic and issue_active from the committed ncu summary of the count kernel"},
+        "hbm": {"achieved_gbs": counters.get("dram_gbs") if counters else None, "peak_gbs": hbm_peak,
+                "frac": counters["dram_gbs"] / hbm_peak if counters and counters.get("dram_gbs") else None,
+                "note": "DRAM read+write bytes of one count-kernel launch over its duration (ncu, committed "
+                        "summary; null when the kernel has changed since)"},
         "count_kernel_ms_per_step": cnt_ms / args.steps,
-        "plain_gpu": {"value": plain_value, "unit": UNIT, "ms_per_step": p_ms / p_steps,
-                      "speedup_of_tiled": value / world / plain_value if plain_value else None},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(6 * s.n),
+        "relevant_events_per_step": rel / args.steps,
+        "plain_gpu": plain,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(6 * n_tot),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / e2e_steps},
         "gpu_launches": int(launches),
-        "kernels": {"sparse_launches_per_step": sparse_launches / args.steps,
-                    "graph_tail_steps": graph_tails},
+        "graph": bool(stats[-1]["graph_tails"]),
+        "c2_mining_pass": c2,
         "c3_batched_counting": c3,
         "serving": serving,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_leg(s, cfg)
+        line["cpu_baseline"] = cpu_baseline_leg(recs)
     print(json.dumps(line), flush=True)
-    st.free()
     ctx.close()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--c4-recs", type=int, default=256, help="recordings of the headline workload (256 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-c3", action="store_true", help="skip the batched-counting (C3) leg")
-    ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency leg")
-    ap.add_argument("--c4-recs", type=int, default=32, help="recordings of the multi-recording set (--workload c4)")
-    ap.add_argument("--c5-jobs", type=int, default=40, help="jobs of the serving sample (--workload c5)")
-    ap.add_argument("--c5-cap", type=int, default=4_000_000, help="largest job of the serving sample (--workload c5)")
-    ap.add_argument("--c5-stress", type=int, default=0, help="add the stress job with this many events (--workload c5)")
-    ap.add_argument("--c5-no-plain", action="store_true", help="skip the plain-path arm (--workload c5)")
-    ap.add_argument("--quick", action="store_true",
-                    help="time the tiled path only (no plain-path, e2e or CPU legs); for profiling")
+    ap.add_argument("--ref-seconds", type=float, default=5.0,
+                    help="--impl reference: seconds of oracle work per step (on all host cores)")
+    ap.add_argument("--no-legs", action="store_true", help="skip the mid-size, batched-counting and serving legs")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--quick", action="store_true", help="time the headline step only (for profiling)")
     ap.add_argument("--case", default=None,
-                    help="run one small fixed invocation for profiling (c2_level2_tiled, c3_mid_sparse, c2_mining)")
+                    help="run one small fixed invocation for profiling (c4_mining, c3_mid, c2_mining)")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
@@ -642,15 +748,6 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-        return
-    if args.workload == "c4":
-        if rank == 0:
-            run_c4(args)
-        return
-    if args.workload == "c5":
-        if rank == 0:
-            print(json.dumps({"workload": "c5", "serving": serving_leg(args.c5_jobs, args.c5_cap, args.c5_stress,
-                                                                       plain=not args.c5_no_plain)}), flush=True)
         return
     if world > 1:
         import torch

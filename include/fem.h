@@ -117,7 +117,10 @@ typedef struct {
                              fallback_recounts; 7 = local tracking with one
                              warp per (episode, segment) work item taken
                              from an atomic queue by one persistent launch
-                             for every multi-node episode of the call */
+                             for every multi-node episode of the call (with
+                             0, consecutive episodes that share their first
+                             N-1 nodes and edges form one item and track
+                             that prefix once) */
     int level_graph;      /* mining: 0 = run the levels as one captured CUDA
                              graph where it applies (all levels when no
                              other override is set and every alphabet has at

@@ -1621,6 +1621,14 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 64, sm);
     const int64_t gs = std::min<int64_t>((cap_threads + 63) / 64, (int64_t)std::max(1, nsm) * std::max(1, per_sm));
     if (cap_threads > 0) f<<<(unsigned)gs, 64, sm, st>>>(sa);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return launch_stitch_dev(st, nsm, rinfo, slot2cand, cand_rec, rec, d_n_slots, cap_slots, counts, fb_list,
+                             fb_count, skip);
+}
+
+int launch_stitch_dev(cudaStream_t st, int nsm, const RecInfo *rinfo, const int32_t *slot2cand,
+                      const uint32_t *cand_rec, const int32_t *rec, const int32_t *d_n_slots, int64_t cap_slots,
+                      uint32_t *counts, int32_t *fb_list, int *fb_count, const uint8_t *skip) {
     // the live segment counts are only known on the device: both stitch
     // kernels run, each taking the episodes on its side of kStitchSplit
     const int64_t gst = std::min<int64_t>((cap_slots + kStitchWarps - 1) / kStitchWarps, (int64_t)std::max(1, nsm) * 8);
@@ -1997,6 +2005,35 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             ta.rec_first = pl.ri.empty() ? 0 : pl.ri[0].recbase;
             ta.n_items = n_items;
             ta.d_n_items = nullptr;
+            if (limit == 0 && pl.ri[0].recbase == 0 && pl.slot_begin == 0 && ctx->tuning.kernel != 7) {
+                // episodes sharing their first N-1 nodes track that prefix
+                // once (kernel 7: one item per episode and segment)
+                const int64_t ns = pl.n_slots;
+                const size_t gw = (size_t)(ns + 2) * 2 + (size_t)(ns + 2) / 1024 + 2 + (size_t)n_recs;
+                void *pg = nullptr;
+                FEM_TRY(scratch(ctx, kSlotTrackGrp, gw * 4 + (size_t)(n_recs + 2) * 8 + 1024, &pg));
+                int64_t *i64 = static_cast<int64_t *>(pg);
+                int32_t *i32 = reinterpret_cast<int32_t *>(i64 + n_recs + 2);
+                TrackGroupIn gi{};
+                gi.slot2cand = d_perm;
+                gi.d_n_slots = nullptr;
+                gi.n_slots_cap = ns;
+                gi.offs = cc.offs;
+                gi.ctypes = cc.types;
+                gi.clo = cc.lo;
+                gi.chi = cc.hi;
+                gi.cand_rec = cc.cand_rec;
+                gi.rinfo = d_ri;
+                gi.n_recs = n_recs;
+                gi.ibase = i64;
+                gi.n_items = i64 + n_recs + 1;
+                gi.gidx = i32;
+                gi.gstart = i32 + (ns + 2);
+                gi.gfirst = i32 + 2 * (ns + 2);
+                gi.scan_tmp = i32 + 2 * (ns + 2) + n_recs;
+                FEM_TRY(track_groups(ctx->stream, ctx->n_sm, gi, &ta));
+                cc.stats.kernel_launches += 4;
+            }
             ta.offs = cc.offs;
             ta.ctypes = cc.types;
             ta.clo = cc.lo;

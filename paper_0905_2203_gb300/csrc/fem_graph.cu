@@ -702,6 +702,15 @@ struct GraphTail {
     int64_t *coff2 = nullptr;              // generated level-2 candidates per recording
     uint32_t *d_thr = nullptr;
     int ring_cap = kRingCap;               // ring entries per node
+    // exact counts by warp-per-item local tracking (one persistent launch
+    // per level, prefix groups); otherwise the node-uniform sparse kernel
+    bool track = false;
+    int track_nblocks = 0;
+    int64_t track_cap = 0;                 // longest per-type list of any recording
+    int32_t *tbuf = nullptr;
+    int64_t *tqueue = nullptr;
+    int32_t *tg_gidx = nullptr, *tg_gstart = nullptr, *tg_gfirst = nullptr, *tg_stmp = nullptr;
+    int64_t *tg_ibase = nullptr, *tg_nitems = nullptr;
     int64_t *segf = nullptr, *segl = nullptr;  // finest / current level's segment starts
     int32_t *pfine = nullptr, *sstep = nullptr;
     int64_t target = 0;                    // (candidate, segment) threads per level
@@ -788,7 +797,19 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     g->segf = segs;
     // (candidate, segment) threads per level: about two waves of the sparse
     // kernel, never more than target + live candidates (one segment each)
-    g->target = (int64_t)2 * ctx->n_sm * 512;
+    g->track = ctx->tuning.kernel == 0;
+    if (g->track) {
+        g->track_nblocks = track_blocks(ctx->n_sm);
+        for (auto *s : g->recs) g->track_cap = std::max(g->track_cap, s->max_list);
+        const size_t fb = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+        while (g->track_nblocks > ctx->n_sm && track_buf_bytes(g->track_nblocks, g->track_cap) > fb / 4)
+            g->track_nblocks -= ctx->n_sm;
+        if (track_buf_bytes(g->track_nblocks, g->track_cap) > fb / 4) return FEM_ERR_NOMEM;
+        // about four work items per resident warp
+        g->target = (int64_t)4 * g->track_nblocks * kTrackWarps;
+    } else {
+        g->target = (int64_t)2 * ctx->n_sm * 512;
+    }
     g->cap_threads = g->target + cap;
     // ring entries per node: the largest window density of any type + 1; the
     // graph does not apply when that exceeds kRingCap or what the deepest
@@ -803,10 +824,14 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             for (uint32_t d : hd) dmax = std::max(dmax, d);
         }
     }
-    if (dmax + 1 > (uint32_t)kRingCap) return FEM_ERR_INVAL;
-    g->ring_cap = (int)dmax + 1;
-    for (int N = std::max(first, 2); N <= L; ++N)
-        if (graph_sparse_smem(N, g->ring_cap) > (size_t)ctx->smem_optin - 1024) return FEM_ERR_INVAL;
+    if (g->track) {
+        g->ring_cap = 1 << 30;  // local tracking keeps no rings: nothing to check
+    } else {
+        if (dmax + 1 > (uint32_t)kRingCap) return FEM_ERR_INVAL;
+        g->ring_cap = (int)dmax + 1;
+        for (int N = std::max(first, 2); N <= L; ++N)
+            if (graph_sparse_smem(N, g->ring_cap) > (size_t)ctx->smem_optin - 1024) return FEM_ERR_INVAL;
+    }
     // level 1 / level 2 sizes
     std::vector<int64_t> ntpre(n_recs + 1, 0), evpre(n_recs + 1, 0), ub_off(n_recs + 1, 0);
     std::vector<uint32_t> nt_h(n_recs);
@@ -861,6 +886,16 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     FEM_TRY(g->get(&fb_list, cap));
     FEM_TRY(g->get(&iota, cap));
     FEM_TRY(g->get(&rec, (size_t)g->cap_threads * kRecWords));
+    if (g->track) {
+        FEM_TRY(g->get(&g->tbuf, track_buf_bytes(g->track_nblocks, g->track_cap) / sizeof(int32_t)));
+        FEM_TRY(g->get(&g->tqueue, 1));
+        FEM_TRY(g->get(&g->tg_gidx, cap + 2));
+        FEM_TRY(g->get(&g->tg_gstart, cap + 2));
+        FEM_TRY(g->get(&g->tg_gfirst, n_recs));
+        FEM_TRY(g->get(&g->tg_stmp, (cap + 2) / 1024 + 2));
+        FEM_TRY(g->get(&g->tg_ibase, n_recs + 1));
+        FEM_TRY(g->get(&g->tg_nitems, 1));
+    }
     FEM_TRY(g->get(&offs, cap + 1));
     FEM_TRY(g->get(&nthreads, 1));
     FEM_TRY(g->get(&ct, (size_t)cap * Nmax));
@@ -1053,10 +1088,51 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         // external event nodes: their timestamps time the count kernels of
         // this level on every launch of the graph
         ok(cudaEventRecordWithFlags(g->ev[2 * N], st, cudaEventRecordExternal));
-        if (cst == FEM_OK)
+        if (cst == FEM_OK && g->track) {
+            TrackArgs ta{};
+            ta.rinfo = d_ri;
+            ta.n_recs = n_recs;
+            ta.offs = offs;
+            ta.ctypes = ct;
+            ta.clo = cl;
+            ta.chi = ch;
+            ta.slot2cand = iota;
+            ta.skip = bounded ? g->skip : nullptr;
+            ta.queue = reinterpret_cast<unsigned long long *>(g->tqueue);
+            ta.buf = g->tbuf;
+            ta.cap = g->track_cap;
+            ta.rec = rec;
+            TrackGroupIn gi{};
+            gi.slot2cand = iota;
+            gi.d_n_slots = cn;
+            gi.n_slots_cap = cap;
+            gi.offs = offs;
+            gi.ctypes = ct;
+            gi.clo = cl;
+            gi.chi = ch;
+            gi.cand_rec = crec;
+            gi.rinfo = d_ri;
+            gi.n_recs = n_recs;
+            gi.gidx = g->tg_gidx;
+            gi.scan_tmp = g->tg_stmp;
+            gi.gstart = g->tg_gstart;
+            gi.gfirst = g->tg_gfirst;
+            gi.ibase = g->tg_ibase;
+            gi.n_items = g->tg_nitems;
+            // level 2 shares no prefix work: one item per (episode, segment)
+            if (N >= 3)
+                cst = track_groups(st, ctx->n_sm, gi, &ta);
+            else
+                ta.d_n_items = nthreads;
+            if (cst == FEM_OK) cst = launch_track(st, g->track_nblocks, ta);
+            if (cst == FEM_OK)
+                cst = launch_stitch_dev(st, ctx->n_sm, d_ri, iota, crec, rec, cn, cap, counts, fb_list, cn + 3,
+                                        bounded ? g->skip : nullptr);
+        } else if (cst == FEM_OK) {
             cst = launch_count_dev(st, nmax, N, g->ring_cap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch,
                                    iota, crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov,
                                    (int)lo_vals.size(), bounded ? g->skip : nullptr);
+        }
         ok(cudaEventRecordWithFlags(g->ev[2 * N + 1], st, cudaEventRecordExternal));
         if (fused) {
             k_g_thr_fused<<<1, 1024, 0, st>>>(counts, ct, cl, ch, crec, g->d_thr, N, cap, nf.types, nf.lo, nf.hi,
@@ -1104,12 +1180,12 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
 
 static std::string graph_key(const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
                              const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, int max_size,
-                             int first, bool prepass, int coarse) {
+                             int first, bool prepass, int coarse, int kernel) {
     std::ostringstream k;
     for (auto *s : recs) k << (const void *)s << ':' << s->n << ';';
     for (size_t i = 0; i < blo.size(); ++i) k << blo[i] << ',' << bhi[i] << ';';
     for (auto t : thr) k << t << ';';
-    k << max_size << '/' << first << '/' << (prepass ? 1 : 0) << '/' << coarse;
+    k << max_size << '/' << first << '/' << (prepass ? 1 : 0) << '/' << coarse << '/' << kernel;
     return k.str();
 }
 
@@ -1156,11 +1232,11 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
         if (s->n_types > 8192 || s->n > INT32_MAX / 2) return FEM_OK;
     // coarse-tick bound of levels >= 3: only with prepass = 1
     const int coarse = ctx->tuning.prepass == 1 ? 1 : 0;
-    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass, coarse);
+    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass, coarse, ctx->tuning.kernel);
     int64_t cap = 4096;
     auto hint = ctx->graph_cap.find(key);
     const int64_t want = std::max<int64_t>(cap_min, hint != ctx->graph_cap.end() ? hint->second : 0);
-    while (cap < want && cap < (1 << 22)) cap <<= 1;
+    while (cap < want && cap < (1 << 24)) cap <<= 1;
     if (cap < want) return FEM_OK;
     GraphTail *g = nullptr;
     auto it = ctx->graphs.find(key);

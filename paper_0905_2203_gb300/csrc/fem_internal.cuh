@@ -73,6 +73,7 @@ struct RecInfo {
 // an atomic counter by a persistent grid.
 constexpr int kTrackWarps = 8;           // warps per block
 constexpr int kTrackMaxBlocksPerSm = 4;  // resident blocks per SM the grid asks for
+constexpr int kTrackGroupMax = 64;       // episodes per prefix group (a new group every 64 slots)
 struct TrackArgs {
     const RecInfo *rinfo;
     int n_recs;
@@ -90,6 +91,31 @@ struct TrackArgs {
     int32_t *buf;                // per warp 4 * cap words (entry lists, ping-pong)
     int64_t cap;                 // at least the longest per-type list of every recording
     int32_t *rec;                // records, kRecWords each
+    // Prefix groups (all null: one item per (episode, segment)).  Group g
+    // holds slots [gstart[g], gstart[g+1]); recording r's groups start at
+    // gfirst[r] and its items (groups x segments) at ibase[r].
+    const int32_t *gstart;
+    const int32_t *gfirst;
+    const int64_t *ibase;
+};
+// Inputs of track_groups: the slots (slot2cand, live count on the device or
+// n_slots_cap), the candidate CSR, per-candidate recordings, the launch's
+// RecInfo table (slot_first and P per recording, on the device), and
+// scratch: gidx[n_slots_cap + 2], scan_tmp[(n_slots_cap + 2) / 1024 + 2],
+// gstart[n_slots_cap + 2], gfirst[n_recs], ibase[n_recs + 1], n_items[1].
+struct TrackGroupIn {
+    const int32_t *slot2cand;
+    const int32_t *d_n_slots;
+    int64_t n_slots_cap;
+    const int64_t *offs;
+    const uint16_t *ctypes;
+    const int32_t *clo;
+    const int32_t *chi;
+    const uint32_t *cand_rec;
+    const RecInfo *rinfo;
+    int n_recs;
+    int32_t *gidx, *scan_tmp, *gstart, *gfirst;
+    int64_t *ibase, *n_items;
 };
 
 // Results of the levels of level-wise mining run in a captured graph.
@@ -288,6 +314,9 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
 // Persistent grid of the local-tracking kernel on this device (blocks), the
 // bytes of its per-warp buffers, and its launch (queue reset + kernel).
 int track_blocks(int n_sm);
+// Builds the prefix groups of a launch on the device and sets the group
+// fields and d_n_items of *a.
+int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, TrackArgs *a);
 size_t track_buf_bytes(int blocks, int64_t cap);
 int launch_track(cudaStream_t st, int blocks, const TrackArgs &a);
 
@@ -296,7 +325,7 @@ enum Slot : int {
     kSlotCandOffs = 1, kSlotCandTypes, kSlotCandLo, kSlotCandHi, kSlotCandRec,
     kSlotPrep, kSlotPerm, kSlotBucket, kSlotRecords, kSlotSeg, kSlotCounts,
     kSlotFallback, kSlotRings, kSlotDensTab, kSlotScanTmp, kSlotMisc, kSlotRecTab, kSlotDensArgs,
-    kSlotTrack,
+    kSlotTrack, kSlotTrackGrp,
     kSlotMine0 = 64,
 };
 
@@ -329,6 +358,11 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
                      const uint32_t *const *dens, const int32_t *lo_vals, int n_lo,
                      const uint8_t *skip = nullptr);
 size_t sparse_smem_bytes(int nmax, int R);
+// Both stitch kernels over the live slots (count on the device) of a launch
+// whose records follow rinfo (per recording: slot_first, recbase, P).
+int launch_stitch_dev(cudaStream_t st, int nsm, const RecInfo *rinfo, const int32_t *slot2cand,
+                      const uint32_t *cand_rec, const int32_t *rec, const int32_t *d_n_slots, int64_t cap_slots,
+                      uint32_t *counts, int32_t *fb_list, int *fb_count, const uint8_t *skip);
 // Segment boundaries (P + 1 entries) of a stream cut into P segments at time changes.
 int launch_segments(cudaStream_t st, const int32_t *time, int64_t n, int P, int64_t *seg);
 // Levels 1..max_size in one captured graph (streams resident; no host step

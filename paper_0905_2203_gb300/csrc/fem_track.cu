@@ -77,6 +77,95 @@ __device__ __forceinline__ int window_rank(int32_t vt, int64_t q) {
     return c;
 }
 
+// One node step for one warp: node k's events ttime[cb, ce) (time order)
+// against node k-1's entries pT/pL[0, m) (pL null: node 0, whose latest start
+// is its time).  An event is valid when the newest entry older than t - lo
+// exists and is not older than t - hi; its latest start is that entry's.
+// Not LAST: the valid events are appended to oT/oL and their number is
+// returned.  LAST: the valid events at or after Tp are passed, in time
+// order, to Algorithm 1 of every entry class in st.
+template <bool LAST>
+__device__ __forceinline__ int64_t node_step(const int32_t *__restrict__ ttime, int64_t cb, int64_t ce,
+                                             const int32_t *__restrict__ pT, const int32_t *__restrict__ pL,
+                                             int64_t m, int32_t lo_e, int32_t hi_e, int32_t *__restrict__ oT,
+                                             int32_t *__restrict__ oL, Machine<2, 0> &st, int32_t Tp, int lane) {
+    int64_t w = 0;   // window start: every remaining query ranks at or after it
+    int64_t wc = 0;  // entries written
+    for (int64_t base = cb; base < ce; base += 32) {
+        const int64_t j = base + lane;
+        const bool in = j < ce;
+        const int32_t t = in ? ttime[j] : INT32_MAX;
+        const int64_t q = in ? (int64_t)t - lo_e : INT64_MAX;
+        const int64_t q0 = (int64_t)__shfl_sync(kFull, t, 0) - lo_e;
+        int64_t idx = 0;
+        bool done = !in;
+        for (;;) {
+            const int64_t wi = w + lane;
+            const int32_t vt = wi < m ? pT[wi] : INT32_MAX;
+            const int32_t top = __shfl_sync(kFull, vt, 31);
+            if ((int64_t)top < q0 && w + 32 < m) {  // the whole window precedes every query
+                w += 32;
+                continue;
+            }
+            const int c = window_rank(vt, q);
+            if (!done && c < 32) {
+                idx = w + c;
+                done = true;
+            }
+            if (__all_sync(kFull, done)) break;
+            w += 32;
+        }
+        bool ok = false;
+        int32_t Lv = 0;
+        if (in && idx > 0) {
+            const int32_t tp = pT[idx - 1];
+            if ((int64_t)tp >= (int64_t)t - hi_e) {
+                ok = true;
+                Lv = pL ? pL[idx - 1] : tp;
+            }
+        }
+        if (!LAST) {
+            const unsigned bm = __ballot_sync(kFull, ok);
+            if (ok) {
+                const int r = __popc(bm & ((1u << lane) - 1u));
+                oT[wc + r] = t;
+                oL[wc + r] = Lv;
+            }
+            wc += __popc(bm);
+        } else {
+            unsigned bm = __ballot_sync(kFull, ok && t >= Tp);
+            while (bm) {
+                const int b = __ffs(bm) - 1;
+                bm &= bm - 1;
+                st.greedy_end(__shfl_sync(kFull, t, b), __shfl_sync(kFull, Lv, b), Tp);
+            }
+        }
+        // the next 32 queries rank at or after this chunk's last one
+        w = __shfl_sync(kFull, idx, 31);
+    }
+    __syncwarp();
+    return wc;
+}
+
+__device__ __forceinline__ void machine_init(Machine<2, 0> &st, int N) {
+    st.N = N;
+    st.ncls = 0;
+    st.live = 0;
+    st.M = INT32_MIN;
+    st.open = 1;
+    st.flags = 0;
+#pragma unroll
+    for (int j = 0; j < kClasses; ++j) {
+        st.cthr[j] = 0;
+        st.cprev[j] = 0;
+        st.ccnt[j] = 0;
+    }
+}
+
+// A work item is one segment p of one recording for either one episode
+// (slot) or, with groups, a run of episode slots [s0, s1) that share their
+// first N-1 nodes and edges: the shared prefix is tracked once, and only the
+// last node step is run per episode.
 __global__ void __launch_bounds__(kTrackWarps * 32, 4) k_count_track(TrackArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -90,141 +179,194 @@ __global__ void __launch_bounds__(kTrackWarps * 32, 4) k_count_track(TrackArgs a
         if (lane == 0) it = atomicAdd(a.queue, 1ull);
         it = __shfl_sync(kFull, it, 0);
         if ((int64_t)it >= n_items) break;
-        const int64_t tr = a.rec_first + (int64_t)it;
-        int lo_r = 0, hi_r = a.n_recs;  // last recording whose records start at or before tr
-        while (hi_r - lo_r > 1) {
-            const int mid = (lo_r + hi_r) >> 1;
-            if (a.rinfo[mid].recbase <= tr) lo_r = mid; else hi_r = mid;
+        int r = 0, P = 1, p = 0, s0 = 0, s1 = 0;
+        if (a.gstart) {
+            int lo_r = 0, hi_r = a.n_recs;  // last recording whose items start at or before it
+            while (hi_r - lo_r > 1) {
+                const int mid = (lo_r + hi_r) >> 1;
+                if (a.ibase[mid] <= (int64_t)it) lo_r = mid; else hi_r = mid;
+            }
+            r = lo_r;
+            P = a.rinfo[r].P;
+            const int64_t local = (int64_t)it - a.ibase[r];
+            const int64_t g = a.gfirst[r] + local / P;
+            p = (int)(local % P);
+            s0 = a.gstart[g];
+            s1 = a.gstart[g + 1];
+        } else {
+            const int64_t tr = a.rec_first + (int64_t)it;
+            int lo_r = 0, hi_r = a.n_recs;  // last recording whose records start at or before tr
+            while (hi_r - lo_r > 1) {
+                const int mid = (lo_r + hi_r) >> 1;
+                if (a.rinfo[mid].recbase <= tr) lo_r = mid; else hi_r = mid;
+            }
+            r = lo_r;
+            P = a.rinfo[r].P;
+            const int64_t local = tr - a.rinfo[r].recbase;
+            s0 = a.rinfo[r].slot_first + (int)(local / P);
+            s1 = s0 + 1;
+            p = (int)(local % P);
         }
-        const RecInfo &ri = a.rinfo[lo_r];
-        const int P = ri.P;
-        const int64_t local = tr - ri.recbase;
-        const int slot = ri.slot_first + (int)(local / P);
-        const int p = (int)(local % P);
-        const int cand = a.slot2cand[slot];
-        if (a.skip && a.skip[cand]) continue;  // the stitch writes its count (0)
-        const int64_t o = a.offs[cand];
-        const int N = (int)(a.offs[cand + 1] - o);
-        const int64_t eo = o - cand;
-
-        Machine<2, 0> st;  // Algorithm 1 per entry class (its rings are unused); the same in every lane
-        st.N = N;
-        st.ncls = 0;
-        st.live = 0;
-        st.M = INT32_MIN;
-        st.open = 1;
-        st.flags = 0;
-#pragma unroll
-        for (int j = 0; j < kClasses; ++j) {
-            st.cthr[j] = 0;
-            st.cprev[j] = 0;
-            st.ccnt[j] = 0;
-        }
+        const RecInfo &ri = a.rinfo[r];
+        const int c0 = a.slot2cand[s0];
+        const int64_t o0 = a.offs[c0];
+        const int N = (int)(a.offs[c0 + 1] - o0);
+        const int64_t eo0 = o0 - c0;
+        // halo: the largest sum of upper bounds over the item's episodes
         int64_t sumhi = 0;
-        for (int k = 0; k < N - 1; ++k) sumhi += a.chi[eo + k];
+        for (int k = 0; k < N - 2; ++k) sumhi += a.chi[eo0 + k];
+        int32_t hmax = 0;
+        for (int s = s0; s < s1 && N >= 2; ++s) {
+            const int c = a.slot2cand[s];
+            hmax = max(hmax, a.chi[a.offs[c] - c + N - 2]);
+        }
+        sumhi += hmax;
         const int64_t seg_b = ri.seg[p], seg_e = ri.seg[p + 1];
-        if (seg_b < seg_e && N >= 2) {
-            const int32_t Tp = ri.time[seg_b];
-            const int64_t haloT = (p == 0) ? INT64_MIN : (int64_t)Tp - sumhi;
-            const int64_t Tend = (seg_e < ri.n) ? (int64_t)ri.time[seg_e] : INT64_MAX;
-            const int64_t *toff = ri.toff;
-            const int32_t *ttime = ri.ttime;
-            // list range of type E inside [haloT, Tend)
-            auto range = [&](uint32_t E, int64_t &b, int64_t &e) {
-                const int64_t b0 = toff[E], b1 = toff[E + 1];
-                if (ri.tseg) {
-                    const int32_t *tq = ri.tseg + (size_t)E * ri.tstride;
-                    const int qmax = ri.tstride - 1;
-                    const int64_t s0 = b0 + tq[min(p * ri.sstep, qmax)];
-                    e = b0 + tq[min((p + 1) * ri.sstep, qmax)];
-                    b = (p == 0) ? s0 : warp_lower_bound(ttime, b0, s0, haloT, lane);
-                } else {
-                    b = (p == 0) ? b0 : warp_lower_bound(ttime, b0, b1, haloT, lane);
-                    e = (seg_e < ri.n) ? warp_lower_bound(ttime, b, b1, Tend, lane) : b1;
-                }
-            };
+        const bool live = seg_b < seg_e && N >= 2;
+        int32_t Tp = 0;
+        int64_t haloT = INT64_MIN, Tend = INT64_MAX;
+        if (live) {
+            Tp = ri.time[seg_b];
+            haloT = (p == 0) ? INT64_MIN : (int64_t)Tp - sumhi;
+            Tend = (seg_e < ri.n) ? (int64_t)ri.time[seg_e] : INT64_MAX;
+        }
+        const int64_t *toff = ri.toff;
+        const int32_t *ttime = ri.ttime;
+        // list range of type E inside [haloT, Tend)
+        auto range = [&](uint32_t E, int64_t &b, int64_t &e) {
+            const int64_t b0 = toff[E], b1 = toff[E + 1];
+            if (ri.tseg) {
+                const int32_t *tq = ri.tseg + (size_t)E * ri.tstride;
+                const int qmax = ri.tstride - 1;
+                const int64_t st0 = b0 + tq[min(p * ri.sstep, qmax)];
+                e = b0 + tq[min((p + 1) * ri.sstep, qmax)];
+                b = (p == 0) ? st0 : warp_lower_bound(ttime, b0, st0, haloT, lane);
+            } else {
+                b = (p == 0) ? b0 : warp_lower_bound(ttime, b0, b1, haloT, lane);
+                e = (seg_e < ri.n) ? warp_lower_bound(ttime, b, b1, Tend, lane) : b1;
+            }
+        };
+        // shared prefix: node 0, then nodes 1..N-2 (entry lists ping-pong)
+        const int32_t *pT = nullptr;
+        const int32_t *pL = nullptr;
+        int64_t m = 0;
+        Machine<2, 0> st;
+        if (live) {
             int64_t pb = 0, pe = 0;
-            range(a.ctypes[o], pb, pe);
-            // node k-1's entries: times pT[0..m), latest starts pL (node 0: its times)
-            const int32_t *pT = ttime + pb;
-            const int32_t *pL = nullptr;
-            int64_t m = pe - pb;
-            for (int k = 1; k < N && m > 0; ++k) {
-                const uint32_t E = a.ctypes[o + k];
-                const int32_t lo_e = a.relaxed ? 0 : a.clo[eo + k - 1];
-                const int32_t hi_e = a.chi[eo + k - 1];
+            range(a.ctypes[o0], pb, pe);
+            pT = ttime + pb;
+            m = pe - pb;
+            for (int k = 1; k < N - 1 && m > 0; ++k) {
                 int64_t cb = 0, ce = 0;
-                range(E, cb, ce);
-                const bool last = (k == N - 1);
+                range(a.ctypes[o0 + k], cb, ce);
                 int32_t *oT = (k & 1) ? bT1 : bT0;
                 int32_t *oL = (k & 1) ? bL1 : bL0;
-                int64_t w = 0;   // window start: every remaining query ranks at or after it
-                int64_t wc = 0;  // entries written for node k
-                for (int64_t base = cb; base < ce; base += 32) {
-                    const int64_t j = base + lane;
-                    const bool in = j < ce;
-                    const int32_t t = in ? ttime[j] : INT32_MAX;
-                    const int64_t q = in ? (int64_t)t - lo_e : INT64_MAX;
-                    const int64_t q0 = (int64_t)__shfl_sync(kFull, t, 0) - lo_e;
-                    int64_t idx = 0;
-                    bool done = !in;
-                    for (;;) {
-                        const int64_t wi = w + lane;
-                        const int32_t vt = wi < m ? pT[wi] : INT32_MAX;
-                        const int32_t top = __shfl_sync(kFull, vt, 31);
-                        if ((int64_t)top < q0 && w + 32 < m) {  // the whole window precedes every query
-                            w += 32;
-                            continue;
-                        }
-                        const int c = window_rank(vt, q);
-                        if (!done && c < 32) {
-                            idx = w + c;
-                            done = true;
-                        }
-                        if (__all_sync(kFull, done)) break;
-                        w += 32;
-                    }
-                    bool ok = false;
-                    int32_t Lv = 0;
-                    if (in && idx > 0) {
-                        const int32_t tp = pT[idx - 1];
-                        if ((int64_t)tp >= (int64_t)t - hi_e) {
-                            ok = true;
-                            Lv = pL ? pL[idx - 1] : tp;
-                        }
-                    }
-                    if (!last) {
-                        const unsigned bm = __ballot_sync(kFull, ok);
-                        if (ok) {
-                            const int r = __popc(bm & ((1u << lane) - 1u));
-                            oT[wc + r] = t;
-                            oL[wc + r] = Lv;
-                        }
-                        wc += __popc(bm);
-                    } else {
-                        unsigned bm = __ballot_sync(kFull, ok && t >= Tp);
-                        while (bm) {
-                            const int b = __ffs(bm) - 1;
-                            bm &= bm - 1;
-                            st.greedy_end(__shfl_sync(kFull, t, b), __shfl_sync(kFull, Lv, b), Tp);
-                        }
-                    }
-                    // the next 32 queries rank at or after this chunk's last one
-                    w = __shfl_sync(kFull, idx, 31);
-                }
-                // node k's entries become the predecessors of node k+1
-                __syncwarp();
+                m = node_step<false>(ttime, cb, ce, pT, pL, m, a.relaxed ? 0 : a.clo[eo0 + k - 1],
+                                     a.chi[eo0 + k - 1], oT, oL, st, 0, lane);
                 pT = oT;
                 pL = oL;
-                m = wc;
             }
         }
-        st.finish();
-        if (lane == 0) write_record(a.rec + tr * kRecWords, st);
+        // last node of every episode of the item
+        for (int s = s0; s < s1; ++s) {
+            const int c = a.slot2cand[s];
+            if (a.skip && a.skip[c]) continue;  // the stitch writes its count (0)
+            machine_init(st, N);
+            if (live && m > 0) {
+                const int64_t oc = a.offs[c], ec = oc - c;
+                int64_t cb = 0, ce = 0;
+                range(a.ctypes[oc + N - 1], cb, ce);
+                node_step<true>(ttime, cb, ce, pT, pL, m, a.relaxed ? 0 : a.clo[ec + N - 2], a.chi[ec + N - 2],
+                                nullptr, nullptr, st, Tp, lane);
+            }
+            st.finish();
+            if (lane == 0) write_record(a.rec + (ri.recbase + (int64_t)(s - ri.slot_first) * P + p) * kRecWords, st);
+        }
     }
 }
 
+// Groups for the grouped launch: flag[s] = 1 where slot s starts a group
+// (first slot, another recording or size, a different prefix of N-1 nodes
+// and N-2 edges, or every kTrackGroupMax-th slot).  Episodes of one to two
+// nodes share nothing and stay alone.
+__global__ void k_track_group_flags(const int32_t *__restrict__ slot2cand, const int32_t *__restrict__ d_n_slots,
+                                    int64_t n_slots_cap, const int64_t *__restrict__ offs,
+                                    const uint16_t *__restrict__ ctypes, const int32_t *__restrict__ clo,
+                                    const int32_t *__restrict__ chi, const uint32_t *__restrict__ cand_rec,
+                                    int32_t *__restrict__ flag) {
+    const int64_t n = d_n_slots ? (int64_t)*d_n_slots : n_slots_cap;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s <= n_slots_cap;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        if (s >= n) {
+            flag[s] = 0;
+            continue;
+        }
+        bool f = (s == 0) || (s % kTrackGroupMax) == 0;
+        if (!f) {
+            const int c = slot2cand[s], b = slot2cand[s - 1];
+            const int64_t oc = offs[c], ob = offs[b];
+            const int N = (int)(offs[c + 1] - oc), Nb = (int)(offs[b + 1] - ob);
+            f = N != Nb || N < 3 || (cand_rec && cand_rec[c] != cand_rec[b]);
+            for (int k = 0; k < N - 1 && !f; ++k) f = ctypes[oc + k] != ctypes[ob + k];
+            for (int k = 0; k < N - 2 && !f; ++k)
+                f = clo[oc - c + k] != clo[ob - b + k] || chi[oc - c + k] != chi[ob - b + k];
+        }
+        flag[s] = f ? 1 : 0;
+    }
+}
+
+// After an exclusive scan of the flags in place (gidx[s] = groups before
+// slot s, gidx[n] = all groups): the first slot of every group, and (one
+// thread) per recording its first group and its first item (groups x
+// segments), and the item count.
+__global__ void k_track_group_starts(const int32_t *__restrict__ gidx, const int32_t *__restrict__ d_n_slots,
+                                     int64_t n_slots_cap, int32_t *__restrict__ gstart) {
+    const int64_t n = d_n_slots ? (int64_t)*d_n_slots : n_slots_cap;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s <= n; s += (int64_t)gridDim.x * blockDim.x) {
+        if (s == n)
+            gstart[gidx[n]] = (int32_t)n;
+        else if (gidx[s + 1] != gidx[s])
+            gstart[gidx[s]] = (int32_t)s;
+    }
+}
+
+__global__ void k_track_group_recs(const int32_t *__restrict__ gidx, const RecInfo *__restrict__ rinfo, int n_recs,
+                                   const int32_t *__restrict__ d_n_slots, int64_t n_slots_cap,
+                                   int32_t *__restrict__ gfirst, int64_t *__restrict__ ibase, int64_t *n_items) {
+    const int64_t n = d_n_slots ? (int64_t)*d_n_slots : n_slots_cap;
+    if (threadIdx.x != 0) return;
+    int64_t base = 0;
+    for (int r = 0; r < n_recs; ++r) {
+        const int64_t sf = (int64_t)rinfo[r].slot_first < n ? (int64_t)rinfo[r].slot_first : n;
+        const int64_t sn1 = (r + 1 < n_recs) ? (int64_t)rinfo[r + 1].slot_first : n;
+        const int64_t sn = sn1 < n ? sn1 : n;
+        const int g0 = gidx[sf], g1 = gidx[sn];
+        gfirst[r] = g0;
+        ibase[r] = base;
+        base += (int64_t)(g1 - g0) * rinfo[r].P;
+    }
+    ibase[n_recs] = base;
+    *n_items = base;
+}
+
 }  // namespace
+
+int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, TrackArgs *a) {
+    const int64_t cap = in.n_slots_cap;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + 256) / 256, 8 * (int64_t)n_sm));
+    k_track_group_flags<<<g, 256, 0, st>>>(in.slot2cand, in.d_n_slots, cap, in.offs, in.ctypes, in.clo, in.chi,
+                                           in.cand_rec, in.gidx);
+    FEM_TRY(scan_exclusive(st, in.gidx, cap + 1, in.scan_tmp, nullptr, nullptr));
+    k_track_group_starts<<<g, 256, 0, st>>>(in.gidx, in.d_n_slots, cap, in.gstart);
+    k_track_group_recs<<<1, 32, 0, st>>>(in.gidx, in.rinfo, in.n_recs, in.d_n_slots, cap, in.gfirst, in.ibase,
+                                         in.n_items);
+    FEM_CUDA_TRY(cudaGetLastError());
+    a->gstart = in.gstart;
+    a->gfirst = in.gfirst;
+    a->ibase = in.ibase;
+    a->d_n_items = in.n_items;
+    return FEM_OK;
+}
 
 int track_blocks(int n_sm) {
     int per_sm = 1;

@@ -329,15 +329,17 @@ def c3_batched(seed: int = 0xFE0003, n_events: int = 4_000_000, n_cand: int = 20
     return s, (offs, types, lo, hi)
 
 
-def c4_recordings(seed: int = 0xFE0004, n_rec: int = 256, n_lo: float = 1e4, n_hi: float = 5e6):
+def c4_recordings(seed: int = 0xFE0004, n_rec: int = 256, n_lo: float = 1e4, n_hi: float = 5e6, which=None):
     """n_rec 60-channel recordings, lengths log-uniform in [n_lo, n_hi], base
     rates 5-20 Hz, 10 us ticks, three chains of 4-6 neurons each; threshold
-    per recording max(20, 0.25% n_r); bins the 4-bin set; sizes <= 6."""
+    per recording max(20, 0.25% n_r); bins the 4-bin set; sizes <= 6.
+    `which` (optional) lists the recordings to draw (each is drawn from its
+    own seed, so a subset equals the same entries of the whole set)."""
     rng = Rng(seed, 7)
     u = rng.uniform(n_rec)
     ns = np.exp(math.log(n_lo) + (math.log(n_hi) - math.log(n_lo)) * u).astype(np.int64)
     out = []
-    for r in range(n_rec):
+    for r in (range(n_rec) if which is None else which):
         rr = Rng(seed * 1315423911 + r, 3)
         rates = 5.0 + 15.0 * rr.uniform(60)
         per_s = float(rates.sum())
@@ -374,8 +376,12 @@ def serving_jobs(seed: int = 0xFE0005, n_jobs: int = 200, n_lo: float = 5e4, n_h
         jobs.append({"seed": seed * 31 + j, "n": n, "n_types": min(nt, 256),
                      "thr_frac": thr_frac, "max_size": min(max_size, 8)})
     if stress_n:
+        # the stress job: 256 types (each about 0.39% of the events) at the
+        # low end of the threshold range, so that every type is frequent and
+        # level 2 counts (or bounds) all 261,120 ordered pairs x bins over
+        # the whole stream; the planted chains carry the deeper levels
         jobs.append({"seed": seed * 31 + 99991, "n": int(stress_n), "n_types": 256,
-                     "thr_frac": 0.005, "max_size": 4})
+                     "thr_frac": 0.001, "max_size": 6})
     return jobs
 
 

@@ -12,8 +12,8 @@ def test_reference_arm_json_line():
     env = dict(os.environ)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         env.pop(k, None)
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "c1", "--steps", "2",
-                          "--warmup", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600,
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--ref-seconds", "0.5",
+                          "--steps", "2", "--warmup", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600,
                          check=True).stdout
     lines = [l for l in out.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -24,6 +24,7 @@ def test_reference_arm_json_line():
         assert k in d
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["cpu_model"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

@@ -102,7 +102,7 @@ def test_golden_cases_on_gpu(fb, ctx):
         st.free()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 4, 5, 6, 7])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5, 6, 7])
 @pytest.mark.parametrize("segments,lanes,tile", [(0, 0, 0), (1, 32, 256), (7, 64, 512), (64, 256, 1024),
                                                   (300, 96, 4096)])
 def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
@@ -111,7 +111,8 @@ def test_random_tiny_streams(fb, ctx, segments, lanes, tile, kernel):
     with the tiled (1) and the sparse (2) counting kernel, with grid-wide
     local tracking (4: latest starts; 5 / 6: occurrence lists compacted by
     atomics / count-scan-write; segment settings do not apply to them) and
-    with warp-per-item local tracking (7; segments apply)."""
+    with warp-per-item local tracking (0: episodes with a common prefix share
+    its steps; 7: one item per episode; segments apply to both)."""
     r = synth.Rng(99, segments + 7)
     ctx.set_tuning(lanes_per_cta=lanes, segments=segments, tile_events=tile, kernel=kernel)
     try:
