@@ -74,7 +74,7 @@ static bool tune_parse(const std::string &text, std::map<std::string, TuneVal> *
         v.kernel = 1;
         const int got = std::sscanf(text.substr(b0 + 1, b1 - b0 - 1).c_str(), "%d , %d , %lf , %d", &v.K, &v.T,
                                     &v.seg_mult, &v.kernel);
-        if (got < 3 || (v.kernel != 1 && v.kernel != 2)) return false;
+        if (got < 3 || v.kernel < 1 || v.kernel > 3) return false;
         if (v.K < 32 || v.K > kMaxWarps * 32 || v.K % 32 || v.T < 256 || v.T > kMaxTile || v.T % 256 ||
             !(v.seg_mult > 0.0 && v.seg_mult < 64.0))
             return false;

@@ -497,8 +497,12 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
     k_stitch(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
              const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
              int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
-             const int32_t *d_n_slots = nullptr, int max_P = INT32_MAX, const uint8_t *skip = nullptr) {
+             const int32_t *d_n_slots = nullptr, int max_P = INT32_MAX, const uint8_t *skip = nullptr,
+             const int *d_maxP = nullptr, int direct_p1 = 0) {
     const int lane = threadIdx.x & 31;
+    // direct_p1: the counting kernel wrote the counts of unsegmented
+    // episodes itself (no records); nothing to do when no recording is cut
+    if (direct_p1 && d_maxP && *d_maxP <= 1) return;
     const int n_live = d_n_slots ? *d_n_slots : n_slots;
     for (int wi = blockIdx.x * kStitchWarps + (threadIdx.x >> 5); wi < n_live; wi += gridDim.x * kStitchWarps) {
         const int slot = slot_begin + wi;
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(kStitchWarps * 32)
         const int r_id = cand_rec ? (int)cand_rec[cand] : 0;
         const RecInfo ri = rinfo[r_id];
         const int P = ri.P;
-        if (P > max_P) continue;
+        if (P > max_P || (direct_p1 && P == 1)) continue;
         if (skip && skip[cand]) {  // pruned by a bound: count 0
             if (lane == 0) counts[cand] = 0;
             continue;
@@ -547,12 +551,13 @@ __global__ void __launch_bounds__(kStitchBlock, 1)
     k_stitch_block(const int32_t *__restrict__ rec, const RecInfo *__restrict__ rinfo,
                    const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec, int slot_begin,
                    int n_slots, uint32_t *__restrict__ counts, int32_t *fb_list, int *fb_count,
-                   const int32_t *d_n_slots, int min_P, const uint8_t *skip = nullptr) {
+                   const int32_t *d_n_slots, int min_P, const uint8_t *skip = nullptr, const int *d_maxP = nullptr) {
     constexpr int W = kStitchBlock / 32;
     __shared__ int32_t s_thr[W][kChunkClasses], s_last[W][kChunkClasses];
     __shared__ uint32_t s_cnt[W][kChunkClasses];
     __shared__ int s_m[W], s_flag[W];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (d_maxP && *d_maxP <= min_P) return;  // no recording is cut into that many segments
     const int n_live = d_n_slots ? *d_n_slots : n_slots;
     for (int wi = blockIdx.x; wi < n_live; wi += gridDim.x) {
         const int slot = slot_begin + wi;
@@ -1623,22 +1628,24 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
     if (cap_threads > 0) f<<<(unsigned)gs, 64, sm, st>>>(sa);
     FEM_CUDA_TRY(cudaGetLastError());
     return launch_stitch_dev(st, nsm, rinfo, slot2cand, cand_rec, rec, d_n_slots, cap_slots, counts, fb_list,
-                             fb_count, skip);
+                             fb_count, skip, nullptr, 0);
 }
 
 int launch_stitch_dev(cudaStream_t st, int nsm, const RecInfo *rinfo, const int32_t *slot2cand,
                       const uint32_t *cand_rec, const int32_t *rec, const int32_t *d_n_slots, int64_t cap_slots,
-                      uint32_t *counts, int32_t *fb_list, int *fb_count, const uint8_t *skip) {
+                      uint32_t *counts, int32_t *fb_list, int *fb_count, const uint8_t *skip, const int *d_maxP,
+                      int direct_p1) {
     // the live segment counts are only known on the device: both stitch
     // kernels run, each taking the episodes on its side of kStitchSplit
     const int64_t gst = std::min<int64_t>((cap_slots + kStitchWarps - 1) / kStitchWarps, (int64_t)std::max(1, nsm) * 8);
     const int64_t gsb = std::min<int64_t>(cap_slots, (int64_t)std::max(1, nsm) * 4);
     if (cap_slots > 0) {
         k_stitch<<<(unsigned)gst, kStitchWarps * 32, 0, st>>>(rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots,
-                                                            counts, fb_list, fb_count, d_n_slots, kStitchSplit, skip);
+                                                            counts, fb_list, fb_count, d_n_slots, kStitchSplit, skip,
+                                                            d_maxP, direct_p1);
         k_stitch_block<<<(unsigned)gsb, kStitchBlock, 0, st>>>(rec, rinfo, slot2cand, cand_rec, 0, (int)cap_slots,
                                                                counts, fb_list, fb_count, d_n_slots, kStitchSplit,
-                                                               skip);
+                                                               skip, d_maxP);
     }
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
@@ -1737,6 +1744,19 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             }
             if (sb != FEM_OK) return sb;
         }
+    // the launch's per-warp entry lists (4 x the longest per-type list each):
+    // fewer resident warps while they would pass a quarter of the free
+    // budget; without room even for one block the per-episode kernels count
+    int track_nblocks = 0;
+    int64_t track_cap = 1;
+    if (track) {
+        for (auto *r : cc.recs) track_cap = std::max(track_cap, r->max_list);
+        const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+        track_nblocks = track_blocks(ctx->n_sm);
+        while (track_nblocks > 1 && track_buf_bytes(track_nblocks, track_cap) > free_b / 4)
+            track_nblocks = track_nblocks > ctx->n_sm ? track_nblocks - ctx->n_sm : track_nblocks / 2;
+        if (track_buf_bytes(track_nblocks, track_cap) > free_b / 4) track = false;
+    }
     const int n_keys = kBuckets * n_recs;
     // --- density tables and per-recording tables
     std::vector<int32_t> lov = cc.lo_vals;
@@ -1892,7 +1912,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         if (sparse) {
             // enough (episode, segment) threads to fill the GPU ~4 times
             // (local tracking: about four work items per resident warp)
-            const double desired = pl.track ? 4.0 * track_blocks(ctx->n_sm) * kTrackWarps : 4.0 * ctx->n_sm * 2048.0;
+            const double desired = pl.track ? 4.0 * track_nblocks * kTrackWarps : 4.0 * ctx->n_sm * 2048.0;
             double work = 0;
             for (int r = 0; r < n_recs; ++r) {
                 const int c = key_off[b * n_recs + r + 1] - key_off[b * n_recs + r];
@@ -1990,11 +2010,8 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             // per-warp entry lists: 4 x (longest per-type list) words each;
             // fewer resident warps when that would pass a quarter of the
             // free budget
-            int64_t cap = 1;
-            for (int r = 0; r < n_recs; ++r) cap = std::max(cap, cc.recs[r]->max_list);
-            int blocks = track_blocks(ctx->n_sm);
-            const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
-            while (blocks > ctx->n_sm && track_buf_bytes(blocks, cap) > free_b / 4) blocks -= ctx->n_sm;
+            const int64_t cap = track_cap;
+            int blocks = track_nblocks;
             const int64_t n_items = limit > 0 ? std::min(limit, pl.records) : pl.records;
             blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (n_items + kTrackWarps - 1) / kTrackWarps));
             void *pb = nullptr;
@@ -2005,15 +2022,21 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             ta.rec_first = pl.ri.empty() ? 0 : pl.ri[0].recbase;
             ta.n_items = n_items;
             ta.d_n_items = nullptr;
-            if (limit == 0 && pl.ri[0].recbase == 0 && pl.slot_begin == 0 && ctx->tuning.kernel != 7) {
-                // episodes sharing their first N-1 nodes track that prefix
-                // once (kernel 7: one item per episode and segment)
+            if (limit == 0) {
+                // items: recordings longest first; episodes sharing their
+                // first N-1 nodes track that prefix once (kernel 7: one item
+                // per episode and segment)
                 const int64_t ns = pl.n_slots;
-                const size_t gw = (size_t)(ns + 2) * 2 + (size_t)(ns + 2) / 1024 + 2 + (size_t)n_recs;
+                const size_t gw = (size_t)(ns + 2) * 2 + (size_t)(ns + 2) / 1024 + 2 + 2 * (size_t)n_recs;
                 void *pg = nullptr;
                 FEM_TRY(scratch(ctx, kSlotTrackGrp, gw * 4 + (size_t)(n_recs + 2) * 8 + 1024, &pg));
                 int64_t *i64 = static_cast<int64_t *>(pg);
                 int32_t *i32 = reinterpret_cast<int32_t *>(i64 + n_recs + 2);
+                std::vector<int32_t> ro(n_recs);
+                std::iota(ro.begin(), ro.end(), 0);
+                std::stable_sort(ro.begin(), ro.end(), [&](int x, int y) { return cc.recs[x]->n > cc.recs[y]->n; });
+                int32_t *d_ro = i32 + 2 * (ns + 2) + n_recs + (ns + 2) / 1024 + 2;
+                FEM_CUDA_TRY(cudaMemcpyAsync(d_ro, ro.data(), 4 * n_recs, cudaMemcpyHostToDevice, ctx->stream));
                 TrackGroupIn gi{};
                 gi.slot2cand = d_perm;
                 gi.d_n_slots = nullptr;
@@ -2025,14 +2048,16 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                 gi.cand_rec = cc.cand_rec;
                 gi.rinfo = d_ri;
                 gi.n_recs = n_recs;
+                gi.rorder = d_ro;
                 gi.ibase = i64;
                 gi.n_items = i64 + n_recs + 1;
                 gi.gidx = i32;
                 gi.gstart = i32 + (ns + 2);
                 gi.gfirst = i32 + 2 * (ns + 2);
                 gi.scan_tmp = i32 + 2 * (ns + 2) + n_recs;
-                FEM_TRY(track_groups(ctx->stream, ctx->n_sm, gi, &ta));
-                cc.stats.kernel_launches += 4;
+                const bool grouped = ctx->tuning.kernel != 7;
+                FEM_TRY(track_groups(ctx->stream, ctx->n_sm, gi, grouped, &ta));
+                cc.stats.kernel_launches += grouped ? 4 : 1;
             }
             ta.offs = cc.offs;
             ta.ctypes = cc.types;
@@ -2045,6 +2070,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             ta.buf = reinterpret_cast<int32_t *>(static_cast<char *>(pb) + 256);
             ta.cap = cap;
             ta.rec = rec_base;
+            ta.counts = limit > 0 ? nullptr : cc.counts;  // unsegmented episodes: counts written directly
             FEM_TRY(launch_track(ctx->stream, blocks, ta));
             cc.stats.kernel_launches += 2;  // queue reset + kernel
             return FEM_OK;
@@ -2154,8 +2180,44 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             continue;
         }
         if (track && b == 0) {
-            // local tracking: one plan, every multi-node episode, no tuning
-            Plan pl = make_plan(b, true, 32, T_def, 1.0, records_needed);
+            // local tracking: one plan, every multi-node episode; the tuner
+            // chooses the segment-count multiplier
+            double seg_mult = 1.0;
+            const bool tunable_t = force_segments == 0 && cc.seg_div == 1.0 && ctx->tuning.segments == 0;
+            if (tunable_t) {
+                int64_t nmax_ev = 0;
+                for (int r = 0; r < n_recs; ++r)
+                    if (key_off[b * n_recs + r + 1] > key_off[b * n_recs + r]) nmax_ev = std::max(nmax_ev, cc.recs[r]->n);
+                const std::string key = tune_key(kTuneTrack, 0, key_off[n_recs], nmax_ev, n_recs);
+                TuneVal tv;
+                if (tune_lookup(ctx, key, &tv)) {
+                    seg_mult = tv.seg_mult;
+                } else if (ctx->tuning.autotune == 1) {
+                    float best = -1.f;
+                    for (double m : {1.0, 0.25, 4.0}) {
+                        Plan pl = make_plan(b, true, 32, T_def, m, 0);
+                        void *pr = nullptr, *ps = nullptr, *pt = nullptr;
+                        FEM_TRY(scratch(ctx, kSlotRecords, (size_t)std::max<int64_t>(pl.records, 1) * kRecWords * 4, &pr));
+                        FEM_TRY(scratch(ctx, kSlotSeg, sizeof(int64_t) * seg_need(pl), &ps));
+                        FEM_TRY(scratch(ctx, kSlotRecTab, tab_need(pl), &pt));
+                        segpos = 0;
+                        tabpos = 0;
+                        RecInfo *dri = nullptr;
+                        const int64_t lim = std::min<int64_t>(pl.records, (int64_t)2 * track_nblocks * kTrackWarps);
+                        cudaEventRecord(ctx->ev0, ctx->stream);
+                        FEM_TRY(launch_plan(pl, static_cast<int32_t *>(pr), static_cast<int64_t *>(ps),
+                                            static_cast<char *>(pt), &dri, lim));
+                        cudaEventRecord(ctx->ev1, ctx->stream);
+                        FEM_CUDA_TRY(cudaEventSynchronize(ctx->ev1));
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+                        const float cost = ms * (float)((double)pl.records / (double)std::max<int64_t>(lim, 1));
+                        if (best < 0.f || cost < best) best = cost, seg_mult = m;
+                    }
+                    tune_store(ctx, key, TuneVal{32, 256, seg_mult, 3});
+                }
+            }
+            Plan pl = make_plan(b, true, 32, T_def, seg_mult, records_needed);
             records_needed += pl.records;
             plans.push_back(std::move(pl));
             continue;
@@ -2306,10 +2368,13 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             cc.stats.sparse_launches++;
         int maxP = 1;
         for (auto &r : pl.ri) maxP = std::max(maxP, r.P);
-        k_stitch<<<(pl.n_slots + kStitchWarps - 1) / kStitchWarps, kStitchWarps * 32, 0, ctx->stream>>>(
-            static_cast<int32_t *>(p_rec), d_ri, d_perm, cc.cand_rec, pl.slot_begin, pl.n_slots, cc.counts, fb_list,
-            d_fbc, nullptr, kStitchSplit);
-        cc.stats.kernel_launches++;
+        // local tracking wrote the counts of unsegmented episodes itself
+        if (!(pl.track && maxP == 1)) {
+            k_stitch<<<(pl.n_slots + kStitchWarps - 1) / kStitchWarps, kStitchWarps * 32, 0, ctx->stream>>>(
+                static_cast<int32_t *>(p_rec), d_ri, d_perm, cc.cand_rec, pl.slot_begin, pl.n_slots, cc.counts,
+                fb_list, d_fbc, nullptr, kStitchSplit, nullptr, nullptr, pl.track ? 1 : 0);
+            cc.stats.kernel_launches++;
+        }
         if (maxP > kStitchSplit) {
             k_stitch_block<<<(unsigned)std::min<int64_t>(pl.n_slots, (int64_t)ctx->n_sm * 4), kStitchBlock, 0,
                              ctx->stream>>>(static_cast<int32_t *>(p_rec), d_ri, d_perm, cc.cand_rec, pl.slot_begin,

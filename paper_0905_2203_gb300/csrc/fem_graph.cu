@@ -395,7 +395,7 @@ __device__ __forceinline__ void level_index(int64_t C, int N, int64_t cap, int64
 // segments, every sstep[r]-th of its pfine[r] finest ones.  Also the
 // per-recording candidate offsets and the RecInfo fields that depend on them.
 __device__ void level_info(const uint32_t *crec, int64_t C, int n_recs, int64_t *coff, RecInfo *ri,
-                           int64_t *nthreads, const int32_t *pfine, int32_t *sstep, int64_t target) {
+                           int64_t *nthreads, const int32_t *pfine, int32_t *sstep, int64_t target, int *maxP) {
     for (int r = threadIdx.x; r <= n_recs; r += blockDim.x) {
         int64_t lo = 0, hi = C;  // first candidate of recording >= r
         while (lo < hi) {
@@ -410,6 +410,7 @@ __device__ void level_info(const uint32_t *crec, int64_t C, int n_recs, int64_t 
         for (int r = 0; r < n_recs; ++r) W += (double)(coff[r + 1] - coff[r]) * (double)ri[r].n;
         const double seg_len = fmax(1.0, W / (double)target);
         int64_t base = 0;
+        int pmax = 1;
         for (int r = 0; r < n_recs; ++r) {
             const int pf = pfine[r];
             const double want = fmin((double)pf, fmax(1.0, ceil((double)ri[r].n / seg_len)));
@@ -421,18 +422,20 @@ __device__ void level_info(const uint32_t *crec, int64_t C, int n_recs, int64_t 
             ri[r].slot_first = (int)coff[r];
             ri[r].recbase = base;
             base += (coff[r + 1] - coff[r]) * P;
+            if (coff[r + 1] > coff[r] && P > pmax) pmax = P;
         }
         *nthreads = base;
+        *maxP = pmax;
     }
     __syncthreads();
 }
 
 __global__ void k_g_levelinfo(const uint32_t *crec, const int32_t *ctr, int N, int64_t cap, int64_t *offs,
                               int32_t *iota, int n_recs, int64_t *coff, RecInfo *ri, int64_t *nthreads,
-                              const int32_t *pfine, int32_t *sstep, int64_t target) {
+                              const int32_t *pfine, int32_t *sstep, int64_t target, int *maxP) {
     const int64_t C = ctr[0];
     level_index(C, N, cap, offs, iota, threadIdx.x, blockDim.x);
-    level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target);
+    level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target, maxP);
 }
 
 // Level N = M + 1 in one block: zero the level's counters, check every
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(1024, 1)
                    const int64_t *foff, const int32_t *ctr_prev, int M, int64_t cap, uint16_t *ct, int32_t *cl,
                    int32_t *ch, uint32_t *crec, int32_t *ctr, unsigned long long *rel, int64_t *offs, int32_t *iota,
                    int n_recs, int64_t *coff, RecInfo *ri, int64_t *nthreads, const int32_t *pfine, int32_t *sstep,
-                   int64_t target) {
+                   int64_t target, int *maxP) {
     __shared__ int64_t s_pp[kFusedRecs + 1];  // pair offsets per recording
     const int N = M + 1;
     {
@@ -500,7 +503,7 @@ __global__ void __launch_bounds__(1024, 1)
     }
     level_index(C, N, cap, offs, iota, threadIdx.x, blockDim.x);
     __syncthreads();  // crec complete
-    level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target);
+    level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target, maxP);
 }
 
 // The level's threshold in one block: flags, scan, write of the frequent
@@ -711,6 +714,8 @@ struct GraphTail {
     int64_t *tqueue = nullptr;
     int32_t *tg_gidx = nullptr, *tg_gstart = nullptr, *tg_gfirst = nullptr, *tg_stmp = nullptr;
     int64_t *tg_ibase = nullptr, *tg_nitems = nullptr;
+    int32_t *rorder = nullptr;             // recordings, longest first (item order)
+    int *d_maxP = nullptr;                 // the current level's largest segment count
     int64_t *segf = nullptr, *segl = nullptr;  // finest / current level's segment starts
     int32_t *pfine = nullptr, *sstep = nullptr;
     int64_t target = 0;                    // (candidate, segment) threads per level
@@ -886,6 +891,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     FEM_TRY(g->get(&fb_list, cap));
     FEM_TRY(g->get(&iota, cap));
     FEM_TRY(g->get(&rec, (size_t)g->cap_threads * kRecWords));
+    FEM_TRY(g->get(&g->d_maxP, 1));
     if (g->track) {
         FEM_TRY(g->get(&g->tbuf, track_buf_bytes(g->track_nblocks, g->track_cap) / sizeof(int32_t)));
         FEM_TRY(g->get(&g->tqueue, 1));
@@ -895,6 +901,11 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_TRY(g->get(&g->tg_stmp, (cap + 2) / 1024 + 2));
         FEM_TRY(g->get(&g->tg_ibase, n_recs + 1));
         FEM_TRY(g->get(&g->tg_nitems, 1));
+        FEM_TRY(g->get(&g->rorder, n_recs));
+        std::vector<int32_t> ro(n_recs);
+        for (int r = 0; r < n_recs; ++r) ro[r] = r;
+        std::stable_sort(ro.begin(), ro.end(), [&](int x, int y) { return g->recs[x]->n > g->recs[y]->n; });
+        FEM_CUDA_TRY(cudaMemcpyAsync(g->rorder, ro.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
     }
     FEM_TRY(g->get(&offs, cap + 1));
     FEM_TRY(g->get(&nthreads, 1));
@@ -1061,7 +1072,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             k_g_prune_write<<<gb2, 256, 0, st>>>(pos, gt, glo, ghi, grec, cap2, ubp, d_uboff, d_nt, d_blo, d_bhi, nb,
                                                  g->d_thr, cap, ct, cl, ch, crec, cn);
             k_g_levelinfo<<<1, 256, 0, st>>>(crec, cn, N, cap, offs, iota, n_recs, coffN, d_ri, nthreads, g->pfine,
-                                             g->sstep, g->target);
+                                             g->sstep, g->target, g->d_maxP);
         } else {
             const int M = N - 1;
             const FLevel &pf = g->F[M];
@@ -1069,14 +1080,14 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             if (fuse_join) {
                 k_g_join_fused<<<1, 1024, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, ct, cl, ch,
                                                    crec, cn, g->rel + N, offs, iota, n_recs, coffN, d_ri, nthreads,
-                                                   g->pfine, g->sstep, g->target);
+                                                   g->pfine, g->sstep, g->target, g->d_maxP);
             } else {
                 k_g_join_count<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos);
                 if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);
                 k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl,
                                                    ch, crec, cn);
                 k_g_levelinfo<<<1, 256, 0, st>>>(crec, cn, N, cap, offs, iota, n_recs, coffN, d_ri, nthreads,
-                                                 g->pfine, g->sstep, g->target);
+                                                 g->pfine, g->sstep, g->target, g->d_maxP);
             }
         }
         const bool bounded = g->coarse && N >= 3;
@@ -1102,6 +1113,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             ta.buf = g->tbuf;
             ta.cap = g->track_cap;
             ta.rec = rec;
+            ta.counts = counts;  // unsegmented recordings: counts written directly
             TrackGroupIn gi{};
             gi.slot2cand = iota;
             gi.d_n_slots = cn;
@@ -1119,15 +1131,15 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             gi.gfirst = g->tg_gfirst;
             gi.ibase = g->tg_ibase;
             gi.n_items = g->tg_nitems;
-            // level 2 shares no prefix work: one item per (episode, segment)
-            if (N >= 3)
-                cst = track_groups(st, ctx->n_sm, gi, &ta);
-            else
-                ta.d_n_items = nthreads;
+            // items: recordings longest first; level 2 shares no prefix
+            // work (one item per episode and segment), levels >= 3 group
+            // episodes by their (N-1)-node prefix
+            gi.rorder = g->rorder;
+            cst = track_groups(st, ctx->n_sm, gi, N >= 3, &ta);
             if (cst == FEM_OK) cst = launch_track(st, g->track_nblocks, ta);
             if (cst == FEM_OK)
                 cst = launch_stitch_dev(st, ctx->n_sm, d_ri, iota, crec, rec, cn, cap, counts, fb_list, cn + 3,
-                                        bounded ? g->skip : nullptr);
+                                        bounded ? g->skip : nullptr, g->d_maxP, 1);
         } else if (cst == FEM_OK) {
             cst = launch_count_dev(st, nmax, N, g->ring_cap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch,
                                    iota, crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov,

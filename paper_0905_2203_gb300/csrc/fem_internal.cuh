@@ -72,7 +72,7 @@ struct RecInfo {
 // kernels (recording-major, then episode slot, then segment) and taken from
 // an atomic counter by a persistent grid.
 constexpr int kTrackWarps = 8;           // warps per block
-constexpr int kTrackMaxBlocksPerSm = 4;  // resident blocks per SM the grid asks for
+constexpr int kTrackMaxBlocksPerSm = 6;  // resident blocks per SM the grid asks for (40 registers)
 constexpr int kTrackGroupMax = 64;       // episodes per prefix group (a new group every 64 slots)
 struct TrackArgs {
     const RecInfo *rinfo;
@@ -91,12 +91,17 @@ struct TrackArgs {
     int32_t *buf;                // per warp 4 * cap words (entry lists, ping-pong)
     int64_t cap;                 // at least the longest per-type list of every recording
     int32_t *rec;                // records, kRecWords each
-    // Prefix groups (all null: one item per (episode, segment)).  Group g
-    // holds slots [gstart[g], gstart[g+1]); recording r's groups start at
-    // gfirst[r] and its items (groups x segments) at ibase[r].
+    uint32_t *counts;            // if set: episodes of unsegmented recordings (P = 1) write their
+                                 // count here instead of a record
+    // Item order and prefix groups (ibase null: items numbered like the
+    // records).  Recordings are taken in the order rorder (null: 0, 1, ...);
+    // the i-th of them starts at item ibase[i]; recording r's first group is
+    // gfirst[r]; group g holds slots [gstart[g], gstart[g+1]) (gstart null:
+    // one slot per group).
     const int32_t *gstart;
     const int32_t *gfirst;
     const int64_t *ibase;
+    const int32_t *rorder;
 };
 // Inputs of track_groups: the slots (slot2cand, live count on the device or
 // n_slots_cap), the candidate CSR, per-candidate recordings, the launch's
@@ -114,6 +119,7 @@ struct TrackGroupIn {
     const uint32_t *cand_rec;
     const RecInfo *rinfo;
     int n_recs;
+    const int32_t *rorder;       // recordings in item order (null: 0, 1, ...)
     int32_t *gidx, *scan_tmp, *gstart, *gfirst;
     int64_t *ibase, *n_items;
 };
@@ -143,8 +149,9 @@ struct TuneVal {
     int K;            // lanes (episodes) per CTA
     int T;            // events per shared-memory stage
     double seg_mult;  // multiplier on the segment-count heuristic
-    int kernel;       // 1 tiled, 2 sparse
+    int kernel;       // 1 tiled, 2 sparse, 3 local tracking (warp per item)
 };
+constexpr int kTuneTrack = 9;  // size-class field of the tuning key of local-tracking launches
 
 }  // namespace fem
 
@@ -314,9 +321,10 @@ int count_plt(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const int64_t
 // Persistent grid of the local-tracking kernel on this device (blocks), the
 // bytes of its per-warp buffers, and its launch (queue reset + kernel).
 int track_blocks(int n_sm);
-// Builds the prefix groups of a launch on the device and sets the group
-// fields and d_n_items of *a.
-int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, TrackArgs *a);
+// Numbers the items of a launch on the device (recordings in the order
+// in.rorder, and with `grouped` the prefix groups) and sets the item fields
+// and d_n_items of *a.
+int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, bool grouped, TrackArgs *a);
 size_t track_buf_bytes(int blocks, int64_t cap);
 int launch_track(cudaStream_t st, int blocks, const TrackArgs &a);
 
@@ -360,9 +368,12 @@ int launch_count_dev(cudaStream_t st, int nmax, int nodes, int R, const RecInfo 
 size_t sparse_smem_bytes(int nmax, int R);
 // Both stitch kernels over the live slots (count on the device) of a launch
 // whose records follow rinfo (per recording: slot_first, recbase, P).
+// d_maxP (optional): the largest segment count of any recording (device);
+// direct_p1: the counting kernel wrote the counts of unsegmented episodes.
 int launch_stitch_dev(cudaStream_t st, int nsm, const RecInfo *rinfo, const int32_t *slot2cand,
                       const uint32_t *cand_rec, const int32_t *rec, const int32_t *d_n_slots, int64_t cap_slots,
-                      uint32_t *counts, int32_t *fb_list, int *fb_count, const uint8_t *skip);
+                      uint32_t *counts, int32_t *fb_list, int *fb_count, const uint8_t *skip, const int *d_maxP,
+                      int direct_p1);
 // Segment boundaries (P + 1 entries) of a stream cut into P segments at time changes.
 int launch_segments(cudaStream_t st, const int32_t *time, int64_t n, int P, int64_t *seg);
 // Levels 1..max_size in one captured graph (streams resident; no host step

@@ -939,7 +939,12 @@ int mg_count_batch(fem_ctx *ctx, const std::vector<MineGroup *> &gs) {
     gs[0]->S.kernel_launches += cs.kernel_launches;
     gs[0]->S.sparse_launches += cs.sparse_launches;
     gs[0]->S.count_kernel_ms += cs.count_kernel_ms;
-    for (MineGroup *g : gs) g->S.candidates_counted += g->done ? 0 : g->n_order;
+    for (MineGroup *g : gs) {
+        if (g->done) continue;
+        g->S.candidates_counted += g->n_order;
+        // every counted candidate of a group is counted over its own recording
+        g->S.counted_episode_events += (double)g->n_order * (double)g->recs[0]->n;
+    }
     return sync_status(ctx);
 }
 

@@ -84,46 +84,57 @@ __device__ __forceinline__ int window_rank(int32_t vt, int64_t q) {
 // Not LAST: the valid events are appended to oT/oL and their number is
 // returned.  LAST: the valid events at or after Tp are passed, in time
 // order, to Algorithm 1 of every entry class in st.
+//
+// Each chunk of 32 events ranks its queries in windows of 32 entries that
+// start one entry before the previous chunk's last rank and move on by 31:
+// the first entry of every window is older than every query still looking,
+// so a lane's predecessor is always in the window where its rank falls and
+// is read from the window's registers by a shuffle.
 template <bool LAST>
-__device__ __forceinline__ int64_t node_step(const int32_t *__restrict__ ttime, int64_t cb, int64_t ce,
-                                             const int32_t *__restrict__ pT, const int32_t *__restrict__ pL,
-                                             int64_t m, int32_t lo_e, int32_t hi_e, int32_t *__restrict__ oT,
-                                             int32_t *__restrict__ oL, Machine<2, 0> &st, int32_t Tp, int lane) {
-    int64_t w = 0;   // window start: every remaining query ranks at or after it
-    int64_t wc = 0;  // entries written
-    for (int64_t base = cb; base < ce; base += 32) {
-        const int64_t j = base + lane;
-        const bool in = j < ce;
-        const int32_t t = in ? ttime[j] : INT32_MAX;
-        const int64_t q = in ? (int64_t)t - lo_e : INT64_MAX;
-        const int64_t q0 = (int64_t)__shfl_sync(kFull, t, 0) - lo_e;
-        int64_t idx = 0;
+__device__ __forceinline__ int node_step(const int32_t *__restrict__ ev, int n_ev, const int32_t *__restrict__ pT,
+                                         const int32_t *__restrict__ pL, int m, int32_t lo_e, int32_t hi_e,
+                                         int32_t *__restrict__ oT, int32_t *__restrict__ oL, Machine<2, 0> &st,
+                                         int32_t Tp, int lane) {
+    // All positions fit 32 bits: a recording has fewer than 2^30 events.
+    // Times are >= 0 and 0 <= lo < hi, so t - lo and t - hi stay in int32.
+    int w = 0;   // entries below the previous chunk's last query
+    int wc = 0;  // entries written
+    int32_t t_next = lane < n_ev ? ev[lane] : INT32_MAX;
+    for (int base = 0; base < n_ev; base += 32) {
+        const bool in = base + lane < n_ev;
+        const int32_t t = t_next;
+        if (base + 32 < n_ev) t_next = (base + 32 + lane < n_ev) ? ev[base + 32 + lane] : INT32_MAX;
+        const int32_t q = t - lo_e;
+        const int32_t q0 = __shfl_sync(kFull, q, 0);
+        int ws = w > 0 ? w - 1 : 0;
+        int idx = 0;
+        int32_t aT = INT32_MIN;
         bool done = !in;
         for (;;) {
-            const int64_t wi = w + lane;
+            const int wi = ws + lane;
             const int32_t vt = wi < m ? pT[wi] : INT32_MAX;
             const int32_t top = __shfl_sync(kFull, vt, 31);
-            if ((int64_t)top < q0 && w + 32 < m) {  // the whole window precedes every query
-                w += 32;
+            if (top < q0 && ws + 32 < m) {  // the whole window precedes every query
+                ws += 31;
                 continue;
             }
-            const int c = window_rank(vt, q);
+            // rank of q among the window's values (ascending across lanes)
+            int c = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1)
+                if (__shfl_sync(kFull, vt, c + s - 1) < q) c += s;
+            if (c == 31 && top < q) c = 32;
+            const int32_t xt = __shfl_sync(kFull, vt, c > 0 ? c - 1 : 0);
             if (!done && c < 32) {
-                idx = w + c;
+                idx = ws + c;
+                aT = c > 0 ? xt : INT32_MIN;
                 done = true;
             }
             if (__all_sync(kFull, done)) break;
-            w += 32;
+            ws += 31;
         }
-        bool ok = false;
-        int32_t Lv = 0;
-        if (in && idx > 0) {
-            const int32_t tp = pT[idx - 1];
-            if ((int64_t)tp >= (int64_t)t - hi_e) {
-                ok = true;
-                Lv = pL ? pL[idx - 1] : tp;
-            }
-        }
+        const bool ok = in && aT != INT32_MIN && aT >= t - hi_e;
+        const int32_t Lv = ok ? (pL ? pL[idx - 1] : aT) : 0;
         if (!LAST) {
             const unsigned bm = __ballot_sync(kFull, ok);
             if (ok) {
@@ -134,10 +145,28 @@ __device__ __forceinline__ int64_t node_step(const int32_t *__restrict__ ttime, 
             wc += __popc(bm);
         } else {
             unsigned bm = __ballot_sync(kFull, ok && t >= Tp);
-            while (bm) {
-                const int b = __ffs(bm) - 1;
-                bm &= bm - 1;
-                st.greedy_end(__shfl_sync(kFull, t, b), __shfl_sync(kFull, Lv, b), Tp);
+            if (bm && !st.open && st.live == 1u) {
+                // steady state (one class): jump from selection to
+                // selection -- the next one is the first later end whose
+                // latest start is after the last selected end
+                int32_t prev = st.cprev[0];
+                uint32_t added = 0;
+                for (;;) {
+                    const unsigned sel = __ballot_sync(kFull, ((bm >> lane) & 1u) && Lv > prev);
+                    if (!sel) break;
+                    const int b = __ffs(sel) - 1;
+                    prev = __shfl_sync(kFull, t, b);
+                    ++added;
+                    bm &= (b == 31) ? 0u : ~((2u << b) - 1u);
+                }
+                st.ccnt[0] += added;
+                st.cprev[0] = prev;
+            } else {
+                while (bm) {
+                    const int b = __ffs(bm) - 1;
+                    bm &= bm - 1;
+                    st.greedy_end(__shfl_sync(kFull, t, b), __shfl_sync(kFull, Lv, b), Tp);
+                }
             }
         }
         // the next 32 queries rank at or after this chunk's last one
@@ -166,7 +195,7 @@ __device__ __forceinline__ void machine_init(Machine<2, 0> &st, int N) {
 // (slot) or, with groups, a run of episode slots [s0, s1) that share their
 // first N-1 nodes and edges: the shared prefix is tracked once, and only the
 // last node step is run per episode.
-__global__ void __launch_bounds__(kTrackWarps * 32, 4) k_count_track(TrackArgs a) {
+__global__ void __launch_bounds__(kTrackWarps * 32, 6) k_count_track(TrackArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int32_t *const bT0 = a.buf + gw * 4 * a.cap;
@@ -180,19 +209,27 @@ __global__ void __launch_bounds__(kTrackWarps * 32, 4) k_count_track(TrackArgs a
         it = __shfl_sync(kFull, it, 0);
         if ((int64_t)it >= n_items) break;
         int r = 0, P = 1, p = 0, s0 = 0, s1 = 0;
-        if (a.gstart) {
-            int lo_r = 0, hi_r = a.n_recs;  // last recording whose items start at or before it
+        if (a.ibase) {
+            // items numbered recording by recording in the order rorder
+            // (longest recordings first), each recording's groups (or
+            // slots) times its segments
+            int lo_r = 0, hi_r = a.n_recs;  // last position whose items start at or before it
             while (hi_r - lo_r > 1) {
                 const int mid = (lo_r + hi_r) >> 1;
                 if (a.ibase[mid] <= (int64_t)it) lo_r = mid; else hi_r = mid;
             }
-            r = lo_r;
+            r = a.rorder ? a.rorder[lo_r] : lo_r;
             P = a.rinfo[r].P;
-            const int64_t local = (int64_t)it - a.ibase[r];
+            const int64_t local = (int64_t)it - a.ibase[lo_r];
             const int64_t g = a.gfirst[r] + local / P;
             p = (int)(local % P);
-            s0 = a.gstart[g];
-            s1 = a.gstart[g + 1];
+            if (a.gstart) {
+                s0 = a.gstart[g];
+                s1 = a.gstart[g + 1];
+            } else {
+                s0 = (int)g;
+                s1 = s0 + 1;
+            }
         } else {
             const int64_t tr = a.rec_first + (int64_t)it;
             int lo_r = 0, hi_r = a.n_recs;  // last recording whose records start at or before tr
@@ -249,19 +286,19 @@ __global__ void __launch_bounds__(kTrackWarps * 32, 4) k_count_track(TrackArgs a
         // shared prefix: node 0, then nodes 1..N-2 (entry lists ping-pong)
         const int32_t *pT = nullptr;
         const int32_t *pL = nullptr;
-        int64_t m = 0;
+        int m = 0;
         Machine<2, 0> st;
         if (live) {
             int64_t pb = 0, pe = 0;
             range(a.ctypes[o0], pb, pe);
             pT = ttime + pb;
-            m = pe - pb;
+            m = (int)(pe - pb);
             for (int k = 1; k < N - 1 && m > 0; ++k) {
                 int64_t cb = 0, ce = 0;
                 range(a.ctypes[o0 + k], cb, ce);
                 int32_t *oT = (k & 1) ? bT1 : bT0;
                 int32_t *oL = (k & 1) ? bL1 : bL0;
-                m = node_step<false>(ttime, cb, ce, pT, pL, m, a.relaxed ? 0 : a.clo[eo0 + k - 1],
+                m = node_step<false>(ttime + cb, (int)(ce - cb), pT, pL, m, a.relaxed ? 0 : a.clo[eo0 + k - 1],
                                      a.chi[eo0 + k - 1], oT, oL, st, 0, lane);
                 pT = oT;
                 pL = oL;
@@ -270,17 +307,29 @@ __global__ void __launch_bounds__(kTrackWarps * 32, 4) k_count_track(TrackArgs a
         // last node of every episode of the item
         for (int s = s0; s < s1; ++s) {
             const int c = a.slot2cand[s];
-            if (a.skip && a.skip[c]) continue;  // the stitch writes its count (0)
+            const bool direct = P == 1 && a.counts;
+            if (a.skip && a.skip[c]) {  // pruned by a bound: count 0 (else the stitch writes it)
+                if (direct && lane == 0) a.counts[c] = 0;
+                continue;
+            }
             machine_init(st, N);
             if (live && m > 0) {
                 const int64_t oc = a.offs[c], ec = oc - c;
                 int64_t cb = 0, ce = 0;
                 range(a.ctypes[oc + N - 1], cb, ce);
-                node_step<true>(ttime, cb, ce, pT, pL, m, a.relaxed ? 0 : a.clo[ec + N - 2], a.chi[ec + N - 2],
-                                nullptr, nullptr, st, Tp, lane);
+                node_step<true>(ttime + cb, (int)(ce - cb), pT, pL, m, a.relaxed ? 0 : a.clo[ec + N - 2],
+                                a.chi[ec + N - 2], nullptr, nullptr, st, Tp, lane);
             }
             st.finish();
-            if (lane == 0) write_record(a.rec + (ri.recbase + (int64_t)(s - ri.slot_first) * P + p) * kRecWords, st);
+            if (lane == 0) {
+                if (direct)
+                    // one segment from the recording's start: the first valid
+                    // end closes the entry classes at class 0, whose count is
+                    // the episode's (what the stitch would read)
+                    a.counts[c] = st.ncls > 0 ? st.ccnt[0] : 0u;
+                else
+                    write_record(a.rec + (ri.recbase + (int64_t)(s - ri.slot_first) * P + p) * kRecWords, st);
+            }
         }
     }
 }
@@ -330,20 +379,27 @@ __global__ void k_track_group_starts(const int32_t *__restrict__ gidx, const int
     }
 }
 
+// Per recording (one thread): its first group (or, without groups, its first
+// slot) and, walking the recordings in the order rorder, the first item of
+// each (groups x segments) and the item count.
 __global__ void k_track_group_recs(const int32_t *__restrict__ gidx, const RecInfo *__restrict__ rinfo, int n_recs,
-                                   const int32_t *__restrict__ d_n_slots, int64_t n_slots_cap,
-                                   int32_t *__restrict__ gfirst, int64_t *__restrict__ ibase, int64_t *n_items) {
+                                   const int32_t *__restrict__ rorder, const int32_t *__restrict__ d_n_slots,
+                                   int64_t n_slots_cap, int32_t *__restrict__ gfirst, int64_t *__restrict__ ibase,
+                                   int64_t *n_items) {
     const int64_t n = d_n_slots ? (int64_t)*d_n_slots : n_slots_cap;
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    auto first = [&](int r) -> int64_t {
+        const int64_t sf = r < n_recs ? (int64_t)rinfo[r].slot_first : n;
+        const int64_t c = sf < n ? sf : n;
+        return gidx ? (int64_t)gidx[c] : c;
+    };
     int64_t base = 0;
-    for (int r = 0; r < n_recs; ++r) {
-        const int64_t sf = (int64_t)rinfo[r].slot_first < n ? (int64_t)rinfo[r].slot_first : n;
-        const int64_t sn1 = (r + 1 < n_recs) ? (int64_t)rinfo[r + 1].slot_first : n;
-        const int64_t sn = sn1 < n ? sn1 : n;
-        const int g0 = gidx[sf], g1 = gidx[sn];
-        gfirst[r] = g0;
-        ibase[r] = base;
-        base += (int64_t)(g1 - g0) * rinfo[r].P;
+    for (int i = 0; i < n_recs; ++i) {
+        const int r = rorder ? rorder[i] : i;
+        const int64_t g0 = first(r), g1 = first(r + 1);
+        gfirst[r] = (int32_t)g0;
+        ibase[i] = base;
+        base += (g1 - g0) * rinfo[r].P;
     }
     ibase[n_recs] = base;
     *n_items = base;
@@ -351,19 +407,22 @@ __global__ void k_track_group_recs(const int32_t *__restrict__ gidx, const RecIn
 
 }  // namespace
 
-int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, TrackArgs *a) {
+int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, bool grouped, TrackArgs *a) {
     const int64_t cap = in.n_slots_cap;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + 256) / 256, 8 * (int64_t)n_sm));
-    k_track_group_flags<<<g, 256, 0, st>>>(in.slot2cand, in.d_n_slots, cap, in.offs, in.ctypes, in.clo, in.chi,
-                                           in.cand_rec, in.gidx);
-    FEM_TRY(scan_exclusive(st, in.gidx, cap + 1, in.scan_tmp, nullptr, nullptr));
-    k_track_group_starts<<<g, 256, 0, st>>>(in.gidx, in.d_n_slots, cap, in.gstart);
-    k_track_group_recs<<<1, 32, 0, st>>>(in.gidx, in.rinfo, in.n_recs, in.d_n_slots, cap, in.gfirst, in.ibase,
-                                         in.n_items);
+    if (grouped) {
+        k_track_group_flags<<<g, 256, 0, st>>>(in.slot2cand, in.d_n_slots, cap, in.offs, in.ctypes, in.clo, in.chi,
+                                               in.cand_rec, in.gidx);
+        FEM_TRY(scan_exclusive(st, in.gidx, cap + 1, in.scan_tmp, nullptr, nullptr));
+        k_track_group_starts<<<g, 256, 0, st>>>(in.gidx, in.d_n_slots, cap, in.gstart);
+    }
+    k_track_group_recs<<<1, 32, 0, st>>>(grouped ? in.gidx : nullptr, in.rinfo, in.n_recs, in.rorder, in.d_n_slots,
+                                         cap, in.gfirst, in.ibase, in.n_items);
     FEM_CUDA_TRY(cudaGetLastError());
-    a->gstart = in.gstart;
+    a->gstart = grouped ? in.gstart : nullptr;
     a->gfirst = in.gfirst;
     a->ibase = in.ibase;
+    a->rorder = in.rorder;
     a->d_n_items = in.n_items;
     return FEM_OK;
 }

@@ -32,7 +32,7 @@ def test_autotune_exact_cached_and_reused(fb, tmp_path):
     table = json.loads(path.read_text())
     assert len(table) >= 1
     for k, (lanes, tile, mult, kernel) in table.items():
-        assert lanes % 32 == 0 and 32 <= lanes <= 256 and tile % 256 == 0 and mult > 0 and kernel in (1, 2)
+        assert lanes % 32 == 0 and 32 <= lanes <= 256 and tile % 256 == 0 and mult > 0 and kernel in (1, 2, 3)
     # a fresh context picks the cached choices up (no further entries needed)
     ctx2 = fb.Context(0)
     ctx2.set_autotune_cache(path)
