@@ -716,6 +716,8 @@ struct GraphTail {
     int64_t *tg_ibase = nullptr, *tg_nitems = nullptr;
     int32_t *rorder = nullptr;             // recordings, longest first (item order)
     int *d_maxP = nullptr;                 // the current level's largest segment count
+    PairUbPlan pub;                        // level-2 pre-pass by end type (when it fits)
+    bool pub_ok = false;
     int64_t *segf = nullptr, *segl = nullptr;  // finest / current level's segment starts
     int32_t *pfine = nullptr, *sstep = nullptr;
     int64_t target = 0;                    // (candidate, segment) threads per level
@@ -739,6 +741,7 @@ struct GraphTail {
     ~GraphTail() {
         if (exec) cudaGraphExecDestroy(exec);
         cudaStreamSynchronize(ctx->stream);
+        pair_ub_release(ctx, &pub);
         for (auto e : ev) cudaEventDestroy(e);
         for (auto &h : held) dev_free(ctx, h.first, h.second);
         if (h_out) cudaFreeHost(h_out);
@@ -952,7 +955,14 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_TRY(g->get(&glo, std::max<int64_t>(cap2, 1)));
         FEM_TRY(g->get(&ghi, std::max<int64_t>(cap2, 1)));
         FEM_TRY(g->get(&grec, std::max<int64_t>(cap2, 1)));
-        if (g->prepass) FEM_TRY(g->get(&ub, std::max<int64_t>(ub_off[n_recs], 1)));
+        if (g->prepass) {
+            FEM_TRY(g->get(&ub, std::max<int64_t>(ub_off[n_recs], 1)));
+            std::vector<int64_t> uo;
+            pair_ub_table_words(g->recs, nb, &uo);
+            const int pst = pair_ub_setup(ctx, g->recs, uo, blo, bhi, &g->pub);
+            if (pst != FEM_OK && pst != FEM_ERR_INVAL) return pst;
+            g->pub_ok = pst == FEM_OK;
+        }
         FEM_CUDA_TRY(cudaMemcpyAsync(d_ntpre, ntpre.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
         FEM_CUDA_TRY(cudaMemcpyAsync(d_evpre, evpre.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
         FEM_CUDA_TRY(cudaMemcpyAsync(d_uboff, ub_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
@@ -1062,8 +1072,12 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                                           grec);
             if (g->prepass) {
                 ok(cudaMemsetAsync(ub, 0, sizeof(uint32_t) * std::max<int64_t>(ub_off[n_recs], 1), st));
-                k_g_pair_ub<<<gbe, ub_threads, ub_smem, st>>>(d_ri, d_tpre, n_recs, d_nt, d_uboff, d_blo, d_bhi, nb,
-                                                              hi_max, ub_words, d_lut, ub);
+                if (g->pub_ok) {
+                    if (cst == FEM_OK) cst = pair_ub_launch(st, g->pub, ub);
+                } else {
+                    k_g_pair_ub<<<gbe, ub_threads, ub_smem, st>>>(d_ri, d_tpre, n_recs, d_nt, d_uboff, d_blo, d_bhi,
+                                                                  nb, hi_max, ub_words, d_lut, ub);
+                }
             }
             const uint32_t *ubp = g->prepass ? ub : nullptr;
             k_g_prune_flags<<<gb2, 256, 0, st>>>(gt, glo, ghi, grec, cn, cap2, ubp, d_uboff, d_nt, d_blo, d_bhi, nb,
