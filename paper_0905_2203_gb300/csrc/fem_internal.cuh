@@ -333,12 +333,14 @@ int launch_track(cudaStream_t st, int blocks, const TrackArgs &a);
 // (a * n_types_r + b) * nb + k] = b-events of recording r with an a-event at
 // a distance inside bin k before them.  pair_ub_setup uploads the tables of a
 // set of recordings (building their per-type lists) and returns
-// FEM_ERR_INVAL when the kernel's shared memory would not fit (the caller
-// then uses the stream-order kernel); the plan's buffer lives until
+// FEM_ERR_INVAL when the alphabet is small (fewer than kPairByTypeMinPairs
+// types x bins) or the kernel's shared memory would not fit: the caller then
+// uses the stream-order kernel; the plan's buffer lives until
 // pair_ub_release.
 constexpr int kPairLutMax = 32768;  // largest hi_max with a distance-to-bins table in shared memory
+constexpr size_t kPairByTypeMinPairs = 1024;  // (types x bins) from which the by-type kernel is used
 struct PairUbPlan {
-    int n_recs = 0, nb = 0;
+    int n_recs = 0, nb = 0, chunk = 0;
     int32_t hi_max = 0;
     int lut_words = 0, hist_words = 0, bit_words = 0;
     size_t smem = 0;

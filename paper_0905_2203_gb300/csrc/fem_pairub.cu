@@ -24,7 +24,7 @@ namespace fem {
 
 namespace {
 
-constexpr int kPairChunk = 1024;  // end events per warp item
+constexpr int kPairChunkMax = 1024;  // end events per warp item (at most)
 constexpr int kPairWarps = 8;
 
 struct PairRec {
@@ -35,7 +35,7 @@ struct PairRec {
     const int32_t *tpos;
     int64_t ub_off;
     uint32_t nt;
-    int32_t nchunk;  // runs per type: ceil(longest list / kPairChunk)
+    int32_t nchunk;  // runs per type: ceil(longest list / chunk)
 };
 
 __global__ void __launch_bounds__(kPairWarps * 32) k_pair_ub_t(const PairRec *__restrict__ recs, int n_recs,
@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair_ub_t(const PairRec *__
                                                                const int32_t *__restrict__ blo,
                                                                const int32_t *__restrict__ bhi, int32_t hi_max,
                                                                const uint8_t *__restrict__ lut_g, int lut_words,
-                                                               int hist_words, int bit_words, uint32_t *ub) {
+                                                               int hist_words, int bit_words, int chunk,
+                                                               uint32_t *ub) {
     extern __shared__ uint32_t sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int i = threadIdx.x; i < lut_words; i += blockDim.x) sm[i] = reinterpret_cast<const uint32_t *>(lut_g)[i];
@@ -61,8 +62,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) k_pair_ub_t(const PairRec *__
         const PairRec &R = recs[lo_r];
         const int64_t local = it - ipre[lo_r];
         const uint32_t b = (uint32_t)(local / R.nchunk);
-        const int64_t j0 = R.toff[b] + (local % R.nchunk) * kPairChunk;
-        const int64_t j1 = min(R.toff[b + 1], j0 + kPairChunk);
+        const int64_t j0 = R.toff[b] + (local % R.nchunk) * chunk;
+        const int64_t j1 = min(R.toff[b + 1], j0 + chunk);
         if (j0 >= j1) continue;  // warp-uniform
         const int hw = (int)R.nt * nb;
         const int bw = (hw + 31) >> 5;
@@ -133,13 +134,26 @@ int pair_ub_setup(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std
     std::vector<PairRec> pr(n_recs);
     std::vector<int64_t> ipre(n_recs + 1, 0);
     uint32_t nt_max = 1;
+    int64_t n_all = 0;
+    for (auto *s : recs) {
+        nt_max = std::max(nt_max, s->n_types);
+        n_all += s->n;
+    }
+    // By end type pays where the alphabet is large (one global atomic per
+    // event and pair is what the stream-order kernels spend); small
+    // alphabets keep the stream-order kernels, which give each event its own
+    // thread.
+    if ((size_t)nt_max * nb < kPairByTypeMinPairs) return FEM_ERR_INVAL;
+    // runs of up to 1024 end events, shorter while the launch would hold
+    // fewer than about eight runs per resident warp
+    int chunk = kPairChunkMax;
+    while (chunk > 64 && n_all / chunk < (int64_t)8 * ctx->n_sm * 32) chunk >>= 1;
     for (int r = 0; r < n_recs; ++r) {
         fem_stream *s = recs[r];
         FEM_TRY(stream_bytype(ctx, s));
-        const int32_t nchunk = (int32_t)std::max<int64_t>(1, (s->max_list + kPairChunk - 1) / kPairChunk);
+        const int32_t nchunk = (int32_t)std::max<int64_t>(1, (s->max_list + chunk - 1) / chunk);
         pr[r] = PairRec{s->d_type, s->d_time, s->d_toff, s->d_ttime, s->d_tpos, ub_off[r], s->n_types, nchunk};
         ipre[r + 1] = ipre[r] + (s->n > 0 ? (int64_t)s->n_types * nchunk : 0);
-        nt_max = std::max(nt_max, s->n_types);
     }
     // bins of each distance 1..hi_max as a byte mask (when it fits)
     std::vector<uint8_t> lut;
@@ -153,6 +167,7 @@ int pair_ub_setup(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std
     p.n_recs = n_recs;
     p.nb = nb;
     p.hi_max = hi_max;
+    p.chunk = chunk;
     p.lut_words = (int)(lut.size() / 4);
     p.hist_words = (int)(nt_max * (uint32_t)nb);
     p.bit_words = (p.hist_words + 31) / 32;
@@ -198,7 +213,7 @@ void pair_ub_release(fem_ctx *ctx, PairUbPlan *plan) {
 int pair_ub_launch(cudaStream_t st, const PairUbPlan &p, uint32_t *ub) {
     k_pair_ub_t<<<(unsigned)p.blocks, kPairWarps * 32, p.smem, st>>>(
         static_cast<const PairRec *>(p.d_recs), p.n_recs, p.d_ipre, p.nb, p.d_blo, p.d_bhi, p.hi_max, p.d_lut,
-        p.lut_words, p.hist_words, p.bit_words, ub);
+        p.lut_words, p.hist_words, p.bit_words, p.chunk, ub);
     FEM_CUDA_TRY(cudaGetLastError());
     return FEM_OK;
 }
