@@ -1520,33 +1520,28 @@ int stream_bytype(fem_ctx *ctx, fem_stream *s) {
     if (s->d_ttime) return FEM_OK;
     if (s->n_types > 8192 || s->n > INT32_MAX / 2) return FEM_ERR_INVAL;
     const int64_t n = s->n;
-    void *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
+    void *p1 = nullptr, *p2 = nullptr;
     FEM_TRY(dev_alloc(ctx, &p1, sizeof(int64_t) * (s->n_types + 1)));
-    int st2 = dev_alloc(ctx, &p2, sizeof(int32_t) * std::max<int64_t>(n, 1));
-    if (st2 == FEM_OK) {
-        st2 = dev_alloc(ctx, &p3, sizeof(int32_t) * std::max<int64_t>(n, 1));
-        if (st2 != FEM_OK) dev_free(ctx, p2, sizeof(int32_t) * std::max<int64_t>(n, 1));
-    }
+    const int st2 = dev_alloc(ctx, &p2, sizeof(int32_t) * std::max<int64_t>(n, 1));
     if (st2 != FEM_OK) {
         dev_free(ctx, p1, sizeof(int64_t) * (s->n_types + 1));
         return st2;
     }
     int64_t *toff = static_cast<int64_t *>(p1);
     int32_t *ttime = static_cast<int32_t *>(p2);
-    int32_t *perm = static_cast<int32_t *>(p3);  // stream position of every list entry (kept)
     const int n_keys = (int)s->n_types;
     const int64_t nblk = std::max<int64_t>(1, (n + kPartBlock - 1) / kPartBlock);
     const int64_t tab_n = (int64_t)n_keys * nblk;
     TmpDev tmp(ctx);
-    int32_t *key, *blk, *stmp, *koff;
+    int32_t *key, *perm, *blk, *stmp, *koff;
     int st = tmp.get(&key, std::max<int64_t>(n, 1));
+    if (st == FEM_OK) st = tmp.get(&perm, std::max<int64_t>(n, 1));
     if (st == FEM_OK) st = tmp.get(&blk, tab_n);
     if (st == FEM_OK) st = tmp.get(&stmp, tab_n / kScanBlock + 2);
     if (st == FEM_OK) st = tmp.get(&koff, n_keys + 1);
     if (st != FEM_OK) {
         dev_free(ctx, p1, sizeof(int64_t) * (s->n_types + 1));
         dev_free(ctx, p2, sizeof(int32_t) * std::max<int64_t>(n, 1));
-        dev_free(ctx, p3, sizeof(int32_t) * std::max<int64_t>(n, 1));
         return st;
     }
     cudaStream_t cs = ctx->stream;
@@ -1571,8 +1566,7 @@ int stream_bytype(fem_ctx *ctx, fem_stream *s) {
     for (uint32_t a = 0; a < s->n_types; ++a) s->max_list = std::max(s->max_list, toff_h[a + 1] - toff_h[a]);
     s->d_toff = toff;
     s->d_ttime = ttime;
-    s->d_tpos = perm;
-    s->bytes += sizeof(int64_t) * (s->n_types + 1) + 2 * sizeof(int32_t) * n;
+    s->bytes += sizeof(int64_t) * (s->n_types + 1) + sizeof(int32_t) * n;
     return FEM_OK;
 }
 
@@ -1955,7 +1949,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                 // (the halo is sum(hi) of time at the stream's mean rate)
                 const double span = std::max(1.0, (double)s->t_last - (double)s->t_first);
                 const double halo_ev = (double)s->n * (double)max_sumhi / span;
-                const double min_seg = std::max(1024.0, 8.0 * halo_ev);
+                const double min_seg = std::max(sparse && track ? (double)kTrackMinSeg : 1024.0, 8.0 * halo_ev);
                 P = (int)std::max<double>(1.0, std::min<double>((double)s->n / seg_len, (double)s->n / min_seg) /
                                                    cc.seg_div);
                 // each segment adds one record the stitch walks per episode

@@ -726,8 +726,6 @@ struct GraphTail {
     int64_t *tg_ibase = nullptr, *tg_nitems = nullptr;
     int32_t *rorder = nullptr;             // recordings, longest first (item order)
     int *d_maxP = nullptr;                 // the current level's largest segment count
-    PairUbPlan pub;                        // level-2 pre-pass by end type (when it fits)
-    bool pub_ok = false;
     int64_t *segf = nullptr, *segl = nullptr;  // finest / current level's segment starts
     int32_t *pfine = nullptr, *sstep = nullptr;
     int64_t target = 0;                    // (candidate, segment) threads per level
@@ -751,7 +749,6 @@ struct GraphTail {
     ~GraphTail() {
         if (exec) cudaGraphExecDestroy(exec);
         cudaStreamSynchronize(ctx->stream);
-        pair_ub_release(ctx, &pub);
         for (auto e : ev) cudaEventDestroy(e);
         for (auto &h : held) dev_free(ctx, h.first, h.second);
         if (h_out) cudaFreeHost(h_out);
@@ -797,7 +794,9 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         // the upper bounds, in events at the recording's mean rate)
         const double span = std::max(1.0, (double)s->t_last - (double)s->t_first);
         const double halo_ev = (double)s->n * (double)sumhi_max / span;
-        const double min_seg = std::max(256.0, 2.0 * halo_ev);
+        // (local tracking: segments of at least 8192 events, so that a warp's
+        // item is long against its halo and per-item set-up)
+        const double min_seg = std::max(ctx->tuning.kernel == 0 ? (double)kTrackMinSeg : 256.0, 2.0 * halo_ev);
         const int P = (int)std::max(1.0, std::min<double>(kMaxPerRec, (double)s->n / min_seg));
         pfine_h[r] = P;
         FEM_TRY(launch_segments(st, s->d_time, s->n, P, segs + (size_t)r * (kMaxPerRec + 1)));
@@ -823,12 +822,9 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         while (g->track_nblocks > ctx->n_sm && track_buf_bytes(g->track_nblocks, g->track_cap) > fb / 4)
             g->track_nblocks -= ctx->n_sm;
         if (track_buf_bytes(g->track_nblocks, g->track_cap) > fb / 4) return FEM_ERR_NOMEM;
-        // about one work item per resident warp: a level with few episodes
-        // is cut into fewer, longer segments (less halo, fewer records to
-        // stitch); a level with many is one item per episode anyway
-        // (measured on the mid-size pass: 0.68 ms per call against 0.82 ms
-        // with four items per warp)
-        g->target = (int64_t)g->track_nblocks * kTrackWarps;
+        // about four work items per resident warp, segments no shorter than
+        // kTrackMinSeg events (the finest segmentation above)
+        g->target = (int64_t)4 * g->track_nblocks * kTrackWarps;
     } else {
         g->target = (int64_t)2 * ctx->n_sm * 512;
     }
@@ -969,14 +965,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_TRY(g->get(&glo, std::max<int64_t>(cap2, 1)));
         FEM_TRY(g->get(&ghi, std::max<int64_t>(cap2, 1)));
         FEM_TRY(g->get(&grec, std::max<int64_t>(cap2, 1)));
-        if (g->prepass) {
-            FEM_TRY(g->get(&ub, std::max<int64_t>(ub_off[n_recs], 1)));
-            std::vector<int64_t> uo;
-            pair_ub_table_words(g->recs, nb, &uo);
-            const int pst = pair_ub_setup(ctx, g->recs, uo, blo, bhi, &g->pub);
-            if (pst != FEM_OK && pst != FEM_ERR_INVAL) return pst;
-            g->pub_ok = pst == FEM_OK;
-        }
+        if (g->prepass) FEM_TRY(g->get(&ub, std::max<int64_t>(ub_off[n_recs], 1)));
         FEM_CUDA_TRY(cudaMemcpyAsync(d_ntpre, ntpre.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
         FEM_CUDA_TRY(cudaMemcpyAsync(d_evpre, evpre.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
         FEM_CUDA_TRY(cudaMemcpyAsync(d_uboff, ub_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
@@ -1086,12 +1075,8 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                                           grec);
             if (g->prepass) {
                 ok(cudaMemsetAsync(ub, 0, sizeof(uint32_t) * std::max<int64_t>(ub_off[n_recs], 1), st));
-                if (g->pub_ok) {
-                    if (cst == FEM_OK) cst = pair_ub_launch(st, g->pub, ub);
-                } else {
-                    k_g_pair_ub<<<gbe, ub_threads, ub_smem, st>>>(d_ri, d_tpre, n_recs, d_nt, d_uboff, d_blo, d_bhi,
-                                                                  nb, hi_max, ub_words, d_lut, ub);
-                }
+                k_g_pair_ub<<<gbe, ub_threads, ub_smem, st>>>(d_ri, d_tpre, n_recs, d_nt, d_uboff, d_blo, d_bhi, nb,
+                                                              hi_max, ub_words, d_lut, ub);
             }
             const uint32_t *ubp = g->prepass ? ub : nullptr;
             k_g_prune_flags<<<gb2, 256, 0, st>>>(gt, glo, ghi, grec, cn, cap2, ubp, d_uboff, d_nt, d_blo, d_bhi, nb,

@@ -74,6 +74,7 @@ struct RecInfo {
 constexpr int kTrackWarps = 8;           // warps per block
 constexpr int kTrackMaxBlocksPerSm = 6;  // resident blocks per SM the grid asks for (40 registers)
 constexpr int kTrackGroupMax = 64;       // episodes per prefix group (a new group every 64 slots)
+constexpr int kTrackMinSeg = 8192;       // shortest segment (events) of a local-tracking item
 struct TrackArgs {
     const RecInfo *rinfo;
     int n_recs;
@@ -206,7 +207,6 @@ struct fem_stream {
     int32_t t_first = 0, t_last = 0;  // first and last event time (n > 0)
     int64_t *d_toff = nullptr;    // per-type event lists (built on first use): offsets [n_types + 1]
     int32_t *d_ttime = nullptr;   // times grouped by type, ascending within a type [n]
-    int32_t *d_tpos = nullptr;    // stream position of each of those entries [n]
     int64_t max_list = 0;         // longest per-type list (set with the lists)
     std::map<int32_t, uint32_t *> dens;  // lo -> per-type max events in a closed window of length lo
     std::map<int, int64_t *> segs;       // P -> segment boundaries (P + 1), cached
@@ -328,35 +328,6 @@ int track_blocks(int n_sm);
 int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, bool grouped, TrackArgs *a);
 size_t track_buf_bytes(int blocks, int64_t cap);
 int launch_track(cudaStream_t st, int blocks, const TrackArgs &a);
-
-// Level-2 upper-bound pre-pass by end type (fem_pairub.cu): ub[ub_off[r] +
-// (a * n_types_r + b) * nb + k] = b-events of recording r with an a-event at
-// a distance inside bin k before them.  pair_ub_setup uploads the tables of a
-// set of recordings (building their per-type lists) and returns
-// FEM_ERR_INVAL when the alphabet is small (fewer than kPairByTypeMinPairs
-// types x bins) or the kernel's shared memory would not fit: the caller then
-// uses the stream-order kernel; the plan's buffer lives until
-// pair_ub_release.
-constexpr int kPairLutMax = 32768;  // largest hi_max with a distance-to-bins table in shared memory
-constexpr size_t kPairByTypeMinPairs = 1024;  // (types x bins) from which the by-type kernel is used
-struct PairUbPlan {
-    int n_recs = 0, nb = 0, chunk = 0;
-    int32_t hi_max = 0;
-    int lut_words = 0, hist_words = 0, bit_words = 0;
-    size_t smem = 0;
-    int blocks = 0;
-    void *buf = nullptr;
-    size_t buf_bytes = 0;
-    void *d_recs = nullptr;
-    int64_t *d_ipre = nullptr;
-    int32_t *d_blo = nullptr, *d_bhi = nullptr;
-    uint8_t *d_lut = nullptr;
-};
-size_t pair_ub_table_words(const std::vector<fem_stream *> &recs, int nb, std::vector<int64_t> *ub_off);
-int pair_ub_setup(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const std::vector<int64_t> &ub_off,
-                  const std::vector<int32_t> &blo, const std::vector<int32_t> &bhi, PairUbPlan *plan);
-void pair_ub_release(fem_ctx *ctx, PairUbPlan *plan);
-int pair_ub_launch(cudaStream_t st, const PairUbPlan &plan, uint32_t *ub);
 
 // Scratch slot ids.
 enum Slot : int {

@@ -567,37 +567,21 @@ int MineGroup::gen_level2() {
     int32_t hi_max = 0;
     for (int k = 0; k < nb; ++k) hi_max = std::max(hi_max, bhi[k]);
     std::vector<const uint32_t *> ubp(n_recs);
-    std::vector<int64_t> uo;
-    const size_t ub_words = pair_ub_table_words(recs, nb, &uo);
-    uint32_t *ub_all;
-    FEM_TRY(tmp.get(&ub_all, std::max<size_t>(ub_words, 1)));
-    FEM_CUDA_TRY(cudaMemsetAsync(ub_all, 0, sizeof(uint32_t) * std::max<size_t>(ub_words, 1), st));
-    for (int r = 0; r < n_recs; ++r) ubp[r] = ub_all + uo[r];
-    // one launch over every recording, by end type; the stream-order kernel
-    // where that one's shared memory would not fit
-    PairUbPlan plan;
-    const int pst = pair_ub_setup(ctx, recs, uo, blo, bhi, &plan);
-    if (pst == FEM_OK) {
-        FEM_TRY(pair_ub_launch(st, plan, ub_all));
-        S.kernel_launches++;
-        pair_ub_release(ctx, &plan);  // stream-ordered reuse: safe after the launch is queued
-    } else if (pst == FEM_ERR_INVAL) {
-        pair_ub_release(ctx, &plan);
-        for (int r = 0; r < n_recs; ++r) {
-            const uint32_t nt = recs[r]->n_types;
-            const int words = (int)((nt * (uint32_t)nb + 31) / 32);
-            int threads = std::min(256, (int)(48 * 1024 / (4 * words)) / 32 * 32);
-            threads = std::max(threads, 32);
-            if (recs[r]->n > 0 && (prev.h_off[r + 1] - prev.h_off[r]) >= 2) {
-                const int64_t blocks = std::min<int64_t>((recs[r]->n + threads - 1) / threads, 8 * ctx->n_sm);
-                k_pair_ub<<<(unsigned)blocks, threads, (size_t)threads * words * 4, st>>>(
-                    recs[r]->d_type, recs[r]->d_time, recs[r]->n, nt, d_blo, d_bhi, nb, hi_max, words,
-                    ub_all + uo[r]);
-                S.kernel_launches++;
-            }
+    for (int r = 0; r < n_recs; ++r) {
+        const uint32_t nt = recs[r]->n_types;
+        uint32_t *u;
+        FEM_TRY(tmp.get(&u, (size_t)nt * nt * nb));
+        FEM_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(uint32_t) * (size_t)nt * nt * nb, st));
+        const int words = (int)((nt * (uint32_t)nb + 31) / 32);
+        int threads = std::min(256, (int)(48 * 1024 / (4 * words)) / 32 * 32);
+        threads = std::max(threads, 32);
+        if (recs[r]->n > 0 && (prev.h_off[r + 1] - prev.h_off[r]) >= 2) {
+            const int64_t blocks = std::min<int64_t>((recs[r]->n + threads - 1) / threads, 8 * ctx->n_sm);
+            k_pair_ub<<<(unsigned)blocks, threads, (size_t)threads * words * 4, st>>>(
+                recs[r]->d_type, recs[r]->d_time, recs[r]->n, nt, d_blo, d_bhi, nb, hi_max, words, u);
+            S.kernel_launches++;
         }
-    } else {
-        return pst;
+        ubp[r] = u;
     }
     const uint32_t **d_ubp;
     uint32_t *d_nt;
