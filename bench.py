@@ -498,6 +498,10 @@ def run_case(name: str):
                       many-recordings set (after one warm-up call);
     c3_mid         -- one count of 20k episodes (sizes 2-8) over a 1M-event
                       bursty stream (after one warm-up call);
+    c3_mid_sparse  -- the same count with the per-thread sparse kernel forced
+                      (fem_tuning.kernel = 2);
+    c3_mid_tiled   -- the same count with the tiled TMA / ballot kernel forced
+                      (fem_tuning.kernel = 1);
     c2_mining      -- one default C2 mining pass (after one warm-up call)."""
     import torch
     from paper_0905_2203_gb300 import binding as fb
@@ -517,10 +521,14 @@ def run_case(name: str):
             res = ctx.mine_levelwise(sts, cfg["bins"], [cfg["threshold"]], cfg["max_size"])
             stats = res.stats()
             res.free()
-    elif name == "c3_mid":
+    elif name in ("c3_mid", "c3_mid_sparse", "c3_mid_tiled"):
         s = synth.bursty_60(0xFE0003, 1_000_000)
         offs, ct, lo, hi = synth.random_candidates(0xFE0003, 20000, 60, 2, 8, synth.BINS_4, s.chains, 0.05)
         sts = [ctx.load_stream(s.types, s.times, s.n_types)]
+        if name == "c3_mid_sparse":
+            ctx.set_tuning(kernel=2)
+        elif name == "c3_mid_tiled":
+            ctx.set_tuning(kernel=1)
         for _ in range(2):
             ctx.count_episodes(sts[0], fb.Cands(offs, ct, lo, hi))
         stats = ctx.last_stats()
@@ -738,7 +746,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--quick", action="store_true", help="time the headline step only (for profiling)")
     ap.add_argument("--case", default=None,
-                    help="run one small fixed invocation for profiling (c4_mining, c3_mid, c2_mining)")
+                    help="run one small fixed invocation for profiling (c4_mining, c3_mid, c3_mid_sparse, "
+                         "c3_mid_tiled, c2_mining)")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
