@@ -498,6 +498,8 @@ extern "C" void fem_ctx_destroy(fem_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     graph_cache_clear(ctx);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
     for (auto &kv : ctx->scratch) dev_free(ctx, kv.second.p, kv.second.cap);
     ctx->scratch.clear();
     dev_free(ctx, ctx->d_status, sizeof(int) * 4);

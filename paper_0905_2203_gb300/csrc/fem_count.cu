@@ -1766,6 +1766,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     std::vector<uint32_t> nt_h(n_recs);
     for (int r = 0; r < n_recs; ++r) {
         nt_h[r] = cc.recs[r]->n_types;
+        if (track) continue;  // window densities size rings; local tracking keeps none
         FEM_TRY(stream_densities(ctx, cc.recs[r], lov));
         for (size_t j = 0; j < lov.size(); ++j) {
             uint32_t *d = nullptr;
@@ -1831,7 +1832,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
     pa.rinfo = reinterpret_cast<const RecInfo *>(mb + o_ri);
     pa.n_types = reinterpret_cast<const uint32_t *>(mb + o_nt);
     pa.lo_vals = reinterpret_cast<const int32_t *>(mb + o_lo);
-    pa.n_lo = (int)lov.size();
+    pa.n_lo = track ? 0 : (int)lov.size();  // without tables every ring is taken as unknown
     pa.dens = reinterpret_cast<const uint32_t *const *>(mb + o_dp);
     pa.n_recs = n_recs;
     pa.mode = cc.mode;

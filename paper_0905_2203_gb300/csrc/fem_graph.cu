@@ -582,7 +582,7 @@ __global__ void k_g_ringcheck(const uint16_t *ct, const int32_t *cl, const uint3
         const uint32_t r = crec[i];
         const uint32_t *fq = ri[r].freq;
         for (int k = 0; k < N; ++k) acc += fq[ct[i * N + k]];
-        for (int k = 0; k < N - 1; ++k) {
+        for (int k = 0; k < N - 1 && dens; ++k) {  // no tables: no rings to check
             const int32_t l = cl[i * (N - 1) + k];
             int j = 0;
             while (j < n_lo && lo_vals[j] != l) ++j;
@@ -751,7 +751,16 @@ struct GraphTail {
         cudaStreamSynchronize(ctx->stream);
         for (auto e : ev) cudaEventDestroy(e);
         for (auto &h : held) dev_free(ctx, h.first, h.second);
-        if (h_out) cudaFreeHost(h_out);
+        if (h_out) {
+            // kept by the context for the next graph (the larger buffer wins)
+            if (!ctx->pinned || ctx->pinned_bytes < out_bytes) {
+                if (ctx->pinned) cudaFreeHost(ctx->pinned);
+                ctx->pinned = h_out;
+                ctx->pinned_bytes = out_bytes;
+            } else {
+                cudaFreeHost(h_out);
+            }
+        }
     }
 };
 
@@ -780,15 +789,20 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     FEM_TRY(g->get(&g->sstep, n_recs));
     std::vector<int32_t> pfine_h(n_recs);
     const int64_t sumhi_max = (int64_t)(L - 1) * hi_max;
-    std::vector<const uint32_t *> dens_h((size_t)n_recs * lo_vals.size());
+    // window densities size the rings of the per-episode kernels; local
+    // tracking keeps no rings and does without them
+    const bool need_dens = ctx->tuning.kernel != 0;
+    std::vector<const uint32_t *> dens_h(need_dens ? (size_t)n_recs * lo_vals.size() : 0);
     for (int r = 0; r < n_recs; ++r) {
         fem_stream *s = g->recs[r];
         FEM_TRY(stream_bytype(ctx, s));
-        FEM_TRY(stream_densities(ctx, s, lo_vals));
-        for (size_t j = 0; j < lo_vals.size(); ++j) {
-            uint32_t *d = nullptr;
-            FEM_TRY(stream_density(ctx, s, lo_vals[j], &d));
-            dens_h[(size_t)r * lo_vals.size() + j] = d;
+        if (need_dens) {
+            FEM_TRY(stream_densities(ctx, s, lo_vals));
+            for (size_t j = 0; j < lo_vals.size(); ++j) {
+                uint32_t *d = nullptr;
+                FEM_TRY(stream_density(ctx, s, lo_vals[j], &d));
+                dens_h[(size_t)r * lo_vals.size() + j] = d;
+            }
         }
         // finest segments: at least 256 events and twice the halo (sum of
         // the upper bounds, in events at the recording's mean rate)
@@ -833,7 +847,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     // graph does not apply when that exceeds kRingCap or what the deepest
     // level's shared memory holds (such streams mine on the host-driven path)
     uint32_t dmax = 1;
-    for (int r = 0; r < n_recs; ++r) {
+    for (int r = 0; r < n_recs && need_dens; ++r) {
         std::vector<uint32_t> hd(g->recs[r]->n_types);
         for (size_t j = 0; j < lo_vals.size(); ++j) {
             FEM_CUDA_TRY(cudaMemcpyAsync(hd.data(), dens_h[(size_t)r * lo_vals.size() + j], 4 * hd.size(),
@@ -1003,7 +1017,15 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             lay.o_lvl[N] = take(tb + 2 * eb + 8 * fc);
         }
         g->out_bytes = (size_t)o;
-        if (cudaHostAlloc(reinterpret_cast<void **>(&g->h_out), g->out_bytes, cudaHostAllocMapped) != cudaSuccess) {
+        // the mapped result buffer of an earlier graph of the context, when
+        // large enough (pinning a large buffer costs more than a launch)
+        if (ctx->pinned && ctx->pinned_bytes >= g->out_bytes) {
+            g->h_out = static_cast<char *>(ctx->pinned);
+            g->out_bytes = ctx->pinned_bytes;
+            ctx->pinned = nullptr;
+            ctx->pinned_bytes = 0;
+        } else if (cudaHostAlloc(reinterpret_cast<void **>(&g->h_out), g->out_bytes, cudaHostAllocMapped) !=
+                   cudaSuccess) {
             cudaGetLastError();
             g->h_out = nullptr;
             return FEM_ERR_NOMEM;
@@ -1109,7 +1131,8 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         if (bounded && cst == FEM_OK)
             cst = coarse_graph_level(st, ctx->n_sm, N, ct, cl, ch, crec, cn, cap, g->d_cdesc, g->coarse_slices,
                                      g->d_thr, g->coarse_min, g->cub, g->skip);
-        k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, d_dens, d_lov, (int)lo_vals.size(), g->ring_cap, d_ri,
+        k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, need_dens ? d_dens : nullptr, d_lov,
+                                          (int)lo_vals.size(), g->ring_cap, d_ri,
                                           cn, g->rel + N, n_recs, g->segf, g->pfine, g->sstep, g->segl);
         // external event nodes: their timestamps time the count kernels of
         // this level on every launch of the graph

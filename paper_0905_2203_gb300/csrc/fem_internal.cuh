@@ -183,6 +183,8 @@ struct fem_ctx {
     std::multimap<size_t, void *> cached;
     size_t cached_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    void *pinned = nullptr;       // mapped host buffer of a destroyed mining graph, for the next one
+    size_t pinned_bytes = 0;
 };
 
 // Coarse-tick tables of a stream for one tick width w (fem_bound.cu):
