@@ -135,6 +135,13 @@ typedef struct {
                              kernel first waits (with the default limit) for
                              its copies in flight, so the context stays
                              usable */
+    int track_last;       /* last node of the warp-per-item local tracking
+                             kernel: 0 = per (episode, segment), driven by
+                             node N-1's events or, when they outnumber node
+                             N-2's entries more than twice, by those entries
+                             (one search per entry for the first end it can
+                             serve); 1 = always by events; 2 = always by
+                             entries */
 } fem_tuning;
 
 /* Per-call statistics filled by the counting / mining calls. */

@@ -51,7 +51,7 @@ class fem_cands(ctypes.Structure):
 class fem_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_cta", I32), ("segments", I32), ("tile_events", I32), ("prepass", I32),
                 ("plain_path", I32), ("autotune", I32), ("kernel", I32), ("level_graph", I32),
-                ("wait_polls", I32)]
+                ("wait_polls", I32), ("track_last", I32)]
 
 
 class fem_stats(ctypes.Structure):
@@ -195,9 +195,9 @@ class Context:
             pass
 
     def set_tuning(self, lanes_per_cta=0, segments=0, tile_events=0, prepass=0, plain_path=0, autotune=0,
-                   kernel=0, level_graph=0, wait_polls=0):
+                   kernel=0, level_graph=0, wait_polls=0, track_last=0):
         t = fem_tuning(lanes_per_cta, segments, tile_events, prepass, plain_path, autotune, kernel, level_graph,
-                       wait_polls)
+                       wait_polls, track_last)
         check(fem_ctx_set_tuning(self.h, ctypes.byref(t)), "fem_ctx_set_tuning")
 
     def reset_tuning(self):

@@ -2072,6 +2072,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
             ta.cap = cap;
             ta.rec = rec_base;
             ta.counts = limit > 0 ? nullptr : cc.counts;  // unsegmented episodes: counts written directly
+            ta.last_mode = ctx->tuning.track_last;
             FEM_TRY(launch_track(ctx->stream, blocks, ta));
             cc.stats.kernel_launches += 2;  // queue reset + kernel
             return FEM_OK;

@@ -1152,6 +1152,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             ta.cap = g->track_cap;
             ta.rec = rec;
             ta.counts = counts;  // unsegmented recordings: counts written directly
+            ta.last_mode = ctx->tuning.track_last;
             TrackGroupIn gi{};
             gi.slot2cand = iota;
             gi.d_n_slots = cn;
@@ -1230,12 +1231,12 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
 
 static std::string graph_key(const std::vector<fem_stream *> &recs, const std::vector<int32_t> &blo,
                              const std::vector<int32_t> &bhi, const std::vector<uint32_t> &thr, int max_size,
-                             int first, bool prepass, int coarse, int kernel) {
+                             int first, bool prepass, int coarse, int kernel, int track_last) {
     std::ostringstream k;
     for (auto *s : recs) k << (const void *)s << ':' << s->n << ';';
     for (size_t i = 0; i < blo.size(); ++i) k << blo[i] << ',' << bhi[i] << ';';
     for (auto t : thr) k << t << ';';
-    k << max_size << '/' << first << '/' << (prepass ? 1 : 0) << '/' << coarse << '/' << kernel;
+    k << max_size << '/' << first << '/' << (prepass ? 1 : 0) << '/' << coarse << '/' << kernel << '/' << track_last;
     return k.str();
 }
 
@@ -1282,7 +1283,8 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
         if (s->n_types > 8192 || s->n > INT32_MAX / 2) return FEM_OK;
     // coarse-tick bound of levels >= 3: only with prepass = 1
     const int coarse = ctx->tuning.prepass == 1 ? 1 : 0;
-    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass, coarse, ctx->tuning.kernel);
+    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass, coarse, ctx->tuning.kernel,
+                                        ctx->tuning.track_last);
     int64_t cap = 4096;
     auto hint = ctx->graph_cap.find(key);
     const int64_t want = std::max<int64_t>(cap_min, hint != ctx->graph_cap.end() ? hint->second : 0);

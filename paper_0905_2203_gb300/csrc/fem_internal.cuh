@@ -75,6 +75,7 @@ constexpr int kTrackWarps = 8;           // warps per block
 constexpr int kTrackMaxBlocksPerSm = 6;  // resident blocks per SM the grid asks for (40 registers)
 constexpr int kTrackGroupMax = 64;       // episodes per prefix group (a new group every 64 slots)
 constexpr int kTrackMinSeg = 8192;       // shortest segment (events) of a local-tracking item
+constexpr int kTrackEntryRatio = 2;      // last node by entries when events > this x entries
 struct TrackArgs {
     const RecInfo *rinfo;
     int n_recs;
@@ -103,6 +104,7 @@ struct TrackArgs {
     const int32_t *gfirst;
     const int64_t *ibase;
     const int32_t *rorder;
+    int last_mode;               // last node: 0 by the shorter side, 1 by events, 2 by entries
 };
 // Inputs of track_groups: the slots (slot2cand, live count on the device or
 // n_slots_cap), the candidate CSR, per-candidate recordings, the launch's

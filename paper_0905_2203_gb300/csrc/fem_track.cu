@@ -63,37 +63,70 @@ __device__ __forceinline__ int64_t warp_lower_bound(const int32_t *__restrict__ 
     return lo + __popc(__ballot_sync(kFull, below));
 }
 
-// Number of the 32 values held one per lane (ascending with the lane) that
-// are below q, for this lane's own q.
-__device__ __forceinline__ int window_rank(int32_t vt, int64_t q) {
-    int c = 0;
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const int32_t v = __shfl_sync(kFull, vt, c + s - 1);
-        if ((int64_t)v < q) c += s;
+// Algorithm 1 over one chunk's valid ends (lane order = time order): the
+// steady state jumps from selection to selection, otherwise every end goes
+// through every entry class.
+__device__ __forceinline__ void greedy_chunk(unsigned bm, int32_t t, int32_t Lv, Machine<2, 0> &st, int32_t Tp,
+                                             int lane) {
+    if (bm && !st.open && st.live == 1u) {
+        // the next selection is the first later end whose latest start is
+        // after the last selected end
+        int32_t prev = st.cprev[0];
+        uint32_t added = 0;
+        for (;;) {
+            const unsigned sel = __ballot_sync(kFull, ((bm >> lane) & 1u) && Lv > prev);
+            if (!sel) break;
+            const int b = __ffs(sel) - 1;
+            prev = __shfl_sync(kFull, t, b);
+            ++added;
+            bm &= (b == 31) ? 0u : ~((2u << b) - 1u);
+        }
+        st.ccnt[0] += added;
+        st.cprev[0] = prev;
+    } else {
+        while (bm) {
+            const int b = __ffs(bm) - 1;
+            bm &= bm - 1;
+            st.greedy_end(__shfl_sync(kFull, t, b), __shfl_sync(kFull, Lv, b), Tp);
+        }
     }
-    const int32_t v31 = __shfl_sync(kFull, vt, 31);
-    if (c == 31 && (int64_t)v31 < q) c = 32;
-    return c;
 }
 
-// One node step for one warp: node k's events ttime[cb, ce) (time order)
-// against node k-1's entries pT/pL[0, m) (pL null: node 0, whose latest start
-// is its time).  An event is valid when the newest entry older than t - lo
-// exists and is not older than t - hi; its latest start is that entry's.
-// Not LAST: the valid events are appended to oT/oL and their number is
-// returned.  LAST: the valid events at or after Tp are passed, in time
-// order, to Algorithm 1 of every entry class in st.
+// Entries of node k-1 as one step sees them: node 0's are its type's event
+// times (latest start = time); later nodes' are (time, latest start) pairs
+// in the warp's buffer, so one 8-byte load brings both.
+template <bool HASL>
+struct Entries;
+template <>
+struct Entries<false> {
+    const int32_t *__restrict__ t;
+    __device__ __forceinline__ int2 get(int i) const {
+        const int32_t v = t[i];
+        return make_int2(v, v);
+    }
+};
+template <>
+struct Entries<true> {
+    const int2 *__restrict__ e;
+    __device__ __forceinline__ int2 get(int i) const { return e[i]; }
+};
+
+// One node step for one warp: node k's events ev[0, n_ev) (time order)
+// against node k-1's entries p[0, m).  An event is valid when the newest
+// entry older than t - lo exists and is not older than t - hi; its latest
+// start is that entry's.  Not LAST: the valid events are appended to out as
+// (t, L) and their number is returned.  LAST: the valid events at or after
+// Tp are passed, in time order, to Algorithm 1 of every entry class in st.
 //
 // Each chunk of 32 events ranks its queries in windows of 32 entries that
 // start one entry before the previous chunk's last rank and move on by 31:
 // the first entry of every window is older than every query still looking,
 // so a lane's predecessor is always in the window where its rank falls and
-// is read from the window's registers by a shuffle.
-template <bool LAST>
-__device__ __forceinline__ int node_step(const int32_t *__restrict__ ev, int n_ev, const int32_t *__restrict__ pT,
-                                         const int32_t *__restrict__ pL, int m, int32_t lo_e, int32_t hi_e,
-                                         int32_t *__restrict__ oT, int32_t *__restrict__ oL, Machine<2, 0> &st,
+// its time and latest start are read from the window's registers by a
+// shuffle.
+template <bool LAST, bool HASL>
+__device__ __forceinline__ int node_step(const int32_t *__restrict__ ev, int n_ev, Entries<HASL> p, int m,
+                                         int32_t lo_e, int32_t hi_e, int2 *__restrict__ out, Machine<2, 0> &st,
                                          int32_t Tp, int lane) {
     // All positions fit 32 bits: a recording has fewer than 2^30 events.
     // Times are >= 0 and 0 <= lo < hi, so t - lo and t - hi stay in int32.
@@ -108,72 +141,138 @@ __device__ __forceinline__ int node_step(const int32_t *__restrict__ ev, int n_e
         const int32_t q0 = __shfl_sync(kFull, q, 0);
         int ws = w > 0 ? w - 1 : 0;
         int idx = 0;
-        int32_t aT = INT32_MIN;
+        int32_t aT = INT32_MIN, aL = 0;
         bool done = !in;
         for (;;) {
             const int wi = ws + lane;
-            const int32_t vt = wi < m ? pT[wi] : INT32_MAX;
-            const int32_t top = __shfl_sync(kFull, vt, 31);
+            const int2 v = wi < m ? p.get(wi) : make_int2(INT32_MAX, 0);
+            const int32_t top = __shfl_sync(kFull, v.x, 31);
             if (top < q0 && ws + 32 < m) {  // the whole window precedes every query
                 ws += 31;
                 continue;
             }
-            // rank of q among the window's values (ascending across lanes)
+            // rank of q among the window's times (ascending across lanes)
             int c = 0;
 #pragma unroll
             for (int s = 16; s >= 1; s >>= 1)
-                if (__shfl_sync(kFull, vt, c + s - 1) < q) c += s;
+                if (__shfl_sync(kFull, v.x, c + s - 1) < q) c += s;
             if (c == 31 && top < q) c = 32;
-            const int32_t xt = __shfl_sync(kFull, vt, c > 0 ? c - 1 : 0);
+            const int src = c > 0 ? c - 1 : 0;
+            const int32_t xt = __shfl_sync(kFull, v.x, src);
+            const int32_t xl = HASL ? __shfl_sync(kFull, v.y, src) : xt;
             if (!done && c < 32) {
                 idx = ws + c;
                 aT = c > 0 ? xt : INT32_MIN;
+                aL = xl;
                 done = true;
             }
             if (__all_sync(kFull, done)) break;
             ws += 31;
         }
         const bool ok = in && aT != INT32_MIN && aT >= t - hi_e;
-        const int32_t Lv = ok ? (pL ? pL[idx - 1] : aT) : 0;
+        const int32_t Lv = ok ? aL : 0;
         if (!LAST) {
             const unsigned bm = __ballot_sync(kFull, ok);
-            if (ok) {
-                const int r = __popc(bm & ((1u << lane) - 1u));
-                oT[wc + r] = t;
-                oL[wc + r] = Lv;
-            }
+            if (ok) out[wc + __popc(bm & ((1u << lane) - 1u))] = make_int2(t, Lv);
             wc += __popc(bm);
         } else {
-            unsigned bm = __ballot_sync(kFull, ok && t >= Tp);
-            if (bm && !st.open && st.live == 1u) {
-                // steady state (one class): jump from selection to
-                // selection -- the next one is the first later end whose
-                // latest start is after the last selected end
-                int32_t prev = st.cprev[0];
-                uint32_t added = 0;
-                for (;;) {
-                    const unsigned sel = __ballot_sync(kFull, ((bm >> lane) & 1u) && Lv > prev);
-                    if (!sel) break;
-                    const int b = __ffs(sel) - 1;
-                    prev = __shfl_sync(kFull, t, b);
-                    ++added;
-                    bm &= (b == 31) ? 0u : ~((2u << b) - 1u);
-                }
-                st.ccnt[0] += added;
-                st.cprev[0] = prev;
-            } else {
-                while (bm) {
-                    const int b = __ffs(bm) - 1;
-                    bm &= bm - 1;
-                    st.greedy_end(__shfl_sync(kFull, t, b), __shfl_sync(kFull, Lv, b), Tp);
-                }
-            }
+            greedy_chunk(__ballot_sync(kFull, ok && t >= Tp), t, Lv, st, Tp, lane);
         }
         // the next 32 queries rank at or after this chunk's last one
         w = __shfl_sync(kFull, idx, 31);
     }
     __syncwarp();
     return wc;
+}
+
+// The last node step driven by node N-2's entries instead of node N-1's
+// events, for entry lists much shorter than the last node's event list.
+//
+// An end t of node N-1 takes the newest entry i with T_i < t - lo, so the
+// ends served by entry i are those in (T_i + lo, T_{i+1} + lo]; they all
+// carry L_i and are valid while t <= T_i + hi.  Within that interval only
+// the first end (at or after Tp) can matter to Algorithm 1: L_i <= T_i < t,
+// so once it has been offered every entry class has its last selection at or
+// above L_i (it selected this end, or it could not), the largest latest start
+// seen is at least L_i, and a later end with the same L_i changes no class.
+// So per entry one search finds the first event at or after
+// max(T_i + lo + 1, Tp), and the end is offered when it lies in the entry's
+// interval and within its upper bound.
+//
+// The warp takes the entries 32 at a time (the next chunk's loaded ahead).
+// Their queries ascend with the lane, so each chunk searches forward from
+// the previous chunk's last answer: one load of 32 probes sb events apart
+// (sb a power of two near the mean number of events per entry) ranks every
+// lane's query into a bucket of sb events by a 5-step search over the lanes'
+// registers, and a binary search of log2(sb) loads inside the bucket ends
+// it.  A lane whose query is beyond all 32 probes waits for the next 32 * sb
+// events.
+template <bool HASL>
+__device__ __forceinline__ void last_by_entries(const int32_t *__restrict__ ev, int n_ev, Entries<HASL> p, int m,
+                                                int32_t lo_e, int32_t hi_e, Machine<2, 0> &st, int32_t Tp,
+                                                int lane) {
+    // Times are >= 0 and 0 <= lo < hi < 2^31, so every bound below fits an
+    // unsigned 32-bit word except T_{i+1} + lo for a missing next entry.
+    const uint32_t lo = (uint32_t)lo_e, hi = (uint32_t)hi_e, tp = (uint32_t)Tp;
+    const int ratio = n_ev / (m > 0 ? m : 1);
+    const int lg = ratio > 1 ? 32 - __clz(ratio - 1) : 0;
+    const int sb = 1 << (lg < 16 ? lg : 16);
+    int cur = 0;  // events below every remaining query
+    int2 E_next = lane < m ? p.get(lane) : make_int2(-1, 0);
+    for (int base = 0; base < m; base += 32) {
+        const bool in = base + lane < m;
+        const int2 E = E_next;
+        const bool more = base + 32 < m;
+        if (more) E_next = (base + 32 + lane < m) ? p.get(base + 32 + lane) : make_int2(-1, 0);
+        const uint32_t T = (uint32_t)E.x;
+        // the next entry's time (none: the interval is open above)
+        uint32_t Tn = __shfl_down_sync(kFull, T, 1);
+        const uint32_t Tn0 = __shfl_sync(kFull, (uint32_t)E_next.x, 0);
+        if (lane == 31) Tn = Tn0;
+        const bool has_next = base + lane + 1 < m;
+        uint32_t q = T + lo + 1u;
+        if (q < tp) q = tp;
+        int idx = n_ev;
+        uint32_t e = 0xFFFFFFFFu;  // the event at idx (none past n_ev)
+        bool done = !in;
+        int c0 = cur;
+        for (;;) {
+            const int pp = c0 + sb * (lane + 1) - 1;
+            const uint32_t pv = pp < n_ev ? (uint32_t)ev[pp] : 0xFFFFFFFFu;
+            int c = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1)
+                if (__shfl_sync(kFull, pv, c + s - 1) < q) c += s;
+            const uint32_t top = __shfl_sync(kFull, pv, 31);
+            if (c == 31 && top < q) c = 32;
+            const uint32_t pc = __shfl_sync(kFull, pv, c < 32 ? c : 31);
+            if (!done && c < 32) {
+                // the first event >= q lies in [c0 + sb*c, c0 + sb*(c+1)),
+                // whose last position holds pc >= q (past n_ev: none)
+                int pos = c0 + sb * c;
+                uint32_t val = pc;
+                for (int h = sb >> 1; h >= 1; h >>= 1) {
+                    const int pq = pos + h - 1;
+                    const uint32_t x = pq < n_ev ? (uint32_t)ev[pq] : 0xFFFFFFFFu;
+                    if (x < q)
+                        pos += h;
+                    else
+                        val = x;
+                }
+                idx = pos;
+                e = val;
+                done = true;
+            }
+            if (__all_sync(kFull, done)) break;
+            c0 += 32 * sb;
+        }
+        const bool ok = in && idx < n_ev && e <= T + hi && (!has_next || e <= Tn + lo);
+        greedy_chunk(__ballot_sync(kFull, ok), (int32_t)e, ok ? E.y : 0, st, Tp, lane);
+        // the next chunk's queries are at or above this chunk's last one
+        const int last = __shfl_sync(kFull, idx, 31);
+        cur = last < n_ev ? last : n_ev;
+    }
+    __syncwarp();
 }
 
 __device__ __forceinline__ void machine_init(Machine<2, 0> &st, int N) {
@@ -198,10 +297,9 @@ __device__ __forceinline__ void machine_init(Machine<2, 0> &st, int N) {
 __global__ void __launch_bounds__(kTrackWarps * 32, 6) k_count_track(TrackArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int32_t *const bT0 = a.buf + gw * 4 * a.cap;
-    int32_t *const bL0 = bT0 + a.cap;
-    int32_t *const bT1 = bT0 + 2 * a.cap;
-    int32_t *const bL1 = bT0 + 3 * a.cap;
+    // two entry lists of (time, latest start) pairs, ping-pong
+    int2 *const b0 = reinterpret_cast<int2 *>(a.buf + gw * 4 * a.cap);
+    int2 *const b1 = b0 + a.cap;
     const int64_t n_items = a.d_n_items ? *a.d_n_items : a.n_items;
     for (;;) {
         unsigned long long it = 0;
@@ -283,25 +381,27 @@ __global__ void __launch_bounds__(kTrackWarps * 32, 6) k_count_track(TrackArgs a
                 e = (seg_e < ri.n) ? warp_lower_bound(ttime, b, b1, Tend, lane) : b1;
             }
         };
-        // shared prefix: node 0, then nodes 1..N-2 (entry lists ping-pong)
-        const int32_t *pT = nullptr;
-        const int32_t *pL = nullptr;
+        // shared prefix: node 0 (its type's times), then nodes 1..N-2
+        // (entry lists in the warp's buffer)
+        Entries<false> p0{nullptr};
+        Entries<true> pe{nullptr};
         int m = 0;
         Machine<2, 0> st;
         if (live) {
-            int64_t pb = 0, pe = 0;
-            range(a.ctypes[o0], pb, pe);
-            pT = ttime + pb;
-            m = (int)(pe - pb);
+            int64_t b = 0, e = 0;
+            range(a.ctypes[o0], b, e);
+            p0.t = ttime + b;
+            m = (int)(e - b);
             for (int k = 1; k < N - 1 && m > 0; ++k) {
                 int64_t cb = 0, ce = 0;
                 range(a.ctypes[o0 + k], cb, ce);
-                int32_t *oT = (k & 1) ? bT1 : bT0;
-                int32_t *oL = (k & 1) ? bL1 : bL0;
-                m = node_step<false>(ttime + cb, (int)(ce - cb), pT, pL, m, a.relaxed ? 0 : a.clo[eo0 + k - 1],
-                                     a.chi[eo0 + k - 1], oT, oL, st, 0, lane);
-                pT = oT;
-                pL = oL;
+                int2 *out = (k & 1) ? b1 : b0;
+                const int32_t lo_k = a.relaxed ? 0 : a.clo[eo0 + k - 1], hi_k = a.chi[eo0 + k - 1];
+                if (k == 1)
+                    m = node_step<false>(ttime + cb, (int)(ce - cb), p0, m, lo_k, hi_k, out, st, 0, lane);
+                else
+                    m = node_step<false>(ttime + cb, (int)(ce - cb), pe, m, lo_k, hi_k, out, st, 0, lane);
+                pe.e = out;
             }
         }
         // last node of every episode of the item
@@ -317,8 +417,23 @@ __global__ void __launch_bounds__(kTrackWarps * 32, 6) k_count_track(TrackArgs a
                 const int64_t oc = a.offs[c], ec = oc - c;
                 int64_t cb = 0, ce = 0;
                 range(a.ctypes[oc + N - 1], cb, ce);
-                node_step<true>(ttime + cb, (int)(ce - cb), pT, pL, m, a.relaxed ? 0 : a.clo[ec + N - 2],
-                                a.chi[ec + N - 2], nullptr, nullptr, st, Tp, lane);
+                const int n_ev = (int)(ce - cb);
+                const int32_t lo_l = a.relaxed ? 0 : a.clo[ec + N - 2], hi_l = a.chi[ec + N - 2];
+                // entries well short of the events: search per entry
+                const bool by_entries =
+                    a.last_mode == 2 || (a.last_mode == 0 && (int64_t)m * kTrackEntryRatio < (int64_t)n_ev);
+                const int32_t *evl = ttime + cb;
+                if (N == 2) {
+                    if (by_entries)
+                        last_by_entries(evl, n_ev, p0, m, lo_l, hi_l, st, Tp, lane);
+                    else
+                        node_step<true>(evl, n_ev, p0, m, lo_l, hi_l, nullptr, st, Tp, lane);
+                } else {
+                    if (by_entries)
+                        last_by_entries(evl, n_ev, pe, m, lo_l, hi_l, st, Tp, lane);
+                    else
+                        node_step<true>(evl, n_ev, pe, m, lo_l, hi_l, nullptr, st, Tp, lane);
+                }
             }
             st.finish();
             if (lane == 0) {

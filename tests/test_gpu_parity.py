@@ -160,6 +160,71 @@ def test_few_episodes_many_segments(fb, ctx, segments, kernel):
     st.free()
 
 
+@pytest.mark.parametrize("track_last", [1, 2])
+@pytest.mark.parametrize("kernel,segments", [(0, 0), (7, 0), (0, 7), (7, 300)])
+def test_track_last_node_by_events_and_by_entries(fb, ctx, kernel, segments, track_last):
+    """The warp-per-item kernel's last node driven by the last node's events
+    (1) or by the entries of the node before it (2), on tiny streams with
+    many equal times, a bursty stream with the 4-bin set, and the mid stream
+    cut into segments (entries whose interval starts before the segment)."""
+    ctx.set_tuning(kernel=kernel, segments=segments, track_last=track_last)
+    try:
+        r = synth.Rng(77, segments + 3)
+        for trial in range(4):
+            n_types = int(r.integers(2, 7, 1)[0])
+            n = int(r.integers(50, 5000, 1)[0])
+            ty, tm = synth.tiny_random_stream(2000 + trial, n, n_types, int(r.integers(n // 3 + 5, 3 * n, 1)[0]))
+            nc = 500
+            sizes = r.integers(2, 6, nc)
+            offs = np.zeros(nc + 1, np.int64)
+            offs[1:] = np.cumsum(sizes)
+            ct = r.integers(0, n_types - 1, int(offs[-1])).astype(np.uint16)
+            ne = int(offs[-1]) - nc
+            lo = r.integers(0, 6, ne).astype(np.int32)
+            hi = (lo + r.integers(1, 12, ne)).astype(np.int32)
+            st = ctx.load_stream(ty, tm, n_types)
+            got = gpu_counts(fb, ctx, st, offs, ct, lo, hi)
+            want = oracle_counts(ty, tm, offs, ct, lo, hi)
+            bad = np.nonzero(got != want)[0]
+            assert bad.size == 0, (trial, bad[:5], got[bad[:5]], want[bad[:5]])
+            st.free()
+        s = synth.bursty_60(0xFE0007, 120_000)
+        st = ctx.load_stream(s.types, s.times, s.n_types)
+        offs, ct, lo, hi = synth.random_candidates(0xFE0007, 1500, 60, 2, 6, synth.BINS_4, s.chains, 0.1)
+        want = oracle_counts(s.types, s.times, offs, ct, lo, hi)
+        assert np.array_equal(gpu_counts(fb, ctx, st, offs, ct, lo, hi), want)
+        assert want.max() > 0
+        st.free()
+        s, cfg = synth.c2_mid()
+        st = ctx.load_stream(s.types, s.times, s.n_types)
+        offs, ct, lo, hi = synth.random_candidates(0xFE0108, 64, s.n_types, 2, 5, cfg["bins"], s.chains, 0.5)
+        want = oracle_counts(s.types, s.times, offs, ct, lo, hi)
+        assert np.array_equal(gpu_counts(fb, ctx, st, offs, ct, lo, hi), want)
+        st.free()
+    finally:
+        ctx.reset_tuning()
+
+
+def test_mining_graph_last_node_by_entries(fb, ctx):
+    """The whole-pass mining graph with the last node forced to each side
+    gives the oracle miner's levels."""
+    s, cfg = synth.c2_mid()
+    st = ctx.load_stream(s.types, s.times, s.n_types)
+    want = oracle.mine_levelwise(s.types, s.times, s.n_types, cfg["bins"], cfg["threshold"], 4)
+    for mode in (1, 2):
+        ctx.set_tuning(track_last=mode)
+        try:
+            res = ctx.mine_levelwise([st], cfg["bins"], [cfg["threshold"]], 4)
+            assert res.stats()["graph_tails"] == 1
+            for N in range(1, 5):
+                eps, counts = res.level(0, N)
+                assert list(zip(eps, counts)) == want[N], (mode, N)
+            res.free()
+        finally:
+            ctx.reset_tuning()
+    st.free()
+
+
 def test_c1_random_candidates(fb, ctx):
     s, _ = synth.c1_tiny()
     st = ctx.load_stream(s.types, s.times, s.n_types)
