@@ -514,6 +514,17 @@ def run_case(name: str):
             res = ctx.mine_levelwise(sts, recs[0][1]["bins"], [c["threshold"] for _, c in recs], 6)
             stats = res.stats()
             res.free()
+    elif name == "c4_mid_mining":
+        # the 12 recordings of 200k-600k events: the level structure of the
+        # whole set at a device footprint small enough for a full profile
+        ns = synth.c4_lengths()
+        pick = [int(i) for i in np.nonzero((ns >= 200_000) & (ns <= 600_000))[0][:12]]
+        recs = synth.c4_recordings(which=pick)
+        sts = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
+        for _ in range(2):
+            res = ctx.mine_levelwise(sts, recs[0][1]["bins"], [c["threshold"] for _, c in recs], 6)
+            stats = res.stats()
+            res.free()
     elif name == "c2_mining":
         s, cfg = synth.c2_mid()
         sts = [ctx.load_stream(s.types, s.times, s.n_types)]
@@ -746,7 +757,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--quick", action="store_true", help="time the headline step only (for profiling)")
     ap.add_argument("--case", default=None,
-                    help="run one small fixed invocation for profiling (c4_mining, c3_mid, c3_mid_sparse, "
+                    help="run one small fixed invocation for profiling (c4_mining, c4_mid_mining, c3_mid, c3_mid_sparse, "
                          "c3_mid_tiled, c2_mining)")
     args = ap.parse_args()
     if args.case:

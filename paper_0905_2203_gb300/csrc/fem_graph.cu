@@ -401,8 +401,17 @@ __global__ void k_g_level_index(const int32_t *ctr, int N, int64_t cap, int64_t 
 // its recordings finely and one with many coarsely: recording r gets P_r
 // segments, every sstep[r]-th of its pfine[r] finest ones.  Also the
 // per-recording candidate offsets and the RecInfo fields that depend on them.
+//
+// With prefix groups (gmax set: recording r's largest group of episodes
+// that one work item counts together), an item is a whole group over one
+// segment, so the work of the largest item grows with the group: such a
+// recording is cut gmax[r] x 4 times finer (the 4 allows for the spread of
+// per-event cost between groups), so that the largest item stays near the
+// mean work of an item rather than far above the mean work per warp.  The
+// factor is halved until the (candidate, segment) records fit cap_threads.
 __device__ void level_info(const uint32_t *crec, int64_t C, int n_recs, int64_t *coff, RecInfo *ri,
-                           int64_t *nthreads, const int32_t *pfine, int32_t *sstep, int64_t target, int *maxP) {
+                           int64_t *nthreads, const int32_t *pfine, int32_t *sstep, int64_t target, int *maxP,
+                           const int32_t *gmax = nullptr, int64_t cap_threads = INT64_MAX) {
     for (int r = threadIdx.x; r <= n_recs; r += blockDim.x) {
         int64_t lo = 0, hi = C;  // first candidate of recording >= r
         while (lo < hi) {
@@ -416,11 +425,27 @@ __device__ void level_info(const uint32_t *crec, int64_t C, int n_recs, int64_t 
         double W = 0;  // episode-events of the level
         for (int r = 0; r < n_recs; ++r) W += (double)(coff[r + 1] - coff[r]) * (double)ri[r].n;
         const double seg_len = fmax(1.0, W / (double)target);
+        // finer cuts for grouped recordings while the records fit (the
+        // plain rule, scale 0, fits by construction: at most target + C)
+        double scale = gmax ? 4.0 : 0.0;
+        for (;;) {
+            int64_t tot = 0;
+            for (int r = 0; r < n_recs; ++r) {
+                const double g = scale > 0.0 ? fmax(1.0, scale * (double)gmax[r]) : 1.0;
+                const int pf = pfine[r];
+                const double want = fmin((double)pf, fmax(1.0, ceil(g * (double)ri[r].n / seg_len)));
+                const int st = (pf + (int)want - 1) / (int)want;
+                tot += (coff[r + 1] - coff[r]) * (int64_t)((pf + st - 1) / st);
+            }
+            if (tot <= cap_threads || scale == 0.0) break;
+            scale = scale > 1.0 / 64 ? scale * 0.5 : 0.0;
+        }
         int64_t base = 0;
         int pmax = 1;
         for (int r = 0; r < n_recs; ++r) {
+            const double g = scale > 0.0 ? fmax(1.0, scale * (double)gmax[r]) : 1.0;
             const int pf = pfine[r];
-            const double want = fmin((double)pf, fmax(1.0, ceil((double)ri[r].n / seg_len)));
+            const double want = fmin((double)pf, fmax(1.0, ceil(g * (double)ri[r].n / seg_len)));
             const int st = (pf + (int)want - 1) / (int)want;
             const int P = (pf + st - 1) / st;
             sstep[r] = st;
@@ -439,13 +464,14 @@ __device__ void level_info(const uint32_t *crec, int64_t C, int n_recs, int64_t 
 
 __global__ void k_g_levelinfo(const uint32_t *crec, const int32_t *ctr, int N, int64_t cap, int64_t *offs,
                               int32_t *iota, int n_recs, int64_t *coff, RecInfo *ri, int64_t *nthreads,
-                              const int32_t *pfine, int32_t *sstep, int64_t target, int *maxP) {
+                              const int32_t *pfine, int32_t *sstep, int64_t target, int *maxP, const int32_t *gmax,
+                              int64_t cap_threads) {
     const int64_t C = ctr[0];
     (void)offs;
     (void)iota;
     (void)N;
     (void)cap;
-    level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target, maxP);
+    level_info(crec, C, n_recs, coff, ri, nthreads, pfine, sstep, target, maxP, gmax, cap_threads);
 }
 
 // Level N = M + 1 in one block: zero the level's counters, check every
@@ -723,6 +749,7 @@ struct GraphTail {
     int32_t *tbuf = nullptr;
     int64_t *tqueue = nullptr;
     int32_t *tg_gidx = nullptr, *tg_gstart = nullptr, *tg_gfirst = nullptr, *tg_stmp = nullptr;
+    int32_t *tg_gmax = nullptr;            // per recording: the level's largest prefix group
     int64_t *tg_ibase = nullptr, *tg_nitems = nullptr;
     int32_t *rorder = nullptr;             // recordings, longest first (item order)
     int *d_maxP = nullptr;                 // the current level's largest segment count
@@ -924,6 +951,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_TRY(g->get(&g->tqueue, 1));
         FEM_TRY(g->get(&g->tg_gidx, cap + 2));
         FEM_TRY(g->get(&g->tg_gstart, cap + 2));
+        FEM_TRY(g->get(&g->tg_gmax, std::max(n_recs, 1)));
         FEM_TRY(g->get(&g->tg_gfirst, n_recs));
         FEM_TRY(g->get(&g->tg_stmp, (cap + 2) / 1024 + 2));
         FEM_TRY(g->get(&g->tg_ibase, n_recs + 1));
@@ -1076,6 +1104,30 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         int64_t *coffN = g->coff + (size_t)N * (n_recs + 1);
         FLevel &nf = g->F[N];
         const bool fuse_join = fused && N >= 3;
+        // the level's slots as the local-tracking group kernels see them
+        auto group_in = [&]() {
+            TrackGroupIn gi{};
+            gi.slot2cand = iota;
+            gi.d_n_slots = cn;
+            gi.n_slots_cap = cap;
+            gi.offs = offs;
+            gi.ctypes = ct;
+            gi.clo = cl;
+            gi.chi = ch;
+            gi.cand_rec = crec;
+            gi.rinfo = d_ri;
+            gi.n_recs = n_recs;
+            gi.gidx = g->tg_gidx;
+            gi.scan_tmp = g->tg_stmp;
+            gi.gstart = g->tg_gstart;
+            gi.gfirst = g->tg_gfirst;
+            gi.ibase = g->tg_ibase;
+            gi.n_items = g->tg_nitems;
+            gi.rorder = g->rorder;
+            gi.gmax = g->tg_gmax;
+            return gi;
+        };
+        bool groups_ready = false;
         if (!fuse_join) {
             ok(cudaMemsetAsync(cn, 0, sizeof(int32_t) * kCtr, st));
             ok(cudaMemsetAsync(g->rel + N, 0, sizeof(unsigned long long), st));
@@ -1108,7 +1160,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                                                  g->d_thr, cap, ct, cl, ch, crec, cn);
             k_g_level_index<<<gb, 256, 0, st>>>(cn, N, cap, offs, iota);
             k_g_levelinfo<<<1, 256, 0, st>>>(crec, cn, N, cap, offs, iota, n_recs, coffN, d_ri, nthreads, g->pfine,
-                                             g->sstep, g->target, g->d_maxP);
+                                             g->sstep, g->target, g->d_maxP, nullptr, g->cap_threads);
         } else {
             const int M = N - 1;
             const FLevel &pf = g->F[M];
@@ -1123,8 +1175,15 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                 k_g_join_write<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos, ct, cl,
                                                    ch, crec, cn);
                 k_g_level_index<<<gb, 256, 0, st>>>(cn, N, cap, offs, iota);
+                // local tracking: the prefix groups first, so that the
+                // segmentation can allow for the largest of them
+                if (g->track && cst == FEM_OK) {
+                    cst = track_group_starts(st, ctx->n_sm, group_in());
+                    groups_ready = cst == FEM_OK;
+                }
                 k_g_levelinfo<<<1, 256, 0, st>>>(crec, cn, N, cap, offs, iota, n_recs, coffN, d_ri, nthreads,
-                                                 g->pfine, g->sstep, g->target, g->d_maxP);
+                                                 g->pfine, g->sstep, g->target, g->d_maxP,
+                                                 groups_ready ? g->tg_gmax : nullptr, g->cap_threads);
             }
         }
         const bool bounded = g->coarse && N >= 3;
@@ -1153,27 +1212,11 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             ta.rec = rec;
             ta.counts = counts;  // unsegmented recordings: counts written directly
             ta.last_mode = ctx->tuning.track_last;
-            TrackGroupIn gi{};
-            gi.slot2cand = iota;
-            gi.d_n_slots = cn;
-            gi.n_slots_cap = cap;
-            gi.offs = offs;
-            gi.ctypes = ct;
-            gi.clo = cl;
-            gi.chi = ch;
-            gi.cand_rec = crec;
-            gi.rinfo = d_ri;
-            gi.n_recs = n_recs;
-            gi.gidx = g->tg_gidx;
-            gi.scan_tmp = g->tg_stmp;
-            gi.gstart = g->tg_gstart;
-            gi.gfirst = g->tg_gfirst;
-            gi.ibase = g->tg_ibase;
-            gi.n_items = g->tg_nitems;
             // items: recordings longest first; level 2 shares no prefix
             // work (one item per episode and segment), levels >= 3 group
             // episodes by their (N-1)-node prefix
-            gi.rorder = g->rorder;
+            TrackGroupIn gi = group_in();
+            gi.starts_ready = groups_ready;
             cst = track_groups(st, ctx->n_sm, gi, N >= 3, &ta);
             if (cst == FEM_OK) cst = launch_track(st, g->track_nblocks, ta);
             if (cst == FEM_OK)

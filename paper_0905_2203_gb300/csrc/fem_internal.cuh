@@ -125,6 +125,8 @@ struct TrackGroupIn {
     const int32_t *rorder;       // recordings in item order (null: 0, 1, ...)
     int32_t *gidx, *scan_tmp, *gstart, *gfirst;
     int64_t *ibase, *n_items;
+    int32_t *gmax;               // if set: per recording, the largest group (track_group_starts)
+    bool starts_ready;           // gidx / gstart already written by track_group_starts
 };
 
 // Results of the levels of level-wise mining run in a captured graph.
@@ -329,6 +331,10 @@ int track_blocks(int n_sm);
 // Numbers the items of a launch on the device (recordings in the order
 // in.rorder, and with `grouped` the prefix groups) and sets the item fields
 // and d_n_items of *a.
+// Prefix groups of the slots (flags, scan, first slot of each group, and,
+// if in.gmax is set, each recording's largest group) without the item
+// numbering, which depends on the segmentation.
+int track_group_starts(cudaStream_t st, int n_sm, const TrackGroupIn &in);
 int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, bool grouped, TrackArgs *a);
 size_t track_buf_bytes(int blocks, int64_t cap);
 int launch_track(cudaStream_t st, int blocks, const TrackArgs &a);

@@ -484,13 +484,22 @@ __global__ void k_track_group_flags(const int32_t *__restrict__ slot2cand, const
 // thread) per recording its first group and its first item (groups x
 // segments), and the item count.
 __global__ void k_track_group_starts(const int32_t *__restrict__ gidx, const int32_t *__restrict__ d_n_slots,
-                                     int64_t n_slots_cap, int32_t *__restrict__ gstart) {
+                                     int64_t n_slots_cap, int32_t *__restrict__ gstart,
+                                     const int32_t *__restrict__ slot2cand, const uint32_t *__restrict__ cand_rec,
+                                     int32_t *__restrict__ gmax) {
     const int64_t n = d_n_slots ? (int64_t)*d_n_slots : n_slots_cap;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s <= n; s += (int64_t)gridDim.x * blockDim.x) {
-        if (s == n)
+        if (s == n) {
             gstart[gidx[n]] = (int32_t)n;
-        else if (gidx[s + 1] != gidx[s])
+        } else if (gidx[s + 1] != gidx[s]) {
             gstart[gidx[s]] = (int32_t)s;
+            if (gmax) {
+                // the group runs to the next start (at most kTrackGroupMax slots)
+                int64_t j = s + 1;
+                while (j < n && gidx[j + 1] == gidx[j]) ++j;
+                atomicMax(gmax + (cand_rec ? cand_rec[slot2cand[s]] : 0u), (int32_t)(j - s));
+            }
+        }
     }
 }
 
@@ -522,15 +531,23 @@ __global__ void k_track_group_recs(const int32_t *__restrict__ gidx, const RecIn
 
 }  // namespace
 
-int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, bool grouped, TrackArgs *a) {
+int track_group_starts(cudaStream_t st, int n_sm, const TrackGroupIn &in) {
     const int64_t cap = in.n_slots_cap;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cap + 256) / 256, 8 * (int64_t)n_sm));
-    if (grouped) {
-        k_track_group_flags<<<g, 256, 0, st>>>(in.slot2cand, in.d_n_slots, cap, in.offs, in.ctypes, in.clo, in.chi,
-                                               in.cand_rec, in.gidx);
-        FEM_TRY(scan_exclusive(st, in.gidx, cap + 1, in.scan_tmp, nullptr, nullptr));
-        k_track_group_starts<<<g, 256, 0, st>>>(in.gidx, in.d_n_slots, cap, in.gstart);
-    }
+    k_track_group_flags<<<g, 256, 0, st>>>(in.slot2cand, in.d_n_slots, cap, in.offs, in.ctypes, in.clo, in.chi,
+                                           in.cand_rec, in.gidx);
+    FEM_TRY(scan_exclusive(st, in.gidx, cap + 1, in.scan_tmp, nullptr, nullptr));
+    if (in.gmax && cudaMemsetAsync(in.gmax, 0, sizeof(int32_t) * std::max(in.n_recs, 1), st) != cudaSuccess)
+        return FEM_ERR_CUDA;
+    k_track_group_starts<<<g, 256, 0, st>>>(in.gidx, in.d_n_slots, cap, in.gstart, in.slot2cand, in.cand_rec,
+                                            in.gmax);
+    FEM_CUDA_TRY(cudaGetLastError());
+    return FEM_OK;
+}
+
+int track_groups(cudaStream_t st, int n_sm, const TrackGroupIn &in, bool grouped, TrackArgs *a) {
+    const int64_t cap = in.n_slots_cap;
+    if (grouped && !in.starts_ready) FEM_TRY(track_group_starts(st, n_sm, in));
     k_track_group_recs<<<1, 32, 0, st>>>(grouped ? in.gidx : nullptr, in.rinfo, in.n_recs, in.rorder, in.d_n_slots,
                                          cap, in.gfirst, in.ibase, in.n_items);
     FEM_CUDA_TRY(cudaGetLastError());

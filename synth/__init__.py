@@ -329,15 +329,19 @@ def c3_batched(seed: int = 0xFE0003, n_events: int = 4_000_000, n_cand: int = 20
     return s, (offs, types, lo, hi)
 
 
+def c4_lengths(seed: int = 0xFE0004, n_rec: int = 256, n_lo: float = 1e4, n_hi: float = 5e6) -> np.ndarray:
+    """The event counts of the many-recordings set (log-uniform in [n_lo, n_hi])."""
+    u = Rng(seed, 7).uniform(n_rec)
+    return np.exp(math.log(n_lo) + (math.log(n_hi) - math.log(n_lo)) * u).astype(np.int64)
+
+
 def c4_recordings(seed: int = 0xFE0004, n_rec: int = 256, n_lo: float = 1e4, n_hi: float = 5e6, which=None):
     """n_rec 60-channel recordings, lengths log-uniform in [n_lo, n_hi], base
     rates 5-20 Hz, 10 us ticks, three chains of 4-6 neurons each; threshold
     per recording max(20, 0.25% n_r); bins the 4-bin set; sizes <= 6.
     `which` (optional) lists the recordings to draw (each is drawn from its
     own seed, so a subset equals the same entries of the whole set)."""
-    rng = Rng(seed, 7)
-    u = rng.uniform(n_rec)
-    ns = np.exp(math.log(n_lo) + (math.log(n_hi) - math.log(n_lo)) * u).astype(np.int64)
+    ns = c4_lengths(seed, n_rec, n_lo, n_hi)
     out = []
     for r in (range(n_rec) if which is None else which):
         rr = Rng(seed * 1315423911 + r, 3)
