@@ -657,6 +657,7 @@ void fem::stream_free_unlocked(fem_stream *s) {
     coarse_free(ctx, s);
     if (s->d_toff) dev_free(ctx, s->d_toff, sizeof(int64_t) * (s->n_types + 1));
     if (s->d_ttime) dev_free(ctx, s->d_ttime, sizeof(int32_t) * std::max<int64_t>(s->n, 1));
+    if (s->d_tidx) dev_free(ctx, s->d_tidx, sizeof(int32_t) * (size_t)s->n_types * (size_t)(s->tcells + 1));
     delete s;
 }
 

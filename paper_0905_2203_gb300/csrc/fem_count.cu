@@ -1570,6 +1570,57 @@ int stream_bytype(fem_ctx *ctx, fem_stream *s) {
     return FEM_OK;
 }
 
+// Time index of the per-type lists (one block row per type): the event at
+// list position j answers the cells after its predecessor's and up to its
+// own; position len answers the cells past the type's last event.
+__global__ void k_tindex(const int64_t *__restrict__ toff, const int32_t *__restrict__ ttime, int32_t tbase,
+                         int shift, int64_t ncell, int32_t *__restrict__ tidx) {
+    const int a = blockIdx.y;
+    const int64_t b = toff[a], len = toff[a + 1] - b;
+    const int32_t *t = ttime + b;
+    int32_t *row = tidx + (int64_t)a * (ncell + 1);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= len; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c_lo = j == 0 ? 0 : ((int64_t)(t[j - 1] - tbase) >> shift) + 1;
+        const int64_t c_hi = j == len ? ncell : ((int64_t)(t[j] - tbase) >> shift);
+        for (int64_t c = c_lo; c <= c_hi; ++c) row[c] = (int32_t)j;
+    }
+}
+
+int stream_tindex(fem_ctx *ctx, fem_stream *s) {
+    if (s->d_tidx) return FEM_OK;
+    FEM_TRY(stream_bytype(ctx, s));
+    const int64_t n = s->n;
+    const double span = n > 0 ? (double)s->t_last - (double)s->t_first + 1.0 : 1.0;
+    // cell width: the power of two nearest the mean gap between events of
+    // one type, n_types * span / n
+    const double gap = n > 0 ? (double)s->n_types * span / (double)n : 1.0;
+    int shift = 0;
+    while (shift < 30 && (double)(2LL << shift) <= gap * 1.4142) ++shift;
+    const int64_t ncell = n > 0 ? (((int64_t)s->t_last - s->t_first) >> shift) + 1 : 1;
+    const size_t bytes = sizeof(int32_t) * (size_t)s->n_types * (size_t)(ncell + 1);
+    void *p = nullptr;
+    FEM_TRY(dev_alloc(ctx, &p, bytes));
+    int32_t *tidx = static_cast<int32_t *>(p);
+    if (n > 0) {
+        const int64_t mean = n / std::max<uint32_t>(s->n_types, 1) + 1;
+        const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((mean + 255) / 256, 64));
+        k_tindex<<<dim3(gx, s->n_types), 256, 0, ctx->stream>>>(s->d_toff, s->d_ttime, s->t_first, shift, ncell,
+                                                                  tidx);
+    } else if (cudaMemsetAsync(tidx, 0, bytes, ctx->stream) != cudaSuccess) {
+        dev_free(ctx, p, bytes);
+        return FEM_ERR_CUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+        dev_free(ctx, p, bytes);
+        return FEM_ERR_CUDA;
+    }
+    s->d_tidx = tidx;
+    s->tshift = shift;
+    s->tcells = ncell;
+    s->bytes += bytes;
+    return FEM_OK;
+}
+
 typedef void (*SparseFn)(SparseArgs);
 
 static SparseFn sparse_fn(int nclass, int rr) {
@@ -1737,7 +1788,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
         if (r->n_types > 8192 || r->n > INT32_MAX / 2) track = false;
     if (track)
         for (auto *r : cc.recs) {
-            const int sb = stream_bytype(ctx, r);
+            const int sb = stream_tindex(ctx, r);
             if (sb == FEM_ERR_NOMEM) {
                 track = false;
                 break;
@@ -1957,6 +2008,7 @@ static int count_core(CountCall &cc, const int32_t *subset, int64_t n_work, int 
                 if (sparse) P = std::min(P, 512);
             }
             pl.ri[r] = RecInfo{s->d_type, s->d_time, s->n, nullptr, P, ks, rb, s->d_freq, s->d_toff, s->d_ttime};
+            recinfo_lists(pl.ri[r], s);
             if (c > 0) {
                 if (!sparse)
                     for (int cb = 0; cb < c; cb += K)

@@ -822,7 +822,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     std::vector<const uint32_t *> dens_h(need_dens ? (size_t)n_recs * lo_vals.size() : 0);
     for (int r = 0; r < n_recs; ++r) {
         fem_stream *s = g->recs[r];
-        FEM_TRY(stream_bytype(ctx, s));
+        FEM_TRY(!need_dens ? stream_tindex(ctx, s) : stream_bytype(ctx, s));
         if (need_dens) {
             FEM_TRY(stream_densities(ctx, s, lo_vals));
             for (size_t j = 0; j < lo_vals.size(); ++j) {
@@ -850,6 +850,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_CUDA_TRY(cudaGetLastError());
         ri_h[r] = RecInfo{s->d_type, s->d_time, s->n, g->segl + (size_t)r * (kMaxPerRec + 1), 1, 0, 0,
                           s->d_freq, s->d_toff, s->d_ttime, tseg, P + 1, 1};
+        recinfo_lists(ri_h[r], s);
     }
     FEM_CUDA_TRY(cudaMemcpyAsync(g->pfine, pfine_h.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
     g->segf = segs;
@@ -908,6 +909,9 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     g->cap2 = cap2;
     const int64_t tot1 = ntpre[n_recs];
     const size_t free_b = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+    // local tracking cuts grouped levels finer (records per candidate and
+    // segment): room for four segments per candidate where the budget has it
+    if (g->track && (size_t)(g->target + 4 * cap) * kRecWords * 4 <= free_b / 4) g->cap_threads = g->target + 4 * cap;
     if ((size_t)g->cap_threads * kRecWords * 4 > free_b / 4) return FEM_ERR_NOMEM;
     // pre-pass launch shape: the bin-mask table (when hi_max < kUbLut), the
     // staged events and a per-thread bitset of n_types x bins bits
@@ -1169,6 +1173,15 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
                 k_g_join_fused<<<1, 1024, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, ct, cl, ch,
                                                    crec, cn, g->rel + N, offs, iota, n_recs, coffN, d_ri, nthreads,
                                                    g->pfine, g->sstep, g->target, g->d_maxP);
+                // local tracking: segment again, allowing for the largest
+                // prefix group
+                if (g->track && cst == FEM_OK) {
+                    cst = track_group_starts(st, ctx->n_sm, group_in());
+                    groups_ready = cst == FEM_OK;
+                    k_g_levelinfo<<<1, 256, 0, st>>>(crec, cn, N, cap, offs, iota, n_recs, coffN, d_ri, nthreads,
+                                                     g->pfine, g->sstep, g->target, g->d_maxP,
+                                                     groups_ready ? g->tg_gmax : nullptr, g->cap_threads);
+                }
             } else {
                 k_g_join_count<<<gb, 256, 0, st>>>(pf.types, pf.lo, pf.hi, pf.rec, pf.foff, cp, M, cap, pos);
                 if (cst == FEM_OK) cst = scan_exclusive(st, pos, cap + 1, scan_tmp, nullptr, nullptr);

@@ -65,6 +65,12 @@ struct RecInfo {
     const int32_t *tseg;
     int tstride;
     int sstep;
+    // Optional (null elsewhere): the per-type time index of the stream (its
+    // fem_stream fields d_tidx, tshift, tcells; tbase = the first event time).
+    const int32_t *tidx;
+    int tshift;
+    int32_t tbase;
+    int64_t tcells;
 };
 
 // Node-by-node local tracking with one warp per (episode, segment) work item
@@ -76,6 +82,7 @@ constexpr int kTrackMaxBlocksPerSm = 6;  // resident blocks per SM the grid asks
 constexpr int kTrackGroupMax = 64;       // episodes per prefix group (a new group every 64 slots)
 constexpr int kTrackMinSeg = 8192;       // shortest segment (events) of a local-tracking item
 constexpr int kTrackEntryRatio = 2;      // last node by entries when events > this x entries
+constexpr int kTrackEntrySlots = 2;      // entries per lane of the entry-driven last node step
 struct TrackArgs {
     const RecInfo *rinfo;
     int n_recs;
@@ -214,6 +221,14 @@ struct fem_stream {
     int64_t *d_toff = nullptr;    // per-type event lists (built on first use): offsets [n_types + 1]
     int32_t *d_ttime = nullptr;   // times grouped by type, ascending within a type [n]
     int64_t max_list = 0;         // longest per-type list (set with the lists)
+    // Per-type time index (built on first use, after the lists): cells of
+    // 2^tshift ticks from t_first; d_tidx[a * (tcells + 1) + c] is the
+    // position in type a's list of its first event at or after
+    // t_first + c * 2^tshift (cell tcells: past every event, the list's
+    // length).  The cell width puts about one event of a type in a cell.
+    int32_t *d_tidx = nullptr;
+    int tshift = 0;
+    int64_t tcells = 0;
     std::map<int32_t, uint32_t *> dens;  // lo -> per-type max events in a closed window of length lo
     std::map<int, int64_t *> segs;       // P -> segment boundaries (P + 1), cached
     std::map<int32_t, fem_coarse_tab> coarse;  // tick width -> coarse-tick tables
@@ -249,6 +264,17 @@ int copy_out(fem_ctx *ctx, void *dst, const void *src_dev, size_t bytes, int dst
 int stream_segments(fem_ctx *ctx, fem_stream *s, int P, const int64_t **seg);
 // Per-type event lists of a stream (built on first use, kept in the stream).
 int stream_bytype(fem_ctx *ctx, fem_stream *s);
+// Per-type time index of a stream (after its lists; built on first use).
+int stream_tindex(fem_ctx *ctx, fem_stream *s);
+// The stream's per-type lists and time index in a RecInfo.
+inline void recinfo_lists(RecInfo &ri, const fem_stream *s) {
+    ri.toff = s->d_toff;
+    ri.ttime = s->d_ttime;
+    ri.tidx = s->d_tidx;
+    ri.tshift = s->tshift;
+    ri.tbase = s->t_first;
+    ri.tcells = s->tcells;
+}
 // Density table for one lo (computed on first use, cached in the stream).
 int stream_density(fem_ctx *ctx, fem_stream *s, int32_t lo, uint32_t **d_dens);
 // Densities for several lower bounds in one pass over the per-type lists

@@ -195,82 +195,72 @@ __device__ __forceinline__ int node_step(const int32_t *__restrict__ ev, int n_e
 // so once it has been offered every entry class has its last selection at or
 // above L_i (it selected this end, or it could not), the largest latest start
 // seen is at least L_i, and a later end with the same L_i changes no class.
-// So per entry one search finds the first event at or after
-// max(T_i + lo + 1, Tp), and the end is offered when it lies in the entry's
-// interval and within its upper bound.
+// So per entry one lookup finds the first event at or after
+// q = max(T_i + lo + 1, Tp), and the end is offered when it lies in the
+// entry's interval and within its upper bound.
 //
-// The warp takes the entries 32 at a time (the next chunk's loaded ahead).
-// Their queries ascend with the lane, so each chunk searches forward from
-// the previous chunk's last answer: one load of 32 probes sb events apart
-// (sb a power of two near the mean number of events per entry) ranks every
-// lane's query into a bucket of sb events by a 5-step search over the lanes'
-// registers, and a binary search of log2(sb) loads inside the bucket ends
-// it.  A lane whose query is beyond all 32 probes waits for the next 32 * sb
-// events.
-template <bool HASL>
-__device__ __forceinline__ void last_by_entries(const int32_t *__restrict__ ev, int n_ev, Entries<HASL> p, int m,
-                                                int32_t lo_e, int32_t hi_e, Machine<2, 0> &st, int32_t Tp,
-                                                int lane) {
+// The lookup uses the stream's per-type time index: the cell of q gives the
+// list position of the first event at or after the cell's start, and a short
+// forward scan (about one event of the type per cell) reaches the first event
+// at or after q.  Lanes look up independently; the warp takes 32 x K entries
+// at a time (entry base + 32 k + lane in lane k's k-th slot) and issues the
+// K index loads of a lane, then its K list loads, side by side, so that each
+// lane has K lookups in flight; then it offers the ends to Algorithm 1 slot
+// by slot (time order).
+//
+// tl: the type's list; [cb, ce): the item's part of it; row: the type's
+// index row (ncell + 1 cells of 2^shift ticks from tbase).
+template <bool HASL, int K>
+__device__ __forceinline__ void last_by_index(const int32_t *__restrict__ tl, int cb, int ce,
+                                              const int32_t *__restrict__ row, int shift, uint32_t tbase,
+                                              int64_t ncell, Entries<HASL> p, int m, int32_t lo_e, int32_t hi_e,
+                                              Machine<2, 0> &st, int32_t Tp, int lane) {
     // Times are >= 0 and 0 <= lo < hi < 2^31, so every bound below fits an
     // unsigned 32-bit word except T_{i+1} + lo for a missing next entry.
     const uint32_t lo = (uint32_t)lo_e, hi = (uint32_t)hi_e, tp = (uint32_t)Tp;
-    const int ratio = n_ev / (m > 0 ? m : 1);
-    const int lg = ratio > 1 ? 32 - __clz(ratio - 1) : 0;
-    const int sb = 1 << (lg < 16 ? lg : 16);
-    int cur = 0;  // events below every remaining query
-    int2 E_next = lane < m ? p.get(lane) : make_int2(-1, 0);
-    for (int base = 0; base < m; base += 32) {
-        const bool in = base + lane < m;
-        const int2 E = E_next;
-        const bool more = base + 32 < m;
-        if (more) E_next = (base + 32 + lane < m) ? p.get(base + 32 + lane) : make_int2(-1, 0);
-        const uint32_t T = (uint32_t)E.x;
-        // the next entry's time (none: the interval is open above)
-        uint32_t Tn = __shfl_down_sync(kFull, T, 1);
-        const uint32_t Tn0 = __shfl_sync(kFull, (uint32_t)E_next.x, 0);
-        if (lane == 31) Tn = Tn0;
-        const bool has_next = base + lane + 1 < m;
-        uint32_t q = T + lo + 1u;
-        if (q < tp) q = tp;
-        int idx = n_ev;
-        uint32_t e = 0xFFFFFFFFu;  // the event at idx (none past n_ev)
-        bool done = !in;
-        int c0 = cur;
-        for (;;) {
-            const int pp = c0 + sb * (lane + 1) - 1;
-            const uint32_t pv = pp < n_ev ? (uint32_t)ev[pp] : 0xFFFFFFFFu;
-            int c = 0;
+    for (int base = 0; base < m; base += 32 * K) {
+        int2 E[K];
 #pragma unroll
-            for (int s = 16; s >= 1; s >>= 1)
-                if (__shfl_sync(kFull, pv, c + s - 1) < q) c += s;
-            const uint32_t top = __shfl_sync(kFull, pv, 31);
-            if (c == 31 && top < q) c = 32;
-            const uint32_t pc = __shfl_sync(kFull, pv, c < 32 ? c : 31);
-            if (!done && c < 32) {
-                // the first event >= q lies in [c0 + sb*c, c0 + sb*(c+1)),
-                // whose last position holds pc >= q (past n_ev: none)
-                int pos = c0 + sb * c;
-                uint32_t val = pc;
-                for (int h = sb >> 1; h >= 1; h >>= 1) {
-                    const int pq = pos + h - 1;
-                    const uint32_t x = pq < n_ev ? (uint32_t)ev[pq] : 0xFFFFFFFFu;
-                    if (x < q)
-                        pos += h;
-                    else
-                        val = x;
-                }
-                idx = pos;
-                e = val;
-                done = true;
-            }
-            if (__all_sync(kFull, done)) break;
-            c0 += 32 * sb;
+        for (int k = 0; k < K; ++k) E[k] = base + 32 * k + lane < m ? p.get(base + 32 * k + lane) : make_int2(-1, 0);
+        const int nx = base + 32 * K;
+        // the first entry of the next chunk (its time bounds this chunk's
+        // last interval)
+        const uint32_t T_after = nx < m ? (uint32_t)p.get(nx).x : 0xFFFFFFFFu;
+        // the K lookups of a lane side by side: index cell, then the first
+        // event of the cell, then (rarely) a few more events
+        uint32_t q[K], x[K];
+        int pos[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            q[k] = (uint32_t)E[k].x + lo + 1u;
+            if (q[k] < tp) q[k] = tp;
+            const uint64_t c = q[k] > tbase ? (uint64_t)((q[k] - tbase) >> shift) : 0;
+            pos[k] = base + 32 * k + lane < m ? row[c < (uint64_t)ncell ? c : (uint64_t)ncell] : ce;
         }
-        const bool ok = in && idx < n_ev && e <= T + hi && (!has_next || e <= Tn + lo);
-        greedy_chunk(__ballot_sync(kFull, ok), (int32_t)e, ok ? E.y : 0, st, Tp, lane);
-        // the next chunk's queries are at or above this chunk's last one
-        const int last = __shfl_sync(kFull, idx, 31);
-        cur = last < n_ev ? last : n_ev;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (pos[k] < cb) pos[k] = cb;
+            x[k] = pos[k] < ce ? (uint32_t)tl[pos[k]] : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            while (x[k] < q[k]) {
+                ++pos[k];
+                x[k] = pos[k] < ce ? (uint32_t)tl[pos[k]] : 0xFFFFFFFFu;
+            }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = base + 32 * k + lane;
+            const uint32_t T = (uint32_t)E[k].x;
+            // the next entry's time: the next lane's, the next slot's first,
+            // or the next chunk's first
+            uint32_t Tn = __shfl_down_sync(kFull, T, 1);
+            const uint32_t Tf = k + 1 < K ? __shfl_sync(kFull, (uint32_t)E[k + 1 < K ? k + 1 : k].x, 0) : T_after;
+            if (lane == 31) Tn = Tf;
+            // x = the first event at or after q (none: past the item's part)
+            const bool ok = i < m && pos[k] < ce && x[k] <= T + hi && (i + 1 >= m || x[k] <= Tn + lo);
+            greedy_chunk(__ballot_sync(kFull, ok), (int32_t)x[k], ok ? E[k].y : 0, st, Tp, lane);
+        }
     }
     __syncwarp();
 }
@@ -294,7 +284,7 @@ __device__ __forceinline__ void machine_init(Machine<2, 0> &st, int N) {
 // (slot) or, with groups, a run of episode slots [s0, s1) that share their
 // first N-1 nodes and edges: the shared prefix is tracked once, and only the
 // last node step is run per episode.
-__global__ void __launch_bounds__(kTrackWarps * 32, 6) k_count_track(TrackArgs a) {
+__global__ void __launch_bounds__(kTrackWarps * 32, kTrackMaxBlocksPerSm) k_count_track(TrackArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     // two entry lists of (time, latest start) pairs, ping-pong
@@ -420,19 +410,25 @@ __global__ void __launch_bounds__(kTrackWarps * 32, 6) k_count_track(TrackArgs a
                 const int n_ev = (int)(ce - cb);
                 const int32_t lo_l = a.relaxed ? 0 : a.clo[ec + N - 2], hi_l = a.chi[ec + N - 2];
                 // entries well short of the events: search per entry
-                const bool by_entries =
-                    a.last_mode == 2 || (a.last_mode == 0 && (int64_t)m * kTrackEntryRatio < (int64_t)n_ev);
+                const bool by_entries = ri.tidx && (a.last_mode == 2 || (a.last_mode == 0 &&
+                                                                         (int64_t)m * kTrackEntryRatio < (int64_t)n_ev));
                 const int32_t *evl = ttime + cb;
-                if (N == 2) {
-                    if (by_entries)
-                        last_by_entries(evl, n_ev, p0, m, lo_l, hi_l, st, Tp, lane);
+                if (by_entries) {
+                    const uint32_t E = a.ctypes[oc + N - 1];
+                    const int64_t t0 = toff[E];
+                    const int32_t *row = ri.tidx + (int64_t)E * (ri.tcells + 1);
+                    if (N == 2)
+                        last_by_index<false, kTrackEntrySlots>(ttime + t0, (int)(cb - t0), (int)(ce - t0), row,
+                                                               ri.tshift, (uint32_t)ri.tbase, ri.tcells, p0, m, lo_l,
+                                                               hi_l, st, Tp, lane);
                     else
-                        node_step<true>(evl, n_ev, p0, m, lo_l, hi_l, nullptr, st, Tp, lane);
+                        last_by_index<true, kTrackEntrySlots>(ttime + t0, (int)(cb - t0), (int)(ce - t0), row,
+                                                              ri.tshift, (uint32_t)ri.tbase, ri.tcells, pe, m, lo_l,
+                                                              hi_l, st, Tp, lane);
+                } else if (N == 2) {
+                    node_step<true>(evl, n_ev, p0, m, lo_l, hi_l, nullptr, st, Tp, lane);
                 } else {
-                    if (by_entries)
-                        last_by_entries(evl, n_ev, pe, m, lo_l, hi_l, st, Tp, lane);
-                    else
-                        node_step<true>(evl, n_ev, pe, m, lo_l, hi_l, nullptr, st, Tp, lane);
+                    node_step<true>(evl, n_ev, pe, m, lo_l, hi_l, nullptr, st, Tp, lane);
                 }
             }
             st.finish();
