@@ -87,10 +87,17 @@ typedef struct {
     int segments;         /* stream segments per recording (>= 1) */
     int tile_events;      /* events per shared-memory stage (multiple of 256) */
     int prepass;          /* upper-bound pre-passes of level-wise mining:
-                             0 = the level-2 pair bound, 1 = also the
-                             coarse-tick bound of fem_upper_bound_coarse on
-                             every level >= 3 (candidates at or below the
-                             threshold skip the exact count), -1 = none */
+                             0 = the level-2 pair bound and, with the
+                             mining graph and local tracking, the level-3
+                             join bound (per candidate the number of events
+                             of its middle type that end its frequent
+                             2-node prefix and start its frequent 2-node
+                             suffix); 1 = both and the coarse-tick bound
+                             of fem_upper_bound_coarse on every level >= 3;
+                             2 = the level-2 pair bound only; -1 = none.
+                             Candidates whose bound is at or below the
+                             threshold skip the exact count and are
+                             reported as pruned, never as counted */
     int plain_path;       /* 1 = count with the one-thread-per-episode plain
                              path (comparison baseline) instead of the tiled
                              kernels */

@@ -524,7 +524,7 @@ extern "C" int fem_ctx_set_tuning(fem_ctx *ctx, const fem_tuning *t) {
         return FEM_ERR_INVAL;
     if (t->segments < 0 || t->tile_events < 0 || (t->tile_events % 256) != 0 ||
         t->tile_events > kMaxTile || t->kernel < 0 || t->kernel > 7 || t->wait_polls < 0 ||
-        t->track_last < 0 || t->track_last > 2)
+        t->track_last < 0 || t->track_last > 2 || t->prepass < -1 || t->prepass > 2)
         return FEM_ERR_INVAL;
     ctx->tuning = *t;
     return FEM_OK;

@@ -588,13 +588,15 @@ __global__ void __launch_bounds__(1024, 1)
 
 // Every node's ring must fit R_cap entries (window density + 1).  Also sums
 // the candidates' relevant events (sum over nodes of the node type's
-// frequency in the candidate's recording) into *rel.
+// frequency in the candidate's recording) into *rel, leaving out those a
+// bound dropped (skip set: they are not counted).
 // It also writes the level's segment boundaries: every sstep[r]-th of the
 // recording's finest ones.
 __global__ void k_g_ringcheck(const uint16_t *ct, const int32_t *cl, const uint32_t *crec, const int32_t *ctr, int N,
                               const uint32_t *const *dens, const int32_t *lo_vals, int n_lo, int R_cap,
                               const RecInfo *ri, int32_t *ctr_w, unsigned long long *rel, int n_recs,
-                              const int64_t *segf, const int32_t *pfine, const int32_t *sstep, int64_t *segl) {
+                              const int64_t *segf, const int32_t *pfine, const int32_t *sstep, int64_t *segl,
+                              const uint8_t *skip) {
     const int64_t gt0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
     for (int r = 0; r < n_recs; ++r) {
         const int P = ri[r].P, st = sstep[r], pf = pfine[r];
@@ -607,6 +609,7 @@ __global__ void k_g_ringcheck(const uint16_t *ct, const int32_t *cl, const uint3
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t r = crec[i];
         const uint32_t *fq = ri[r].freq;
+        if (skip && skip[i]) continue;  // dropped by a bound: not counted
         for (int k = 0; k < N; ++k) acc += fq[ct[i * N + k]];
         for (int k = 0; k < N - 1 && dens; ++k) {  // no tables: no rings to check
             const int32_t l = cl[i * (N - 1) + k];
@@ -676,6 +679,7 @@ struct FLevel {
 // event sums, then per level its frequent set (capacity-sized regions).
 struct PackLayout {
     int64_t o_ctr, o_coff, o_coff2, o_rel;  // byte offsets
+    int64_t o_skip3;                        // level 3: candidates per recording the join bound dropped
     int64_t o_lvl[FEM_MAX_NODES + 1];       // per level: types, then lo, hi, rec, counts
     int64_t fcap[FEM_MAX_NODES + 1];        // per level capacity
 };
@@ -689,14 +693,15 @@ __device__ __forceinline__ void pack_copy(char *dst, const char *src, int64_t by
 }
 
 __global__ void k_g_pack(const int *status, const int32_t *ctr, const int64_t *coff, const int64_t *coff2,
-                         const unsigned long long *rel, const FLevel *F, PackLayout lay, int first, int L,
-                         int n_recs, char *out) {
+                         const unsigned long long *rel, const unsigned long long *skip3, const FLevel *F,
+                         PackLayout lay, int first, int L, int n_recs, char *out) {
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
     if (t0 == 0) *reinterpret_cast<int *>(out) = *status;
     pack_copy(out + lay.o_ctr, reinterpret_cast<const char *>(ctr), 4 * (int64_t)(L + 1) * kCtr, t0, gs);
     pack_copy(out + lay.o_coff, reinterpret_cast<const char *>(coff), 8 * (int64_t)(L + 1) * (n_recs + 1), t0, gs);
     pack_copy(out + lay.o_coff2, reinterpret_cast<const char *>(coff2), 8 * (int64_t)(n_recs + 1), t0, gs);
     pack_copy(out + lay.o_rel, reinterpret_cast<const char *>(rel), 8 * (int64_t)(L + 1), t0, gs);
+    if (skip3) pack_copy(out + lay.o_skip3, reinterpret_cast<const char *>(skip3), 8 * (int64_t)n_recs, t0, gs);
     for (int N = first; N <= L; ++N) {
         const int64_t Fn = ctr[N * kCtr + 1], fc = lay.fcap[N];
         const FLevel f = F[N];
@@ -733,6 +738,15 @@ struct GraphTail {
     CoarseDesc *d_cdesc = nullptr;
     uint32_t *cub = nullptr;
     uint8_t *skip = nullptr;
+    // level-3 join bound (local tracking with the pre-passes on): bitsets of
+    // the frequent 2-node episodes, the (X, Y, bin) table, skipped counts
+    bool jb_on = false;                    // asked for (tuning)
+    bool jb = false;                       // built
+    int64_t jb_cap_words = 0, jb_tab_n = 0;
+    uint32_t *jb_v = nullptr, *jb_s = nullptr, *jb_nt = nullptr;
+    int64_t *jb_base = nullptr, *jb_tab_off = nullptr;
+    int32_t *jb_stride = nullptr, *jb_tab = nullptr;
+    unsigned long long *jb_skipc = nullptr;
     int64_t cap = 0, cap2 = 0, cap_threads = 0;
     std::vector<std::pair<void *, size_t>> held;
     std::vector<FLevel> F;                 // F[N] for N = 1..max_size
@@ -1042,6 +1056,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         lay.o_coff = take(8 * (int64_t)(L + 1) * (n_recs + 1));
         lay.o_coff2 = take(8 * (int64_t)(n_recs + 1));
         lay.o_rel = take(8 * (int64_t)(L + 1));
+        lay.o_skip3 = take(8 * (int64_t)std::max(n_recs, 1));
         for (int N = first; N <= L; ++N) {
             const int64_t fc = N == 1 ? std::max<int64_t>(tot1, 1) : cap;
             lay.fcap[N] = fc;
@@ -1079,6 +1094,38 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         FEM_CUDA_TRY(cudaMemcpyAsync(g->d_cdesc, cd.data(), sizeof(CoarseDesc) * n_recs, cudaMemcpyHostToDevice, st));
     } else {
         g->coarse = 0;
+    }
+    // level-3 join bound: per frequent 2-node episode two bitsets of its
+    // recording's longest list / 32 words each; capacity for every ordered
+    // pair x bin of a recording being frequent, capped by the budget (a
+    // level whose bitsets do not fit is not bounded)
+    g->jb = g->jb_on && g->track && g->prepass && L >= 3 && first <= 3 && nb > 0;
+    if (g->jb) {
+        std::vector<int32_t> stride_h(n_recs);
+        int64_t worst = 0;
+        for (int r = 0; r < n_recs; ++r) {
+            stride_h[r] = (int32_t)((g->recs[r]->max_list + 31) / 32);
+            worst += std::min<int64_t>((int64_t)nt_h[r] * nt_h[r] * nb, cap) * stride_h[r];
+        }
+        const size_t fb = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+        g->jb_cap_words = std::min<int64_t>(std::min<int64_t>(worst, (int64_t)1 << 28), (int64_t)(fb / 32));
+        g->jb_tab_n = std::max<int64_t>(ub_off[n_recs], 1);
+        if (g->jb_cap_words < 1024) {
+            g->jb = false;
+        } else {
+            FEM_TRY(g->get(&g->jb_v, (size_t)g->jb_cap_words));
+            FEM_TRY(g->get(&g->jb_s, (size_t)g->jb_cap_words));
+            FEM_TRY(g->get(&g->jb_base, (size_t)n_recs + 1));
+            FEM_TRY(g->get(&g->jb_stride, (size_t)n_recs));
+            FEM_TRY(g->get(&g->jb_tab, (size_t)g->jb_tab_n));
+            FEM_TRY(g->get(&g->jb_tab_off, (size_t)n_recs + 1));
+            FEM_TRY(g->get(&g->jb_nt, (size_t)n_recs));
+            FEM_TRY(g->get(&g->jb_skipc, (size_t)n_recs));
+            if (!g->skip) FEM_TRY(g->get(&g->skip, (size_t)cap));
+            FEM_CUDA_TRY(cudaMemcpyAsync(g->jb_stride, stride_h.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
+            FEM_CUDA_TRY(cudaMemcpyAsync(g->jb_tab_off, ub_off.data(), 8 * (n_recs + 1), cudaMemcpyHostToDevice, st));
+            FEM_CUDA_TRY(cudaMemcpyAsync(g->jb_nt, nt_h.data(), 4 * n_recs, cudaMemcpyHostToDevice, st));
+        }
     }
     FEM_CUDA_TRY(cudaStreamSynchronize(st));
 
@@ -1203,9 +1250,46 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         if (bounded && cst == FEM_OK)
             cst = coarse_graph_level(st, ctx->n_sm, N, ct, cl, ch, crec, cn, cap, g->d_cdesc, g->coarse_slices,
                                      g->d_thr, g->coarse_min, g->cub, g->skip);
+        const bool jbound = g->jb && N == 3;
+        if (jbound && cst == FEM_OK) {
+            const FLevel &f2 = g->F[2];
+            JoinBoundArgs ja{};
+            ja.ri = d_ri;
+            ja.n_recs = n_recs;
+            ja.stride = g->jb_stride;
+            ja.f2types = f2.types;
+            ja.f2lo = f2.lo;
+            ja.f2hi = f2.hi;
+            ja.f2rec = f2.rec;
+            ja.f2foff = f2.foff;
+            ja.f2n = g->ctr + 2 * kCtr + 1;
+            ja.tab_off = g->jb_tab_off;
+            ja.nt = g->jb_nt;
+            ja.tab = g->jb_tab;
+            ja.tab_n = g->jb_tab_n;
+            ja.blo = d_blo;
+            ja.bhi = d_bhi;
+            ja.nb = nb;
+            ja.ct = ct;
+            ja.cl = cl;
+            ja.ch = ch;
+            ja.crec = crec;
+            ja.cn = cn;
+            ja.thr = g->d_thr;
+            ja.vbits = g->jb_v;
+            ja.sbits = g->jb_s;
+            ja.cap_words = g->jb_cap_words;
+            ja.base = g->jb_base;
+            ja.skip = g->skip;
+            ja.or_skip = bounded ? 1 : 0;
+            ja.skipc = g->jb_skipc;
+            cst = join_bound_level3(st, ctx->n_sm, ja);
+        }
+        const bool skipping = bounded || jbound;
         k_g_ringcheck<<<gb, 256, 0, st>>>(ct, cl, crec, cn, N, need_dens ? d_dens : nullptr, d_lov,
                                           (int)lo_vals.size(), g->ring_cap, d_ri,
-                                          cn, g->rel + N, n_recs, g->segf, g->pfine, g->sstep, g->segl);
+                                          cn, g->rel + N, n_recs, g->segf, g->pfine, g->sstep, g->segl,
+                                          skipping ? g->skip : nullptr);
         // external event nodes: their timestamps time the count kernels of
         // this level on every launch of the graph
         ok(cudaEventRecordWithFlags(g->ev[2 * N], st, cudaEventRecordExternal));
@@ -1218,7 +1302,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             ta.clo = cl;
             ta.chi = ch;
             ta.slot2cand = iota;
-            ta.skip = bounded ? g->skip : nullptr;
+            ta.skip = skipping ? g->skip : nullptr;
             ta.queue = reinterpret_cast<unsigned long long *>(g->tqueue);
             ta.buf = g->tbuf;
             ta.cap = g->track_cap;
@@ -1234,11 +1318,11 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             if (cst == FEM_OK) cst = launch_track(st, g->track_nblocks, ta);
             if (cst == FEM_OK)
                 cst = launch_stitch_dev(st, ctx->n_sm, d_ri, iota, crec, rec, cn, cap, counts, fb_list, cn + 3,
-                                        bounded ? g->skip : nullptr, g->d_maxP, 1);
+                                        skipping ? g->skip : nullptr, g->d_maxP, 1);
         } else if (cst == FEM_OK) {
             cst = launch_count_dev(st, nmax, N, g->ring_cap, d_ri, n_recs, nthreads, g->cap_threads, offs, ct, cl, ch,
                                    iota, crec, rec, cn, cap, counts, fb_list, cn + 3, d_dens, d_lov,
-                                   (int)lo_vals.size(), bounded ? g->skip : nullptr);
+                                   (int)lo_vals.size(), skipping ? g->skip : nullptr);
         }
         ok(cudaEventRecordWithFlags(g->ev[2 * N + 1], st, cudaEventRecordExternal));
         if (fused) {
@@ -1254,8 +1338,9 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
         ok(cudaGetLastError());
     }
     if (cst == FEM_OK) {
-        k_g_pack<<<(unsigned)(2 * ctx->n_sm), 256, 0, st>>>(ctx->d_status, g->ctr, g->coff, g->coff2, g->rel, d_F,
-                                                           g->lay, first, L, n_recs, d_out);
+        k_g_pack<<<(unsigned)(2 * ctx->n_sm), 256, 0, st>>>(ctx->d_status, g->ctr, g->coff, g->coff2, g->rel,
+                                                           g->jb ? g->jb_skipc : nullptr, d_F, g->lay, first, L,
+                                                           n_recs, d_out);
         ok(cudaGetLastError());
     }
     const cudaError_t ce = cudaStreamEndCapture(st, &graph);
@@ -1337,10 +1422,12 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
     const int n_recs = (int)recs.size();
     for (auto *s : recs)
         if (s->n_types > 8192 || s->n > INT32_MAX / 2) return FEM_OK;
-    // coarse-tick bound of levels >= 3: only with prepass = 1
+    // coarse-tick bound of levels >= 3: only with prepass = 1; level-3 join
+    // bound: with prepass 0 (the default) or 1
     const int coarse = ctx->tuning.prepass == 1 ? 1 : 0;
-    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass, coarse, ctx->tuning.kernel,
-                                        ctx->tuning.track_last);
+    const bool jb_on = ctx->tuning.prepass == 0 || ctx->tuning.prepass == 1;
+    const std::string key = graph_key(recs, blo, bhi, thr, max_size, first, prepass, coarse + 2 * (jb_on ? 1 : 0),
+                                      ctx->tuning.kernel, ctx->tuning.track_last);
     int64_t cap = 4096;
     auto hint = ctx->graph_cap.find(key);
     const int64_t want = std::max<int64_t>(cap_min, hint != ctx->graph_cap.end() ? hint->second : 0);
@@ -1364,6 +1451,7 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
         ng->max_size = max_size;
         ng->first = first;
         ng->prepass = prepass;
+        ng->jb_on = jb_on;
         ng->coarse = coarse;
         ng->coarse_min = 0;
         ng->cap = cap;
@@ -1445,6 +1533,11 @@ static int run_graph(fem_ctx *ctx, const std::vector<fem_stream *> &recs, const 
         if (N >= 2) {
             tl.coff.assign(coff + (size_t)N * (n_recs + 1), coff + (size_t)(N + 1) * (n_recs + 1));
             tl.goff = (N == 2 && first <= 2) ? std::vector<int64_t>(coff2, coff2 + n_recs + 1) : tl.coff;
+            tl.skipped.assign(n_recs, 0);
+            if (N == 3 && g->jb) {
+                const int64_t *sk = reinterpret_cast<const int64_t *>(ho + g->lay.o_skip3);
+                tl.skipped.assign(sk, sk + n_recs);
+            }
         }
         const int64_t Fn = c[1], fc = g->lay.fcap[N];
         const char *o = ho + g->lay.o_lvl[N];

@@ -139,9 +139,10 @@ struct TrackGroupIn {
 // Results of the levels of level-wise mining run in a captured graph.
 struct TailLevel {
     int N = 0;
-    int64_t C = 0;                    // candidates counted at this level
+    int64_t C = 0;                    // candidates of this level after the level-2 pruning
     std::vector<int64_t> coff;        // per-recording offsets of the counted candidates
     std::vector<int64_t> goff;        // per-recording offsets of the generated ones (level 2: before pruning)
+    std::vector<int64_t> skipped;     // per recording: counted candidates a bound dropped before the count
     std::vector<uint16_t> types;      // frequent episodes, fixed stride N
     std::vector<int32_t> lo, hi;
     std::vector<uint32_t> rec, counts;
@@ -357,6 +358,39 @@ int track_blocks(int n_sm);
 // Numbers the items of a launch on the device (recordings in the order
 // in.rorder, and with `grouped` the prefix groups) and sets the item fields
 // and d_n_items of *a.
+// Upper bound of every level-3 candidate from its two frequent 2-node
+// sub-episodes (fem_joinbound.cu): per frequent 2-node episode a bitset of
+// its valid ends and one of its valid starts; skip[c] = 1 where the
+// popcount of their AND is at or below the threshold.
+struct JoinBoundArgs {
+    const RecInfo *ri;          // per recording: lists and time index
+    int n_recs;
+    const int32_t *stride;      // per recording: words per bitset
+    const uint16_t *f2types;    // the frequent 2-node episodes (stride 2), their
+    const int32_t *f2lo, *f2hi; // edges, recordings, per-recording offsets and
+    const uint32_t *f2rec;      // (device) count
+    const int64_t *f2foff;
+    const int32_t *f2n;
+    const int64_t *tab_off;     // (X, Y, bin) table: per-recording offsets,
+    const uint32_t *nt;         // types per recording, the table itself
+    int32_t *tab;
+    int64_t tab_n;
+    const int32_t *blo, *bhi;
+    int nb;
+    const uint16_t *ct;         // level-3 candidates (stride 3 / 2), recordings,
+    const int32_t *cl, *ch;     // (device) count
+    const uint32_t *crec;
+    const int32_t *cn;
+    const uint32_t *thr;        // per recording
+    uint32_t *vbits, *sbits;    // bitsets (cap_words words each)
+    int64_t cap_words;
+    int64_t *base;              // n_recs + 1: first word per recording, total
+    uint8_t *skip;
+    int or_skip;                // keep flags already set by another bound
+    unsigned long long *skipc;  // per recording: skipped candidates
+};
+int join_bound_level3(cudaStream_t st, int n_sm, const JoinBoundArgs &a);
+
 // Prefix groups of the slots (flags, scan, first slot of each group, and,
 // if in.gmax is set, each recording's largest group) without the item
 // numbering, which depends on the segmentation.

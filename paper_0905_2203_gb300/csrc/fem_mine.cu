@@ -775,7 +775,8 @@ int MineGroup::advance() {
 }
 
 // Copies the levels a captured graph produced into the result and the
-// statistics (level 2 counts the candidates the pre-pass dropped as pruned).
+// statistics (the candidates the level-2 pre-pass and the level-3 join bound
+// dropped count as pruned).
 static void fill_graph_levels(MineGroup &g, const TailResult &tr) {
     const int n_recs = g.nrec();
     for (const TailLevel &tl : tr.levels) {
@@ -784,8 +785,11 @@ static void fill_graph_levels(MineGroup &g, const TailResult &tr) {
             if (tl.C == 0) break;
             g.S.candidates_counted += tl.C;
             for (int r = 0; r < n_recs; ++r) {
+                // a bound's dropped candidates count as pruned, not counted
+                const int64_t sk = r < (int)tl.skipped.size() ? tl.skipped[r] : 0;
+                g.S.candidates_counted -= sk;
                 const double gr = (double)(tl.goff[r + 1] - tl.goff[r]);
-                const double cr = (double)(tl.coff[r + 1] - tl.coff[r]);
+                const double cr = (double)(tl.coff[r + 1] - tl.coff[r] - sk);
                 g.S.episode_events += gr * (double)g.recs[r]->n;
                 g.S.counted_episode_events += cr * (double)g.recs[r]->n;
                 g.S.candidates_pruned += (int64_t)(gr - cr);

@@ -347,7 +347,10 @@ __global__ void __launch_bounds__(kTrackWarps * 32, kTrackMaxBlocksPerSm) k_coun
         }
         sumhi += hmax;
         const int64_t seg_b = ri.seg[p], seg_e = ri.seg[p + 1];
-        const bool live = seg_b < seg_e && N >= 2;
+        // (no prefix work when a bound dropped every episode of the item)
+        bool kept = !a.skip;
+        for (int s = s0 + lane; s < s1 && !kept; s += 32) kept = !a.skip[a.slot2cand[s]];
+        const bool live = seg_b < seg_e && N >= 2 && __any_sync(kFull, kept);
         int32_t Tp = 0;
         int64_t haloT = INT64_MIN, Tend = INT64_MAX;
         if (live) {

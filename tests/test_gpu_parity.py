@@ -932,3 +932,34 @@ def test_coarse_bound_edges_and_full_size(fb, ctx):
     want = cb.coarse_ub_many(s.types, s.times, *_sub(offs, ct, lo, hi, sample), w)
     assert np.array_equal(ub[sample], want)
     st.free()
+
+
+def test_level3_join_bound_prunes_without_changing_results(fb, ctx):
+    """The level-3 join bound (the default pre-pass with the mining graph):
+    the same levels as with the level-2 pair bound only and with no bound at
+    all, on three recordings of the many-recordings set; it drops level-3
+    candidates (reported as pruned, not counted) and the relevant-event
+    count only covers what was counted."""
+    recs = synth.c4_recordings(which=[4, 19, 22])
+    sts = [ctx.load_stream(s.types, s.times, s.n_types) for s, _ in recs]
+    bins = recs[0][1]["bins"]
+    thr = [c["threshold"] for _, c in recs]
+    out = {}
+    try:
+        for pp in (0, 2, -1):
+            ctx.set_tuning(prepass=pp)
+            res = ctx.mine_levelwise(sts, bins, thr, 5)
+            out[pp] = ([res.level(r, N) for r in range(len(sts)) for N in range(1, 6)], res.stats())
+            res.free()
+    finally:
+        ctx.reset_tuning()
+    assert out[0][0] == out[2][0] == out[-1][0]
+    s0, s2, sn = out[0][1], out[2][1], out[-1][1]
+    assert s0["graph_tails"] == 1 and s2["graph_tails"] == 1
+    assert s0["candidates_pruned"] > s2["candidates_pruned"] > 0 == sn["candidates_pruned"]
+    assert s0["candidates_counted"] + s0["candidates_pruned"] == s2["candidates_counted"] + s2["candidates_pruned"]
+    assert s0["counted_episode_events"] < s2["counted_episode_events"]
+    assert s0["relevant_events"] < s2["relevant_events"]
+    assert sum(len(out[0][0][r * 5 + 2][0]) for r in range(len(sts))) > 0  # some level-3 episode is frequent
+    for st in sts:
+        st.free()
