@@ -1099,7 +1099,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
     // recording's longest list / 32 words each; capacity for every ordered
     // pair x bin of a recording being frequent, capped by the budget (a
     // level whose bitsets do not fit is not bounded)
-    g->jb = g->jb_on && g->track && g->prepass && L >= 3 && first <= 3 && nb > 0;
+    g->jb = g->jb_on && g->track && L >= 3 && first <= 3 && nb > 0;
     if (g->jb) {
         std::vector<int32_t> stride_h(n_recs);
         int64_t worst = 0;
@@ -1279,6 +1279,7 @@ static int build_graph(GraphTail *g, const std::vector<int32_t> &blo, const std:
             ja.vbits = g->jb_v;
             ja.sbits = g->jb_s;
             ja.cap_words = g->jb_cap_words;
+            ja.nch = (int)std::max<int64_t>(1, (g->track_cap + 1023) / 1024);
             ja.base = g->jb_base;
             ja.skip = g->skip;
             ja.or_skip = bounded ? 1 : 0;

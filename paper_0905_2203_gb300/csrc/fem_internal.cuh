@@ -384,6 +384,7 @@ struct JoinBoundArgs {
     const uint32_t *thr;        // per recording
     uint32_t *vbits, *sbits;    // bitsets (cap_words words each)
     int64_t cap_words;
+    int nch;                    // chunks of 1024 events in the longest list
     int64_t *base;              // n_recs + 1: first word per recording, total
     uint8_t *skip;
     int or_skip;                // keep flags already set by another bound

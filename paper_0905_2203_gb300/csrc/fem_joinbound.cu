@@ -73,19 +73,24 @@ __global__ void k_jb_base(JoinBoundArgs a) {
     a.base[a.n_recs] = acc;
 }
 
-// One warp per frequent 2-node episode: its V and S bitsets.
+// The V and S bitsets of every frequent 2-node episode, one warp per
+// (episode, chunk of 1024 list events): 32 words, one ballot per 32 events.
 __global__ void k_jb_bits(JoinBoundArgs a) {
     if (a.base[a.n_recs] > a.cap_words) return;
     const int lane = threadIdx.x & 31;
-    const int64_t F = *a.f2n;
+    const int64_t items = (int64_t)*a.f2n * a.nch;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t f = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; f < F; f += nw) {
+    for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < items; it += nw) {
+        const int64_t f = it / a.nch;
+        const int ch = (int)(it % a.nch);
         const uint32_t r = a.f2rec[f];
         const RecInfo &ri = a.ri[r];
         const uint32_t X = a.f2types[2 * f], Y = a.f2types[2 * f + 1];
-        const int32_t lo = a.f2lo[f], hi = a.f2hi[f];
         const int64_t xb = ri.toff[X], yb = ri.toff[Y];
         const int lenX = (int)(ri.toff[X + 1] - xb), lenY = (int)(ri.toff[Y + 1] - yb);
+        const int b0 = ch * 1024;
+        if (b0 >= lenX && b0 >= lenY) continue;
+        const int32_t lo = a.f2lo[f], hi = a.f2hi[f];
         const int32_t *tlX = ri.ttime + xb;
         const int32_t *tlY = ri.ttime + yb;
         const int32_t *rowX = ri.tidx + (int64_t)X * (ri.tcells + 1);
@@ -93,7 +98,7 @@ __global__ void k_jb_bits(JoinBoundArgs a) {
         const int64_t wb = a.base[r] + (f - a.f2foff[r]) * (int64_t)a.stride[r];
         // V: a Y event at t is a valid end when the newest X event before
         // t - lo exists and is not before t - hi
-        for (int b = 0; b < lenY; b += 32) {
+        for (int b = b0; b < lenY && b < b0 + 1024; b += 32) {
             bool v = false;
             if (b + lane < lenY) {
                 const int32_t t = tlY[b + lane];
@@ -108,7 +113,7 @@ __global__ void k_jb_bits(JoinBoundArgs a) {
         }
         // S: an X event at t is a valid start when the first Y event after
         // t + lo is not after t + hi
-        for (int b = 0; b < lenX; b += 32) {
+        for (int b = b0; b < lenX && b < b0 + 1024; b += 32) {
             bool s = false;
             if (b + lane < lenX) {
                 const uint32_t t = (uint32_t)tlX[b + lane];
