@@ -260,7 +260,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": C4_DESC, "sample": "oracle on a bounded sample per step"},
+        "config": {"workload": C4_DESC + f" ({args.c4_recs} recordings)",
+                   "sample": "oracle on a bounded sample per step"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc,
                          "cpu_model": cpu_model()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -745,7 +746,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": C4_DESC + f" ({len(recs)} recordings, n={n_tot})",
+        "config": {"workload": C4_DESC + f" ({len(recs)} recordings)", "events": n_tot,
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs ({6 * n_tot / 1e9:.2f} GB of streams) larger than L2; a 256 MB buffer is also "
                          f"written between timed steps",
