@@ -146,9 +146,9 @@ typedef struct {
                              kernel: 0 = per (episode, segment), driven by
                              node N-1's events or, when they outnumber node
                              N-2's entries more than twice, by those entries
-                             (one search per entry for the first end it can
-                             serve); 1 = always by events; 2 = always by
-                             entries */
+                             (one lookup in the stream's per-type time index
+                             per entry, for the first end it can serve);
+                             1 = always by events; 2 = always by entries */
 } fem_tuning;
 
 /* Per-call statistics filled by the counting / mining calls. */
